@@ -1,0 +1,265 @@
+/*
+ * ddamg.h -- C ABI of the GB300 (sm_103a) 2-level DD-alpha-AMG solver for
+ * Wilson-clover fermions (Ishikawa & Kanamori, "Porting DDalphaAMG solver to
+ * K computer", arXiv 1811.00355).
+ *
+ * The method (paper Sec. 2): flexible GMRES preconditioned by the two-level
+ * operator M = P D_c^-1 R + S (1 - D P D_c^-1 R)  (Eq. 5), with a
+ * multiplicative Schwarz (SAP) smoother S whose block solver is site even-odd
+ * preconditioned MR, a coarse operator D_c = <lambda_i(X,s)|D|lambda_j(Y,t)>
+ * (Eq. 2) built from n test vectors projected on aggregates and chiralities
+ * (Eq. 1), restriction R (Eq. 3) and prolongation P (Eq. 4), and an even-odd
+ * preconditioned GMRES coarse solver stopped at a relative residual of 5e-2.
+ * The test vectors come from the adaptive setup of Sec. 2.
+ *
+ * Conventions (the paper fixes none of them; these are the library's):
+ *   D psi(x) = (4 + m0) psi(x) + C(x) psi(x)
+ *              - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                            + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)],
+ *   C(x) = -(csw/32) sum_{mu != nu} g_mu g_nu (x) (Q_munu(x) - Q_numu(x)),
+ *   Q_munu the four-leaf clover of plaquettes at x.  Hermitian chiral gamma
+ *   basis: g_k = [[0, -i sigma_k], [i sigma_k, 0]], g_t = [[0, 1], [1, 0]],
+ *   g5 = diag(1, 1, -1, -1).  Periodic in x, y, z; antiperiodic in t (the
+ *   library applies the sign to time hops that cross the lattice edge).
+ *
+ * Host exchange layouts (used by every call that takes or returns fields):
+ *   site      = x + Lx*(y + Ly*(z + Lz*t))
+ *   gauge     = double complex [site][mu=x,y,z,t][row 3][col 3], interleaved
+ *               (re, im); U_mu(x) links x to x+mu; every link must be SU(3)
+ *               (unitary, det 1): the library stores two rows and rebuilds
+ *               the third, and rejects links that are off SU(3) by > 1e-9.
+ *   spinor    = double complex [site][spin 4][colour 3]
+ *   coarse    = double complex [X][s*n_v + i]: X the lexicographic index of
+ *               the aggregate on the coarse lattice L/agg_block, s the
+ *               chirality (0: spins 0,1; 1: spins 2,3), i the test vector.
+ *   coarse op = double complex [X][d][2n_v][2n_v]: d = 0 self block,
+ *               d = 1 + 2mu link to X+mu, d = 2 + 2mu link to X-mu.
+ *   packed Hermitian 6x6 block = 36 doubles: the 6 real diagonal entries,
+ *               then the 15 strictly-upper entries row-major as (re, im).
+ *
+ * Several right-hand sides (nrhs) are stored one after the other.
+ *
+ * Ownership and errors: the caller owns every buffer it passes; nothing is
+ * retained after a call returns.  The handle owns all device state.  Every
+ * call returns a status; no call aborts or throws.  The message of the last
+ * failure is returned by ddamg_last_error().  Parameters are validated before
+ * any allocation.  Calls with on_device = 1 take device pointers (same
+ * layouts, FP64) and run on the handle's stream; every call synchronises that
+ * stream before it returns.  A handle is not thread-safe.
+ */
+#ifndef DDAMG_H
+#define DDAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DDAMG_API __attribute__((visibility("default")))
+#else
+#define DDAMG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddamg_ctx *ddamg_handle;
+
+typedef enum {
+  DDAMG_OK = 0,
+  DDAMG_EINVAL = 1,   /* invalid parameter, size or layout                   */
+  DDAMG_ENOMEM = 2,   /* device allocation failed or hbm_budget exceeded     */
+  DDAMG_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed         */
+  DDAMG_ENOCONV = 4,  /* iteration cap reached; best x and residual returned */
+  DDAMG_ENUMERIC = 5, /* NaN or Inf met in a norm                            */
+  DDAMG_ETIMEOUT = 6, /* a bounded device-side wait gave up                  */
+  DDAMG_ESTATE = 7    /* call needs state the handle does not have yet       */
+} ddamg_status;
+
+/* Arithmetic of the smoother, coarse grid and projections.  The outer
+ * FGMRES, its residual r = b - D x and the test-vector orthonormalisation
+ * are always FP64. */
+typedef enum { DDAMG_FP64 = 0, DDAMG_FP32 = 1 } ddamg_precision;
+
+typedef struct {
+  int L[4];            /* lattice extents x, y, z, t; each even             */
+  int sap_block[4];    /* Schwarz block extents: even, divide L, and L/block
+                          even in every direction (red/black block colours) */
+  int agg_block[4];    /* aggregate extents; this library requires them to
+                          equal sap_block (the paper's setting, Sec. 4)      */
+  int n_v;             /* number of test vectors, >= 1                      */
+  double m0, csw;      /* bare mass and clover coefficient                  */
+  int setup_iters;     /* adaptive setup iterations (paper: 4)              */
+  int n_sap;           /* SAP cycles per smoother application (paper: 4)    */
+  int mr_iters;        /* MR iterations per block solve                     */
+  double coarse_tol;   /* coarse GMRES relative residual (paper: 5e-2)      */
+  int coarse_restart;  /* coarse GMRES restart length                       */
+  int coarse_max_iter; /* coarse GMRES iteration cap                        */
+  int precision;       /* ddamg_precision of the inner solver               */
+  int outer_restart;   /* FGMRES restart length                             */
+  int max_outer_iter;  /* FGMRES iteration cap per right-hand side          */
+  uint64_t seed;       /* seed of the initial random test vectors           */
+  size_t hbm_budget;   /* device-memory admission limit in bytes, 0 = none  */
+} ddamg_params;
+
+typedef struct {
+  int outer_iters;        /* FGMRES iterations (all restarts)                */
+  int restarts;           /* FGMRES restart cycles                           */
+  int coarse_iters;       /* coarse GMRES iterations summed over M calls     */
+  int precond_calls;      /* applications of M                               */
+  double true_residual;   /* ||b - D x|| / ||b|| in FP64                     */
+  int converged;          /* 1 if true_residual <= tol                       */
+  double seconds;         /* wall time of this right-hand side               */
+} ddamg_solve_info;
+
+typedef struct {
+  uint64_t kernel_launches;   /* launches of the library's own kernels       */
+  uint64_t dslash_launches;   /* launches of the site-parallel D kernel      */
+  double dslash_ms;           /* their device time when timing is enabled    */
+  uint64_t sap_launches;      /* launches of the SAP block kernel            */
+  double sap_ms;
+  uint64_t coarse_launches;   /* launches of the coarse GMRES kernel         */
+  double coarse_ms;
+  size_t device_bytes;        /* device memory held by the handle            */
+} ddamg_stats;
+
+/* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,
+ * coarse tol 5e-2, FP32 inner precision, restart 30). */
+DDAMG_API void ddamg_default_params(ddamg_params *p);
+
+/* Name of a status code (static string). */
+DDAMG_API const char *ddamg_status_string(ddamg_status s);
+
+/* Create a handle: validate p, allocate, upload the gauge field (host or
+ * device pointer, layout above), build the clover term and its inverse
+ * (Sec. 3: two 6x6 Hermitian blocks per site, stored packed) in FP64 and in
+ * the inner precision.  No test vectors yet.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  On failure *out is NULL. */
+DDAMG_API ddamg_status ddamg_create(const ddamg_params *p, const double *gauge,
+                          int gauge_on_device, void *cuda_stream,
+                          ddamg_handle *out);
+
+/* ddamg_create followed by the adaptive setup (Sec. 2) from random initial
+ * vectors drawn on the device from p->seed (Philox4x32-10, Box-Muller). */
+DDAMG_API ddamg_status ddamg_setup(const ddamg_params *p, const double *gauge,
+                         int gauge_on_device, void *cuda_stream,
+                         ddamg_handle *out);
+
+/* Adaptive setup (Sec. 2) on an existing handle: initial vectors are
+ * init_vectors (n_v spinor fields, host or device) or, if NULL, drawn from
+ * p->seed; each is smoothed by SAP from a zero start; then setup_iters times
+ * {orthonormalise per (X, s); assemble D_c; lambda_i <- M lambda_i}; finally
+ * orthonormalise and assemble D_c once more. */
+DDAMG_API ddamg_status ddamg_run_setup(ddamg_handle h, const double *init_vectors,
+                             int on_device);
+
+/* Change m0 / csw keeping the test vectors (the paper's "new kappa", Sec. 4):
+ * rebuild the clover term, its inverse and D_c. */
+DDAMG_API ddamg_status ddamg_update_mass(ddamg_handle h, double m0, double csw);
+
+/* Solve D x_k = rhs_k (k < nrhs) to ||b - D x|| <= tol ||b|| in FP64 with
+ * FGMRES preconditioned by M (Sec. 2), one right-hand side at a time, from a
+ * zero start.  rhs and x are nrhs spinor fields (host or device).  info
+ * (nullable) receives nrhs records.  Returns DDAMG_ENOCONV if a right-hand
+ * side hit max_outer_iter (its best x and residual are still written). */
+DDAMG_API ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double *rhs,
+                         double *x, int on_device, double tol,
+                         ddamg_solve_info *info);
+
+/* ---- single steps of the method, for checking and benchmarking ---------- */
+
+/* out = D in (Wilson-clover operator above) in the given precision. */
+DDAMG_API ddamg_status ddamg_apply_D(ddamg_handle h, int precision, int nrhs,
+                           const double *in, double *out, int on_device);
+
+/* out = A in with A(x) = (4 + m0) + C(x) (inverse = 0) or A(x)^-1 in
+ * (inverse = 1), site by site (Sec. 3: packed Hermitian blocks). */
+DDAMG_API ddamg_status ddamg_apply_clover(ddamg_handle h, int precision, int inverse,
+                                int nrhs, const double *in, double *out,
+                                int on_device);
+
+/* Export A (inverse = 0) or A^-1 (inverse = 1) as [site][chirality 2][36]
+ * packed Hermitian doubles (host buffer of 72 V doubles). */
+DDAMG_API ddamg_status ddamg_get_clover(ddamg_handle h, int inverse, double *out);
+
+/* One colour of one Schwarz sweep from a zero start (Sec. 2): on every block
+ * of colour `colour` (parity of the block coordinates) out = K_B in, K_B the
+ * site even-odd MR block solve with mr_iters iterations; zero elsewhere. */
+DDAMG_API ddamg_status ddamg_block_solve(ddamg_handle h, int precision, int colour,
+                               int nrhs, const double *in, double *out,
+                               int on_device);
+
+/* The SAP smoother (Sec. 2): n_sap cycles of colour 0 then colour 1 blocks,
+ * from a zero start, applied to in. */
+DDAMG_API ddamg_status ddamg_sap(ddamg_handle h, int precision, int nrhs,
+                       const double *in, double *out, int on_device);
+
+/* Replace the test vectors by n_v spinor fields (as given, not
+ * orthonormalised) / read the current ones (host buffer, n_v fields). */
+DDAMG_API ddamg_status ddamg_set_test_vectors(ddamg_handle h, const double *vecs,
+                                    int on_device);
+DDAMG_API ddamg_status ddamg_get_test_vectors(ddamg_handle h, double *vecs);
+
+/* Orthonormalise the test vectors inside every aggregate X and chirality s
+ * (classical Gram-Schmidt applied twice, i = 1..n, FP64), so that the
+ * projections of Eq. 1 satisfy P^H P = 1. */
+DDAMG_API ddamg_status ddamg_orthonormalize(ddamg_handle h);
+
+/* Assemble D_c (Eq. 2) from the current test vectors in the inner
+ * precision, and invert its self blocks for the even-odd coarse solve. */
+DDAMG_API ddamg_status ddamg_build_coarse(ddamg_handle h);
+
+/* Export D_c in the coarse-op layout (host buffer, NX*9*(2n)^2 complex). */
+DDAMG_API ddamg_status ddamg_get_coarse_op(ddamg_handle h, double *out);
+
+/* Eq. 3: out[X][s n + i] = <lambda_i(X,s)|in>; nrhs fine -> coarse. */
+DDAMG_API ddamg_status ddamg_restrict(ddamg_handle h, int precision, int nrhs,
+                            const double *in, double *out, int on_device);
+
+/* Eq. 4: out = sum x_c(X,s,i) lambda_i(X,s); nrhs coarse -> fine. */
+DDAMG_API ddamg_status ddamg_prolong(ddamg_handle h, int precision, int nrhs,
+                           const double *in, double *out, int on_device);
+
+/* out = D_c in (the 9-point coarse stencil); precision must be the inner
+ * precision of the handle. */
+DDAMG_API ddamg_status ddamg_apply_coarse(ddamg_handle h, int precision, int nrhs,
+                                const double *in, double *out, int on_device);
+
+/* Even-odd preconditioned coarse GMRES (Sec. 2) to relative residual tol of
+ * the even-site Schur system, then odd-site back substitution.  iters
+ * (nullable) receives nrhs iteration counts. */
+DDAMG_API ddamg_status ddamg_coarse_solve(ddamg_handle h, int precision, int nrhs,
+                                const double *in, double *out, int on_device,
+                                double tol, int *iters);
+
+/* out = M in (Eq. 5, post-smoothing only) in the inner precision. */
+DDAMG_API ddamg_status ddamg_apply_M(ddamg_handle h, int precision, int nrhs,
+                           const double *in, double *out, int on_device);
+
+/* Index maps as the device stores them, per lexicographic fine site (host
+ * int32 buffers of V entries, any may be NULL): site parity (x+y+z+t) mod 2,
+ * Schwarz block index (lexicographic on the block grid), block colour,
+ * aggregate index; coarse_parity has one entry per coarse site. */
+DDAMG_API ddamg_status ddamg_get_index_maps(ddamg_handle h, int32_t *parity,
+                                  int32_t *block, int32_t *colour,
+                                  int32_t *aggregate, int32_t *coarse_parity);
+
+/* Launch counters and (if enabled) device times of the main kernels. */
+DDAMG_API ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats *out);
+DDAMG_API ddamg_status ddamg_reset_stats(ddamg_handle h);
+/* Record CUDA events around the timed kernels (default off). */
+DDAMG_API ddamg_status ddamg_enable_kernel_timing(ddamg_handle h, int enable);
+
+/* Fill n_v * V spinor fields with the device generator's initial vectors
+ * for seed (host buffer), for checking the generator. */
+DDAMG_API ddamg_status ddamg_random_vectors(ddamg_handle h, uint64_t seed, int n,
+                                  double *out);
+
+DDAMG_API const char *ddamg_last_error(ddamg_handle h);
+DDAMG_API void ddamg_destroy(ddamg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDAMG_H */

@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) 2-level DD-alpha-AMG solver for Wilson-clover fermions.
+
+The solver is the CUDA library ``libddamg.so`` behind the C ABI of
+``include/ddamg.h``; :mod:`._ddamg` is its ctypes binding.  Importing this
+package loads nothing; :func:`load` (or creating a :class:`DDAMG`) loads the
+library and fails loudly if it has not been built.
+"""
+from ._ddamg import (FP32, FP64, DDAMG, DDAMGError, Params, SolveInfo, Stats,
+                     default_params, load)
+
+__all__ = ["FP32", "FP64", "DDAMG", "DDAMGError", "Params", "SolveInfo", "Stats",
+           "default_params", "load"]

@@ -1,0 +1,352 @@
+"""ctypes binding of the C ABI in ``include/ddamg.h`` (argument marshalling only).
+
+Every computation runs in ``libddamg.so``; this module converts NumPy host
+arrays or torch CUDA tensors to pointers, calls the library and raises on a
+non-zero status.  Field layouts are the host exchange layouts of the header:
+spinors ``complex128 [nrhs][V][4][3]``, gauge ``complex128 [V][4][3][3]``,
+coarse vectors ``complex128 [nrhs][NX][2 n_v]``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libddamg.so")
+
+FP64 = 0
+FP32 = 1
+
+STATUS = {0: "DDAMG_OK", 1: "DDAMG_EINVAL", 2: "DDAMG_ENOMEM", 3: "DDAMG_ECUDA",
+          4: "DDAMG_ENOCONV", 5: "DDAMG_ENUMERIC", 6: "DDAMG_ETIMEOUT", 7: "DDAMG_ESTATE"}
+
+
+class DDAMGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("L", C.c_int * 4), ("sap_block", C.c_int * 4), ("agg_block", C.c_int * 4),
+        ("n_v", C.c_int), ("m0", C.c_double), ("csw", C.c_double),
+        ("setup_iters", C.c_int), ("n_sap", C.c_int), ("mr_iters", C.c_int),
+        ("coarse_tol", C.c_double), ("coarse_restart", C.c_int), ("coarse_max_iter", C.c_int),
+        ("precision", C.c_int), ("outer_restart", C.c_int), ("max_outer_iter", C.c_int),
+        ("seed", C.c_uint64), ("hbm_budget", C.c_size_t),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("outer_iters", C.c_int), ("restarts", C.c_int), ("coarse_iters", C.c_int),
+        ("precond_calls", C.c_int), ("true_residual", C.c_double), ("converged", C.c_int),
+        ("seconds", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("kernel_launches", C.c_uint64), ("dslash_launches", C.c_uint64), ("dslash_ms", C.c_double),
+        ("sap_launches", C.c_uint64), ("sap_ms", C.c_double),
+        ("coarse_launches", C.c_uint64), ("coarse_ms", C.c_double), ("device_bytes", C.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_H = C.c_void_p
+
+SIGNATURES = {
+    "ddamg_default_params": (None, [C.POINTER(Params)]),
+    "ddamg_status_string": (C.c_char_p, [_I]),
+    "ddamg_create": (_I, [C.POINTER(Params), _P, _I, _P, C.POINTER(_H)]),
+    "ddamg_setup": (_I, [C.POINTER(Params), _P, _I, _P, C.POINTER(_H)]),
+    "ddamg_run_setup": (_I, [_H, _P, _I]),
+    "ddamg_update_mass": (_I, [_H, _D, _D]),
+    "ddamg_solve": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(SolveInfo)]),
+    "ddamg_apply_D": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_apply_clover": (_I, [_H, _I, _I, _I, _P, _P, _I]),
+    "ddamg_get_clover": (_I, [_H, _I, _P]),
+    "ddamg_block_solve": (_I, [_H, _I, _I, _I, _P, _P, _I]),
+    "ddamg_sap": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_set_test_vectors": (_I, [_H, _P, _I]),
+    "ddamg_get_test_vectors": (_I, [_H, _P]),
+    "ddamg_orthonormalize": (_I, [_H]),
+    "ddamg_build_coarse": (_I, [_H]),
+    "ddamg_get_coarse_op": (_I, [_H, _P]),
+    "ddamg_restrict": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_prolong": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_apply_coarse": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_coarse_solve": (_I, [_H, _I, _I, _P, _P, _I, _D, _P]),
+    "ddamg_apply_M": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_get_index_maps": (_I, [_H, _P, _P, _P, _P, _P]),
+    "ddamg_get_stats": (_I, [_H, C.POINTER(Stats)]),
+    "ddamg_reset_stats": (_I, [_H]),
+    "ddamg_enable_kernel_timing": (_I, [_H, _I]),
+    "ddamg_random_vectors": (_I, [_H, C.c_uint64, _I, _P]),
+    "ddamg_last_error": (C.c_char_p, [_H]),
+    "ddamg_destroy": (None, [_H]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libddamg.so is missing at {path}: build it with "
+                           "paper_1811_00355_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().ddamg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k in ("L", "sap_block", "agg_block"):
+            getattr(p, k)[:] = list(v)
+        else:
+            setattr(p, k, v)
+    if "sap_block" in kw and "agg_block" not in kw:
+        p.agg_block[:] = list(kw["sap_block"])
+    return p
+
+
+# ---------------------------------------------------------------------------
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a contiguous complex128/float64/int32 buffer."""
+    if _is_torch_cuda(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), 1
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+def _like(a, shape, dtype=np.complex128):
+    if _is_torch_cuda(a):
+        import torch
+        tdt = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=a.device)
+    return np.empty(shape, dtype)
+
+
+class DDAMG:
+    """One gauge field with its clover term, test vectors and coarse operator."""
+
+    def __init__(self, params: Params, gauge, stream=None):
+        self.lib = load()
+        self.p = params
+        self.V = int(np.prod(list(params.L)))
+        self.n_v = params.n_v
+        self.NX = self.V // int(np.prod(list(params.sap_block)))
+        h = _H()
+        gp, dev = _ptr(gauge)
+        st = C.c_void_p(stream) if stream else None
+        self._check(self.lib.ddamg_create(C.byref(params), gp, dev, st, C.byref(h)), None)
+        self.h = h
+
+    # -- plumbing ----------------------------------------------------------------
+    def _check(self, status, h="self"):
+        if status != 0:
+            hh = self.h if h == "self" else h
+            msg = self.lib.ddamg_last_error(hh).decode()
+            raise DDAMGError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ddamg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _fine_out(self, a, n):
+        return _like(a, (n, self.V, 4, 3))
+
+    def _nrhs(self, a):
+        return a.shape[0] if len(a.shape) == 4 else 1
+
+    # -- setup and solve ---------------------------------------------------------
+    def run_setup(self, init=None):
+        if init is None:
+            self._check(self.lib.ddamg_run_setup(self.h, None, 0))
+        else:
+            p, dev = _ptr(init)
+            self._check(self.lib.ddamg_run_setup(self.h, p, dev))
+
+    def update_mass(self, m0, csw):
+        self._check(self.lib.ddamg_update_mass(self.h, m0, csw))
+
+    def solve(self, rhs, tol=1e-10, allow_noconv=False):
+        n = self._nrhs(rhs)
+        x = self._fine_out(rhs, n).reshape(rhs.shape)
+        info = (SolveInfo * n)()
+        pi, dev = _ptr(rhs)
+        po, _ = _ptr(x)
+        st = self.lib.ddamg_solve(self.h, n, pi, po, dev, tol, info)
+        if not (allow_noconv and st == 4):
+            self._check(st)
+        return x, [i.as_dict() for i in info]
+
+    # -- single steps ----------------------------------------------------------------
+    def _fine_op(self, fn, x, *args):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(fn(self.h, *args[:-1], n, pi, po, dev) if args else fn(self.h, n, pi, po, dev))
+        return out
+
+    def apply_D(self, x, precision=FP64):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_apply_D(self.h, precision, n, pi, po, dev))
+        return out
+
+    def apply_clover(self, x, inverse=False, precision=FP64):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_apply_clover(self.h, precision, int(inverse), n, pi, po, dev))
+        return out
+
+    def get_clover(self, inverse=False):
+        out = np.empty((self.V, 2, 36))
+        self._check(self.lib.ddamg_get_clover(self.h, int(inverse), C.c_void_p(out.ctypes.data)))
+        return out
+
+    def block_solve(self, x, colour, precision=FP64):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_block_solve(self.h, precision, colour, n, pi, po, dev))
+        return out
+
+    def sap(self, x, precision=FP64):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_sap(self.h, precision, n, pi, po, dev))
+        return out
+
+    def set_test_vectors(self, vecs):
+        p, dev = _ptr(vecs)
+        self._check(self.lib.ddamg_set_test_vectors(self.h, p, dev))
+
+    def get_test_vectors(self):
+        out = np.empty((self.n_v, self.V, 4, 3), np.complex128)
+        self._check(self.lib.ddamg_get_test_vectors(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def orthonormalize(self):
+        self._check(self.lib.ddamg_orthonormalize(self.h))
+
+    def build_coarse(self):
+        self._check(self.lib.ddamg_build_coarse(self.h))
+
+    def get_coarse_op(self):
+        n2 = 2 * self.n_v
+        out = np.empty((self.NX, 9, n2, n2), np.complex128)
+        self._check(self.lib.ddamg_get_coarse_op(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def restrict(self, x, precision=FP64):
+        n = self._nrhs(x)
+        out = _like(x, (n, self.NX, 2 * self.n_v))
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_restrict(self.h, precision, n, pi, po, dev))
+        return out if len(x.shape) == 4 else out[0]
+
+    def prolong(self, xc, precision=FP64):
+        n = xc.shape[0] if len(xc.shape) == 3 else 1
+        out = _like(xc, (n, self.V, 4, 3))
+        pi, dev = _ptr(xc)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_prolong(self.h, precision, n, pi, po, dev))
+        return out if len(xc.shape) == 3 else out[0]
+
+    def apply_coarse(self, xc, precision):
+        n = xc.shape[0] if len(xc.shape) == 3 else 1
+        out = _like(xc, tuple(xc.shape))
+        pi, dev = _ptr(xc)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_apply_coarse(self.h, precision, n, pi, po, dev))
+        return out
+
+    def coarse_solve(self, bc, tol, precision):
+        n = bc.shape[0] if len(bc.shape) == 3 else 1
+        out = _like(bc, tuple(bc.shape))
+        its = np.zeros(n, np.int32)
+        pi, dev = _ptr(bc)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_coarse_solve(self.h, precision, n, pi, po, dev, tol,
+                                                C.c_void_p(its.ctypes.data)))
+        return out, its
+
+    def apply_M(self, x, precision):
+        n = self._nrhs(x)
+        out = self._fine_out(x, n).reshape(x.shape)
+        pi, dev = _ptr(x)
+        po, _ = _ptr(out)
+        self._check(self.lib.ddamg_apply_M(self.h, precision, n, pi, po, dev))
+        return out
+
+    def index_maps(self):
+        V, NX = self.V, self.NX
+        arrs = {k: np.empty(V, np.int32) for k in ("parity", "block", "colour", "aggregate")}
+        arrs["coarse_parity"] = np.empty(NX, np.int32)
+        self._check(self.lib.ddamg_get_index_maps(
+            self.h, *(C.c_void_p(arrs[k].ctypes.data)
+                      for k in ("parity", "block", "colour", "aggregate", "coarse_parity"))))
+        return arrs
+
+    def random_vectors(self, seed, n):
+        out = np.empty((n, self.V, 4, 3), np.complex128)
+        self._check(self.lib.ddamg_random_vectors(self.h, seed, n, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def stats(self):
+        s = Stats()
+        self._check(self.lib.ddamg_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        self._check(self.lib.ddamg_reset_stats(self.h))
+
+    def enable_kernel_timing(self, on=True):
+        self._check(self.lib.ddamg_enable_kernel_timing(self.h, int(on)))

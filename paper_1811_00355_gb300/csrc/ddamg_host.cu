@@ -1,0 +1,1185 @@
+// Host driver and C ABI of the library (declared in include/ddamg.h).
+//
+// The handle owns every device buffer.  Fields live on the device in the
+// block-major layout of common.cuh; the host exchange layout (lexicographic,
+// FP64) is converted by kernels.  The outer flexible GMRES (paper Sec. 2) is
+// driven from the host with one device-to-host read per iteration; the
+// preconditioner M (Eq. 5), the SAP smoother and the coarse solve run as
+// kernels without host synchronisation.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <complex>
+#include <chrono>
+
+#include "../../include/ddamg.h"
+#include "kernels.h"
+
+using namespace ddamg;
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr uint32_t NEG = 0x80000000u;
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace
+
+struct ddamg_ctx {
+  ddamg_params p{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  Geom g{};
+  int n2 = 0;
+  size_t V24 = 0;  // reals per spinor field
+
+  // device memory bookkeeping
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  // tables
+  uint32_t* d_nbr = nullptr;
+  int* d_lex = nullptr;
+  int16_t* d_bnbr = nullptr;
+  int16_t* d_face = nullptr;
+  int* d_cnbr = nullptr;
+  int* d_cpar = nullptr;
+  int* d_ceven = nullptr;
+  int* d_codd = nullptr;
+  int* d_cpos = nullptr;
+
+  // gauge and clover
+  double* d_gauge_lex = nullptr;
+  double* g64 = nullptr;
+  float* g32 = nullptr;
+  double *A64 = nullptr, *Ai64 = nullptr;
+  float *A32 = nullptr, *Ai32 = nullptr;
+  unsigned long long* d_dev = nullptr;
+
+  // test vectors and coarse operator
+  double* lam64 = nullptr;
+  float* lam32 = nullptr;
+  bool have_vectors = false;
+  bool have_coarse = false;
+  void* Dc = nullptr;
+  void* Ainv = nullptr;
+  void* cwork = nullptr;
+  int* d_iters = nullptr;        // per-rhs coarse iterations
+  int* d_iters_acc = nullptr;    // running total
+  int* d_status = nullptr;       // device status word
+
+  // scratch
+  double* red = nullptr;
+  double* dots = nullptr;        // 3 x (restart + 1) complex
+  double* lexbuf = nullptr;      // lexicographic staging
+  size_t lexbuf_fields = 0;
+  std::vector<void*> tmp;        // pool of nrhs-capable temporaries
+  size_t tmp_fields = 0;
+  int tmp_real = 0;
+
+  // outer FGMRES
+  double* fV = nullptr;          // (m+1) fields
+  double* fZ = nullptr;          // m fields
+  double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fw = nullptr;
+  void* fin = nullptr;           // inner-precision in/out for M
+  void* fout = nullptr;
+  double* d_coef = nullptr;
+
+  // stats
+  bool timing = false;
+  uint64_t launches0 = 0;
+  uint64_t n_dslash = 0, n_sap = 0, n_coarse = 0;
+  std::vector<Timer> tm_dslash, tm_sap, tm_coarse;
+  std::vector<Timer> pool;
+};
+
+namespace {
+
+ddamg_status fail(ddamg_ctx* h, ddamg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return s;
+}
+
+#define CK(...)                                                                           \
+  do {                                                                                    \
+    cudaError_t e_ = (__VA_ARGS__);                                                       \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, DDAMG_ECUDA, "%s failed: %s (%s:%d)", #__VA_ARGS__,                  \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+  } while (0)
+
+#define TRY(...)                                 \
+  do {                                           \
+    ddamg_status s_ = (__VA_ARGS__);             \
+    if (s_ != DDAMG_OK) return s_;               \
+  } while (0)
+
+ddamg_status dalloc(ddamg_ctx* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->p.hbm_budget && h->bytes + bytes > h->p.hbm_budget)
+    return fail(h, DDAMG_ENOMEM, "device memory budget exceeded: need %zu more bytes, %zu of %zu held",
+                bytes, h->bytes, h->p.hbm_budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, DDAMG_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  return DDAMG_OK;
+}
+template <class T>
+ddamg_status dalloc_t(ddamg_ctx* h, T** p, size_t count) {
+  void* v = nullptr;
+  ddamg_status s = dalloc(h, &v, count * sizeof(T));
+  *p = reinterpret_cast<T*>(v);
+  return s;
+}
+
+bool is_prec(int p) { return p == DDAMG_FP64 || p == DDAMG_FP32; }
+
+ddamg_status validate(const ddamg_params* p, std::string& why) {
+  auto bad = [&](const char* m) {
+    why = m;
+    return DDAMG_EINVAL;
+  };
+  if (!p) return bad("params is NULL");
+  for (int mu = 0; mu < 4; ++mu) {
+    if (p->L[mu] < 2 || p->L[mu] % 2) return bad("every lattice extent must be even and >= 2");
+    if (p->sap_block[mu] < 2 || p->sap_block[mu] % 2) return bad("Schwarz block extents must be even and >= 2");
+    if (p->L[mu] % p->sap_block[mu]) return bad("Schwarz block extents must divide the lattice extents");
+    if ((p->L[mu] / p->sap_block[mu]) % 2)
+      return bad("the number of Schwarz blocks along every axis must be even (red/black colouring)");
+    if (p->agg_block[mu] != p->sap_block[mu]) return bad("aggregates must equal the Schwarz blocks");
+  }
+  long long V = 1, Vb = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    V *= p->L[mu];
+    Vb *= p->sap_block[mu];
+  }
+  if (V > (1ll << 30)) return bad("lattice too large (more than 2^30 sites)");
+  if (Vb > 1024) return bad("Schwarz blocks larger than 1024 sites are not supported");
+  if (p->n_v < 1 || p->n_v > 32) return bad("n_v must be in [1, 32]");
+  if (p->setup_iters < 0 || p->n_sap < 1 || p->mr_iters < 0) return bad("setup_iters >= 0, n_sap >= 1, mr_iters >= 0");
+  if (!(p->coarse_tol > 0.0) || p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_max_iter < 1)
+    return bad("coarse_tol > 0, coarse_restart in [1, 64], coarse_max_iter >= 1");
+  if (!is_prec(p->precision)) return bad("precision must be DDAMG_FP64 or DDAMG_FP32");
+  if (p->outer_restart < 1 || p->outer_restart > 62 || p->max_outer_iter < 1)
+    return bad("outer_restart in [1, 62], max_outer_iter >= 1");
+  if (!std::isfinite(p->m0) || !std::isfinite(p->csw)) return bad("m0 and csw must be finite");
+  return DDAMG_OK;
+}
+
+// ---- geometry tables --------------------------------------------------------
+ddamg_status build_tables(ddamg_ctx* h) {
+  const ddamg_params& p = h->p;
+  Geom& g = h->g;
+  int V = 1, Vb = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    g.L[mu] = p.L[mu];
+    g.b[mu] = p.sap_block[mu];
+    g.grid[mu] = p.L[mu] / p.sap_block[mu];
+    V *= p.L[mu];
+    Vb *= p.sap_block[mu];
+  }
+  g.V = V;
+  g.Vb = Vb;
+  g.nb = V / Vb;
+  const int* L = g.L;
+  auto dev_of = [&](const int c[4]) {
+    int bc[4], l[4];
+    for (int mu = 0; mu < 4; ++mu) {
+      bc[mu] = c[mu] / g.b[mu];
+      l[mu] = c[mu] - bc[mu] * g.b[mu];
+    }
+    int B = bc[0] + g.grid[0] * (bc[1] + g.grid[1] * (bc[2] + g.grid[2] * bc[3]));
+    int ll = l[0] + g.b[0] * (l[1] + g.b[1] * (l[2] + g.b[2] * l[3]));
+    int par = (l[0] + l[1] + l[2] + l[3]) & 1;
+    return B * Vb + par * (Vb / 2) + (ll >> 1);
+  };
+  std::vector<int> lex_of_dev(V), dev_of_lex(V);
+  std::vector<uint32_t> nbr((size_t)8 * V);
+  for (int s = 0; s < V; ++s) {
+    int c[4], r = s;
+    c[0] = r % L[0]; r /= L[0];
+    c[1] = r % L[1]; r /= L[1];
+    c[2] = r % L[2];
+    c[3] = r / L[2];
+    int d = dev_of(c);
+    lex_of_dev[d] = s;
+    dev_of_lex[s] = d;
+  }
+  for (int d = 0; d < V; ++d) {
+    int s = lex_of_dev[d];
+    int c[4], r = s;
+    c[0] = r % L[0]; r /= L[0];
+    c[1] = r % L[1]; r /= L[1];
+    c[2] = r % L[2];
+    c[3] = r / L[2];
+    for (int mu = 0; mu < 4; ++mu) {
+      for (int sg = 0; sg < 2; ++sg) {
+        int cc[4] = {c[0], c[1], c[2], c[3]};
+        bool wrap;
+        if (sg == 0) { cc[mu] += 1; wrap = cc[mu] == L[mu]; if (wrap) cc[mu] = 0; }
+        else { cc[mu] -= 1; wrap = cc[mu] < 0; if (wrap) cc[mu] = L[mu] - 1; }
+        uint32_t e = (uint32_t)dev_of(cc);
+        if (mu == 3 && wrap) e |= NEG;
+        nbr[(size_t)(2 * mu + sg) * V + d] = e;
+      }
+    }
+  }
+  // block-local neighbours and faces (identical for every block)
+  std::vector<int16_t> bnbr((size_t)8 * Vb, -1), face((size_t)8 * Vb, -1);
+  std::vector<int> nface(8, 0);
+  for (int ll = 0; ll < Vb; ++ll) {
+    int l[4], r = ll;
+    l[0] = r % g.b[0]; r /= g.b[0];
+    l[1] = r % g.b[1]; r /= g.b[1];
+    l[2] = r % g.b[2];
+    l[3] = r / g.b[2];
+    int par = (l[0] + l[1] + l[2] + l[3]) & 1;
+    int q = par * (Vb / 2) + (ll >> 1);
+    for (int mu = 0; mu < 4; ++mu)
+      for (int sg = 0; sg < 2; ++sg) {
+        int m[4] = {l[0], l[1], l[2], l[3]};
+        m[mu] += sg == 0 ? 1 : -1;
+        if (m[mu] < 0 || m[mu] >= g.b[mu]) {
+          face[(size_t)(2 * mu + sg) * Vb + nface[2 * mu + sg]++] = (int16_t)q;
+          continue;
+        }
+        int l2 = m[0] + g.b[0] * (m[1] + g.b[1] * (m[2] + g.b[2] * m[3]));
+        int par2 = (m[0] + m[1] + m[2] + m[3]) & 1;
+        bnbr[(size_t)(2 * mu + sg) * Vb + q] = (int16_t)(par2 * (Vb / 2) + (l2 >> 1));
+      }
+  }
+  // coarse lattice
+  const int nb = g.nb;
+  std::vector<int> cnbr((size_t)9 * nb), cpar(nb), ceven, codd, cpos(nb);
+  for (int X = 0; X < nb; ++X) {
+    int c[4], r = X;
+    c[0] = r % g.grid[0]; r /= g.grid[0];
+    c[1] = r % g.grid[1]; r /= g.grid[1];
+    c[2] = r % g.grid[2];
+    c[3] = r / g.grid[2];
+    cpar[X] = (c[0] + c[1] + c[2] + c[3]) & 1;
+    cnbr[X] = X;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int sg = 0; sg < 2; ++sg) {
+        int cc[4] = {c[0], c[1], c[2], c[3]};
+        cc[mu] = (cc[mu] + (sg == 0 ? 1 : -1) + g.grid[mu]) % g.grid[mu];
+        cnbr[(size_t)(1 + 2 * mu + sg) * nb + X] =
+            cc[0] + g.grid[0] * (cc[1] + g.grid[1] * (cc[2] + g.grid[2] * cc[3]));
+      }
+    if (cpar[X] == 0) { cpos[X] = (int)ceven.size(); ceven.push_back(X); }
+    else { cpos[X] = (int)codd.size(); codd.push_back(X); }
+  }
+  TRY(dalloc_t(h, &h->d_nbr, nbr.size()));
+  TRY(dalloc_t(h, &h->d_lex, (size_t)V));
+  TRY(dalloc_t(h, &h->d_bnbr, bnbr.size()));
+  TRY(dalloc_t(h, &h->d_face, face.size()));
+  TRY(dalloc_t(h, &h->d_cnbr, cnbr.size()));
+  TRY(dalloc_t(h, &h->d_cpar, (size_t)nb));
+  TRY(dalloc_t(h, &h->d_ceven, ceven.size()));
+  TRY(dalloc_t(h, &h->d_codd, codd.size()));
+  TRY(dalloc_t(h, &h->d_cpos, (size_t)nb));
+  CK(cudaMemcpy(h->d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_lex, lex_of_dev.data(), (size_t)V * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_bnbr, bnbr.data(), bnbr.size() * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_face, face.data(), face.size() * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_cnbr, cnbr.data(), cnbr.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_cpar, cpar.data(), (size_t)nb * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_ceven, ceven.data(), ceven.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_codd, codd.data(), codd.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_cpos, cpos.data(), (size_t)nb * 4, cudaMemcpyHostToDevice));
+  g.nbr = h->d_nbr;
+  g.lex_of_dev = h->d_lex;
+  g.bnbr = h->d_bnbr;
+  g.face = h->d_face;
+  g.cnbr = h->d_cnbr;
+  g.cparity = h->d_cpar;
+  g.ceven = h->d_ceven;
+  g.codd = h->d_codd;
+  g.cpos = h->d_cpos;
+  return DDAMG_OK;
+}
+
+// ---- temporaries --------------------------------------------------------------
+// lexicographic FP64 staging for nf fields
+ddamg_status need_lexbuf(ddamg_ctx* h, size_t nf) {
+  if (h->lexbuf_fields >= nf) return DDAMG_OK;
+  void* p;
+  TRY(dalloc(h, &p, nf * h->V24 * sizeof(double)));
+  h->lexbuf = (double*)p;
+  h->lexbuf_fields = nf;
+  return DDAMG_OK;
+}
+// k temporaries of nf fields each, in doubles (big enough for either precision)
+ddamg_status need_tmp(ddamg_ctx* h, size_t nf, int k) {
+  if (h->tmp_fields >= nf && (int)h->tmp.size() >= k) return DDAMG_OK;
+  size_t want = nf > h->tmp_fields ? nf : h->tmp_fields;
+  h->tmp.clear();
+  for (int i = 0; i < (k > 6 ? k : 6); ++i) {
+    void* p;
+    TRY(dalloc(h, &p, want * h->V24 * sizeof(double)));
+    h->tmp.push_back(p);
+  }
+  h->tmp_fields = want;
+  return DDAMG_OK;
+}
+
+Timer next_timer(ddamg_ctx* h) {
+  if (h->pool.empty()) {
+    Timer t;
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+    return t;
+  }
+  Timer t = h->pool.back();
+  h->pool.pop_back();
+  return t;
+}
+
+template <class F>
+cudaError_t timed(ddamg_ctx* h, std::vector<Timer>& log, F&& f) {
+  if (!h->timing) return f();
+  Timer t = next_timer(h);
+  cudaEventRecord(t.a, h->st);
+  cudaError_t e = f();
+  cudaEventRecord(t.b, h->st);
+  log.push_back(t);
+  return e;
+}
+
+// ---- in/out of fields -----------------------------------------------------------
+// host/device FP64 lexicographic -> device field of precision R (nf fields)
+template <class R>
+ddamg_status import_fields(ddamg_ctx* h, const double* src, int on_device, int nf, R* dst) {
+  const double* lex = src;
+  if (!on_device) {
+    TRY(need_lexbuf(h, nf));
+    CK(cudaMemcpyAsync(h->lexbuf, src, nf * h->V24 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    lex = h->lexbuf;
+  }
+  CK(pack_spinor<R>(h->g, lex, dst, nf, h->st));
+  return DDAMG_OK;
+}
+template <class R>
+ddamg_status export_fields(ddamg_ctx* h, const R* src, int nf, double* dst, int on_device) {
+  double* lex = dst;
+  if (!on_device) {
+    TRY(need_lexbuf(h, nf));
+    lex = h->lexbuf;
+  }
+  CK(unpack_spinor<R>(h->g, src, lex, nf, h->st));
+  if (!on_device)
+    CK(cudaMemcpyAsync(dst, lex, nf * h->V24 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+template <class R> const R* gauge_of(ddamg_ctx* h);
+template <> const float* gauge_of<float>(ddamg_ctx* h) { return h->g32; }
+template <> const double* gauge_of<double>(ddamg_ctx* h) { return h->g64; }
+template <class R> const R* clov_of(ddamg_ctx* h, bool inv);
+template <> const float* clov_of<float>(ddamg_ctx* h, bool inv) { return inv ? h->Ai32 : h->A32; }
+template <> const double* clov_of<double>(ddamg_ctx* h, bool inv) { return inv ? h->Ai64 : h->A64; }
+template <class R> const R* lam_of(ddamg_ctx* h);
+template <> const float* lam_of<float>(ddamg_ctx* h) { return h->lam32; }
+template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
+
+// ---- operators on device fields ---------------------------------------------------
+template <class R>
+ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
+  ++h->n_dslash;
+  CK(timed(h, h->tm_dslash, [&] {
+    return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
+  }));
+  return DDAMG_OK;
+}
+
+// SAP from zero: x = S b
+template <class R>
+ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf) {
+  CK(cudaMemsetAsync(x, 0, nf * h->V24 * sizeof(R), h->st));
+  for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
+    for (int c = 0; c < 2; ++c) {
+      ++h->n_sap;
+      bool zero = cyc == 0 && c == 0;
+      CK(timed(h, h->tm_sap, [&] {
+        return sap_sweep<R>(h->g, c, h->p.mr_iters, zero, b, x, gauge_of<R>(h), clov_of<R>(h, false),
+                            clov_of<R>(h, true), nf, h->st);
+      }));
+    }
+  return DDAMG_OK;
+}
+
+template <class R>
+ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double tol, int* iters_dev) {
+  CoarseSolveArgs a;
+  a.Dc = h->Dc;
+  a.Ainv = h->Ainv;
+  a.n = h->p.n_v;
+  a.tol = tol;
+  a.restart = h->p.coarse_restart;
+  a.max_iter = h->p.coarse_max_iter;
+  ++h->n_coarse;
+  CK(timed(h, h->tm_coarse, [&] {
+    return coarse_gmres<R>(h->g, a, bc, xc, nf, h->cwork, iters_dev, h->d_iters_acc, h->d_status, h->st);
+  }));
+  return DDAMG_OK;
+}
+
+// out = M in  (Eq. 5): x1 = P D_c^-1 R in; out = x1 + SAP(in - D x1)
+// uses tmp[0..3]
+template <class R>
+ddamg_status op_M(ddamg_ctx* h, const R* in, R* out, int nf) {
+  TRY(need_tmp(h, nf, 6));
+  R* r1 = (R*)h->tmp[0];
+  R* e = (R*)h->tmp[1];
+  R* bc = (R*)h->tmp[2];
+  R* xc = (R*)h->tmp[3];
+  const int n = h->p.n_v;
+  CK(restrict_op<R>(h->g, lam_of<R>(h), n, in, bc, nf, h->st));
+  TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, nullptr));
+  CK(prolong_op<R>(h->g, lam_of<R>(h), n, xc, out, nf, false, h->st));
+  TRY(op_dslash<R>(h, DSLASH_RES, out, in, r1, nf));
+  TRY(op_sap<R>(h, r1, e, nf));
+  CK(axpby<R>(1.0, e, 1.0, out, nf * h->V24, h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status check_status(ddamg_ctx* h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (st != 0) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
+    return fail(h, DDAMG_ETIMEOUT, "a device-side grid barrier gave up waiting (status %d)", st);
+  }
+  return DDAMG_OK;
+}
+
+// ---- coarse operator ----------------------------------------------------------------
+ddamg_status alloc_coarse(ddamg_ctx* h) {
+  if (h->Dc) return DDAMG_OK;
+  const int rs = h->p.precision == DDAMG_FP64 ? 8 : 4;
+  const size_t n2 = h->n2;
+  TRY(dalloc(h, &h->Dc, (size_t)h->g.nb * 9 * n2 * n2 * 2 * rs));
+  TRY(dalloc(h, &h->Ainv, (size_t)h->g.nb * n2 * n2 * 2 * rs));
+  TRY(dalloc(h, &h->cwork, coarse_gmres_work_bytes(h->g, h->p.n_v, h->p.coarse_restart, rs)));
+  return DDAMG_OK;
+}
+
+ddamg_status sync_lam32(ddamg_ctx* h) {
+  if (h->p.precision == DDAMG_FP32) {
+    if (!h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
+    CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+  }
+  return DDAMG_OK;
+}
+
+ddamg_status build_coarse_op(ddamg_ctx* h) {
+  if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  TRY(alloc_coarse(h));
+  TRY(sync_lam32(h));
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+  if (h->p.precision == DDAMG_FP32) {
+    CK(assemble_coarse<float>(h->g, h->lam32, h->p.n_v, h->g32, h->A32, (float*)h->Dc, h->st));
+    CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
+  } else {
+    CK(assemble_coarse<double>(h->g, h->lam64, h->p.n_v, h->g64, h->A64, (double*)h->Dc, h->st));
+    CK(invert_self_blocks<double>(h->g, (double*)h->Dc, h->p.n_v, (double*)h->Ainv, h->d_status, h->st));
+  }
+  int sing = 0;
+  CK(cudaMemcpyAsync(&sing, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (sing) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
+    return fail(h, DDAMG_ENUMERIC, "a coarse self block is singular");
+  }
+  h->have_coarse = true;
+  return DDAMG_OK;
+}
+
+// ---- precision changes of spinor fields -----------------------------------------------
+template <class R>
+ddamg_status to_inner(ddamg_ctx* h, const double* src, R* dst, int nf) {
+  if constexpr (sizeof(R) == 8)
+    CK(cudaMemcpyAsync(dst, src, nf * h->V24 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  else
+    CK(convert_spinor<R, double>(h->g, src, dst, nf, h->st));
+  return DDAMG_OK;
+}
+template <class R>
+ddamg_status from_inner(ddamg_ctx* h, const R* src, double* dst, int nf) {
+  if constexpr (sizeof(R) == 8)
+    CK(cudaMemcpyAsync(dst, src, nf * h->V24 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  else
+    CK(convert_spinor<double, R>(h->g, src, dst, nf, h->st));
+  return DDAMG_OK;
+}
+
+// ---- adaptive setup -----------------------------------------------------------------
+template <class R>
+ddamg_status setup_impl(ddamg_ctx* h) {
+  const int n = h->p.n_v;
+  TRY(need_tmp(h, n, 6));
+  R* a = (R*)h->tmp[4];
+  R* b = (R*)h->tmp[5];
+  // lambda_i <- SAP(lambda_i)
+  TRY(to_inner<R>(h, h->lam64, a, n));
+  TRY(op_sap<R>(h, a, b, n));
+  TRY(from_inner<R>(h, b, h->lam64, n));
+  for (int it = 0; it < h->p.setup_iters; ++it) {
+    CK(orthonormalise(h->g, h->lam64, n, h->st));
+    TRY(build_coarse_op(h));
+    // lambda_i <- M lambda_i
+    TRY(to_inner<R>(h, h->lam64, a, n));
+    TRY(op_M<R>(h, a, b, n));
+    TRY(from_inner<R>(h, b, h->lam64, n));
+    TRY(check_status(h));
+  }
+  CK(orthonormalise(h->g, h->lam64, n, h->st));
+  TRY(build_coarse_op(h));
+  return check_status(h);
+}
+
+// ---- outer FGMRES (FP64) -----------------------------------------------------------
+template <class R>
+ddamg_status precond_to_f64(ddamg_ctx* h, const double* v, double* z) {
+  if (sizeof(R) == 8) return op_M<double>(h, v, z, 1);
+  float* fin = (float*)h->fin;
+  float* fout = (float*)h->fout;
+  TRY(to_inner<float>(h, v, fin, 1));
+  TRY(op_M<float>(h, fin, fout, 1));
+  return from_inner<float>(h, fout, z, 1);
+}
+
+ddamg_status alloc_outer(ddamg_ctx* h) {
+  if (h->fV) return DDAMG_OK;
+  const int m = h->p.outer_restart;
+  TRY(dalloc_t(h, &h->fV, (size_t)(m + 1) * h->V24));
+  TRY(dalloc_t(h, &h->fZ, (size_t)m * h->V24));
+  TRY(dalloc_t(h, &h->fx, h->V24));
+  TRY(dalloc_t(h, &h->fb, h->V24));
+  TRY(dalloc_t(h, &h->fr, h->V24));
+  TRY(dalloc_t(h, &h->fw, h->V24));
+  TRY(dalloc(h, &h->fin, h->V24 * sizeof(double)));
+  TRY(dalloc(h, &h->fout, h->V24 * sizeof(double)));
+  TRY(dalloc_t(h, &h->d_coef, (size_t)2 * (m + 1)));
+  return DDAMG_OK;
+}
+
+template <class R>
+ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
+  const int m = h->p.outer_restart;
+  const size_t N = h->V24;          // reals
+  const size_t NC = N / 2;          // complex
+  double* V = h->fV;
+  double* Z = h->fZ;
+  auto Vk = [&](int k) { return V + (size_t)k * N; };
+  auto Zk = [&](int k) { return Z + (size_t)k * N; };
+  std::vector<const double*> vlist(m + 1), zlist(m);
+  for (int k = 0; k <= m; ++k) vlist[k] = Vk(k);
+  for (int k = 0; k < m; ++k) zlist[k] = Zk(k);
+  int iters = 0, restarts = 0, calls = 0;
+  CK(cudaMemsetAsync(h->fx, 0, N * 8, h->st));
+  CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
+  // ||b||
+  double host[2 * 3 * 64];
+  CK(norm2<double>(h->fb, NC, h->red, h->dots, h->st));
+  CK(cudaMemcpyAsync(host, h->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const double bnorm = std::sqrt(host[0]);
+  if (!std::isfinite(bnorm)) return fail(h, DDAMG_ENUMERIC, "right-hand side norm is not finite");
+  CK(cudaMemcpyAsync(h->fr, h->fb, N * 8, cudaMemcpyDeviceToDevice, h->st));
+  double beta = bnorm;
+  bool converged = bnorm == 0.0;
+  std::vector<cd> Hc((size_t)(m + 1) * m), g(m + 1), sn(m), y(m);
+  std::vector<double> cs(m);
+  while (!converged && iters < h->p.max_outer_iter) {
+    // V0 = r / beta
+    CK(axpby<double>(1.0 / beta, h->fr, 0.0, Vk(0), N, h->st));
+    std::fill(g.begin(), g.end(), cd(0));
+    g[0] = beta;
+    int kdone = 0;
+    for (int k = 0; k < m; ++k) {
+      TRY(precond_to_f64<R>(h, Vk(k), Zk(k)));
+      ++calls;
+      TRY(op_dslash<double>(h, DSLASH_D, Zk(k), nullptr, h->fw, 1));
+      // classical Gram-Schmidt, two passes; coefficients stay on the device
+      for (int pass = 0; pass < 2; ++pass) {
+        double* c = h->dots + 2 * (m + 1) * pass;
+        CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c, h->st));
+        CK(multi_axpy<double>(vlist.data(), k + 1, c, -1.0, h->fw, NC, h->st));
+      }
+      double* nn = h->dots + 4 * (m + 1);
+      CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
+      CK(scale_by_inv_norm<double>(h->fw, Vk(k + 1), nn, N, h->st));
+      CK(cudaMemcpyAsync(host, h->dots, (4 * (m + 1) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      std::vector<cd> col(k + 2);
+      for (int j = 0; j <= k; ++j)
+        col[j] = cd(host[2 * j] + host[2 * (m + 1) + 2 * j], host[2 * j + 1] + host[2 * (m + 1) + 2 * j + 1]);
+      const double hn = std::sqrt(host[4 * (m + 1)]);
+      if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the FGMRES basis norm");
+      col[k + 1] = hn;
+      for (int j = 0; j < k; ++j) {
+        cd t = cs[j] * col[j] + sn[j] * col[j + 1];
+        col[j + 1] = -std::conj(sn[j]) * col[j] + cs[j] * col[j + 1];
+        col[j] = t;
+      }
+      double a1 = std::abs(col[k]), a2 = std::abs(col[k + 1]);
+      if (a2 == 0.0) { cs[k] = 1.0; sn[k] = 0.0; }
+      else if (a1 == 0.0) { cs[k] = 0.0; sn[k] = std::conj(col[k + 1]) / a2; col[k] = a2; }
+      else {
+        double rho = std::hypot(a1, a2);
+        cd ph = col[k] / a1;
+        cs[k] = a1 / rho;
+        sn[k] = ph * std::conj(col[k + 1]) / rho;
+        col[k] = ph * rho;
+      }
+      for (int j = 0; j <= k; ++j) Hc[(size_t)j * m + k] = col[j];
+      g[k + 1] = -std::conj(sn[k]) * g[k];
+      g[k] = cs[k] * g[k];
+      ++iters;
+      kdone = k + 1;
+      if (std::abs(g[k + 1]) <= tol * bnorm || iters >= h->p.max_outer_iter || hn == 0.0) break;
+    }
+    for (int i = kdone - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int j = i + 1; j < kdone; ++j) acc -= Hc[(size_t)i * m + j] * y[j];
+      y[i] = acc / Hc[(size_t)i * m + i];
+    }
+    for (int j = 0; j < kdone; ++j) {
+      host[2 * j] = y[j].real();
+      host[2 * j + 1] = y[j].imag();
+    }
+    CK(cudaMemcpyAsync(h->d_coef, host, 2 * kdone * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(multi_axpy<double>(zlist.data(), kdone, h->d_coef, 1.0, h->fx, NC, h->st));
+    // true residual
+    TRY(op_dslash<double>(h, DSLASH_RES, h->fx, h->fb, h->fr, 1));
+    CK(norm2<double>(h->fr, NC, h->red, h->dots, h->st));
+    CK(cudaMemcpyAsync(host, h->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    beta = std::sqrt(host[0]);
+    ++restarts;
+    if (!std::isfinite(beta)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the true residual");
+    converged = beta <= tol * bnorm;
+  }
+  TRY(check_status(h));
+  int cit = 0;
+  CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
+  if (info) {
+    info->outer_iters = iters;
+    info->restarts = restarts;
+    info->coarse_iters = cit;
+    info->precond_calls = calls;
+    info->true_residual = bnorm > 0 ? beta / bnorm : 0.0;
+    info->converged = converged ? 1 : 0;
+  }
+  if (!converged) return fail(h, DDAMG_ENOCONV, "FGMRES reached max_outer_iter (residual %.3e)", beta / bnorm);
+  return DDAMG_OK;
+}
+
+bool is_prec_ok(ddamg_ctx* h, int prec) {
+  if (!is_prec(prec)) {
+    fail(h, DDAMG_EINVAL, "precision must be DDAMG_FP64 or DDAMG_FP32");
+    return false;
+  }
+  return true;
+}
+
+template <class F>
+ddamg_status dispatch(ddamg_ctx* h, int prec, F&& f) {
+  if (!is_prec_ok(h, prec)) return DDAMG_EINVAL;
+  if (prec == DDAMG_FP64) return f((double*)nullptr);
+  return f((float*)nullptr);
+}
+
+// coarse vectors: host/device FP64 -> device R
+template <class R>
+ddamg_status coarse_in(ddamg_ctx* h, const double* src, int on_device, size_t nc, R* dst) {
+  const double* s = src;
+  if (!on_device) {
+    TRY(need_lexbuf(h, (2 * nc + h->V24 - 1) / h->V24 + 1));
+    CK(cudaMemcpyAsync(h->lexbuf, src, 2 * nc * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    s = h->lexbuf;
+  }
+  CK(coarse_from_f64<R>(s, dst, nc, h->st));
+  return DDAMG_OK;
+}
+template <class R>
+ddamg_status coarse_out(ddamg_ctx* h, const R* src, size_t nc, double* dst, int on_device) {
+  double* d = dst;
+  if (!on_device) {
+    TRY(need_lexbuf(h, (2 * nc + h->V24 - 1) / h->V24 + 1));
+    d = h->lexbuf;
+  }
+  CK(coarse_to_f64<R>(src, d, nc, h->st));
+  if (!on_device) CK(cudaMemcpyAsync(dst, d, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void ddamg_default_params(ddamg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  for (int mu = 0; mu < 4; ++mu) {
+    p->L[mu] = 16;
+    p->sap_block[mu] = 4;
+    p->agg_block[mu] = 4;
+  }
+  p->n_v = 20;
+  p->m0 = -0.3;
+  p->csw = 1.2;
+  p->setup_iters = 4;
+  p->n_sap = 4;
+  p->mr_iters = 4;
+  p->coarse_tol = 5e-2;
+  p->coarse_restart = 30;
+  p->coarse_max_iter = 300;
+  p->precision = DDAMG_FP32;
+  p->outer_restart = 30;
+  p->max_outer_iter = 1000;
+  p->seed = 1;
+  p->hbm_budget = 0;
+}
+
+const char* ddamg_status_string(ddamg_status s) {
+  switch (s) {
+    case DDAMG_OK: return "DDAMG_OK";
+    case DDAMG_EINVAL: return "DDAMG_EINVAL";
+    case DDAMG_ENOMEM: return "DDAMG_ENOMEM";
+    case DDAMG_ECUDA: return "DDAMG_ECUDA";
+    case DDAMG_ENOCONV: return "DDAMG_ENOCONV";
+    case DDAMG_ENUMERIC: return "DDAMG_ENUMERIC";
+    case DDAMG_ETIMEOUT: return "DDAMG_ETIMEOUT";
+    case DDAMG_ESTATE: return "DDAMG_ESTATE";
+  }
+  return "unknown status";
+}
+
+static thread_local std::string g_create_error;
+
+ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_on_device, void* stream,
+                          ddamg_handle* out) {
+  if (!out) return DDAMG_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (validate(p, why) != DDAMG_OK) {
+    g_create_error = why;
+    return DDAMG_EINVAL;
+  }
+  if (!gauge) {
+    g_create_error = "gauge is NULL";
+    return DDAMG_EINVAL;
+  }
+  ddamg_ctx* h = new ddamg_ctx();
+  h->p = *p;
+  h->st = (cudaStream_t)stream;
+  h->n2 = 2 * p->n_v;
+  ddamg_status s = [&]() -> ddamg_status {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(h, DDAMG_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    TRY(build_tables(h));
+    h->V24 = (size_t)h->g.V * 24;
+    const size_t V = h->g.V;
+    TRY(dalloc_t(h, &h->d_gauge_lex, V * 72));
+    TRY(dalloc_t(h, &h->g64, V * 48));
+    TRY(dalloc_t(h, &h->g32, V * 48));
+    TRY(dalloc_t(h, &h->A64, V * 72));
+    TRY(dalloc_t(h, &h->Ai64, V * 72));
+    TRY(dalloc_t(h, &h->A32, V * 72));
+    TRY(dalloc_t(h, &h->Ai32, V * 72));
+    TRY(dalloc_t(h, &h->d_dev, 1));
+    TRY(dalloc_t(h, &h->d_iters, 4096));
+    TRY(dalloc_t(h, &h->d_iters_acc, 1));
+    TRY(dalloc_t(h, &h->d_status, 1));
+    TRY(dalloc_t(h, &h->red, reduce_scratch_len(64)));
+    TRY(dalloc_t(h, &h->dots, (size_t)6 * 64 + 8));
+    TRY(dalloc_t(h, &h->lam64, (size_t)p->n_v * h->V24));
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    CK(cudaMemsetAsync(h->d_dev, 0, sizeof(unsigned long long), h->st));
+    CK(cudaMemcpyAsync(h->d_gauge_lex, gauge, V * 72 * sizeof(double),
+                       gauge_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    CK(import_gauge(h->g, h->d_gauge_lex, h->g64, h->g32, h->d_dev, h->st));
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, h->d_dev, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    double dev;
+    std::memcpy(&dev, &bits, sizeof dev);
+    if (!(dev <= 1e-9))
+      return fail(h, DDAMG_EINVAL, "gauge links are not SU(3): max deviation %.3e", dev);
+    CK(build_clover(h->g, h->d_gauge_lex, p->m0, p->csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return DDAMG_OK;
+  }();
+  if (s != DDAMG_OK) {
+    g_create_error = h->err;
+    ddamg_destroy(h);
+    return s;
+  }
+  *out = h;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_run_setup(ddamg_handle h, const double* init, int on_device) {
+  if (!h) return DDAMG_EINVAL;
+  const int n = h->p.n_v;
+  if (init) {
+    TRY(import_fields<double>(h, init, on_device, n, h->lam64));
+  } else {
+    TRY(need_lexbuf(h, n));
+    CK(random_spinors(h->g, h->p.seed, n, h->lexbuf, h->st));
+    CK(pack_spinor<double>(h->g, h->lexbuf, h->lam64, n, h->st));
+  }
+  h->have_vectors = true;
+  h->have_coarse = false;
+  ddamg_status s = h->p.precision == DDAMG_FP64 ? setup_impl<double>(h) : setup_impl<float>(h);
+  if (s != DDAMG_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_setup(const ddamg_params* p, const double* gauge, int gauge_on_device, void* stream,
+                         ddamg_handle* out) {
+  ddamg_status s = ddamg_create(p, gauge, gauge_on_device, stream, out);
+  if (s != DDAMG_OK) return s;
+  s = ddamg_run_setup(*out, nullptr, 0);
+  if (s != DDAMG_OK) {
+    g_create_error = (*out)->err;
+    ddamg_destroy(*out);
+    *out = nullptr;
+  }
+  return s;
+}
+
+ddamg_status ddamg_update_mass(ddamg_handle h, double m0, double csw) {
+  if (!h) return DDAMG_EINVAL;
+  if (!std::isfinite(m0) || !std::isfinite(csw)) return fail(h, DDAMG_EINVAL, "m0 and csw must be finite");
+  h->p.m0 = m0;
+  h->p.csw = csw;
+  CK(build_clover(h->g, h->d_gauge_lex, m0, csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  if (h->have_coarse) TRY(build_coarse_op(h));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double* rhs, double* x, int on_device, double tol,
+                         ddamg_solve_info* info) {
+  if (!h) return DDAMG_EINVAL;
+  if (nrhs < 0 || (nrhs > 0 && (!rhs || !x))) return fail(h, DDAMG_EINVAL, "bad nrhs / buffers");
+  if (!(tol > 0.0)) return fail(h, DDAMG_EINVAL, "tol must be > 0");
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "run the setup first");
+  TRY(alloc_outer(h));
+  ddamg_status worst = DDAMG_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    auto t0 = std::chrono::steady_clock::now();
+    TRY(import_fields<double>(h, rhs + k * h->V24, on_device, 1, h->fb));
+    ddamg_solve_info inf{};
+    ddamg_status s = h->p.precision == DDAMG_FP64 ? fgmres<double>(h, tol, &inf) : fgmres<float>(h, tol, &inf);
+    if (s != DDAMG_OK && s != DDAMG_ENOCONV) return s;
+    if (s == DDAMG_ENOCONV) worst = s;
+    TRY(export_fields<double>(h, h->fx, 1, x + k * h->V24, on_device));
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) info[k] = inf;
+  }
+  return worst;
+}
+
+ddamg_status ddamg_apply_D(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[0]));
+    TRY(op_dslash<R>(h, DSLASH_D, (R*)h->tmp[0], nullptr, (R*)h->tmp[1], nrhs));
+    return export_fields<R>(h, (R*)h->tmp[1], nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_apply_clover(ddamg_handle h, int prec, int inverse, int nrhs, const double* in, double* out,
+                                int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[0]));
+    CK(dslash<R>(h->g, DSLASH_CLOVER, (R*)h->tmp[0], nullptr, (R*)h->tmp[1], gauge_of<R>(h),
+                 clov_of<R>(h, inverse != 0), nrhs, h->st));
+    return export_fields<R>(h, (R*)h->tmp[1], nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_get_clover(ddamg_handle h, int inverse, double* out) {
+  if (!h || !out) return DDAMG_EINVAL;
+  size_t nd = (size_t)h->g.V * 72;
+  if (h->lexbuf_fields * h->V24 < nd) TRY(need_lexbuf(h, (nd + h->V24 - 1) / h->V24));
+  CK(export_clover(h->g, inverse ? h->Ai64 : h->A64, h->lexbuf, h->st));
+  CK(cudaMemcpyAsync(out, h->lexbuf, nd * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_block_solve(ddamg_handle h, int prec, int colour, int nrhs, const double* in, double* out,
+                               int on_device) {
+  if (!h || nrhs < 1 || !in || !out || (colour != 0 && colour != 1)) return DDAMG_EINVAL;
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    R* b = (R*)h->tmp[0];
+    R* x = (R*)h->tmp[1];
+    TRY(import_fields<R>(h, in, on_device, nrhs, b));
+    CK(cudaMemsetAsync(x, 0, nrhs * h->V24 * sizeof(R), h->st));
+    ++h->n_sap;
+    CK(sap_sweep<R>(h->g, colour, h->p.mr_iters, true, b, x, gauge_of<R>(h), clov_of<R>(h, false),
+                    clov_of<R>(h, true), nrhs, h->st));
+    return export_fields<R>(h, x, nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_sap(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[4]));
+    TRY(op_sap<R>(h, (R*)h->tmp[4], (R*)h->tmp[5], nrhs));
+    return export_fields<R>(h, (R*)h->tmp[5], nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_set_test_vectors(ddamg_handle h, const double* vecs, int on_device) {
+  if (!h || !vecs) return DDAMG_EINVAL;
+  TRY(import_fields<double>(h, vecs, on_device, h->p.n_v, h->lam64));
+  CK(cudaStreamSynchronize(h->st));
+  h->have_vectors = true;
+  h->have_coarse = false;
+  return sync_lam32(h);
+}
+
+ddamg_status ddamg_get_test_vectors(ddamg_handle h, double* vecs) {
+  if (!h || !vecs) return DDAMG_EINVAL;
+  if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  return export_fields<double>(h, h->lam64, h->p.n_v, vecs, 0);
+}
+
+ddamg_status ddamg_orthonormalize(ddamg_handle h) {
+  if (!h) return DDAMG_EINVAL;
+  if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  CK(orthonormalise(h->g, h->lam64, h->p.n_v, h->st));
+  TRY(sync_lam32(h));
+  CK(cudaStreamSynchronize(h->st));
+  h->have_coarse = false;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_build_coarse(ddamg_handle h) {
+  if (!h) return DDAMG_EINVAL;
+  TRY(build_coarse_op(h));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_get_coarse_op(ddamg_handle h, double* out) {
+  if (!h || !out) return DDAMG_EINVAL;
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no coarse operator");
+  size_t nc = (size_t)h->g.nb * 9 * h->n2 * h->n2;
+  double* tmpd;
+  TRY(dalloc_t(h, &tmpd, 2 * nc));
+  if (h->p.precision == DDAMG_FP32) CK(coarse_to_f64<float>((const float*)h->Dc, tmpd, nc, h->st));
+  else CK(coarse_to_f64<double>((const double*)h->Dc, tmpd, nc, h->st));
+  CK(cudaMemcpyAsync(out, tmpd, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  // release the export buffer
+  cudaFree(tmpd);
+  h->allocs.pop_back();
+  h->bytes -= 2 * nc * sizeof(double);
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_restrict(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    if (sizeof(R) == 4 && !h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
+    if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[0]));
+    CK(restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st));
+    return coarse_out<R>(h, (R*)h->tmp[1], (size_t)nrhs * h->g.nb * h->n2, out, on_device);
+  });
+}
+
+ddamg_status ddamg_prolong(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    if (sizeof(R) == 4 && !h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
+    if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(coarse_in<R>(h, in, on_device, (size_t)nrhs * h->g.nb * h->n2, (R*)h->tmp[0]));
+    CK(prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, false, h->st));
+    return export_fields<R>(h, (R*)h->tmp[1], nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_apply_coarse(ddamg_handle h, int prec, int nrhs, const double* in, double* out,
+                                int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no coarse operator");
+  if (prec != h->p.precision) return fail(h, DDAMG_EINVAL, "the coarse operator is stored in the inner precision");
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    size_t nc = (size_t)nrhs * h->g.nb * h->n2;
+    TRY(coarse_in<R>(h, in, on_device, nc, (R*)h->tmp[0]));
+    CK(coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st));
+    return coarse_out<R>(h, (R*)h->tmp[1], nc, out, on_device);
+  });
+}
+
+ddamg_status ddamg_coarse_solve(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device,
+                                double tol, int* iters) {
+  if (!h || nrhs < 1 || nrhs > 4096 || !in || !out || !(tol > 0.0)) return DDAMG_EINVAL;
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no coarse operator");
+  if (prec != h->p.precision) return fail(h, DDAMG_EINVAL, "the coarse operator is stored in the inner precision");
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    size_t nc = (size_t)nrhs * h->g.nb * h->n2;
+    TRY(coarse_in<R>(h, in, on_device, nc, (R*)h->tmp[0]));
+    TRY(op_coarse_solve<R>(h, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, tol, h->d_iters));
+    TRY(check_status(h));
+    if (iters) CK(cudaMemcpy(iters, h->d_iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost));
+    return coarse_out<R>(h, (R*)h->tmp[1], nc, out, on_device);
+  });
+}
+
+ddamg_status ddamg_apply_M(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
+  if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no coarse operator");
+  if (prec != h->p.precision) return fail(h, DDAMG_EINVAL, "M runs in the inner precision");
+  return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
+    using R = std::remove_pointer_t<decltype(tag)>;
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[4]));
+    TRY(op_M<R>(h, (R*)h->tmp[4], (R*)h->tmp[5], nrhs));
+    TRY(check_status(h));
+    return export_fields<R>(h, (R*)h->tmp[5], nrhs, out, on_device);
+  });
+}
+
+ddamg_status ddamg_get_index_maps(ddamg_handle h, int32_t* parity, int32_t* block, int32_t* colour,
+                                  int32_t* aggregate, int32_t* coarse_parity) {
+  if (!h) return DDAMG_EINVAL;
+  const size_t V = h->g.V;
+  int* buf;
+  TRY(dalloc_t(h, &buf, 3 * V));
+  CK(index_maps(h->g, buf, buf + V, buf + 2 * V, h->st));
+  std::vector<int> hb(3 * V);
+  CK(cudaMemcpyAsync(hb.data(), buf, 3 * V * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  cudaFree(buf);
+  h->allocs.pop_back();
+  h->bytes -= 3 * V * sizeof(int);
+  if (parity) std::memcpy(parity, hb.data(), V * 4);
+  if (block) std::memcpy(block, hb.data() + V, V * 4);
+  if (colour) std::memcpy(colour, hb.data() + 2 * V, V * 4);
+  if (aggregate) std::memcpy(aggregate, hb.data() + V, V * 4);   // aggregates = Schwarz blocks
+  if (coarse_parity) CK(cudaMemcpy(coarse_parity, h->d_cpar, h->g.nb * sizeof(int), cudaMemcpyDeviceToHost));
+  return DDAMG_OK;
+}
+
+static double sum_timers(ddamg_ctx* h, std::vector<Timer>& v) {
+  double ms = 0.0;
+  for (auto& t : v) {
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, t.a, t.b) == cudaSuccess) ms += f;
+  }
+  return ms;
+}
+
+ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
+  if (!h || !out) return DDAMG_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  out->kernel_launches = g_launches - h->launches0;
+  out->dslash_launches = h->n_dslash;
+  out->sap_launches = h->n_sap;
+  out->coarse_launches = h->n_coarse;
+  out->dslash_ms = sum_timers(h, h->tm_dslash);
+  out->sap_ms = sum_timers(h, h->tm_sap);
+  out->coarse_ms = sum_timers(h, h->tm_coarse);
+  out->device_bytes = h->bytes;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_reset_stats(ddamg_handle h) {
+  if (!h) return DDAMG_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  h->launches0 = g_launches;
+  h->n_dslash = h->n_sap = h->n_coarse = 0;
+  for (auto* v : {&h->tm_dslash, &h->tm_sap, &h->tm_coarse}) {
+    for (auto& t : *v) h->pool.push_back(t);
+    v->clear();
+  }
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_enable_kernel_timing(ddamg_handle h, int enable) {
+  if (!h) return DDAMG_EINVAL;
+  h->timing = enable != 0;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_random_vectors(ddamg_handle h, uint64_t seed, int n, double* out) {
+  if (!h || n < 1 || !out) return DDAMG_EINVAL;
+  TRY(need_lexbuf(h, n));
+  CK(random_spinors(h->g, seed, n, h->lexbuf, h->st));
+  CK(cudaMemcpyAsync(out, h->lexbuf, n * h->V24 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+const char* ddamg_last_error(ddamg_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void ddamg_destroy(ddamg_handle h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto* v : {&h->tm_dslash, &h->tm_sap, &h->tm_coarse, &h->pool})
+    for (auto& t : *v) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+  delete h;
+}
+
+}  // extern "C"

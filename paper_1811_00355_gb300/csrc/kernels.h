@@ -1,0 +1,149 @@
+// Host-side launchers of the library's CUDA kernels (no torch types).  Every
+// launcher enqueues on `st` and returns the cudaGetLastError() of its launch.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddamg {
+
+// Geometry of the fine lattice as the kernels see it.
+struct Geom {
+  int L[4];        // lattice extents
+  int b[4];        // Schwarz block (= aggregate) extents
+  int grid[4];     // blocks per direction
+  int V;           // sites
+  int Vb;          // sites per block
+  int nb;          // blocks (= coarse sites)
+  const uint32_t* nbr;      // [8][V] neighbour device index | NEG_BIT, dir 2mu fwd, 2mu+1 bwd
+  const int* lex_of_dev;    // [V]
+  const int16_t* bnbr;      // [8][Vb] block-local neighbour (other parity half index) or -1
+  const int16_t* face;      // [8][Vb] block-local sites whose hop in dir leaves the block
+                            //   (first Vb / b[mu] entries of each row are used)
+  const int* cnbr;          // [9][nb] coarse neighbour of each stencil direction
+  const int* cparity;       // [nb] coarse parity
+  const int* ceven;         // [nb/2] coarse sites of parity 0
+  const int* codd;          // [nb/2] coarse sites of parity 1
+  const int* cpos;          // [nb] position of a coarse site in its parity list
+};
+
+// kernel launch counter (incremented by each launcher)
+extern uint64_t g_launches;
+
+// ---- layout conversion ------------------------------------------------------
+// host layout (FP64 lexicographic, interleaved complex) <-> device fields
+template <class R>
+cudaError_t pack_spinor(const Geom& g, const double* lex, R* dev, int nrhs, cudaStream_t st);
+template <class R>
+cudaError_t unpack_spinor(const Geom& g, const R* dev, double* lex, int nrhs, cudaStream_t st);
+// flat element-wise conversion (same layout on both sides: coarse vectors)
+template <class RD, class RS>
+cudaError_t convert_field(const RS* src, RD* dst, size_t nreal, cudaStream_t st);
+// spinor fields between the FP64 and FP32 device layouts (nf fields)
+template <class RD, class RS>
+cudaError_t convert_spinor(const Geom& g, const RS* src, RD* dst, int nf, cudaStream_t st);
+
+// ---- gauge and clover -------------------------------------------------------
+// compress lexicographic FP64 links into the two-row device layouts; the
+// largest deviation from SU(3) (|U U^H - 1|, |det U - 1|) is max-reduced into
+// *dev_dev (as ordered bits of a non-negative double)
+cudaError_t import_gauge(const Geom& g, const double* lex, double* g64, float* g32,
+                         unsigned long long* dev_dev, cudaStream_t st);
+// A = (4 + m0) + C and A^-1, packed, in FP64 and FP32 device layouts
+cudaError_t build_clover(const Geom& g, const double* lex_gauge, double m0, double csw,
+                         double* A64, double* Ai64, float* A32, float* Ai32, cudaStream_t st);
+// export packed blocks to [lex site][2][36] doubles
+cudaError_t export_clover(const Geom& g, const double* dev, double* lex, cudaStream_t st);
+
+// ---- fine operator ----------------------------------------------------------
+enum DslashMode { DSLASH_D = 0, DSLASH_RES = 1, DSLASH_CLOVER = 2 };
+// DSLASH_D: y = D x; DSLASH_RES: y = b - D x; DSLASH_CLOVER: y = A x
+template <class R>
+cudaError_t dslash(const Geom& g, int mode, const R* x, const R* b, R* y, const R* gauge,
+                   const R* clover, int nrhs, cudaStream_t st);
+
+// ---- BLAS-1 on flat complex arrays (n complex numbers) -------------------------
+// partial sums per CTA land in `scratch` (>= reduce_scratch_len(k) doubles)
+size_t reduce_scratch_len(int k);
+// out[j] = <v_j, w> for j < k (complex, FP64 accumulate); out in device memory
+template <class R>
+cudaError_t multi_dot(const R* const* v, int k, const R* w, size_t n, double* scratch,
+                      double* out, cudaStream_t st);
+// out[0] = ||w||^2
+template <class R>
+cudaError_t norm2(const R* w, size_t n, double* scratch, double* out, cudaStream_t st);
+// w += sum_j coef[j] * v_j with coef = sign * (complex doubles in device memory)
+template <class R>
+cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign, R* w,
+                       size_t n, cudaStream_t st);
+// y = a x + b y (real scalars)
+template <class R>
+cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t st);
+// y = x * (1/s[0]) with s a device scalar holding a squared norm (sqrt taken)
+template <class R>
+cudaError_t scale_by_inv_norm(const R* x, R* y, const double* s, size_t n, cudaStream_t st);
+
+// ---- random initial vectors (Philox4x32-10 + Box-Muller) ----------------------
+cudaError_t random_spinors(const Geom& g, uint64_t seed, int n, double* dev64, cudaStream_t st);
+
+// ---- index maps for checking -------------------------------------------------
+cudaError_t index_maps(const Geom& g, int* parity, int* block, int* colour, cudaStream_t st);
+
+// ---- SAP smoother -------------------------------------------------------------
+// one colour of a Schwarz sweep on all blocks of that colour:
+//   r = b - D x (or r = b if x_is_zero), e = MR-even-odd block solve of r,
+//   x += e (x is overwritten with e if x_is_zero)
+template <class R>
+cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b,
+                      R* x, const R* gauge, const R* clover, const R* clover_inv, int nrhs,
+                      cudaStream_t st);
+size_t sap_smem_bytes(const Geom& g, int real_size);
+
+// ---- coarse grid ----------------------------------------------------------------
+// classical Gram-Schmidt twice per (aggregate, chirality) on n FP64 fields
+cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st);
+// b_c = R b  (coarse layout [rhs][X][2n] complex)
+template <class R>
+cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs,
+                        cudaStream_t st);
+// x (+)= P x_c
+template <class R>
+cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs,
+                       bool accumulate, cudaStream_t st);
+// D_c [X][9][2n][2n] from the test vectors
+template <class R>
+cudaError_t assemble_coarse(const Geom& g, const R* lam, int n, const R* gauge,
+                            const R* clover, R* Dc, cudaStream_t st);
+// inverses of the self blocks [X][2n][2n] (FP64 Gauss-Jordan, stored as R)
+template <class R>
+cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* singular,
+                               cudaStream_t st);
+// y = D_c x (all sites)
+template <class R>
+cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs,
+                         cudaStream_t st);
+// coarse host layout <-> device coarse layout (same order, conversion only)
+template <class R>
+cudaError_t coarse_from_f64(const double* src, R* dst, size_t ncomplex, cudaStream_t st);
+template <class R>
+cudaError_t coarse_to_f64(const R* src, double* dst, size_t ncomplex, cudaStream_t st);
+
+// even-odd preconditioned restarted GMRES on D_c: one persistent cooperative
+// kernel solves all right-hand sides one after the other.  `work` must hold
+// coarse_gmres_work_bytes() bytes; iters[rhs] receives the iteration counts,
+// *status 0 (ok) or DDAMG_ETIMEOUT-style codes from the bounded grid barrier.
+struct CoarseSolveArgs {
+  const void* Dc;
+  const void* Ainv;
+  int n;            // test vectors (2n components per coarse site)
+  double tol;
+  int restart;      // <= 64
+  int max_iter;
+};
+size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size);
+template <class R>
+cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& a, const R* b, R* x, int nrhs,
+                         void* work, int* iters, int* iters_acc, int* status, cudaStream_t st);
+
+}  // namespace ddamg

@@ -1,0 +1,309 @@
+"""Parity of every step of the CUDA path with the CPU oracle, through the C ABI.
+
+Per-apply relative (norm-wise) error bounds: FP64 1e-13, FP32 1e-6; index
+maps bit-exact; every solution reaches a true FP64 residual <= 1e-10.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle.coarse import (Aggregation, CoarseOperator, coarse_operator,
+                           orthonormalise, prolong, restrict)
+from oracle.dirac import pack_hermitian, chiral_blocks
+from oracle.lattice import index_maps
+from oracle.solver import Params, TwoLevelMG
+from tests.gpu_common import (FULL, MID, SMALL, TOL32, TOL64, make, oracle_op, rel,
+                              smoother, t)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_1811_00355_gb300 as P
+    P.load()
+    assert torch.cuda.is_available()
+
+
+def _P():
+    import paper_1811_00355_gb300 as P
+    return P
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+def test_index_maps_bit_exact(cfg):
+    s = make(cfg, _P().FP64)
+    got = s.index_maps()
+    ref = index_maps(cfg[0], cfg[1], cfg[1])
+    for k in ("parity", "block", "colour", "aggregate", "coarse_parity"):
+        assert np.array_equal(got[k], ref[k].numpy()), k
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+def test_clover_packed_blocks(cfg):
+    L, b, eps, m0, csw, n_v, seed = cfg
+    s = make(cfg, _P().FP64)
+    op = oracle_op(L, eps, seed, m0, csw)
+    assert rel(s.get_clover(False), op.packed_clover(False).numpy()) < TOL64
+    assert rel(s.get_clover(True), op.packed_clover(True).numpy()) < TOL64
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID, FULL])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_wilson_clover_D(cfg, prec):
+    L, b, eps, m0, csw, n_v, seed = cfg
+    s = make(cfg, prec)
+    op = oracle_op(L, eps, seed, m0, csw)
+    x = syn.gaussian_spinors(2, L, 40)
+    y = s.apply_D(x, precision=prec)
+    ref = op.apply(t(x)).numpy()
+    tol = TOL64 if prec == 0 else TOL32
+    for k in range(2):
+        assert rel(y[k], ref[k]) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_clover_and_inverse_apply(prec):
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, prec)
+    op = oracle_op(L, eps, seed, m0, csw)
+    x = syn.gaussian_spinors(1, L, 41)
+    tol = TOL64 if prec == 0 else TOL32
+    assert rel(s.apply_clover(x, False, prec), op.site(t(x)).numpy()) < tol
+    assert rel(s.apply_clover(x, True, prec), op.site(t(x), inverse=True).numpy()) < tol
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_solve(cfg, prec):
+    L = cfg[0]
+    s = make(cfg, prec)
+    sm = smoother(cfg)
+    r = syn.gaussian_spinors(1, L, 42)
+    for c in (0, 1):
+        got = s.block_solve(r, c, prec)
+        ref = sm.block_solve(t(r[0]), c, 4).numpy()
+        tol = 1e-12 if prec == 0 else 5 * TOL32
+        assert rel(got[0], ref) < tol
+        # zero on the blocks of the other colour
+        other = sm.mask[1 - c, None].numpy().real.astype(bool)[:, 0, 0]
+        assert np.abs(got[0][other]).max() == 0.0
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sap(cfg, prec):
+    L = cfg[0]
+    s = make(cfg, prec)
+    sm = smoother(cfg)
+    r = syn.gaussian_spinors(1, L, 43)
+    got = s.sap(r, prec)
+    ref = sm.apply(t(r[0]), 4, 4).numpy()
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert rel(got[0], ref) < tol
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+def test_orthonormalise(cfg):
+    L, b, eps, m0, csw, n_v, seed = cfg
+    s = make(cfg, _P().FP64)
+    lam = syn.gaussian_spinors(n_v, L, 44)
+    s.set_test_vectors(lam)
+    s.orthonormalize()
+    op = oracle_op(L, eps, seed, m0, csw)
+    ref = orthonormalise(t(lam), Aggregation(op.geom, b)).numpy()
+    assert rel(s.get_test_vectors(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("cfg", [SMALL, MID])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_restrict_prolong(cfg, prec):
+    L, b, eps, m0, csw, n_v, seed = cfg
+    s = make(cfg, prec)
+    op = oracle_op(L, eps, seed, m0, csw)
+    agg = Aggregation(op.geom, b)
+    lam = orthonormalise(t(syn.gaussian_spinors(n_v, L, 45)), agg)
+    s.set_test_vectors(np.ascontiguousarray(lam.numpy()))
+    x = syn.gaussian_spinors(2, L, 46)
+    tol = TOL64 if prec == 0 else TOL32
+    bc = s.restrict(x, prec)
+    ref = restrict(lam, agg, t(x)).numpy()
+    assert rel(bc, ref) < tol
+    y = np.ascontiguousarray(ref)
+    got = s.prolong(y, prec)
+    assert rel(got, prolong(lam, agg, t(y)).numpy()) < tol
+
+
+@pytest.fixture(scope="module")
+def coarse_pair():
+    """GPU handles (FP64 and FP32) sharing orthonormal test vectors with the oracle."""
+    out = {}
+    L, b, eps, m0, csw, n_v, seed = MID
+    op = oracle_op(L, eps, seed, m0, csw)
+    agg = Aggregation(op.geom, b)
+    lam = orthonormalise(t(syn.gaussian_spinors(n_v, L, 47)), agg)
+    Dc = coarse_operator(op, lam, agg)
+    cop = CoarseOperator(Dc, agg.coarse)
+    for prec in (0, 1):
+        s = make(MID, prec)
+        s.set_test_vectors(np.ascontiguousarray(lam.numpy()))
+        s.build_coarse()
+        out[prec] = s
+    return out, lam, agg, cop
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coarse_operator(coarse_pair, prec):
+    handles, lam, agg, cop = coarse_pair
+    got = handles[prec].get_coarse_op()
+    tol = 1e-12 if prec == 0 else TOL32
+    assert rel(got, cop.Dc.numpy()) < tol
+    for X in (0, 5, agg.NX - 1):
+        assert rel(got[X], cop.Dc[X].numpy()) < 10 * tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coarse_stencil(coarse_pair, prec):
+    handles, lam, agg, cop = coarse_pair
+    rng = np.random.default_rng(48)
+    x = rng.standard_normal((2, agg.NX, 2 * lam.shape[0])) + 1j * rng.standard_normal((2, agg.NX, 2 * lam.shape[0]))
+    got = handles[prec].apply_coarse(x, prec)
+    ref = cop.apply(t(x)).numpy()
+    assert rel(got, ref) < (TOL64 if prec == 0 else TOL32)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coarse_even_odd_gmres(coarse_pair, prec):
+    handles, lam, agg, cop = coarse_pair
+    rng = np.random.default_rng(49)
+    b = rng.standard_normal((2, agg.NX, 2 * lam.shape[0])) + 1j * rng.standard_normal((2, agg.NX, 2 * lam.shape[0]))
+    # loose tolerance of the method: same iteration count as the oracle's
+    x, its = handles[prec].coarse_solve(b, 5e-2, prec)
+    for k in range(2):
+        xr, ir = cop.solve(t(b[k]), 5e-2, 30, 300)
+        assert abs(int(its[k]) - ir) <= (0 if prec == 0 else 1)
+        if prec == 0:
+            assert rel(x[k], xr.numpy()) < 1e-11
+    # tight tolerance: the dense solve
+    tol = 1e-12 if prec == 0 else 1e-5
+    x, its = handles[prec].coarse_solve(b, tol, prec)
+    Dd = cop.dense().numpy()
+    for k in range(2):
+        xd = np.linalg.solve(Dd, b[k].reshape(-1)).reshape(b[k].shape)
+        assert rel(x[k], xd) < (1e-10 if prec == 0 else 1e-4)
+
+
+def test_preconditioner_M_fp64():
+    L, b, eps, m0, csw, n_v, seed = SMALL
+    s = make(SMALL, 0)
+    mg = TwoLevelMG(t(syn.gauge_field(L, eps, seed)),
+                    Params(L, b, b, n_v, m0, csw, setup_iters=3))
+    lam = orthonormalise(t(syn.gaussian_spinors(n_v, L, 50)), mg.agg)
+    mg.set_test_vectors(lam, orthonormalised=True)
+    s.set_test_vectors(np.ascontiguousarray(lam.numpy()))
+    s.build_coarse()
+    r = syn.gaussian_spinors(1, L, 51)
+    got = s.apply_M(r, 0)
+    ref = mg.apply_M(t(r[0])).numpy()
+    assert rel(got[0], ref) < 1e-11
+
+
+def test_setup_fp64_matches_oracle():
+    """Same initial vectors -> the FP64 setup reproduces the oracle's test
+    vectors and coarse operator up to rounding."""
+    L, b, eps, m0, csw, n_v, seed = SMALL
+    s = make(SMALL, 0, setup_iters=3)
+    lam0 = syn.gaussian_spinors(n_v, L, 1)
+    s.run_setup(lam0)
+    mg = TwoLevelMG(t(syn.gauge_field(L, eps, seed)), Params(L, b, b, n_v, m0, csw, setup_iters=3))
+    mg.setup(t(lam0))
+    assert rel(s.get_test_vectors(), mg.lam.numpy()) < 1e-9
+    assert rel(s.get_coarse_op(), mg.cop.Dc.numpy()) < 1e-9
+
+
+def test_solve_small_fp64_matches_dense():
+    L, b, eps, m0, csw, n_v, seed = SMALL
+    s = make(SMALL, 0, setup_iters=3)
+    s.run_setup(syn.gaussian_spinors(n_v, L, 1))
+    op = oracle_op(L, eps, seed, m0, csw)
+    D = op.dense().numpy()
+    rhs = syn.gaussian_spinors(2, L, 2)
+    x, info = s.solve(rhs, 1e-10)
+    cond = np.linalg.cond(D)
+    for k in range(2):
+        res = rel(op.apply(t(x[k])).numpy(), rhs[k])
+        assert res <= 1e-10 and info[k]["converged"] == 1
+        xd = np.linalg.solve(D, rhs[k].reshape(-1)).reshape(rhs[k].shape)
+        assert rel(x[k], xd) <= cond * 1e-10
+
+
+def test_solve_full_workload_point_sources():
+    """16^4, FP32 smoother / coarse solve, FP64 outer FGMRES: the 12 point
+    sources reach a true residual <= 1e-10 checked by the oracle's D."""
+    L, b, eps, m0, csw, n_v, seed = FULL
+    s = make(FULL, 1)
+    s.run_setup()
+    op = oracle_op(L, eps, seed, m0, csw)
+    rhs = syn.point_sources(L)
+    x, info = s.solve(np.ascontiguousarray(rhs), 1e-10)
+    for k in range(12):
+        res = rel(op.apply(t(x[k])).numpy(), rhs[k])
+        assert res <= 1e-10, (k, res, info[k])
+
+
+def test_random_vectors_match_philox_definition():
+    P = _P()
+    s = make(SMALL, 0)
+    got = s.random_vectors(1234, 2)
+    V = got.shape[1]
+    x = np.arange(V, dtype=np.uint64)
+    for i in range(2):
+        ref = np.empty((V, 24))
+        for blk in range(6):
+            w = syn.Philox4x32.block((x, np.full(V, i), np.full(V, blk), np.zeros(V)), (1234, 0))
+            for pr in range(2):
+                u1 = (w[2 * pr].astype(np.float64) + 1.0) * 2.0 ** -32
+                u2 = w[2 * pr + 1].astype(np.float64) * 2.0 ** -32
+                r = np.sqrt(-2.0 * np.log(u1))
+                ref[:, blk * 4 + pr * 2] = r * np.cos(2 * np.pi * u2)
+                ref[:, blk * 4 + pr * 2 + 1] = r * np.sin(2 * np.pi * u2)
+        assert np.abs(got[i].view(np.float64).reshape(V, 24) - ref).max() < 1e-12
+
+
+def test_status_codes_on_device():
+    P = _P()
+    L = SMALL[0]
+    s = make(SMALL, 0, setup_iters=1, max_outer_iter=2)
+    with pytest.raises(P.DDAMGError) as e:
+        s.solve(syn.gaussian_spinors(1, L, 3))
+    assert e.value.status == 7          # no setup yet
+    s.run_setup(syn.gaussian_spinors(8, L, 1))
+    x, info = s.solve(syn.gaussian_spinors(1, L, 3), 1e-12, allow_noconv=True)
+    assert info[0]["converged"] == 0 and info[0]["outer_iters"] == 2
+    bad = syn.gaussian_spinors(1, L, 3)
+    bad[0, 5, 1, 1] = np.nan
+    with pytest.raises(P.DDAMGError) as e:
+        s.solve(bad)
+    assert e.value.status == 5
+    with pytest.raises(P.DDAMGError) as e:
+        make(SMALL, 0, hbm_budget=1 << 16)
+    assert e.value.status == 2
+    U = syn.gauge_field(L, 0.3, 0).copy()
+    U[3, 2] *= 1.01
+    p = P.default_params(L=L, sap_block=(2, 2, 2, 2), n_v=8)
+    with pytest.raises(P.DDAMGError) as e:
+        P.DDAMG(p, U)
+    assert e.value.status == 1
+
+
+def test_device_pointer_path_and_determinism():
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1)
+    s.run_setup()
+    rhs = syn.gaussian_spinors(1, L, 60)
+    xh, _ = s.solve(rhs, 1e-10)
+    xd, _ = s.solve(torch.from_numpy(rhs).cuda(), 1e-10)
+    assert np.array_equal(xh, xd.cpu().numpy())
