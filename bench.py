@@ -1,0 +1,356 @@
+"""Benchmark: 12 point-source solves of the Wilson-clover operator to a true
+FP64 relative residual of 1e-10, including the adaptive setup, with the
+2-level DD-alpha-AMG solver on one GB300.
+
+Workload (synthetic, seeded): 16^4 lattice, near-unit SU(3) links
+U = exp(i 0.25 H) (seed 1), m0 = -0.3, csw = 1.2, antiperiodic in time;
+4^4 Schwarz blocks = aggregates, 4 SAP cycles of 4 MR iterations, n_v = 20
+test vectors from 4 setup iterations; FP32 smoother / coarse GMRES / projections,
+FP64 outer FGMRES; the 12 spin-colour point sources at the origin solved
+one after the other.  One step = setup (clover term, test vectors, coarse
+operator) + 12 solves, with the links resident in device memory.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own replica of the workload; nothing is exchanged between GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "12-RHS solves/s at 1e-10 incl. setup"
+UNIT = "solves/s"
+WORKLOAD = dict(L=(16, 16, 16, 16), block=(4, 4, 4, 4), eps=0.25, seed=1, m0=-0.3, csw=1.2,
+                n_v=20, setup_iters=4, n_sap=4, mr_iters=4, coarse_tol=5e-2, tol=1e-10)
+# algorithmic (compulsory) bytes per site of one launch of each timed kernel,
+# FP32 storage with two-row links: SAP sweep reads b, x, 4 links, A, A^-1 and
+# writes x on its blocks; the coarse GMRES iteration streams the coarse
+# operator once (self + 8 links on every site) plus A_oo^-1 on the odd sites.
+SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
+L2_BYTES = 129 * 2 ** 20
+# outer-solver preconditioner calls of this workload (12 point sources), as
+# measured on the CUDA path; used only to scale the reference arm's sample
+REFERENCE_PRECOND_CALLS = 12 * 12
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "of measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.strip().splitlines():
+            parts = [v.strip() for v in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload_params(P):
+    w = WORKLOAD
+    return P.default_params(L=w["L"], sap_block=w["block"], n_v=w["n_v"], m0=w["m0"], csw=w["csw"],
+                            setup_iters=w["setup_iters"], n_sap=w["n_sap"], mr_iters=w["mr_iters"],
+                            coarse_tol=w["coarse_tol"], precision=P.FP32, seed=12345)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1811_00355_gb300 as P
+    import synthetic as syn
+
+    rank, local, world = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    P.load()
+    w = WORKLOAD
+    L = w["L"]
+    V = int(np.prod(L))
+    U_host = syn.gauge_field(L, w["eps"], w["seed"] + rank)
+    b_host = np.ascontiguousarray(syn.point_sources(L))
+    U_dev = torch.from_numpy(U_host).cuda()
+    b_dev = torch.from_numpy(b_host).cuda()
+    stream = torch.cuda.current_stream()
+    params = workload_params(P)
+    solver = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        solver.run_setup()
+        x, info = solver.solve(b_dev, w["tol"])
+        return x, info
+
+    for _ in range(args.warmup):
+        x, info = step()
+    torch.cuda.synchronize()
+    bad = [i for i in info if not (i["converged"] and i["true_residual"] <= w["tol"])]
+    if bad:
+        raise RuntimeError(f"warm-up solves did not converge: {bad}")
+
+    solver.reset_stats()
+    solver.enable_kernel_timing(True)
+    times = []
+    infos = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                     # evict L2 between timed steps
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st = solver.stats()
+    solver.enable_kernel_timing(False)
+    for info in infos:
+        for i in info:
+            if not (i["converged"] and i["true_residual"] <= w["tol"]):
+                raise RuntimeError(f"a timed solve missed the tolerance: {i}")
+    T = sum(times)
+    if world > 1:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+    solves = 12 * args.steps * world
+    value = solves / T
+    ms_per_step = 1e3 * T / args.steps
+
+    # roofline of the dominant timed kernel
+    pk, pk_kind = peaks()
+    classes = {"sap_sweep": (st["sap_ms"], st["sap_launches"]),
+               "coarse_gmres": (st["coarse_ms"], st["coarse_launches"]),
+               "dslash": (st["dslash_ms"], st["dslash_launches"])}
+    dom = max(classes, key=lambda k: classes[k][0])
+    ms, n = classes[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": None, "traffic": None, "peak_kind": pk_kind + " (burst copy)",
+            "share_of_step": round(ms / (1e3 * T / world) if T else 0.0, 3)}
+    if dom == "sap_sweep" and n:
+        per_launch = (V // 2) * SAP_BYTES_PER_SITE
+        achieved = per_launch / (ms / n * 1e-3) / 1e9
+        roof.update(achieved=round(achieved, 1), frac=round(achieved / pk["hbm_gbs"], 4),
+                    algorithmic_bytes_per_launch=per_launch, avg_launch_us=round(1e3 * ms / n, 2))
+    elif dom == "coarse_gmres" and n:
+        nx = V // 256
+        n2 = 2 * w["n_v"]
+        per_iter = nx * 9 * n2 * n2 * 8 + (nx // 2) * n2 * n2 * 8
+        its = sum(i["coarse_iters"] for info in infos for i in info)
+        per_launch = per_iter * its / max(1, sum(i["precond_calls"] for info in infos for i in info))
+        achieved = per_launch / (ms / n * 1e-3) / 1e9
+        roof.update(achieved=round(achieved, 1), frac=round(achieved / pk["hbm_gbs"], 4),
+                    algorithmic_bytes_per_launch=int(per_launch), avg_launch_us=round(1e3 * ms / n, 2))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        solver.close()
+        torch.cuda.synchronize()
+        x_host = np.empty_like(b_host)
+        et = []
+        for k in range(max(1, min(args.steps, 3)) + 1):
+            t0 = time.perf_counter()
+            s2 = P.DDAMG(params, U_host, stream=stream.cuda_stream)
+            s2.run_setup()
+            xh, inf = s2.solve(b_host, w["tol"])
+            s2.close()
+            t1 = time.perf_counter()
+            if k:
+                et.append(t1 - t0)
+        e2e = {"value": round(12 / statistics.mean(et) * world, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(U_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        counts = {"precond_calls": sum(i["precond_calls"] for i in infos[-1])}
+        cpu = cpu_baseline(counts)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "16^4 Wilson-clover, eps 0.25, m0 -0.3, csw 1.2, 4^4 blocks, n_v 20, "
+                                   "4 setup iters, 12 point sources one at a time, tol 1e-10",
+                       "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(st["kernel_launches"]), "clocks": clk.summary(),
+            "solve_stats": {"outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in infos[-1]),
+                            "precond_calls": sum(i["precond_calls"] for i in infos[-1]),
+                            "coarse_iters": sum(i["coarse_iters"] for i in infos[-1]),
+                            "max_true_residual": max(i["true_residual"] for info in infos for i in info),
+                            "step_seconds": [round(t, 4) for t in times]},
+            "kernel_ms": {k: round(v[0], 3) for k, v in classes.items()},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def _oracle_sample():
+    """Time the oracle's operations on the 16^4 workload once each (seconds)."""
+    import torch
+    import synthetic as syn
+    from oracle.coarse import CoarseOperator, coarse_operator, orthonormalise
+    from oracle.solver import Params, TwoLevelMG
+    w = WORKLOAD
+    L = w["L"]
+    mg = TwoLevelMG(torch.from_numpy(syn.gauge_field(L, w["eps"], w["seed"])),
+                    Params(L, w["block"], w["block"], w["n_v"], w["m0"], w["csw"],
+                           setup_iters=w["setup_iters"]))
+    lam = torch.from_numpy(syn.gaussian_spinors(w["n_v"], L, 7))
+    b = torch.from_numpy(syn.point_sources(L)[0])
+    t = {}
+    t0 = time.perf_counter()
+    mg.set_test_vectors(lam)                       # orthonormalise + D_c
+    t["build"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mg.smoother(b)
+    t["sap"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    z = mg.apply_M(b)
+    t["M"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mg.op.apply(z)
+    t["D"] = time.perf_counter() - t0
+    return t
+
+
+def _oracle_seconds(t, precond_calls):
+    w = WORKLOAD
+    n, it = w["n_v"], w["setup_iters"]
+    return (n * t["sap"] + (it + 1) * t["build"] + it * n * t["M"]
+            + precond_calls * (t["M"] + t["D"]))
+
+
+def cpu_baseline(counts):
+    import torch
+    t0 = time.perf_counter()
+    t = _oracle_sample()
+    wall = time.perf_counter() - t0
+    secs = _oracle_seconds(t, counts["precond_calls"])
+    return {"value": round(12 / secs, 6), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": ("oracle timed once per operation on the 16^4 workload (one SAP, one orthonormalise + "
+                       "D_c assembly, one M, one D: %.1f s of CPU work); scaled by the workload's "
+                       "operation counts (n_v SAPs, %d builds, %d setup M, %d outer iterations)"
+                       % (wall, WORKLOAD["setup_iters"] + 1, WORKLOAD["setup_iters"] * WORKLOAD["n_v"],
+                          counts["precond_calls"])),
+            "extrapolated_seconds": round(secs, 1), "op_seconds": {k: round(v, 3) for k, v in t.items()}}
+
+
+def run_reference(args):
+    import torch
+    rank, local, world = env_rank()
+    if rank != 0:
+        return
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        t = _oracle_sample()
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(_oracle_seconds(t, REFERENCE_PRECOND_CALLS))
+    secs = statistics.mean(times)
+    value = 12 / secs
+    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * secs, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "16^4 Wilson-clover, eps 0.25, m0 -0.3, csw 1.2, 4^4 blocks, n_v 20, "
+                                   "4 setup iters, 12 point sources one at a time, tol 1e-10",
+                       "parallelism": "cpu"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "kind": "oracle",
+                             "cores": torch.get_num_threads(),
+                             "sample": "each step times the oracle's SAP, D_c build, M and D once on the "
+                                       "16^4 workload and scales by the workload's operation counts"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,7 +145,8 @@ DDAMG_API ddamg_status ddamg_setup(const ddamg_params *p, const double *gauge,
                          int gauge_on_device, void *cuda_stream,
                          ddamg_handle *out);
 
-/* Adaptive setup (Sec. 2) on an existing handle: initial vectors are
+/* Adaptive setup (Sec. 2) on an existing handle: the clover term and its
+ * inverse are rebuilt from the resident links; initial vectors are
  * init_vectors (n_v spinor fields, host or device) or, if NULL, drawn from
  * p->seed; each is smoothed by SAP from a zero start; then setup_iters times
  * {orthonormalise per (X, s); assemble D_c; lambda_i <- M lambda_i}; finally

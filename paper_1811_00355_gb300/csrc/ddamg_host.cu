@@ -598,7 +598,7 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
   CK(cudaMemsetAsync(h->fx, 0, N * 8, h->st));
   CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
   // ||b||
-  double host[2 * 3 * 64];
+  double host[6 * 64 + 16];
   CK(norm2<double>(h->fb, NC, h->red, h->dots, h->st));
   CK(cudaMemcpyAsync(host, h->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -619,21 +619,36 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       TRY(precond_to_f64<R>(h, Vk(k), Zk(k)));
       ++calls;
       TRY(op_dslash<double>(h, DSLASH_D, Zk(k), nullptr, h->fw, 1));
-      // classical Gram-Schmidt, two passes; coefficients stay on the device
-      for (int pass = 0; pass < 2; ++pass) {
-        double* c = h->dots + 2 * (m + 1) * pass;
-        CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c, h->st));
-        CK(multi_axpy<double>(vlist.data(), k + 1, c, -1.0, h->fw, NC, h->st));
-      }
-      double* nn = h->dots + 4 * (m + 1);
+      // classical Gram-Schmidt with a second pass only when the first one
+      // cancelled much of w (||w_after|| < ||w_before|| / sqrt 2, "twice is
+      // enough"); the coefficients stay on the device, ||w_before||^2 comes
+      // with the first multi-dot
+      vlist[k + 1] = h->fw;
+      double* c1 = h->dots;
+      double* c2 = h->dots + 2 * (m + 2);
+      double* nn = h->dots + 4 * (m + 2);
+      CK(multi_dot<double>(vlist.data(), k + 2, h->fw, NC, h->red, c1, h->st));
+      CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
       CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
-      CK(scale_by_inv_norm<double>(h->fw, Vk(k + 1), nn, N, h->st));
-      CK(cudaMemcpyAsync(host, h->dots, (4 * (m + 1) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(host, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       CK(cudaStreamSynchronize(h->st));
       std::vector<cd> col(k + 2);
-      for (int j = 0; j <= k; ++j)
-        col[j] = cd(host[2 * j] + host[2 * (m + 1) + 2 * j], host[2 * j + 1] + host[2 * (m + 1) + 2 * j + 1]);
-      const double hn = std::sqrt(host[4 * (m + 1)]);
+      for (int j = 0; j <= k; ++j) col[j] = cd(host[2 * j], host[2 * j + 1]);
+      double n_before = host[2 * (k + 1)];
+      double n_after = host[4 * (m + 2)];
+      if (n_after < 0.5 * n_before) {
+        CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
+        CK(multi_axpy<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->st));
+        CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
+        CK(cudaMemcpyAsync(host + 2 * (m + 2), c2, (2 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (int j = 0; j <= k; ++j) col[j] += cd(host[2 * (m + 2) + 2 * j], host[2 * (m + 2) + 2 * j + 1]);
+        n_after = host[4 * (m + 2)];
+      }
+      vlist[k + 1] = Vk(k + 1);
+      CK(scale_by_inv_norm<double>(h->fw, Vk(k + 1), nn, N, h->st));
+      const double hn = std::sqrt(n_after);
       if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the FGMRES basis norm");
       col[k + 1] = hn;
       for (int j = 0; j < k; ++j) {
@@ -817,7 +832,7 @@ ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_
     TRY(dalloc_t(h, &h->d_iters_acc, 1));
     TRY(dalloc_t(h, &h->d_status, 1));
     TRY(dalloc_t(h, &h->red, reduce_scratch_len(64)));
-    TRY(dalloc_t(h, &h->dots, (size_t)6 * 64 + 8));
+    TRY(dalloc_t(h, &h->dots, (size_t)6 * 64 + 16));
     TRY(dalloc_t(h, &h->lam64, (size_t)p->n_v * h->V24));
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->d_dev, 0, sizeof(unsigned long long), h->st));
@@ -847,6 +862,9 @@ ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_
 ddamg_status ddamg_run_setup(ddamg_handle h, const double* init, int on_device) {
   if (!h) return DDAMG_EINVAL;
   const int n = h->p.n_v;
+  // the clover term and its inverse are part of the setup (rebuilt from the
+  // resident links, so a repeated setup redoes all of its work)
+  CK(build_clover(h->g, h->d_gauge_lex, h->p.m0, h->p.csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
   if (init) {
     TRY(import_fields<double>(h, init, on_device, n, h->lam64));
   } else {
@@ -1008,8 +1026,8 @@ ddamg_status ddamg_get_coarse_op(ddamg_handle h, double* out) {
   size_t nc = (size_t)h->g.nb * 9 * h->n2 * h->n2;
   double* tmpd;
   TRY(dalloc_t(h, &tmpd, 2 * nc));
-  if (h->p.precision == DDAMG_FP32) CK(coarse_to_f64<float>((const float*)h->Dc, tmpd, nc, h->st));
-  else CK(coarse_to_f64<double>((const double*)h->Dc, tmpd, nc, h->st));
+  if (h->p.precision == DDAMG_FP32) CK(coarse_export<float>((const float*)h->Dc, h->p.n_v, (size_t)h->g.nb * 9, tmpd, h->st));
+  else CK(coarse_export<double>((const double*)h->Dc, h->p.n_v, (size_t)h->g.nb * 9, tmpd, h->st));
   CK(cudaMemcpyAsync(out, tmpd, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   // release the export buffer

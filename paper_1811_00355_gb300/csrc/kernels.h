@@ -111,14 +111,19 @@ cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, i
 template <class R>
 cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs,
                        bool accumulate, cudaStream_t st);
-// D_c [X][9][2n][2n] from the test vectors
+// D_c [X][9][2n][2n] from the test vectors; every 2n x 2n block is stored
+// column-major on the device (entry (r, c) at c * 2n + r)
 template <class R>
 cudaError_t assemble_coarse(const Geom& g, const R* lam, int n, const R* gauge,
                             const R* clover, R* Dc, cudaStream_t st);
-// inverses of the self blocks [X][2n][2n] (FP64 Gauss-Jordan, stored as R)
+// inverses of the self blocks [X][2n][2n] (FP64 Gauss-Jordan, stored as R,
+// column-major like D_c)
 template <class R>
 cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* singular,
                                cudaStream_t st);
+// nblocks column-major blocks -> row-major complex doubles (host layout)
+template <class R>
+cudaError_t coarse_export(const R* Dc, int n, size_t nblocks, double* out, cudaStream_t st);
 // y = D_c x (all sites)
 template <class R>
 cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs,

@@ -1,0 +1,721 @@
+// Even-odd preconditioned restarted GMRES on the coarse operator, paper
+// Sec. 2: the coarse solver works on the even-site Schur complement
+//   S = A_ee - D_eo A_oo^-1 D_oe     (A = self blocks of D_c)
+// with right-hand side b_e - D_eo A_oo^-1 b_o, stops when the Schur residual
+// reaches tol * ||rhs|| (the method's 5e-2), and back-substitutes
+// x_o = A_oo^-1 (b_o - D_oe x_e).
+//
+// One persistent cooperative kernel solves all right-hand sides, NR of them
+// in lockstep (one Krylov space, Hessenberg matrix and stopping test each),
+// so that the grid-wide barriers of an iteration are shared.  Every CTA owns
+// `per` even and `per` odd coarse sites; its slice of the Krylov basis, of
+// x_e and of the right-hand side stays in shared memory.  Only the vectors a
+// neighbour reads (w and the odd-site temporaries) go through global memory,
+// loaded with ld.cg.  Arnoldi uses classical Gram-Schmidt with one
+// re-orthogonalisation pass; reductions are deterministic (fixed trees).
+// A grid barrier per phase: odd hop, first and second Gram-Schmidt pass,
+// norm -> four per iteration.  Every barrier wait is bounded; on time-out
+// the kernel records DDAMG_ETIMEOUT (6) and returns.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ddamg {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int NW = TPB / 32;
+constexpr int MAXM = 64;
+constexpr int NRMAX = 8;
+constexpr long long SPIN_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ cpx<float> ldc(const cpx<float>* p) {
+  float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk(t.x, t.y);
+}
+__device__ __forceinline__ cpx<double> ldc(const cpx<double>* p) {
+  double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk(t.x, t.y);
+}
+
+template <class T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ bool grid_barrier(unsigned* bar, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    unsigned my = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == my) {
+        if (++spins > SPIN_LIMIT) { atomicExch(status, 6); ok = 0; break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)status != 0) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// shared-memory plan, identical on host and device
+struct Plan {
+  size_t V, x, rl, w, sv, mvp, tmp;                                    // cpx offsets (bytes)
+  size_t hc, h2, Rf, cs, sn, gv, yv, beta, bnorm, hn, scale;           // double offsets
+  size_t act, kd, tot, conv;                                            // int offsets
+  size_t bytes;        // total shared memory
+  size_t local_bytes;  // V + x + rl + w (moved to global when too large)
+};
+
+__host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+
+__host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, bool local_in_smem) {
+  Plan p;
+  const size_t c = 2 * (size_t)rs;
+  size_t o = 0;
+  size_t lb = 0;
+  auto put = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return r; };
+  if (local_in_smem) {
+    p.V = put((size_t)(m + 1) * NR * L * c);
+    p.x = put((size_t)NR * L * c);
+    p.rl = put((size_t)NR * L * c);
+    p.w = put((size_t)NR * L * c);
+    lb = o;
+  } else {
+    size_t g = 0;
+    auto putg = [&](size_t bytes) { size_t r = g; g = al16(g + bytes); return r; };
+    p.V = putg((size_t)(m + 1) * NR * L * c);
+    p.x = putg((size_t)NR * L * c);
+    p.rl = putg((size_t)NR * L * c);
+    p.w = putg((size_t)NR * L * c);
+    lb = g;
+  }
+  p.sv = put((size_t)NR * 9 * n2 * c);
+  p.mvp = put((size_t)9 * NR * n2 * c);
+  p.tmp = put((size_t)NR * n2 * c);
+  p.hc = put((size_t)NR * 2 * (m + 1) * 8);
+  p.h2 = put((size_t)NR * 2 * (m + 1) * 8);
+  p.Rf = put((size_t)NR * m * (m + 1) * 8);
+  p.cs = put((size_t)NR * m * 8);
+  p.sn = put((size_t)NR * 2 * m * 8);
+  p.gv = put((size_t)NR * 2 * (m + 1) * 8);
+  p.yv = put((size_t)NR * 2 * m * 8);
+  p.beta = put((size_t)NR * 8);
+  p.bnorm = put((size_t)NR * 8);
+  p.hn = put((size_t)NR * 8);
+  p.scale = put((size_t)NR * 8);
+  p.act = put((size_t)NR * 4);
+  p.kd = put((size_t)NR * 4);
+  p.tot = put((size_t)NR * 4);
+  p.conv = put((size_t)NR * 4);
+  p.bytes = o;
+  p.local_bytes = lb;
+  return p;
+}
+
+template <class R>
+struct CGA {
+  Geom g;
+  const cpx<R>* Dc;
+  const cpx<R>* Ainv;
+  int n2;
+  double tol;
+  int m;
+  int max_iter;
+  const cpx<R>* b;
+  cpx<R>* x;
+  int nrhs;
+  int NR;
+  int NE;
+  int per;
+  int local_in_smem;
+  cpx<R>* wg;        // [NR][NE][n2]
+  cpx<R>* to;        // [NR][NE][n2]
+  cpx<R>* xg;        // [NR][NE][n2]
+  unsigned char* lglob;   // per-CTA local arrays when they do not fit in smem
+  size_t lstride;         // bytes per CTA in lglob
+  double* part;      // [(MAXM + 1) * NR][G][2]
+  unsigned* bar;
+  int* iters;
+  int* iters_acc;
+  int* status;
+};
+
+// Multi-right-hand-side block product on one coarse site, whole CTA:
+//   out[r][row] = sum_{d in [d0, d1)} sum_c M_d[row][c] sv[r][d][c]
+// Blocks are column-major, so a thread streams RPU rows down the columns
+// (16-byte loads, neighbouring threads on neighbouring rows) and applies each
+// loaded entry to all NR vectors.  The column range is split into CC chunks
+// when there are few directions.  Partials land in mvp[unit-group][r][row] and
+// are summed in a fixed order.
+template <class R, int NR>
+__device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const cpx<R>* sv, int d0, int d1,
+                                            int n2, cpx<R>* mvp, cpx<R>* out, int out_stride) {
+  using T = typename U16<R>::T;
+  constexpr int RPU = 16 / (2 * sizeof(R));
+  const int NP = n2 / RPU;
+  const int ND = d1 - d0;
+  const int CC = ND >= 8 ? 1 : 8 / ND;
+  const int CW = (n2 + CC - 1) / CC;
+  const int units = ND * CC * NP;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int grp = u / NP, j = u - grp * NP;
+    const int dd = grp / CC, cc = grp - dd * CC, d = d0 + dd;
+    const int c0 = cc * CW, c1 = min(n2, c0 + CW);
+    const T* col = reinterpret_cast<const T*>(M + (size_t)d * n2 * n2) + j;
+    cpx<R> acc[NR][RPU];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int q = 0; q < RPU; ++q) acc[r][q] = mk(R(0), R(0));
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) {
+      T mm = __ldg(col + (size_t)c * NP);
+      cpx<R> e0, e1;
+      if constexpr (RPU == 2) { e0 = mk((R)mm.x, (R)mm.y); e1 = mk((R)mm.z, (R)mm.w); }
+      else { e0 = mk((R)mm.x, (R)mm.y); e1 = e0; }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        cpx<R> v = sv[(r * 9 + d) * n2 + c];
+        fma(acc[r][0], e0, v);
+        if constexpr (RPU == 2) fma(acc[r][1], e1, v);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int q = 0; q < RPU; ++q) mvp[((size_t)grp * NR + r) * n2 + RPU * j + q] = acc[r][q];
+  }
+  __syncthreads();
+  const int ngrp = ND * CC;
+  for (int idx = threadIdx.x; idx < NR * n2; idx += blockDim.x) {
+    const int r = idx / n2, row = idx - r * n2;
+    cpx<R> s = mk(R(0), R(0));
+    for (int gq = 0; gq < ngrp; ++gq) s = s + mvp[((size_t)gq * NR + r) * n2 + row];
+    out[(size_t)r * out_stride + row] = s;
+  }
+  __syncthreads();
+}
+
+template <class R, int NR>
+__global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  // small dense state (Hessenberg column, Givens, least squares, norms) and
+  // cross-CTA sums in the working precision: FP64 arithmetic is scarce on
+  // GB300, FP32 is ample for a solve to a relative residual of 5e-2
+  using A = R;
+  const int n2 = a.n2, m = a.m, NE = a.NE;
+  const int L = a.per * n2;
+  const Plan P = make_plan(NR, L, n2, m, sizeof(R), a.local_in_smem != 0);
+  unsigned char* lbase = a.local_in_smem ? sm : a.lglob + (size_t)blockIdx.x * a.lstride;
+  cpx<R>* V = reinterpret_cast<cpx<R>*>(lbase + P.V);     // [m+1][NR][L]
+  cpx<R>* xl = reinterpret_cast<cpx<R>*>(lbase + P.x);    // [NR][L]
+  cpx<R>* rl = reinterpret_cast<cpx<R>*>(lbase + P.rl);   // [NR][L]
+  cpx<R>* wl = reinterpret_cast<cpx<R>*>(lbase + P.w);    // [NR][L]
+  cpx<R>* sv = reinterpret_cast<cpx<R>*>(sm + P.sv);      // [NR][9][n2]
+  cpx<R>* mvp = reinterpret_cast<cpx<R>*>(sm + P.mvp);    // [9][NR][n2]
+  cpx<R>* tmp = reinterpret_cast<cpx<R>*>(sm + P.tmp);    // [NR][n2]
+  A* hc = reinterpret_cast<A*>(sm + P.hc);      // [NR][2(m+1)]
+  A* h2 = reinterpret_cast<A*>(sm + P.h2);      // [NR][2(m+1)]
+  A* Rf = reinterpret_cast<A*>(sm + P.Rf);      // [NR][m(m+1)] packed columns
+  A* cs = reinterpret_cast<A*>(sm + P.cs);      // [NR][m]
+  A* sn = reinterpret_cast<A*>(sm + P.sn);      // [NR][2m]
+  A* gv = reinterpret_cast<A*>(sm + P.gv);      // [NR][2(m+1)]
+  A* yv = reinterpret_cast<A*>(sm + P.yv);      // [NR][2m]
+  A* beta = reinterpret_cast<A*>(sm + P.beta);
+  A* bnorm = reinterpret_cast<A*>(sm + P.bnorm);
+  A* hnv = reinterpret_cast<A*>(sm + P.hn);
+  A* scl = reinterpret_cast<A*>(sm + P.scale);
+  int* act = reinterpret_cast<int*>(sm + P.act);          // active in this cycle
+  int* kd = reinterpret_cast<int*>(sm + P.kd);            // basis size of this cycle
+  int* tot = reinterpret_cast<int*>(sm + P.tot);          // iterations so far
+  int* conv = reinterpret_cast<int*>(sm + P.conv);        // converged (or gave up)
+  __shared__ int any_s;
+
+  const int G = gridDim.x;
+  const int lo = min(NE, (int)blockIdx.x * a.per);
+  const int hi = min(NE, lo + a.per);
+  const int nown = hi - lo;
+  const int Lo = nown * n2;          // owned local elements
+  const size_t vstr = (size_t)NE * n2;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tx = threadIdx.x;
+  const int TRI = m * (m + 1) / 2;
+
+  auto Vk = [&](int k, int r) { return V + ((size_t)k * NR + r) * L; };
+
+  // stage neighbours of odd site X from global vectors src[r] (scaled), d >= 1
+  auto stage_odd = [&](int X, const cpx<R>* src) {
+    for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
+      const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
+      cpx<R> v = mk(R(0), R(0));
+      if (d > 0) v = (R)scl[r] * ldc(src + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
+      sv[idx] = v;
+    }
+    __syncthreads();
+  };
+  // odd phase: to[r][ko] = A_oo^-1 sum_{d>=1} Dc[X][d] src[r][nbr]
+  auto phase_odd = [&](const cpx<R>* src) {
+    for (int ko = lo; ko < hi; ++ko) {
+      const int X = a.g.codd[ko];
+      stage_odd(X, src);
+      mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, 1, 9, n2, mvp, tmp, n2);
+      for (int idx = tx; idx < NR * n2; idx += TPB) {
+        const int r = idx / n2, c = idx - r * n2;
+        sv[(r * 9) * n2 + c] = tmp[idx];
+      }
+      __syncthreads();
+      mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, a.to + (size_t)ko * n2, (int)vstr);
+    }
+  };
+  // even phase: out[r][kk] = (self ? A_ee v : 0) - sum_{d>=1} Dc[X][d] to[r][nbr] (+ bsrc)
+  auto phase_even = [&](const cpx<R>* vself, bool self, cpx<R>* out, const cpx<R>* bsrc) {
+    for (int ke = lo; ke < hi; ++ke) {
+      const int X = a.g.ceven[ke], kk = ke - lo;
+      for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
+        const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
+        cpx<R> v;
+        if (d == 0) v = self ? vself[(size_t)r * L + kk * n2 + c] : mk(R(0), R(0));
+        else v = -ldc(a.to + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
+        sv[idx] = v;
+      }
+      __syncthreads();
+      mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, self ? 0 : 1, 9, n2, mvp, out + kk * n2, L);
+      if (bsrc) {
+        for (int idx = tx; idx < NR * n2; idx += TPB) {
+          const int r = idx / n2, c = idx - r * n2;
+          out[(size_t)r * L + kk * n2 + c] = out[(size_t)r * L + kk * n2 + c] + bsrc[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c];
+        }
+        __syncthreads();
+      }
+    }
+  };
+  // partial dots (r, j < kcount) of V_j[r] with wl[r]; slot = j * NR + r
+  auto partial = [&](int kcount, bool norm) {
+    const int pairs = norm ? NR : kcount * NR;
+    for (int pr = wid; pr < pairs; pr += NW) {
+      const int j = norm ? 0 : pr / NR, r = norm ? pr : pr - (pr / NR) * NR;
+      R re = 0, im = 0;
+      if (act[r]) {
+        const cpx<R>* vj = norm ? wl + (size_t)r * L : Vk(j, r);
+        const cpx<R>* ww = wl + (size_t)r * L;
+        for (int e = lane; e < Lo; e += 32) {
+          cpx<R> p = vj[e], q = ww[e];
+          re += p.re * q.re + p.im * q.im;
+          im += p.re * q.im - p.im * q.re;
+        }
+      }
+      re = wsum(re);
+      im = wsum(im);
+      if (lane == 0) {
+        a.part[((size_t)pr * G + blockIdx.x) * 2] = (double)re;
+        a.part[((size_t)pr * G + blockIdx.x) * 2 + 1] = (double)im;
+      }
+    }
+  };
+  // gather slot sums into dst[r][2 j] (norm: dst[r])
+  auto gather = [&](int kcount, bool norm, A* dst, int dstride) {
+    const int pairs = norm ? NR : kcount * NR;
+    for (int pr = wid; pr < pairs; pr += NW) {
+      A re = 0, im = 0;
+      for (int c = lane; c < G; c += 32) {
+        re += (A)__ldcg(a.part + ((size_t)pr * G + c) * 2);
+        im += (A)__ldcg(a.part + ((size_t)pr * G + c) * 2 + 1);
+      }
+      re = wsum(re);
+      im = wsum(im);
+      if (lane == 0) {
+        if (norm) {
+          dst[(size_t)pr * dstride] = re;     // squared norm (real)
+        } else {
+          const int j = pr / NR, r = pr - j * NR;
+          dst[(size_t)r * dstride + 2 * j] = re;
+          dst[(size_t)r * dstride + 2 * j + 1] = im;
+        }
+      }
+    }
+    __syncthreads();
+  };
+
+  for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
+    const int nr = min(NR, a.nrhs - r0);
+    const cpx<R>* bb = a.b + (size_t)r0 * a.g.nb * n2;
+    cpx<R>* xx = a.x + (size_t)r0 * a.g.nb * n2;
+    if (tx < NR) {
+      act[tx] = tx < nr ? 1 : 0;
+      conv[tx] = tx < nr ? 0 : 1;
+      tot[tx] = 0;
+      scl[tx] = A(1);
+    }
+    __syncthreads();
+    // to = A_oo^-1 b_o
+    for (int ko = lo; ko < hi; ++ko) {
+      const int X = a.g.codd[ko];
+      for (int idx = tx; idx < NR * n2; idx += TPB) {
+        const int r = idx / n2, c = idx - r * n2;
+        sv[(r * 9) * n2 + c] = r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0));
+      }
+      __syncthreads();
+      mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, a.to + (size_t)ko * n2, (int)vstr);
+    }
+    if (!grid_barrier(a.bar, a.status)) return;
+    // rhs_e = b_e - D_eo to ; x_e = 0 ; w = rhs_e
+    phase_even(nullptr, false, rl, bb);
+    for (int idx = tx; idx < NR * L; idx += TPB) {
+      const int r = idx / L, e = idx - r * L;
+      cpx<R> v = (r < nr && e < Lo) ? rl[idx] : mk(R(0), R(0));
+      rl[idx] = v;
+      wl[idx] = v;
+      xl[idx] = mk(R(0), R(0));
+    }
+    __syncthreads();
+    partial(1, true);
+    if (!grid_barrier(a.bar, a.status)) return;
+    gather(1, true, bnorm, 1);
+    if (tx < NR) {
+      bnorm[tx] = sqrt(bnorm[tx]);
+      beta[tx] = bnorm[tx];
+      if (!(bnorm[tx] > A(0))) { conv[tx] = 1; act[tx] = 0; }
+    }
+    __syncthreads();
+
+    while (true) {
+      // start a cycle for every right-hand side that is not done
+      if (tx < NR) {
+        const bool go = !conv[tx] && tot[tx] < a.max_iter;
+        act[tx] = go ? 1 : 0;
+        if (!go) conv[tx] = 1;
+        kd[tx] = 0;
+        gv[tx * 2 * (m + 1)] = beta[tx];
+        gv[tx * 2 * (m + 1) + 1] = A(0);
+        scl[tx] = beta[tx] > A(0) ? A(1) / beta[tx] : A(0);
+      }
+      __syncthreads();
+      if (tx == 0) {
+        int any = 0;
+        for (int r = 0; r < NR; ++r) any |= act[r];
+        any_s = any;
+      }
+      __syncthreads();
+      if (!any_s) break;
+      // V_0 = w / beta (local) and the global copy of w for the neighbours
+      for (int idx = tx; idx < NR * L; idx += TPB) {
+        const int r = idx / L, e = idx - r * L;
+        cpx<R> v = wl[idx];
+        Vk(0, r)[e] = (R)scl[r] * v;
+        if (e < Lo) a.wg[r * vstr + (size_t)lo * n2 + e] = v;
+      }
+      if (!grid_barrier(a.bar, a.status)) return;
+      for (int k = 0; k < m; ++k) {
+        // w = S V_k: odd phase from the neighbours' unnormalised w (scale 1/h)
+        phase_odd(a.wg);
+        if (!grid_barrier(a.bar, a.status)) return;
+        phase_even(V + (size_t)k * NR * L, true, wl, nullptr);
+        for (int pass = 0; pass < 2; ++pass) {
+          partial(k + 1, false);
+          if (!grid_barrier(a.bar, a.status)) return;
+          A* hh = pass == 0 ? hc : h2;
+          gather(k + 1, false, hh, 2 * (m + 1));
+          for (int idx = tx; idx < NR * Lo; idx += TPB) {
+            const int r = idx / Lo, e = idx - r * Lo;
+            if (!act[r]) continue;
+            cpx<R> w0 = wl[(size_t)r * L + e];
+            const A* hr = hh + (size_t)r * 2 * (m + 1);
+            for (int j = 0; j <= k; ++j) {
+              cpx<R> v = Vk(j, r)[e];
+              cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
+              w0 = w0 - c * v;
+            }
+            wl[(size_t)r * L + e] = w0;
+            if (pass == 1) a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
+          }
+          if (pass == 1 && tx < NR)
+            for (int j = 0; j <= k; ++j) {
+              hc[(size_t)tx * 2 * (m + 1) + 2 * j] += h2[(size_t)tx * 2 * (m + 1) + 2 * j];
+              hc[(size_t)tx * 2 * (m + 1) + 2 * j + 1] += h2[(size_t)tx * 2 * (m + 1) + 2 * j + 1];
+            }
+          __syncthreads();
+        }
+        // ||w||: this barrier also publishes the neighbours' w for the next odd phase
+        partial(1, true);
+        if (!grid_barrier(a.bar, a.status)) return;
+        gather(1, true, hnv, 1);
+        // Givens per right-hand side (thread r), V_{k+1} = w / h
+        if (tx < NR && act[tx]) {
+          const int r = tx;
+          const A hn = sqrt(hnv[r]);
+          A* col = hc + (size_t)r * 2 * (m + 1);
+          col[2 * (k + 1)] = hn;
+          col[2 * (k + 1) + 1] = A(0);
+          A* csr = cs + (size_t)r * m;
+          A* snr = sn + (size_t)r * 2 * m;
+          for (int j = 0; j < k; ++j) {
+            A c = csr[j], sr = snr[2 * j], si = snr[2 * j + 1];
+            A ar = col[2 * j], ai = col[2 * j + 1], br = col[2 * j + 2], bi = col[2 * j + 3];
+            A tr = c * ar + (sr * br - si * bi), ti = c * ai + (sr * bi + si * br);
+            A ur = -(sr * ar + si * ai) + c * br, ui = -(sr * ai - si * ar) + c * bi;
+            col[2 * j] = tr; col[2 * j + 1] = ti; col[2 * j + 2] = ur; col[2 * j + 3] = ui;
+          }
+          A ar = col[2 * k], ai = col[2 * k + 1], br = col[2 * k + 2], bi = col[2 * k + 3];
+          A a1 = sqrt(ar * ar + ai * ai), a2 = sqrt(br * br + bi * bi);
+          A c, sr, si, rr, ri;
+          if (a2 == A(0)) { c = A(1); sr = A(0); si = A(0); rr = ar; ri = ai; }
+          else if (a1 == A(0)) { c = A(0); sr = br / a2; si = -bi / a2; rr = a2; ri = A(0); }
+          else {
+            A rho = hypot(a1, a2);
+            A pr = ar / a1, pi = ai / a1;
+            c = a1 / rho;
+            sr = (pr * br + pi * bi) / rho;
+            si = (pi * br - pr * bi) / rho;
+            rr = pr * rho; ri = pi * rho;
+          }
+          csr[k] = c; snr[2 * k] = sr; snr[2 * k + 1] = si;
+          col[2 * k] = rr; col[2 * k + 1] = ri;
+          A* Rr = Rf + (size_t)r * 2 * TRI;
+          const int base = k * (k + 1) / 2;          // packed column k: entries 0..k
+          for (int j = 0; j <= k; ++j) { Rr[2 * (base + j)] = col[2 * j]; Rr[2 * (base + j) + 1] = col[2 * j + 1]; }
+          A* g = gv + (size_t)r * 2 * (m + 1);
+          A gr = g[2 * k], gi = g[2 * k + 1];
+          g[2 * (k + 1)] = -(sr * gr + si * gi);
+          g[2 * (k + 1) + 1] = -(sr * gi - si * gr);
+          g[2 * k] = c * gr;
+          g[2 * k + 1] = c * gi;
+          A res = sqrt(g[2 * (k + 1)] * g[2 * (k + 1)] + g[2 * (k + 1) + 1] * g[2 * (k + 1) + 1]);
+          kd[r] = k + 1;
+          tot[r] += 1;
+          scl[r] = hn > A(0) ? A(1) / hn : A(0);
+          hnv[r] = hn;
+          if (res <= (A)a.tol * bnorm[r] || hn == A(0) || tot[r] >= a.max_iter) act[r] = 0;
+        }
+        __syncthreads();
+        for (int idx = tx; idx < NR * Lo; idx += TPB) {
+          const int r = idx / Lo, e = idx - r * Lo;
+          Vk(k + 1, r)[e] = (R)scl[r] * wl[(size_t)r * L + e];
+        }
+        if (tx == 0) {
+          int any = 0;
+          for (int r = 0; r < NR; ++r) any |= act[r];
+          any_s = any;
+        }
+        __syncthreads();
+        if (!any_s) break;
+      }
+      // y = R^-1 g ; x_e += V y   (every right-hand side of this cycle)
+      if (tx < NR && !conv[tx]) {
+        const int r = tx, kk = kd[r];
+        const A* Rr = Rf + (size_t)r * 2 * TRI;
+        const A* g = gv + (size_t)r * 2 * (m + 1);
+        A* y = yv + (size_t)r * 2 * m;
+        for (int i = kk - 1; i >= 0; --i) {
+          A accr = g[2 * i], acci = g[2 * i + 1];
+          for (int j = i + 1; j < kk; ++j) {
+            const int pj = j * (j + 1) / 2 + i;
+            A rr = Rr[2 * pj], ri = Rr[2 * pj + 1];
+            accr -= rr * y[2 * j] - ri * y[2 * j + 1];
+            acci -= rr * y[2 * j + 1] + ri * y[2 * j];
+          }
+          const int pd = i * (i + 1) / 2 + i;
+          A dr = Rr[2 * pd], di = Rr[2 * pd + 1];
+          A dn = dr * dr + di * di;
+          y[2 * i] = (accr * dr + acci * di) / dn;
+          y[2 * i + 1] = (acci * dr - accr * di) / dn;
+        }
+      }
+      __syncthreads();
+      for (int idx = tx; idx < NR * Lo; idx += TPB) {
+        const int r = idx / Lo, e = idx - r * Lo;
+        if (conv[r]) continue;
+        const A* y = yv + (size_t)r * 2 * m;
+        cpx<R> s = xl[(size_t)r * L + e];
+        for (int j = 0; j < kd[r]; ++j) s = s + mk((R)y[2 * j], (R)y[2 * j + 1]) * Vk(j, r)[e];
+        xl[(size_t)r * L + e] = s;
+        a.xg[r * vstr + (size_t)lo * n2 + e] = s;
+      }
+      if (tx < NR) scl[tx] = A(1);
+      if (!grid_barrier(a.bar, a.status)) return;
+      // true residual w = rhs_e - S x_e
+      phase_odd(a.xg);
+      if (!grid_barrier(a.bar, a.status)) return;
+      phase_even(xl, true, wl, nullptr);
+      for (int idx = tx; idx < NR * Lo; idx += TPB) {
+        const int r = idx / Lo, e = idx - r * Lo;
+        wl[(size_t)r * L + e] = rl[(size_t)r * L + e] - wl[(size_t)r * L + e];
+      }
+      if (tx < NR) act[tx] = conv[tx] ? 0 : 1;
+      __syncthreads();
+      partial(1, true);
+      if (!grid_barrier(a.bar, a.status)) return;
+      gather(1, true, beta, 1);
+      if (tx < NR && !conv[tx]) {
+        beta[tx] = sqrt(beta[tx]);
+        if (beta[tx] <= (A)a.tol * bnorm[tx]) conv[tx] = 1;
+      }
+      __syncthreads();
+    }
+    // x_o = A_oo^-1 (b_o - D_oe x_e); write x
+    for (int idx = tx; idx < NR * Lo; idx += TPB) {
+      const int r = idx / Lo, e = idx - r * Lo;
+      a.xg[r * vstr + (size_t)lo * n2 + e] = xl[(size_t)r * L + e];
+    }
+    if (tx < NR) scl[tx] = -A(1);
+    if (!grid_barrier(a.bar, a.status)) return;
+    for (int ko = lo; ko < hi; ++ko) {
+      const int X = a.g.codd[ko];
+      stage_odd(X, a.xg);
+      mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, 1, 9, n2, mvp, tmp, n2);
+      for (int idx = tx; idx < NR * n2; idx += TPB) {
+        const int r = idx / n2, c = idx - r * n2;
+        sv[(r * 9) * n2 + c] = tmp[idx] + (r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0)));
+      }
+      __syncthreads();
+      mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, tmp, n2);
+      for (int idx = tx; idx < nr * n2; idx += TPB) {
+        const int r = idx / n2, c = idx - r * n2;
+        xx[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] = tmp[idx];
+      }
+    }
+    for (int idx = tx; idx < nr * Lo; idx += TPB) {
+      const int r = idx / Lo, e = idx - r * Lo;
+      const int ke = lo + e / n2, c = e - (e / n2) * n2;
+      xx[(size_t)r * a.g.nb * n2 + (size_t)a.g.ceven[ke] * n2 + c] = xl[(size_t)r * L + e];
+    }
+    if (blockIdx.x == 0 && tx < nr) {
+      if (a.iters) a.iters[r0 + tx] = tot[tx];
+      if (a.iters_acc) atomicAdd(a.iters_acc, tot[tx]);
+    }
+    if (!grid_barrier(a.bar, a.status)) return;
+  }
+}
+
+constexpr size_t SMEM_BUDGET = 200 * 1024;
+
+template <class R>
+const void* kernel_for(int NR) {
+  switch (NR) {
+    case 1: return (const void*)k_cgmres<R, 1>;
+    case 2: return (const void*)k_cgmres<R, 2>;
+    case 4: return (const void*)k_cgmres<R, 4>;
+    default: return (const void*)k_cgmres<R, 8>;
+  }
+}
+
+struct Choice {
+  int NR, G, per;
+  bool local;
+  Plan plan;
+};
+
+template <class R>
+Choice choose(const Geom& g, int n2, int m, int nrhs) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int NE = g.nb / 2;
+  Choice best{};
+  int first = nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+  for (int NR = first; NR >= 1; NR /= 2) {
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool local = pass == 0;
+      // grid: as many CTAs as fit (two per SM at most), each owning >= 1 site
+      for (int per = 1; per <= NE; ++per) {
+        int G = (NE + per - 1) / per;
+        Plan p = make_plan(NR, per * n2, n2, m, sizeof(R), local);
+        if (p.bytes > SMEM_BUDGET) break;
+        int occ = 0;
+        const void* fn = kernel_for<R>(NR);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, p.bytes);
+        if (occ < 1) break;
+        if (G <= occ * sms) return Choice{NR, G, per, local, p};
+      }
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size) {
+  // vectors wg, to, xg for NRMAX right-hand sides, partial sums, barrier,
+  // and room for per-CTA local arrays when they do not fit in shared memory
+  const size_t NE = g.nb / 2, n2 = 2 * n;
+  const size_t vec = NRMAX * NE * n2 * 2 * (size_t)real_size;
+  size_t bytes = al16(3 * vec);
+  bytes += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  bytes += 256;
+  bytes += al16((size_t)(restart + 4) * NRMAX * 2 * NE * n2 * 2 * real_size + 64 * NE);
+  return bytes;
+}
+
+template <class R>
+cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R* x, int nrhs, void* work,
+                         int* iters, int* iters_acc, int* status, cudaStream_t st) {
+  if (ca.restart > MAXM || ca.restart < 1 || nrhs < 1) return cudaErrorInvalidValue;
+  const int n2 = 2 * ca.n;
+  Choice ch = choose<R>(g, n2, ca.restart, nrhs);
+  if (ch.NR == 0) return cudaErrorInvalidConfiguration;
+  CGA<R> a;
+  a.g = g;
+  a.Dc = reinterpret_cast<const cpx<R>*>(ca.Dc);
+  a.Ainv = reinterpret_cast<const cpx<R>*>(ca.Ainv);
+  a.n2 = n2;
+  a.tol = ca.tol;
+  a.m = ca.restart;
+  a.max_iter = ca.max_iter;
+  a.b = reinterpret_cast<const cpx<R>*>(b);
+  a.x = reinterpret_cast<cpx<R>*>(x);
+  a.nrhs = nrhs;
+  a.NR = ch.NR;
+  a.NE = g.nb / 2;
+  a.per = ch.per;
+  a.local_in_smem = ch.local ? 1 : 0;
+  const size_t NE = a.NE;
+  const size_t vec = (size_t)NRMAX * NE * n2;
+  unsigned char* w8 = reinterpret_cast<unsigned char*>(work);
+  a.wg = reinterpret_cast<cpx<R>*>(w8);
+  a.to = a.wg + vec;
+  a.xg = a.to + vec;
+  size_t off = al16(3 * vec * sizeof(cpx<R>));
+  a.part = reinterpret_cast<double*>(w8 + off);
+  off += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  a.bar = reinterpret_cast<unsigned*>(w8 + off);
+  off += 256;
+  a.lglob = w8 + off;
+  a.lstride = al16(ch.plan.local_bytes);
+  a.iters = iters;
+  a.iters_acc = iters_acc;
+  a.status = status;
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const void* fn = kernel_for<R>(ch.NR);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ch.plan.bytes);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel(fn, dim3(ch.G), dim3(TPB), args, ch.plan.bytes, st);
+  ++g_launches;
+  return e;
+}
+
+template cudaError_t coarse_gmres<float>(const Geom&, const CoarseSolveArgs&, const float*, float*, int, void*,
+                                         int*, int*, int*, cudaStream_t);
+template cudaError_t coarse_gmres<double>(const Geom&, const CoarseSolveArgs&, const double*, double*, int,
+                                          void*, int*, int*, int*, cudaStream_t);
+
+}  // namespace ddamg

@@ -21,21 +21,25 @@ namespace ddamg {
 
 namespace {
 
-template <class R>
-struct Sh {
-  using T = typename U16<R>::T;
-};
+// Four threads per site: thread sub = 0..3 of a site applies the two hops
+// of direction mu = sub and owns the three colour components of spin sub of
+// every site vector (res, e, p, ...).  Hop partial sums of the four threads
+// are combined by a reduce-scatter of warp shuffles.
 
-// link mu of local site q from the staged block links ([unit][Vb] in smem)
+constexpr int LPAD = 2;   // padding of the staged link rows (bank groups)
+
 template <class R>
-__device__ __forceinline__ void smem_link(const typename U16<R>::T* sl, int Vb, int q, int mu,
-                                          Link<R>& U) {
+using T16 = typename U16<R>::T;
+
+// link mu of local site q from the staged block links (rows of Vb + LPAD units)
+template <class R>
+__device__ __forceinline__ void smem_link(const T16<R>* sl, int Vbp, int q, int mu, Link<R>& U) {
   using LY = Layout<R, GAUGE_NR>;
   constexpr int NUL = LINK_NR / LY::PER;
   R v[LINK_NR];
 #pragma unroll
   for (int u = 0; u < NUL; ++u) {
-    typename U16<R>::T t = sl[(mu * NUL + u) * Vb + q];
+    T16<R> t = sl[(mu * NUL + u) * Vbp + q];
     if constexpr (LY::PER == 4) {
       v[4 * u] = t.x; v[4 * u + 1] = t.y; v[4 * u + 2] = t.z; v[4 * u + 3] = t.w;
     } else {
@@ -47,56 +51,195 @@ __device__ __forceinline__ void smem_link(const typename U16<R>::T* sl, int Vb, 
   complete_link(U);
 }
 
-// spinor of half-index h from a shared SoA buffer buf[12][Vh]
 template <class R>
 __device__ __forceinline__ void smem_spinor(const cpx<R>* buf, int Vh, int h, Spinor<R>& s) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) s.c[k] = buf[k * Vh + h];
 }
+
+// one complex component k of site d in a global spinor field
 template <class R>
-__device__ __forceinline__ void smem_store(cpx<R>* buf, int Vh, int h, const Spinor<R>& s) {
+__device__ __forceinline__ size_t comp_off(int d, int Vb, int k) {
+  using LY = Layout<R, SPINOR_NR>;
+  constexpr int CPU = LY::PER / 2;   // complex numbers per 16-byte unit
+  int B = d / Vb, q = d - B * Vb;
+  return (((size_t)B * LY::NU + k / CPU) * Vb + q) * LY::PER + (k % CPU) * 2;
+}
+__device__ __forceinline__ cpx<float> ld_comp(const float* f, size_t off) {
+  float2 t = __ldcg(reinterpret_cast<const float2*>(f + off));
+  return mk(t.x, t.y);
+}
+__device__ __forceinline__ cpx<double> ld_comp(const double* f, size_t off) {
+  double2 t = __ldcg(reinterpret_cast<const double2*>(f + off));
+  return mk(t.x, t.y);
+}
+__device__ __forceinline__ void st_comp(float* f, size_t off, cpx<float> v) {
+  *reinterpret_cast<float2*>(f + off) = make_float2(v.re, v.im);
+}
+__device__ __forceinline__ void st_comp(double* f, size_t off, cpx<double> v) {
+  *reinterpret_cast<double2*>(f + off) = make_double2(v.re, v.im);
+}
+
+template <class R>
+__device__ __forceinline__ cpx<R> shfl_x(cpx<R> v, int m) {
+  return mk(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
+
+// reduce-scatter of a 12-component partial sum over the 4 threads of a site:
+// thread sub receives the full sum of components 3 sub .. 3 sub + 2
+template <class R>
+__device__ __forceinline__ void reduce_scatter(const Spinor<R>& acc, int sub, cpx<R> out[3]) {
+  const bool hi = sub >= 2;      // chirality block of this thread
+  cpx<R> keep[6];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) buf[k * Vh + h] = s.c[k];
-}
-
-// block-local hop of one direction at local site q; the neighbour values
-// (other parity) come from buf
-template <int MU, class R>
-__device__ __forceinline__ void hop_block_dir(const int16_t* __restrict__ bnbr,
-                                              const typename U16<R>::T* sl, const cpx<R>* buf,
-                                              int Vb, int Vh, int q, Spinor<R>& acc) {
-  cpx<R> h[2][3], y[2][3];
-  Spinor<R> nb;
-  int qf = __ldg(bnbr + (2 * MU) * Vb + q);
-  if (qf >= 0) {
-    smem_spinor<R>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
-    project<MU, -1>(nb, h);
-    Link<R> U;
-    smem_link<R>(sl, Vb, q, MU, U);
-    su3_mul(U, h, y);
-    accumulate<MU, -1>(acc, y, R(1));
+  for (int i = 0; i < 6; ++i) {
+    cpx<R> send = hi ? acc.c[i] : acc.c[6 + i];
+    keep[i] = (hi ? acc.c[6 + i] : acc.c[i]) + shfl_x(send, 2);
   }
-  int qb = __ldg(bnbr + (2 * MU + 1) * Vb + q);
-  if (qb >= 0) {
-    smem_spinor<R>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
-    project<MU, +1>(nb, h);
-    Link<R> U;
-    smem_link<R>(sl, Vb, qb, MU, U);
-    su3_mul_dag(U, h, y);
-    accumulate<MU, +1>(acc, y, R(1));
+  const bool odd = sub & 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cpx<R> send = odd ? keep[i] : keep[3 + i];
+    out[i] = (odd ? keep[3 + i] : keep[i]) + shfl_x(send, 1);
   }
 }
 
+// the 6 components of this thread's chirality block: own 3 + partner's 3
 template <class R>
-__device__ __forceinline__ void hop_block(const int16_t* bnbr, const typename U16<R>::T* sl,
-                                          const cpx<R>* buf, int Vb, int Vh, int q,
-                                          Spinor<R>& acc) {
+__device__ __forceinline__ void chiral6(const cpx<R> own[3], int sub, cpx<R> v6[6]) {
+  const bool odd = sub & 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cpx<R> other = shfl_x(own[i], 1);
+    v6[i] = odd ? other : own[i];
+    v6[3 + i] = odd ? own[i] : other;
+  }
+}
+
+// own 3 rows of the packed Hermitian block (chirality sub / 2) times v6
+template <class R>
+__device__ __forceinline__ void clover_rows(const R* __restrict__ clov, int d, int Vb, int sub,
+                                            const cpx<R> v6[6], cpx<R> y[3]) {
+  using LY = Layout<R, CLOVER_NR>;
+  constexpr int NUB = 36 / LY::PER;
+  R P[36];
+  load_units<R, CLOVER_NR>(clov, d, Vb, (sub >> 1) * NUB, NUB, P);
+  cpx<R> y6[6];
+  herm6<R>(P, v6, y6);
+  const bool odd = sub & 1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = odd ? y6[3 + i] : y6[i];
+}
+
+// Runtime direction: with g_mu = [[0, B], [B^H, 0]] every B_mu has one
+// non-zero per row, B[r][pi(r)] = c_r with pi the identity (z, t) or the
+// swap (x, y) and c_r in {+-1, +-i}.  Writing the projector this way keeps
+// the four threads of a site (four directions) in one instruction stream.
+template <class R>
+struct Dir {
+  bool swp;
+  cpx<R> c0, c1;
+};
+template <class R>
+__device__ __forceinline__ Dir<R> make_dir(int mu) {
+  Dir<R> d;
+  d.swp = mu < 2;
+  if (mu == 0) { d.c0 = mk(R(0), R(-1)); d.c1 = mk(R(0), R(-1)); }
+  else if (mu == 1) { d.c0 = mk(R(-1), R(0)); d.c1 = mk(R(1), R(0)); }
+  else if (mu == 2) { d.c0 = mk(R(0), R(-1)); d.c1 = mk(R(0), R(1)); }
+  else { d.c0 = mk(R(1), R(0)); d.c1 = mk(R(1), R(0)); }
+  return d;
+}
+// h_r = s_r + sigma c_r s_{2 + pi(r)}
+template <class R>
+__device__ __forceinline__ void project_rt(const Spinor<R>& p, const Dir<R>& dr, R sigma, cpx<R> h[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cpx<R> s2 = p.c[6 + a], s3 = p.c[9 + a];
+    cpx<R> t0 = dr.swp ? s3 : s2, t1 = dr.swp ? s2 : s3;
+    h[0][a] = p.c[a] + sigma * (dr.c0 * t0);
+    h[1][a] = p.c[3 + a] + sigma * (dr.c1 * t1);
+  }
+}
+// acc += sc [y; sigma B^H y],  (B^H y)_r = conj(c_pi(r)) y_pi(r)
+template <class R>
+__device__ __forceinline__ void accumulate_rt(Spinor<R>& acc, const cpx<R> y[2][3], const Dir<R>& dr,
+                                              R sigma, R sc) {
+  cpx<R> k2 = conj(dr.swp ? dr.c1 : dr.c0), k3 = conj(dr.swp ? dr.c0 : dr.c1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cpx<R> y0 = sc * y[0][a], y1 = sc * y[1][a];
+    acc.c[a] = acc.c[a] + y0;
+    acc.c[3 + a] = acc.c[3 + a] + y1;
+    acc.c[6 + a] = acc.c[6 + a] + sigma * (k2 * (dr.swp ? y1 : y0));
+    acc.c[9 + a] = acc.c[9 + a] + sigma * (k3 * (dr.swp ? y0 : y1));
+  }
+}
+
+// own 3 components of the sum of the block-internal hops at local site q;
+// this thread applies the two hops of direction mu = sub
+template <class R>
+__device__ __forceinline__ void hop_block(const int16_t* __restrict__ bnbr, const T16<R>* sl,
+                                          const cpx<R>* buf, int Vb, int Vbp, int Vh, int q, int sub,
+                                          cpx<R> out[3]) {
+  Spinor<R> acc;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc.c[k] = mk(R(0), R(0));
-  hop_block_dir<0>(bnbr, sl, buf, Vb, Vh, q, acc);
-  hop_block_dir<1>(bnbr, sl, buf, Vb, Vh, q, acc);
-  hop_block_dir<2>(bnbr, sl, buf, Vb, Vh, q, acc);
-  hop_block_dir<3>(bnbr, sl, buf, Vb, Vh, q, acc);
+  const Dir<R> dr = make_dir<R>(sub);
+  cpx<R> hh[2][3], y[2][3];
+  Spinor<R> nb;
+  int qf = __ldg(bnbr + (2 * sub) * Vb + q);
+  if (qf >= 0) {   // (1 - g_mu) U_mu(x) x(x + mu)
+    smem_spinor<R>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
+    project_rt<R>(nb, dr, R(-1), hh);
+    Link<R> U;
+    smem_link<R>(sl, Vbp, q, sub, U);
+    su3_mul(U, hh, y);
+    accumulate_rt<R>(acc, y, dr, R(-1), R(1));
+  }
+  int qb = __ldg(bnbr + (2 * sub + 1) * Vb + q);
+  if (qb >= 0) {   // (1 + g_mu) U_mu(x - mu)^H x(x - mu)
+    smem_spinor<R>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
+    project_rt<R>(nb, dr, R(1), hh);
+    Link<R> U;
+    smem_link<R>(sl, Vbp, qb, sub, U);
+    su3_mul_dag(U, hh, y);
+    accumulate_rt<R>(acc, y, dr, R(1), R(1));
+  }
+  reduce_scatter<R>(acc, sub, out);
+}
+
+// own 3 components of the full (global) hopping sum at device site d
+template <class R>
+__device__ __forceinline__ void hop_global(const Geom& g, const R* x, const R* gauge, int d, int sub,
+                                           cpx<R> out[3]) {
+  Spinor<R> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc.c[k] = mk(R(0), R(0));
+  const Dir<R> dr = make_dir<R>(sub);
+  cpx<R> hh[2][3], y[2][3];
+  Spinor<R> nb;
+  {
+    uint32_t e = __ldg(g.nbr + (size_t)(2 * sub) * g.V + d);
+    int n = (int)(e & ~NEG_BIT);
+    load_spinor_cg<R>(x, n, g.Vb, nb);
+    project_rt<R>(nb, dr, R(-1), hh);
+    Link<R> U;
+    load_link<R>(gauge, d, g.Vb, sub, U);
+    su3_mul(U, hh, y);
+    accumulate_rt<R>(acc, y, dr, R(-1), (e & NEG_BIT) ? R(-1) : R(1));
+  }
+  {
+    uint32_t e = __ldg(g.nbr + (size_t)(2 * sub + 1) * g.V + d);
+    int n = (int)(e & ~NEG_BIT);
+    load_spinor_cg<R>(x, n, g.Vb, nb);
+    project_rt<R>(nb, dr, R(1), hh);
+    Link<R> U;
+    load_link<R>(gauge, n, g.Vb, sub, U);
+    su3_mul_dag(U, hh, y);
+    accumulate_rt<R>(acc, y, dr, R(1), (e & NEG_BIT) ? R(-1) : R(1));
+  }
+  reduce_scatter<R>(acc, sub, out);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -105,18 +248,35 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block sum of three doubles, result broadcast to all threads
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  int nw = blockDim.x >> 5;
-  if (l == 0) { sh[3 * w] = a; sh[3 * w + 1] = b; sh[3 * w + 2] = c; }
+template <class R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum of three per-thread partials in the working precision (warp
+// trees, then one warp over the per-warp sums), broadcast to every thread
+template <class R>
+__device__ __forceinline__ void block_sum3(R ra, R rb, R rc, R& a, R& b, R& c, R* sh) {
+  ra = warp_sum_r<R>(ra);
+  rb = warp_sum_r<R>(rb);
+  rc = warp_sum_r<R>(rc);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  if (l == 0) { sh[3 * w] = ra; sh[3 * w + 1] = rb; sh[3 * w + 2] = rc; }
   __syncthreads();
-  a = b = c = 0.0;
-  for (int i = 0; i < nw; ++i) { a += sh[3 * i]; b += sh[3 * i + 1]; c += sh[3 * i + 2]; }
+  if (w == 0) {
+    R x = l < nw ? sh[3 * l] : R(0), y = l < nw ? sh[3 * l + 1] : R(0), z = l < nw ? sh[3 * l + 2] : R(0);
+    x = warp_sum_r<R>(x);
+    y = warp_sum_r<R>(y);
+    z = warp_sum_r<R>(z);
+    if (l == 0) { sh[96] = x; sh[97] = y; sh[98] = z; }
+  }
   __syncthreads();
+  a = sh[96];
+  b = sh[97];
+  c = sh[98];
 }
 
 // block index of the k-th block of colour c (block-grid extent 0 even)
@@ -133,163 +293,485 @@ __device__ __forceinline__ int block_of_colour(const Geom& g, int c, int k) {
 }
 
 template <class R>
-__global__ void k_sap_sweep(Geom g, int colour, int mr_iters, int x_is_zero,
-                            const R* __restrict__ b, R* __restrict__ x,
-                            const R* __restrict__ gauge, const R* __restrict__ clov,
-                            const R* __restrict__ clov_inv) {
-  using T = typename U16<R>::T;
+__global__ void __launch_bounds__(512) k_sap_sweep(Geom g, int colour, int mr_iters, int x_is_zero,
+                                                   const R* __restrict__ b, R* __restrict__ x,
+                                                   const R* __restrict__ gauge, const R* __restrict__ clov,
+                                                   const R* __restrict__ clov_inv) {
   using LYG = Layout<R, GAUGE_NR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int Vb = g.Vb, Vh = Vb / 2;
-  T* sl = reinterpret_cast<T*>(smem_raw);                               // [NU][Vb]
-  cpx<R>* E = reinterpret_cast<cpx<R>*>(sl + (size_t)LYG::NU * Vb);      // [12][Vh]
-  cpx<R>* O = E + 12 * Vh;                                               // [12][Vh]
-  cpx<R>* Ro = O + 12 * Vh;                                              // [12][Vh]
-  double* red = reinterpret_cast<double*>(Ro + 12 * Vh);                 // [3 * warps]
+  const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
+  T16<R>* sl = reinterpret_cast<T16<R>*>(smem_raw);                      // [NU][Vb + LPAD]
+  cpx<R>* E = reinterpret_cast<cpx<R>*>(sl + (size_t)LYG::NU * Vbp);      // [12][Vh]
+  cpx<R>* O = E + 12 * Vh;                                                // [12][Vh]
+  R* red = reinterpret_cast<R*>(O + 12 * Vh);                             // [3 * warps + 3]
 
   const int B = block_of_colour(g, colour, blockIdx.x);
   const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
   b += off;
   x += off;
-  const int h = threadIdx.x;
+  const int h = threadIdx.x >> 2, sub = threadIdx.x & 3;
   const bool act = h < Vh;
-  const int de = B * Vb + h, dO = B * Vb + Vh + h;
+  const int hs = act ? h : 0;                 // inactive lanes shadow site 0 (no stores)
+  const int de = B * Vb + hs, dO = B * Vb + Vh + hs;
 
   // stage the block's links (contiguous in the block-major layout)
   {
-    const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * LYG::NU * Vb;
-    for (int i = threadIdx.x; i < LYG::NU * Vb; i += blockDim.x) sl[i] = __ldg(src + i);
+    const T16<R>* src = reinterpret_cast<const T16<R>*>(gauge) + (size_t)B * LYG::NU * Vb;
+    for (int i = threadIdx.x; i < LYG::NU * Vb; i += blockDim.x) {
+      int u = i / Vb, q = i - u * Vb;
+      sl[u * Vbp + q] = __ldg(src + i);
+    }
   }
 
-  // residual on the block
-  Spinor<R> re;    // even-site residual
-  if (act) {
-    Spinor<R> ro;
+  // residual r = b - D x on the own components of both sites
+  cpx<R> re[3], ro[3];
+  {
+#pragma unroll
     for (int par = 0; par < 2; ++par) {
-      int d = par ? dO : de;
-      Spinor<R> r;
-      load_spinor<R>(b, d, Vb, r);
+      const int d = par ? dO : de;
+      cpx<R> r[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r[i] = ld_comp(b, comp_off<R>(d, Vb, 3 * sub + i));
       if (!x_is_zero) {
-        Spinor<R> xs, ax, acc;
-        load_spinor_cg<R>(x, d, Vb, xs);
-        clover_mul<R>(clov, d, Vb, xs, ax);
+        cpx<R> hop[3], x6[6], ax[3];
+        hop_global<R>(g, x, gauge, d, sub, hop);
+        const int c0 = 6 * (sub >> 1);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc.c[k] = mk(R(0), R(0));
-        hop_dir<0>(g, x, gauge, d, acc);
-        hop_dir<1>(g, x, gauge, d, acc);
-        hop_dir<2>(g, x, gauge, d, acc);
-        hop_dir<3>(g, x, gauge, d, acc);
+        for (int i = 0; i < 6; ++i) x6[i] = ld_comp(x, comp_off<R>(d, Vb, c0 + i));
+        clover_rows<R>(clov, d, Vb, sub, x6, ax);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          r.c[k].re -= ax.c[k].re - R(0.5) * acc.c[k].re;
-          r.c[k].im -= ax.c[k].im - R(0.5) * acc.c[k].im;
+        for (int i = 0; i < 3; ++i) {
+          r[i].re -= ax[i].re - R(0.5) * hop[i].re;
+          r[i].im -= ax[i].im - R(0.5) * hop[i].im;
         }
       }
-      if (par) ro = r; else re = r;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (par) ro[i] = r[i];
+        else re[i] = r[i];
+      }
     }
-    smem_store<R>(Ro, Vh, h, ro);
     // u_o = A_oo^-1 r_o
-    Spinor<R> u;
-    clover_mul<R>(clov_inv, dO, Vb, ro, u);
-    smem_store<R>(O, Vh, h, u);
+    cpx<R> v6[6], u[3];
+    chiral6<R>(ro, sub, v6);
+    clover_rows<R>(clov_inv, dO, Vb, sub, v6, u);
+    if (act)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = u[i];
   }
   __syncthreads();
 
   // rhs_e = r_e - D_eo u_o = r_e + 1/2 hop(u_o)
-  Spinor<R> res, xe;
-  if (act) {
-    Spinor<R> t;
-    hop_block<R>(g.bnbr, sl, O, Vb, Vh, h, t);
+  cpx<R> res[3], xe[3];
+  {
+    cpx<R> t[3];
+    hop_block<R>(g.bnbr, sl, O, Vb, Vbp, Vh, hs, sub, t);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      res.c[k].re = fma_r(R(0.5), t.c[k].re, re.c[k].re);
-      res.c[k].im = fma_r(R(0.5), t.c[k].im, re.c[k].im);
-      xe.c[k] = mk(R(0), R(0));
+    for (int i = 0; i < 3; ++i) {
+      res[i].re = fma_r(R(0.5), t[i].re, re[i].re);
+      res[i].im = fma_r(R(0.5), t[i].im, re[i].im);
+      xe[i] = mk(R(0), R(0));
     }
   }
 
   for (int it = 0; it < mr_iters; ++it) {
-    if (act) smem_store<R>(E, Vh, h, res);
-    __syncthreads();
-    if (act) {  // odd: w = A_oo^-1 D_oe res = A_oo^-1 (-1/2 hop(res))
-      Spinor<R> t, w;
-      hop_block<R>(g.bnbr, sl, E, Vb, Vh, Vh + h, t);
+    __syncthreads();       // readers of E / O from the previous step are done
+    if (act)
 #pragma unroll
-      for (int k = 0; k < 12; ++k) t.c[k] = R(-0.5) * t.c[k];
-      clover_mul<R>(clov_inv, dO, Vb, t, w);
-      smem_store<R>(O, Vh, h, w);
+      for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = res[i];
+    __syncthreads();
+    {  // odd: w = A_oo^-1 D_oe res = A_oo^-1 (-1/2 hop(res))
+      cpx<R> t[3], v6[6], w[3];
+      hop_block<R>(g.bnbr, sl, E, Vb, Vbp, Vh, Vh + hs, sub, t);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) t[i] = R(-0.5) * t[i];
+      chiral6<R>(t, sub, v6);
+      clover_rows<R>(clov_inv, dO, Vb, sub, v6, w);
+      if (act)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = w[i];
     }
     __syncthreads();
-    double pr_re = 0.0, pr_im = 0.0, pp = 0.0;
-    Spinor<R> p;
-    if (act) {  // even: p = A_ee res - D_eo w = A_ee res + 1/2 hop(w)
-      Spinor<R> t;
-      clover_mul<R>(clov, de, Vb, res, p);
-      hop_block<R>(g.bnbr, sl, O, Vb, Vh, h, t);
+    R pr_re = 0, pr_im = 0, pp_r = 0;
+    cpx<R> p[3];
+    {  // even: p = A_ee res - D_eo w = A_ee res + 1/2 hop(w)
+      cpx<R> t[3], v6[6];
+      chiral6<R>(res, sub, v6);
+      clover_rows<R>(clov, de, Vb, sub, v6, p);
+      hop_block<R>(g.bnbr, sl, O, Vb, Vbp, Vh, hs, sub, t);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        p.c[k].re = fma_r(R(0.5), t.c[k].re, p.c[k].re);
-        p.c[k].im = fma_r(R(0.5), t.c[k].im, p.c[k].im);
-        pr_re += (double)p.c[k].re * res.c[k].re + (double)p.c[k].im * res.c[k].im;
-        pr_im += (double)p.c[k].re * res.c[k].im - (double)p.c[k].im * res.c[k].re;
-        pp += (double)p.c[k].re * p.c[k].re + (double)p.c[k].im * p.c[k].im;
+      for (int i = 0; i < 3; ++i) {
+        p[i].re = fma_r(R(0.5), t[i].re, p[i].re);
+        p[i].im = fma_r(R(0.5), t[i].im, p[i].im);
+        if (act) {
+          pr_re += p[i].re * res[i].re + p[i].im * res[i].im;
+          pr_im += p[i].re * res[i].im - p[i].im * res[i].re;
+          pp_r += p[i].re * p[i].re + p[i].im * p[i].im;
+        }
       }
     }
-    block_sum3(pr_re, pr_im, pp, red);
-    if (act && pp > 0.0) {
-      R are = (R)(pr_re / pp), aim = (R)(pr_im / pp);
-      cpx<R> a = mk(are, aim);
+    R dpr_re, dpr_im, pp;
+    block_sum3<R>(pr_re, pr_im, pp_r, dpr_re, dpr_im, pp, red);
+    if (pp > R(0)) {
+      cpx<R> a = mk(dpr_re / pp, dpr_im / pp);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        fma(xe.c[k], a, res.c[k]);
-        cpx<R> ap = a * p.c[k];
-        res.c[k] = res.c[k] - ap;
+      for (int i = 0; i < 3; ++i) {
+        fma(xe[i], a, res[i]);
+        res[i] = res[i] - a * p[i];
       }
     }
   }
 
   // e_o = A_oo^-1 (r_o - D_oe e_e) = A_oo^-1 (r_o + 1/2 hop(e_e))
-  if (act) smem_store<R>(E, Vh, h, xe);
   __syncthreads();
+  if (act)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = xe[i];
+  __syncthreads();
+  cpx<R> eo[3];
+  {
+    cpx<R> t[3], v6[6];
+    hop_block<R>(g.bnbr, sl, E, Vb, Vbp, Vh, Vh + hs, sub, t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t[i].re = fma_r(R(0.5), t[i].re, ro[i].re);
+      t[i].im = fma_r(R(0.5), t[i].im, ro[i].im);
+    }
+    chiral6<R>(t, sub, v6);
+    clover_rows<R>(clov_inv, dO, Vb, sub, v6, eo);
+  }
   if (act) {
-    Spinor<R> t, ro, eo;
-    hop_block<R>(g.bnbr, sl, E, Vb, Vh, Vh + h, t);
-    smem_spinor<R>(Ro, Vh, h, ro);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      ro.c[k].re = fma_r(R(0.5), t.c[k].re, ro.c[k].re);
-      ro.c[k].im = fma_r(R(0.5), t.c[k].im, ro.c[k].im);
-    }
-    clover_mul<R>(clov_inv, dO, Vb, ro, eo);
-    if (!x_is_zero) {
-      Spinor<R> xo, xev;
-      load_spinor_cg<R>(x, de, Vb, xev);
-      load_spinor_cg<R>(x, dO, Vb, xo);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        xe.c[k] = xe.c[k] + xev.c[k];
-        eo.c[k] = eo.c[k] + xo.c[k];
+    for (int i = 0; i < 3; ++i) {
+      size_t oe = comp_off<R>(de, Vb, 3 * sub + i), oo = comp_off<R>(dO, Vb, 3 * sub + i);
+      cpx<R> ve = xe[i], vo = eo[i];
+      if (!x_is_zero) {
+        ve = ve + ld_comp(x, oe);
+        vo = vo + ld_comp(x, oo);
       }
+      st_comp(x, oe, ve);
+      st_comp(x, oo, vo);
     }
-    store_spinor<R>(x, de, Vb, xe);
-    store_spinor<R>(x, dO, Vb, eo);
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 sweep with warp-uniform directions (Schwarz blocks whose half volume is
+// a multiple of 32).  Hop phases: thread (mu, h) = (t / Vh, t % Vh) applies
+// the two hops of direction mu at site h of one parity, with the compile-time
+// projectors, and writes its 12-component partial to P[mu][12][Vh].  Site
+// phases: thread (sub, h) owns spin sub of site h, sums the four partials and
+// applies its three rows of the chiral clover block (staged in shared
+// memory together with the block's links).
+// ---------------------------------------------------------------------------
+namespace fast {
+
+using f2 = cpx<float>;
+
+// packed Hermitian rows [3 half, 3 half + 3) of a chiral block times v6; P36 in
+// smem as [9 float4][Vh] starting at site h
+__device__ __forceinline__ void rows3(const float4* Ablk, int Vh, int h, int half, const f2 v6[6], f2 y[3]) {
+  float P[36];
+#pragma unroll
+  for (int u = 0; u < 9; ++u) {
+    float4 t = Ablk[u * Vh + h];
+    P[4 * u] = t.x; P[4 * u + 1] = t.y; P[4 * u + 2] = t.z; P[4 * u + 3] = t.w;
+  }
+  f2 y6[6];
+  herm6<float>(P, v6, y6);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
+}
+// same, with the block read from global memory (clover field, device site d)
+__device__ __forceinline__ void rows3_g(const float* clov, int d, int Vb, int cb, int half, const f2 v6[6], f2 y[3]) {
+  float P[36];
+  load_units<float, CLOVER_NR>(clov, d, Vb, cb * 9, 9, P);
+  f2 y6[6];
+  herm6<float>(P, v6, y6);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_local(const int16_t* __restrict__ bnbr, const float4* sl, const f2* buf,
+                                          int Vb, int Vbp, int Vh, int q, Spinor<float>& acc) {
+  f2 hh[2][3], y[2][3];
+  Spinor<float> nb;
+  int qf = __ldg(bnbr + (2 * MU) * Vb + q);
+  if (qf >= 0) {
+    smem_spinor<float>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
+    project<MU, -1>(nb, hh);
+    Link<float> U;
+    smem_link<float>(sl, Vbp, q, MU, U);
+    su3_mul(U, hh, y);
+    accumulate<MU, -1>(acc, y, 1.f);
+  }
+  int qb = __ldg(bnbr + (2 * MU + 1) * Vb + q);
+  if (qb >= 0) {
+    smem_spinor<float>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
+    project<MU, +1>(nb, hh);
+    Link<float> U;
+    smem_link<float>(sl, Vbp, qb, MU, U);
+    su3_mul_dag(U, hh, y);
+    accumulate<MU, +1>(acc, y, 1.f);
+  }
+}
+
+// hop phase inside the block: P[mu][k][h] for site q = qoff + h, values from buf
+__device__ __forceinline__ void hop_phase(const int16_t* bnbr, const float4* sl, const f2* buf, int Vb, int Vbp,
+                                          int Vh, int qoff, int mu, int h, f2* P) {
+  Spinor<float> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
+  const int q = qoff + h;
+  switch (mu) {
+    case 0: hop_local<0>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
+    case 1: hop_local<1>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
+    case 2: hop_local<2>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
+    default: hop_local<3>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) P[(mu * 12 + k) * Vh + h] = acc.c[k];
+}
+
+// global hop phase (residual): full neighbourhood, device site d
+__device__ __forceinline__ void hop_phase_g(const Geom& g, const float* x, const float* gauge, int d, int mu,
+                                            int h, int Vh, f2* P) {
+  Spinor<float> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
+  switch (mu) {
+    case 0: hop_dir<0>(g, x, gauge, d, acc); break;
+    case 1: hop_dir<1>(g, x, gauge, d, acc); break;
+    case 2: hop_dir<2>(g, x, gauge, d, acc); break;
+    default: hop_dir<3>(g, x, gauge, d, acc); break;
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) P[(mu * 12 + k) * Vh + h] = acc.c[k];
+}
+
+// sum over directions of component k of site h
+__device__ __forceinline__ f2 psum(const f2* P, int Vh, int k, int h) {
+  return (P[(0 * 12 + k) * Vh + h] + P[(1 * 12 + k) * Vh + h]) + (P[(2 * 12 + k) * Vh + h] + P[(3 * 12 + k) * Vh + h]);
+}
+
+__global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_iters, int x_is_zero,
+                                                  const float* __restrict__ b, float* __restrict__ x,
+                                                  const float* __restrict__ gauge, const float* __restrict__ clov,
+                                                  const float* __restrict__ clov_inv) {
+  using LYG = Layout<float, GAUGE_NR>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
+  float4* sl = reinterpret_cast<float4*>(smem_raw);                    // [12][Vb + LPAD]
+  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh]
+  float4* Aoi = Aee + 18 * Vh;                                          // [2 cb][9][Vh]
+  f2* E = reinterpret_cast<f2*>(Aoi + 18 * Vh);                         // [12][Vh]
+  f2* O = E + 12 * Vh;                                                  // [12][Vh]
+  f2* RO = O + 12 * Vh;                                                 // [12][Vh]
+  f2* P = RO + 12 * Vh;                                                 // [4][12][Vh]
+  float* red = reinterpret_cast<float*>(P + 48 * Vh);                   // [3 * warps + 3]
+
+  const int B = block_of_colour(g, colour, blockIdx.x);
+  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  b += off;
+  x += off;
+  const int t = threadIdx.x;
+  const int mu = t / Vh, h = t - mu * Vh;      // hop phases
+  const int sub = mu;                          // site phases: spin sub of site h
+  const int cb = sub >> 1, half = sub & 1;
+  const int de = B * Vb + h, dO = B * Vb + Vh + h;
+
+  // stage links, A_ee and A_oo^-1 of the block
+  {
+    const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
+    for (int i = t; i < LYG::NU * Vb; i += blockDim.x) {
+      int u = i / Vb, q = i - u * Vb;
+      sl[u * Vbp + q] = __ldg(src + i);
+    }
+    const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
+    const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
+    for (int i = t; i < 18 * Vh; i += blockDim.x) {
+      int u = i / Vh, hh = i - u * Vh;
+      Aee[i] = __ldg(ca + (size_t)u * Vb + hh);
+      Aoi[i] = __ldg(ci + (size_t)u * Vb + Vh + hh);
+    }
+  }
+
+  // residual r = b - D x on both parities (own components)
+  f2 re[3], ro[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    re[i] = ld_comp(b, comp_off<float>(de, Vb, 3 * sub + i));
+    ro[i] = ld_comp(b, comp_off<float>(dO, Vb, 3 * sub + i));
+  }
+  if (!x_is_zero) {
+#pragma unroll 1
+    for (int par = 0; par < 2; ++par) {
+      const int d = par ? dO : de;
+      hop_phase_g(g, x, gauge, d, mu, h, Vh, P);
+      __syncthreads();
+      f2 x6[6], ax[3];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) x6[i] = ld_comp(x, comp_off<float>(d, Vb, 6 * cb + i));
+      rows3_g(clov, d, Vb, cb, half, x6, ax);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        f2 hs = psum(P, Vh, 3 * sub + i, h);
+        f2 v = mk(ax[i].re - 0.5f * hs.re, ax[i].im - 0.5f * hs.im);
+        if (par) ro[i] = ro[i] - v;
+        else re[i] = re[i] - v;
+      }
+      __syncthreads();
+    }
+  }
+  // u_o = A_oo^-1 r_o
+#pragma unroll
+  for (int i = 0; i < 3; ++i) RO[(3 * sub + i) * Vh + h] = ro[i];
+  __syncthreads();
+  {
+    f2 v6[6], u[3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v6[i] = RO[(6 * cb + i) * Vh + h];
+    rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, u);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = u[i];
+  }
+  __syncthreads();
+  // rhs_e = r_e + 1/2 hop(u_o)
+  hop_phase(g.bnbr, sl, O, Vb, Vbp, Vh, 0, mu, h, P);
+  __syncthreads();
+  f2 res[3], xe[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    f2 hs = psum(P, Vh, 3 * sub + i, h);
+    res[i] = mk(fmaf(0.5f, hs.re, re[i].re), fmaf(0.5f, hs.im, re[i].im));
+    xe[i] = mk(0.f, 0.f);
+  }
+
+  for (int it = 0; it < mr_iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = res[i];
+    __syncthreads();
+    // odd: w = A_oo^-1 (-1/2 hop(res))
+    hop_phase(g.bnbr, sl, E, Vb, Vbp, Vh, Vh, mu, h, P);
+    __syncthreads();
+    {
+      f2 v6[6], w[3];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v6[i] = -0.5f * psum(P, Vh, 6 * cb + i, h);
+      rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, w);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = w[i];
+    }
+    __syncthreads();
+    // even: p = A_ee res + 1/2 hop(w)
+    hop_phase(g.bnbr, sl, O, Vb, Vbp, Vh, 0, mu, h, P);
+    __syncthreads();
+    f2 pv[3];
+    float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
+    {
+      f2 v6[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v6[i] = E[(6 * cb + i) * Vh + h];
+      rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, pv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        f2 hs = psum(P, Vh, 3 * sub + i, h);
+        pv[i] = mk(fmaf(0.5f, hs.re, pv[i].re), fmaf(0.5f, hs.im, pv[i].im));
+        pr_re += pv[i].re * res[i].re + pv[i].im * res[i].im;
+        pr_im += pv[i].re * res[i].im - pv[i].im * res[i].re;
+        pp_r += pv[i].re * pv[i].re + pv[i].im * pv[i].im;
+      }
+    }
+    float dre, dim, pp;
+    block_sum3<float>(pr_re, pr_im, pp_r, dre, dim, pp, red);
+    if (pp > 0.f) {
+      f2 a = mk(dre / pp, dim / pp);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        fma(xe[i], a, res[i]);
+        res[i] = res[i] - a * pv[i];
+      }
+    }
+  }
+
+  // e_o = A_oo^-1 (r_o + 1/2 hop(e_e))
+#pragma unroll
+  for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = xe[i];
+  __syncthreads();
+  hop_phase(g.bnbr, sl, E, Vb, Vbp, Vh, Vh, mu, h, P);
+  __syncthreads();
+  f2 eo[3];
+  {
+    f2 v6[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      f2 hs = psum(P, Vh, 6 * cb + i, h);
+      f2 r0 = RO[(6 * cb + i) * Vh + h];
+      v6[i] = mk(fmaf(0.5f, hs.re, r0.re), fmaf(0.5f, hs.im, r0.im));
+    }
+    rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, eo);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    size_t oe = comp_off<float>(de, Vb, 3 * sub + i), oo = comp_off<float>(dO, Vb, 3 * sub + i);
+    f2 ve = xe[i], vo = eo[i];
+    if (!x_is_zero) {
+      ve = ve + ld_comp(x, oe);
+      vo = vo + ld_comp(x, oo);
+    }
+    st_comp(x, oe, ve);
+    st_comp(x, oo, vo);
+  }
+}
+
+}  // namespace fast
+
 }  // namespace
 
+static int sap_threads(const Geom& g) { return ((4 * (g.Vb / 2) + 31) / 32) * 32; }
+
 size_t sap_smem_bytes(const Geom& g, int real_size) {
-  size_t units = (size_t)GAUGE_NR * real_size / 16 * g.Vb;        // staged links
-  size_t bufs = 3 * 12 * (size_t)(g.Vb / 2) * 2 * real_size;       // E, O, Ro
-  int threads = ((g.Vb / 2 + 31) / 32) * 32;
-  return units * 16 + bufs + 3 * sizeof(double) * (threads / 32);
+  size_t units = (size_t)GAUGE_NR * real_size / 16 * (g.Vb + LPAD);   // staged links
+  size_t bufs = 2 * 12 * (size_t)(g.Vb / 2) * 2 * real_size;          // E, O
+  return units * 16 + bufs + 100 * sizeof(double);
+}
+
+static size_t sap_fast_smem(const Geom& g) {
+  const int Vh = g.Vb / 2;
+  size_t bytes = (size_t)12 * (g.Vb + LPAD) * 16;   // links
+  bytes += (size_t)2 * 18 * Vh * 16;                // A_ee, A_oo^-1
+  bytes += (size_t)(3 * 12 + 48) * Vh * 8;          // E, O, RO, P
+  bytes += 100 * sizeof(double);
+  return bytes;
+}
+
+static bool sap_fast_ok(const Geom& g) {
+  const int Vh = g.Vb / 2;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_fast_smem(g) <= 227 * 1024;
 }
 
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs,
                       cudaStream_t st) {
-  int threads = ((g.Vb / 2 + 31) / 32) * 32;
+  if constexpr (sizeof(R) == 4) {
+    if (sap_fast_ok(g)) {
+      static bool cfg = false;
+      if (!cfg) {
+        cudaError_t e = cudaFuncSetAttribute(fast::k_sap_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        cfg = true;
+      }
+      dim3 grid(g.nb / 2, nrhs);
+      fast::k_sap_fast<<<grid, 2 * g.Vb, sap_fast_smem(g), st>>>(g, colour, mr_iters, x_is_zero ? 1 : 0, b, x,
+                                                                 gauge, clover, clover_inv);
+      ++g_launches;
+      return cudaGetLastError();
+    }
+  }
+  int threads = sap_threads(g);
   size_t smem = sap_smem_bytes(g, sizeof(R));
   static bool configured[2] = {false, false};
   cudaError_t e;
