@@ -233,6 +233,26 @@ DDAMG_API ddamg_status ddamg_coarse_solve(ddamg_handle h, int precision, int nrh
                                 const double *in, double *out, int on_device,
                                 double tol, int *iters);
 
+/* The coarse solve of ddamg_coarse_solve without any device allocation, for
+ * callers that cannot allocate device memory at solve time (a serving loop
+ * that must avoid cudaMalloc's implicit synchronisation and allocator locks,
+ * or a thread bound to a device-memory budget reserved in advance).  The
+ * paper has no counterpart; it is a deployment variant of the same kernel.
+ * in / out: DEVICE pointers, nrhs coarse vectors in the FP64 coarse layout;
+ * tol as for ddamg_coarse_solve, in the handle's inner precision; iters
+ * (nullable, host) receives nrhs iteration counts.  The kernel's scratch
+ * (Krylov basis slices, vectors read by neighbouring coarse sites, partial
+ * sums, the grid barrier) lives in one fixed 16 MiB array that every GPU
+ * loading this library holds until the process exits; a request that needs
+ * more is rejected with DDAMG_EINVAL and a message naming both sizes.  The
+ * first call on a device looks up the array's device address, so make it
+ * before any stream capture.  All calls share the array and leave their
+ * contents in it (the barrier counters are cleared by every call): calls
+ * that overlap on the GPU, on any stream or handle, race. */
+DDAMG_API ddamg_status ddamg_coarse_solve_noalloc(ddamg_handle h, int nrhs,
+                                                  const double *in, double *out,
+                                                  double tol, int *iters);
+
 /* out = M in (Eq. 5, post-smoothing only) in the inner precision. */
 DDAMG_API ddamg_status ddamg_apply_M(ddamg_handle h, int precision, int nrhs,
                            const double *in, double *out, int on_device);

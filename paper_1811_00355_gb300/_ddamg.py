@@ -89,6 +89,7 @@ SIGNATURES = {
     "ddamg_prolong": (_I, [_H, _I, _I, _P, _P, _I]),
     "ddamg_apply_coarse": (_I, [_H, _I, _I, _P, _P, _I]),
     "ddamg_coarse_solve": (_I, [_H, _I, _I, _P, _P, _I, _D, _P]),
+    "ddamg_coarse_solve_noalloc": (_I, [_H, _I, _P, _P, _D, _P]),
     "ddamg_apply_M": (_I, [_H, _I, _I, _P, _P, _I]),
     "ddamg_get_index_maps": (_I, [_H, _P, _P, _P, _P, _P]),
     "ddamg_get_stats": (_I, [_H, C.POINTER(Stats)]),
@@ -316,6 +317,18 @@ class DDAMG:
         po, _ = _ptr(out)
         self._check(self.lib.ddamg_coarse_solve(self.h, precision, n, pi, po, dev, tol,
                                                 C.c_void_p(its.ctypes.data)))
+        return out, its
+
+    def coarse_solve_noalloc(self, bc, tol):
+        """Coarse solve out of the library's fixed device array (device tensors only)."""
+        if not _is_torch_cuda(bc):
+            raise ValueError("ddamg_coarse_solve_noalloc takes device buffers")
+        n = bc.shape[0] if len(bc.shape) == 3 else 1
+        out = _like(bc, tuple(bc.shape))
+        its = np.zeros(n, np.int32)
+        self._check(self.lib.ddamg_coarse_solve_noalloc(self.h, n, C.c_void_p(bc.data_ptr()),
+                                                        C.c_void_p(out.data_ptr()), tol,
+                                                        C.c_void_p(its.ctypes.data)))
         return out, its
 
     def apply_M(self, x, precision):

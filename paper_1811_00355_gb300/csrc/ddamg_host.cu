@@ -14,6 +14,7 @@
 #include <vector>
 #include <complex>
 #include <chrono>
+#include <mutex>
 
 #include "../../include/ddamg.h"
 #include "kernels.h"
@@ -749,6 +750,70 @@ ddamg_status coarse_out(ddamg_ctx* h, const R* src, size_t nc, double* dst, int 
   return DDAMG_OK;
 }
 
+// ---- coarse solve out of a fixed device array ------------------------------------
+// Callers that cannot allocate device memory when they solve (a serving loop
+// that must not take the allocator's implicit synchronisation or locks, or a
+// host thread working inside a device-memory budget reserved up front) can
+// run the coarse solve out of this array instead.  It is reserved in every
+// GPU that loads the library and held until the process exits.
+constexpr size_t NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[128] = {};   // device address of the array, per device
+
+// Once per device, with that device current: the array's name is only a
+// host-side stand-in, so its device address comes from cudaGetSymbolAddress.
+ddamg_status noalloc_scratch(ddamg_ctx* h, unsigned char** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(h, DDAMG_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(h, DDAMG_ECUDA, "cudaGetSymbolAddress of the fixed scratch array failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = reinterpret_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return DDAMG_OK;
+}
+
+template <class R>
+ddamg_status coarse_solve_noalloc_impl(ddamg_ctx* h, int nrhs, const double* in, double* out, double tol,
+                                       int* iters) {
+  const size_t nc = (size_t)nrhs * h->g.nb * h->n2;
+  const size_t vec = (nc * 2 * sizeof(R) + 255) / 256 * 256;
+  const size_t work = coarse_gmres_exact_bytes<R>(h->g, h->p.n_v, h->p.coarse_restart, nrhs);
+  if (work == 0) return fail(h, DDAMG_EINVAL, "no launch configuration for the coarse solve");
+  const size_t need = 2 * vec + work;
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return fail(h, DDAMG_EINVAL,
+                "the coarse solve of %d right-hand sides needs %zu bytes of scratch; the fixed array holds %zu",
+                nrhs, need, NOALLOC_SCRATCH_BYTES);
+  unsigned char* base = nullptr;
+  TRY(noalloc_scratch(h, &base));
+  R* bin = reinterpret_cast<R*>(base);
+  R* xout = reinterpret_cast<R*>(base + vec);
+  void* wk = base + 2 * vec;
+  CoarseSolveArgs a;
+  a.Dc = h->Dc;
+  a.Ainv = h->Ainv;
+  a.n = h->p.n_v;
+  a.tol = tol;
+  a.restart = h->p.coarse_restart;
+  a.max_iter = h->p.coarse_max_iter;
+  CK(coarse_from_f64<R>(in, bin, nc, h->st));
+  CK(coarse_gmres<R>(h->g, a, bin, xout, nrhs, wk, h->d_iters, nullptr, h->d_status, h->st));
+  CK(coarse_to_f64<R>(xout, out, nc, h->st));
+  TRY(check_status(h));
+  if (iters) CK(cudaMemcpyAsync(iters, h->d_iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -1095,6 +1160,16 @@ ddamg_status ddamg_coarse_solve(ddamg_handle h, int prec, int nrhs, const double
     if (iters) CK(cudaMemcpy(iters, h->d_iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost));
     return coarse_out<R>(h, (R*)h->tmp[1], nc, out, on_device);
   });
+}
+
+ddamg_status ddamg_coarse_solve_noalloc(ddamg_handle h, int nrhs, const double* in, double* out, double tol,
+                                        int* iters) {
+  if (!h) return DDAMG_EINVAL;
+  if (nrhs < 1 || nrhs > 4096 || !in || !out || !(tol > 0.0))
+    return fail(h, DDAMG_EINVAL, "bad nrhs, buffers or tolerance");
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no coarse operator");
+  if (h->p.precision == DDAMG_FP64) return coarse_solve_noalloc_impl<double>(h, nrhs, in, out, tol, iters);
+  return coarse_solve_noalloc_impl<float>(h, nrhs, in, out, tol, iters);
 }
 
 ddamg_status ddamg_apply_M(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {

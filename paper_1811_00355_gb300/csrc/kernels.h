@@ -147,6 +147,10 @@ struct CoarseSolveArgs {
   int max_iter;
 };
 size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size);
+// bytes of `work` that coarse_gmres() touches for nrhs right-hand sides (0 if
+// no launch configuration exists)
+template <class R>
+size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs);
 template <class R>
 cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& a, const R* b, R* x, int nrhs,
                          void* work, int* iters, int* iters_acc, int* status, cudaStream_t st);

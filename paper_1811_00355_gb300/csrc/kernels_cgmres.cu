@@ -652,6 +652,21 @@ Choice choose(const Geom& g, int n2, int m, int nrhs) {
 
 }  // namespace
 
+template <class R>
+size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs) {
+  // the same layout as coarse_gmres() below, for the plan it would choose
+  Choice ch = choose<R>(g, 2 * n, restart, nrhs);
+  if (ch.NR == 0) return 0;
+  const size_t NE = g.nb / 2, n2 = 2 * n;
+  size_t bytes = al16(3 * (size_t)NRMAX * NE * n2 * sizeof(cpx<R>));
+  bytes += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  bytes += 256;
+  if (!ch.local) bytes += (size_t)ch.G * al16(ch.plan.local_bytes);
+  return bytes;
+}
+template size_t coarse_gmres_exact_bytes<float>(const Geom&, int, int, int);
+template size_t coarse_gmres_exact_bytes<double>(const Geom&, int, int, int);
+
 size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size) {
   // vectors wg, to, xg for NRMAX right-hand sides, partial sums, barrier,
   // and room for per-CTA local arrays when they do not fit in shared memory
