@@ -92,12 +92,33 @@ struct ddamg_ctx {
   void* fout = nullptr;
   double* d_coef = nullptr;
 
-  // stats
+  // stats: per kernel class (0 D, 1 SAP sweep, 2 coarse solve) launch counts
+  // and device time; timers recorded outside graphs wait in `pending`
   bool timing = false;
   uint64_t launches0 = 0;
-  uint64_t n_dslash = 0, n_sap = 0, n_coarse = 0;
-  std::vector<Timer> tm_dslash, tm_sap, tm_coarse;
+  uint64_t n_cls[3] = {0, 0, 0};
+  double ms_cls[3] = {0.0, 0.0, 0.0};
+  std::vector<std::pair<int, Timer>> pending;
   std::vector<Timer> pool;
+
+  // CUDA graphs of the outer FGMRES iterations, one per Krylov index k
+  struct GraphTimer {
+    int cls;
+    Timer t;
+  };
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<GraphTimer> timers;
+    uint64_t launches = 0;
+    uint64_t n_cls[3] = {0, 0, 0};
+    int gen = -1;
+    bool timing = false;
+  };
+  std::vector<IterGraph> graphs;
+  int gen = 0;                          // bumped whenever buffers move
+  std::vector<GraphTimer>* capture_timers = nullptr;
+  double* h_pinned = nullptr;           // device-to-host landing buffer
+  cudaStream_t cap_st = nullptr;        // private stream used only to record graphs
 };
 
 namespace {
@@ -331,6 +352,7 @@ ddamg_status need_tmp(ddamg_ctx* h, size_t nf, int k) {
   if (h->tmp_fields >= nf && (int)h->tmp.size() >= k) return DDAMG_OK;
   size_t want = nf > h->tmp_fields ? nf : h->tmp_fields;
   h->tmp.clear();
+  ++h->gen;   // captured graphs refer to the old temporaries
   for (int i = 0; i < (k > 6 ? k : 6); ++i) {
     void* p;
     TRY(dalloc(h, &p, want * h->V24 * sizeof(double)));
@@ -353,14 +375,34 @@ Timer next_timer(ddamg_ctx* h) {
 }
 
 template <class F>
-cudaError_t timed(ddamg_ctx* h, std::vector<Timer>& log, F&& f) {
+cudaError_t timed(ddamg_ctx* h, int cls, F&& f) {
+  ++h->n_cls[cls];
   if (!h->timing) return f();
-  Timer t = next_timer(h);
-  cudaEventRecord(t.a, h->st);
+  Timer t;
+  if (h->capture_timers) {           // events owned by the graph being captured
+    cudaEventCreate(&t.a);
+    cudaEventCreate(&t.b);
+  } else {
+    t = next_timer(h);
+  }
+  // inside a capture the records must become event nodes of the graph
+  const unsigned flags = h->capture_timers ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaEventRecordWithFlags(t.a, h->st, flags);
   cudaError_t e = f();
-  cudaEventRecord(t.b, h->st);
-  log.push_back(t);
+  cudaEventRecordWithFlags(t.b, h->st, flags);
+  if (h->capture_timers) h->capture_timers->push_back({cls, t});
+  else h->pending.push_back({cls, t});
   return e;
+}
+
+void collect_pending(ddamg_ctx* h) {
+  for (auto& pt : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pt.second.a, pt.second.b) == cudaSuccess) h->ms_cls[pt.first] += ms;
+    else cudaGetLastError();
+    h->pool.push_back(pt.second);
+  }
+  h->pending.clear();
 }
 
 // ---- in/out of fields -----------------------------------------------------------
@@ -403,8 +445,7 @@ template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 // ---- operators on device fields ---------------------------------------------------
 template <class R>
 ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
-  ++h->n_dslash;
-  CK(timed(h, h->tm_dslash, [&] {
+  CK(timed(h, 0, [&] {
     return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
   }));
   return DDAMG_OK;
@@ -416,11 +457,10 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf) {
   CK(cudaMemsetAsync(x, 0, nf * h->V24 * sizeof(R), h->st));
   for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
     for (int c = 0; c < 2; ++c) {
-      ++h->n_sap;
       bool zero = cyc == 0 && c == 0;
-      CK(timed(h, h->tm_sap, [&] {
+      CK(timed(h, 1, [&] {
         return sap_sweep<R>(h->g, c, h->p.mr_iters, zero, b, x, gauge_of<R>(h), clov_of<R>(h, false),
-                            clov_of<R>(h, true), nf, h->st);
+                            clov_of<R>(h, true), nf, h->d_status, h->st);
       }));
     }
   return DDAMG_OK;
@@ -435,8 +475,7 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   a.tol = tol;
   a.restart = h->p.coarse_restart;
   a.max_iter = h->p.coarse_max_iter;
-  ++h->n_coarse;
-  CK(timed(h, h->tm_coarse, [&] {
+  CK(timed(h, 2, [&] {
     return coarse_gmres<R>(h->g, a, bc, xc, nf, h->cwork, iters_dev, h->d_iters_acc, h->d_status, h->st);
   }));
   return DDAMG_OK;
@@ -580,7 +619,108 @@ ddamg_status alloc_outer(ddamg_ctx* h) {
   TRY(dalloc(h, &h->fin, h->V24 * sizeof(double)));
   TRY(dalloc(h, &h->fout, h->V24 * sizeof(double)));
   TRY(dalloc_t(h, &h->d_coef, (size_t)2 * (m + 1)));
+  if (!h->h_pinned) CK(cudaHostAlloc(&h->h_pinned, (6 * 64 + 16) * sizeof(double), cudaHostAllocDefault));
+  h->graphs.resize(m);
   return DDAMG_OK;
+}
+
+// everything an outer iteration's graph touches must exist before capture
+ddamg_status prepare_capture(ddamg_ctx* h) {
+  TRY(alloc_outer(h));
+  if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  TRY(need_tmp(h, 1, 6));
+  if (h->p.precision == DDAMG_FP32) coarse_gmres_exact_bytes<float>(h->g, h->p.n_v, h->p.coarse_restart, 1);
+  else coarse_gmres_exact_bytes<double>(h->g, h->p.n_v, h->p.coarse_restart, 1);
+  return DDAMG_OK;
+}
+
+// The device work of one outer iteration k: z_k = M v_k, w = D z_k, two
+// classical Gram-Schmidt passes (the preconditioned direction is nearly in
+// the Krylov space, so the first pass always cancels most of w), ||w||^2,
+// the coefficients to pinned host memory, v_{k+1} = w / ||w||.
+template <class R>
+ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlist, double* vk, double* zk,
+                               double* vk1) {
+  const int m = h->p.outer_restart;
+  const size_t N = h->V24, NC = N / 2;
+  TRY(precond_to_f64<R>(h, vk, zk));
+  TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->fw, 1));
+  double* c1 = h->dots;
+  double* c2 = h->dots + 2 * (m + 2);
+  double* nn = h->dots + 4 * (m + 2);
+  CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c1, h->st));
+  CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
+  CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
+  CK(multi_axpy<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->st));
+  CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
+  CK(cudaMemcpyAsync(h->h_pinned, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(scale_by_inv_norm<double>(h->fw, vk1, nn, N, h->st));
+  return DDAMG_OK;
+}
+
+// Launch iteration k from its CUDA graph (captured on first use, and again
+// whenever buffers moved or kernel timing was switched).
+template <class R>
+ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlist, double* vk, double* zk,
+                           double* vk1) {
+  auto& G = h->graphs[k];
+  if (!G.exec || G.gen != h->gen || G.timing != h->timing) {
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+    for (auto& gt : G.timers) {
+      cudaEventDestroy(gt.t.a);
+      cudaEventDestroy(gt.t.b);
+    }
+    G.timers.clear();
+    const uint64_t l0 = g_launches;
+    uint64_t c0[3] = {h->n_cls[0], h->n_cls[1], h->n_cls[2]};
+    // record on the handle's private stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured); replay on h->st
+    cudaStream_t user = h->st;
+    h->st = h->cap_st;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      h->st = user;
+      CK(e);
+    }
+    h->capture_timers = &G.timers;
+    ddamg_status s = enqueue_iteration<R>(h, k, vlist, vk, zk, vk1);
+    h->capture_timers = nullptr;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->st, &graph);
+    h->st = user;
+    G.launches = g_launches - l0;
+    for (int c = 0; c < 3; ++c) {
+      G.n_cls[c] = h->n_cls[c] - c0[c];
+      h->n_cls[c] = c0[c];
+    }
+    g_launches = l0;
+    if (s != DDAMG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    G.gen = h->gen;
+    G.timing = h->timing;
+  }
+  CK(cudaGraphLaunch(G.exec, h->st));
+  g_launches += G.launches;
+  for (int c = 0; c < 3; ++c) h->n_cls[c] += G.n_cls[c];
+  return DDAMG_OK;
+}
+
+// device time of the timed kernels of graph k's last replay (stream idle)
+void collect_graph(ddamg_ctx* h, int k) {
+  for (auto& gt : h->graphs[k].timers) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, gt.t.a, gt.t.b) == cudaSuccess) h->ms_cls[gt.cls] += ms;
+    else cudaGetLastError();   // a failed query must not surface at the next launch
+  }
 }
 
 template <class R>
@@ -617,38 +757,15 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
     g[0] = beta;
     int kdone = 0;
     for (int k = 0; k < m; ++k) {
-      TRY(precond_to_f64<R>(h, Vk(k), Zk(k)));
+      TRY(run_iteration<R>(h, k, vlist, Vk(k), Zk(k), Vk(k + 1)));
       ++calls;
-      TRY(op_dslash<double>(h, DSLASH_D, Zk(k), nullptr, h->fw, 1));
-      // classical Gram-Schmidt with a second pass only when the first one
-      // cancelled much of w (||w_after|| < ||w_before|| / sqrt 2, "twice is
-      // enough"); the coefficients stay on the device, ||w_before||^2 comes
-      // with the first multi-dot
-      vlist[k + 1] = h->fw;
-      double* c1 = h->dots;
-      double* c2 = h->dots + 2 * (m + 2);
-      double* nn = h->dots + 4 * (m + 2);
-      CK(multi_dot<double>(vlist.data(), k + 2, h->fw, NC, h->red, c1, h->st));
-      CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
-      CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
-      CK(cudaMemcpyAsync(host, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       CK(cudaStreamSynchronize(h->st));
+      collect_graph(h, k);
+      const double* hp = h->h_pinned;
       std::vector<cd> col(k + 2);
-      for (int j = 0; j <= k; ++j) col[j] = cd(host[2 * j], host[2 * j + 1]);
-      double n_before = host[2 * (k + 1)];
-      double n_after = host[4 * (m + 2)];
-      if (n_after < 0.5 * n_before) {
-        CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
-        CK(multi_axpy<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->st));
-        CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
-        CK(cudaMemcpyAsync(host + 2 * (m + 2), c2, (2 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                           h->st));
-        CK(cudaStreamSynchronize(h->st));
-        for (int j = 0; j <= k; ++j) col[j] += cd(host[2 * (m + 2) + 2 * j], host[2 * (m + 2) + 2 * j + 1]);
-        n_after = host[4 * (m + 2)];
-      }
-      vlist[k + 1] = Vk(k + 1);
-      CK(scale_by_inv_norm<double>(h->fw, Vk(k + 1), nn, N, h->st));
+      for (int j = 0; j <= k; ++j)
+        col[j] = cd(hp[2 * j] + hp[2 * (m + 2) + 2 * j], hp[2 * j + 1] + hp[2 * (m + 2) + 2 * j + 1]);
+      const double n_after = hp[4 * (m + 2)];
       const double hn = std::sqrt(n_after);
       if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the FGMRES basis norm");
       col[k + 1] = hn;
@@ -975,7 +1092,7 @@ ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double* rhs, double* x,
   if (nrhs < 0 || (nrhs > 0 && (!rhs || !x))) return fail(h, DDAMG_EINVAL, "bad nrhs / buffers");
   if (!(tol > 0.0)) return fail(h, DDAMG_EINVAL, "tol must be > 0");
   if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "run the setup first");
-  TRY(alloc_outer(h));
+  TRY(prepare_capture(h));
   ddamg_status worst = DDAMG_OK;
   for (int k = 0; k < nrhs; ++k) {
     auto t0 = std::chrono::steady_clock::now();
@@ -1035,9 +1152,10 @@ ddamg_status ddamg_block_solve(ddamg_handle h, int prec, int colour, int nrhs, c
     R* x = (R*)h->tmp[1];
     TRY(import_fields<R>(h, in, on_device, nrhs, b));
     CK(cudaMemsetAsync(x, 0, nrhs * h->V24 * sizeof(R), h->st));
-    ++h->n_sap;
+    ++h->n_cls[1];
     CK(sap_sweep<R>(h->g, colour, h->p.mr_iters, true, b, x, gauge_of<R>(h), clov_of<R>(h, false),
-                    clov_of<R>(h, true), nrhs, h->st));
+                    clov_of<R>(h, true), nrhs, h->d_status, h->st));
+    TRY(check_status(h));
     return export_fields<R>(h, x, nrhs, out, on_device);
   });
 }
@@ -1049,6 +1167,7 @@ ddamg_status ddamg_sap(ddamg_handle h, int prec, int nrhs, const double* in, dou
     TRY(need_tmp(h, nrhs, 6));
     TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[4]));
     TRY(op_sap<R>(h, (R*)h->tmp[4], (R*)h->tmp[5], nrhs));
+    TRY(check_status(h));
     return export_fields<R>(h, (R*)h->tmp[5], nrhs, out, on_device);
   });
 }
@@ -1207,25 +1326,17 @@ ddamg_status ddamg_get_index_maps(ddamg_handle h, int32_t* parity, int32_t* bloc
   return DDAMG_OK;
 }
 
-static double sum_timers(ddamg_ctx* h, std::vector<Timer>& v) {
-  double ms = 0.0;
-  for (auto& t : v) {
-    float f = 0.f;
-    if (cudaEventElapsedTime(&f, t.a, t.b) == cudaSuccess) ms += f;
-  }
-  return ms;
-}
-
 ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   if (!h || !out) return DDAMG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
+  collect_pending(h);
   out->kernel_launches = g_launches - h->launches0;
-  out->dslash_launches = h->n_dslash;
-  out->sap_launches = h->n_sap;
-  out->coarse_launches = h->n_coarse;
-  out->dslash_ms = sum_timers(h, h->tm_dslash);
-  out->sap_ms = sum_timers(h, h->tm_sap);
-  out->coarse_ms = sum_timers(h, h->tm_coarse);
+  out->dslash_launches = h->n_cls[0];
+  out->sap_launches = h->n_cls[1];
+  out->coarse_launches = h->n_cls[2];
+  out->dslash_ms = h->ms_cls[0];
+  out->sap_ms = h->ms_cls[1];
+  out->coarse_ms = h->ms_cls[2];
   out->device_bytes = h->bytes;
   return DDAMG_OK;
 }
@@ -1233,11 +1344,11 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
 ddamg_status ddamg_reset_stats(ddamg_handle h) {
   if (!h) return DDAMG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
+  collect_pending(h);
   h->launches0 = g_launches;
-  h->n_dslash = h->n_sap = h->n_coarse = 0;
-  for (auto* v : {&h->tm_dslash, &h->tm_sap, &h->tm_coarse}) {
-    for (auto& t : *v) h->pool.push_back(t);
-    v->clear();
+  for (int c = 0; c < 3; ++c) {
+    h->n_cls[c] = 0;
+    h->ms_cls[c] = 0.0;
   }
   return DDAMG_OK;
 }
@@ -1267,11 +1378,20 @@ void ddamg_destroy(ddamg_handle h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
-  for (auto* v : {&h->tm_dslash, &h->tm_sap, &h->tm_coarse, &h->pool})
-    for (auto& t : *v) {
-      cudaEventDestroy(t.a);
-      cudaEventDestroy(t.b);
+  collect_pending(h);
+  for (auto& t : h->pool) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto& gph : h->graphs) {
+    if (gph.exec) cudaGraphExecDestroy(gph.exec);
+    for (auto& gt : gph.timers) {
+      cudaEventDestroy(gt.t.a);
+      cudaEventDestroy(gt.t.b);
     }
+  }
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   delete h;
 }
 

@@ -94,10 +94,11 @@ cudaError_t index_maps(const Geom& g, int* parity, int* block, int* colour, cuda
 // one colour of a Schwarz sweep on all blocks of that colour:
 //   r = b - D x (or r = b if x_is_zero), e = MR-even-odd block solve of r,
 //   x += e (x is overwritten with e if x_is_zero)
+// *status receives DDAMG_ETIMEOUT (6) if a bounded wait for staged data gives up
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b,
                       R* x, const R* gauge, const R* clover, const R* clover_inv, int nrhs,
-                      cudaStream_t st);
+                      int* status, cudaStream_t st);
 size_t sap_smem_bytes(const Geom& g, int real_size);
 
 // ---- coarse grid ----------------------------------------------------------------

@@ -11,10 +11,13 @@
 // `per` even and `per` odd coarse sites; its slice of the Krylov basis, of
 // x_e and of the right-hand side stays in shared memory.  Only the vectors a
 // neighbour reads (w and the odd-site temporaries) go through global memory,
-// loaded with ld.cg.  Arnoldi uses classical Gram-Schmidt with one
-// re-orthogonalisation pass; reductions are deterministic (fixed trees).
-// A grid barrier per phase: odd hop, first and second Gram-Schmidt pass,
-// norm -> four per iteration.  Every barrier wait is bounded; on time-out
+// loaded with ld.cg.  Arnoldi orthogonalises with classical Gram-Schmidt:
+// in FP64 with one re-orthogonalisation pass and an explicit norm (four grid
+// barriers per iteration: odd hop, two passes, norm); in FP32 with a single
+// pass whose reduction also carries ||w||^2, the new norm following from
+// Pythagoras (three barriers: odd hop, dots, publication of w), with an
+// explicit norm only when that difference cancels.  Reductions are
+// deterministic (fixed trees).  Every barrier wait is bounded; on time-out
 // the kernel records DDAMG_ETIMEOUT (6) and returns.
 #include <algorithm>
 
@@ -151,7 +154,7 @@ struct CGA {
   cpx<R>* xg;        // [NR][NE][n2]
   unsigned char* lglob;   // per-CTA local arrays when they do not fit in smem
   size_t lstride;         // bytes per CTA in lglob
-  double* part;      // [(MAXM + 1) * NR][G][2]
+  double* part;      // [(MAXM + 2) * NR][G][2]
   unsigned* bar;
   int* iters;
   int* iters_acc;
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   int* tot = reinterpret_cast<int*>(sm + P.tot);          // iterations so far
   int* conv = reinterpret_cast<int*>(sm + P.conv);        // converged (or gave up)
   __shared__ int any_s;
+  __shared__ int exn[NR];      // explicit norm needed (FP32 path)
 
   const int G = gridDim.x;
   const int lo = min(NE, (int)blockIdx.x * a.per);
@@ -354,6 +358,33 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
     __syncthreads();
   };
 
+  // squared norms of wl[r] into the slots after the (kcount x NR) dot slots
+  auto partial_norm_slot = [&](int kcount) {
+    for (int r = wid; r < NR; r += NW) {
+      R sq = 0;
+      if (act[r]) {
+        const cpx<R>* ww = wl + (size_t)r * L;
+        for (int e = lane; e < Lo; e += 32) sq += norm2(ww[e]);
+      }
+      sq = wsum(sq);
+      if (lane == 0) {
+        const size_t pr = (size_t)kcount * NR + r;
+        a.part[(pr * G + blockIdx.x) * 2] = (double)sq;
+        a.part[(pr * G + blockIdx.x) * 2 + 1] = 0.0;
+      }
+    }
+  };
+  auto gather_norm_slot = [&](int kcount, A* dst) {
+    for (int r = wid; r < NR; r += NW) {
+      const size_t pr = (size_t)kcount * NR + r;
+      A sq = 0;
+      for (int c = lane; c < G; c += 32) sq += (A)__ldcg(a.part + (pr * G + c) * 2);
+      sq = wsum(sq);
+      if (lane == 0) dst[r] = sq;
+    }
+    __syncthreads();
+  };
+
   for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
     const int nr = min(NR, a.nrhs - r0);
     const cpx<R>* bb = a.b + (size_t)r0 * a.g.nb * n2;
@@ -428,40 +459,89 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         phase_odd(a.wg);
         if (!grid_barrier(a.bar, a.status)) return;
         phase_even(V + (size_t)k * NR * L, true, wl, nullptr);
-        for (int pass = 0; pass < 2; ++pass) {
+        if constexpr (sizeof(R) == 4) {
+          // FP32: one classical Gram-Schmidt pass whose reduction also carries
+          // ||w||^2, so ||w_new||^2 = ||w||^2 - sum_j |h_j|^2 (Pythagoras); an
+          // explicit norm is taken only if that difference has cancelled
           partial(k + 1, false);
+          partial_norm_slot(k + 1);
           if (!grid_barrier(a.bar, a.status)) return;
-          A* hh = pass == 0 ? hc : h2;
-          gather(k + 1, false, hh, 2 * (m + 1));
+          gather(k + 1, false, hc, 2 * (m + 1));
+          gather_norm_slot(k + 1, hnv);
+          if (tx < NR) {
+            const A* hr = hc + (size_t)tx * 2 * (m + 1);
+            A s2 = hnv[tx];
+            for (int j = 0; j <= k; ++j) s2 -= hr[2 * j] * hr[2 * j] + hr[2 * j + 1] * hr[2 * j + 1];
+            exn[tx] = (act[tx] && !(s2 > A(1e-3) * hnv[tx])) ? 1 : 0;
+            hnv[tx] = s2 > A(0) ? s2 : A(0);
+          }
+          __syncthreads();
           for (int idx = tx; idx < NR * Lo; idx += TPB) {
             const int r = idx / Lo, e = idx - r * Lo;
             if (!act[r]) continue;
             cpx<R> w0 = wl[(size_t)r * L + e];
-            const A* hr = hh + (size_t)r * 2 * (m + 1);
+            const A* hr = hc + (size_t)r * 2 * (m + 1);
             for (int j = 0; j <= k; ++j) {
               cpx<R> v = Vk(j, r)[e];
               cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
               w0 = w0 - c * v;
             }
             wl[(size_t)r * L + e] = w0;
-            if (pass == 1) a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
+            a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
           }
-          if (pass == 1 && tx < NR)
-            for (int j = 0; j <= k; ++j) {
-              hc[(size_t)tx * 2 * (m + 1) + 2 * j] += h2[(size_t)tx * 2 * (m + 1) + 2 * j];
-              hc[(size_t)tx * 2 * (m + 1) + 2 * j + 1] += h2[(size_t)tx * 2 * (m + 1) + 2 * j + 1];
-            }
+          if (tx == 0) {
+            int any = 0;
+            for (int r = 0; r < NR; ++r) any |= exn[r];
+            any_s = any;
+          }
           __syncthreads();
+          // this barrier publishes the neighbours' w for the next odd phase
+          if (any_s) {
+            partial(1, true);
+            if (!grid_barrier(a.bar, a.status)) return;
+            gather(1, true, h2, 1);
+            if (tx < NR && exn[tx]) hnv[tx] = h2[tx];
+            __syncthreads();
+          } else {
+            if (!grid_barrier(a.bar, a.status)) return;
+          }
+        } else {
+          // FP64: classical Gram-Schmidt with one re-orthogonalisation pass
+          for (int pass = 0; pass < 2; ++pass) {
+            partial(k + 1, false);
+            if (!grid_barrier(a.bar, a.status)) return;
+            A* hh = pass == 0 ? hc : h2;
+            gather(k + 1, false, hh, 2 * (m + 1));
+            for (int idx = tx; idx < NR * Lo; idx += TPB) {
+              const int r = idx / Lo, e = idx - r * Lo;
+              if (!act[r]) continue;
+              cpx<R> w0 = wl[(size_t)r * L + e];
+              const A* hr = hh + (size_t)r * 2 * (m + 1);
+              for (int j = 0; j <= k; ++j) {
+                cpx<R> v = Vk(j, r)[e];
+                cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
+                w0 = w0 - c * v;
+              }
+              wl[(size_t)r * L + e] = w0;
+              if (pass == 1) a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
+            }
+            if (pass == 1 && tx < NR)
+              for (int j = 0; j <= k; ++j) {
+                hc[(size_t)tx * 2 * (m + 1) + 2 * j] += h2[(size_t)tx * 2 * (m + 1) + 2 * j];
+                hc[(size_t)tx * 2 * (m + 1) + 2 * j + 1] += h2[(size_t)tx * 2 * (m + 1) + 2 * j + 1];
+              }
+            __syncthreads();
+          }
+          // ||w||: this barrier also publishes the neighbours' w for the next odd phase
+          partial(1, true);
+          if (!grid_barrier(a.bar, a.status)) return;
+          gather(1, true, hnv, 1);
         }
-        // ||w||: this barrier also publishes the neighbours' w for the next odd phase
-        partial(1, true);
-        if (!grid_barrier(a.bar, a.status)) return;
-        gather(1, true, hnv, 1);
         // Givens per right-hand side (thread r), V_{k+1} = w / h
         if (tx < NR && act[tx]) {
           const int r = tx;
           const A hn = sqrt(hnv[r]);
-          A* col = hc + (size_t)r * 2 * (m + 1);
+          A* col = hc + (size_t)r * 2 * (m + 1);   // this column of the Hessenberg matrix
           col[2 * (k + 1)] = hn;
           col[2 * (k + 1) + 1] = A(0);
           A* csr = cs + (size_t)r * m;
@@ -622,8 +702,46 @@ struct Choice {
   Plan plan;
 };
 
+// current dynamic shared-memory limit of each kernel instance, so that the
+// attribute is set only when it changes
+template <class R>
+cudaError_t smem_attr(int NR, size_t bytes) {
+  static size_t current[4] = {0, 0, 0, 0};
+  size_t& c = current[NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : 3];
+  if (c == bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel_for<R>(NR), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
+template <class R>
+Choice choose_uncached(const Geom& g, int n2, int m, int nrhs);
+
+// launch configurations are cached: the occupancy queries behind them cost
+// far more host time than a coarse solve's launch
 template <class R>
 Choice choose(const Geom& g, int n2, int m, int nrhs) {
+  struct Entry {
+    int dev, nb, n2, m, first;
+    Choice c;
+  };
+  static Entry cache[16];
+  static int used = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int first = nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+  for (int i = 0; i < used; ++i) {
+    const Entry& e = cache[i];
+    if (e.dev == dev && e.nb == g.nb && e.n2 == n2 && e.m == m && e.first == first) return e.c;
+  }
+  Choice c = choose_uncached<R>(g, n2, m, nrhs);
+  Entry e{dev, g.nb, n2, m, first, c};
+  cache[used < 16 ? used++ : (dev + g.nb + first) % 16] = e;
+  return c;
+}
+
+template <class R>
+Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -640,7 +758,7 @@ Choice choose(const Geom& g, int n2, int m, int nrhs) {
         if (p.bytes > SMEM_BUDGET) break;
         int occ = 0;
         const void* fn = kernel_for<R>(NR);
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.bytes);
+        if (smem_attr<R>(NR, p.bytes) != cudaSuccess) break;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, p.bytes);
         if (occ < 1) break;
         if (G <= occ * sms) return Choice{NR, G, per, local, p};
@@ -659,7 +777,7 @@ size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs) {
   if (ch.NR == 0) return 0;
   const size_t NE = g.nb / 2, n2 = 2 * n;
   size_t bytes = al16(3 * (size_t)NRMAX * NE * n2 * sizeof(cpx<R>));
-  bytes += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  bytes += al16((size_t)(MAXM + 2) * NRMAX * NE * 2 * sizeof(double));
   bytes += 256;
   if (!ch.local) bytes += (size_t)ch.G * al16(ch.plan.local_bytes);
   return bytes;
@@ -673,7 +791,7 @@ size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size)
   const size_t NE = g.nb / 2, n2 = 2 * n;
   const size_t vec = NRMAX * NE * n2 * 2 * (size_t)real_size;
   size_t bytes = al16(3 * vec);
-  bytes += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  bytes += al16((size_t)(MAXM + 2) * NRMAX * NE * 2 * sizeof(double));
   bytes += 256;
   bytes += al16((size_t)(restart + 4) * NRMAX * 2 * NE * n2 * 2 * real_size + 64 * NE);
   return bytes;
@@ -709,7 +827,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.xg = a.to + vec;
   size_t off = al16(3 * vec * sizeof(cpx<R>));
   a.part = reinterpret_cast<double*>(w8 + off);
-  off += al16((size_t)(MAXM + 1) * NRMAX * NE * 2 * sizeof(double));
+  off += al16((size_t)(MAXM + 2) * NRMAX * NE * 2 * sizeof(double));
   a.bar = reinterpret_cast<unsigned*>(w8 + off);
   off += 256;
   a.lglob = w8 + off;
@@ -720,10 +838,20 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const void* fn = kernel_for<R>(ch.NR);
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ch.plan.bytes);
+  e = smem_attr<R>(ch.NR, ch.plan.bytes);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
-  e = cudaLaunchCooperativeKernel(fn, dim3(ch.G), dim3(TPB), args, ch.plan.bytes, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ch.G);
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = ch.plan.bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs co-resident (grid barrier)
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelExC(&cfg, fn, args);
   ++g_launches;
   return e;
 }

@@ -45,69 +45,72 @@ __device__ __forceinline__ void block_sum2_all(double& a, double& b, double* sh)
 }
 
 // ---------------------------------------------------------------------------
-// orthonormalisation: CTA per (aggregate, chirality), thread per site
+// orthonormalisation: CTA per (aggregate, chirality), thread per site.
+// Classical Gram-Schmidt, two passes, FP64: for vector i every thread forms
+// its partial products with all earlier vectors j < i at once, and the CTA
+// reduces the i coefficients together (one barrier per pass, not per j).
 // ---------------------------------------------------------------------------
 __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
-  extern __shared__ double osh[];          // [2 * warps] + [2 * n] coefficients
+  extern __shared__ double osh[];          // red [warps][n][2], coef [n][2]
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
   double* red = osh;
-  double* coef = osh + 2 * (blockDim.x >> 5);
+  double* coef = osh + (size_t)2 * nw * n;
   const int X = blockIdx.x, s = blockIdx.y;
   const size_t fstride = (size_t)g.V * SPINOR_NR;
   using LY = Layout<double, SPINOR_NR>;
+  const int q = threadIdx.x;
+  const bool own = q < g.Vb;
+  const size_t b = LY::base(X * g.Vb + (own ? q : 0), g.Vb);
+  auto at = [&](int j, int u) -> double2* {
+    return reinterpret_cast<double2*>(lam + j * fstride) + b + (size_t)(6 * s + u) * g.Vb;
+  };
   for (int i = 0; i < n; ++i) {
-    for (int pass = 0; pass < 2; ++pass) {
-      // coefficients <lambda_j, lambda_i> for j < i, from the same lambda_i
+    double2 v[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) v[u] = own ? *at(i, u) : make_double2(0.0, 0.0);
+    for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
         double re = 0.0, im = 0.0;
-        for (int q = threadIdx.x; q < g.Vb; q += blockDim.x) {
-          size_t b = LY::base(X * g.Vb + q, g.Vb);
-          for (int u = 6 * s; u < 6 * s + 6; ++u) {
-            double2 a = reinterpret_cast<const double2*>(lam + j * fstride)[b + (size_t)u * g.Vb];
-            double2 c = reinterpret_cast<const double2*>(lam + i * fstride)[b + (size_t)u * g.Vb];
-            re += a.x * c.x + a.y * c.y;
-            im += a.x * c.y - a.y * c.x;
+        if (own) {
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            double2 a = *at(j, u);
+            re += a.x * v[u].x + a.y * v[u].y;
+            im += a.x * v[u].y - a.y * v[u].x;
           }
         }
-        block_sum2_all(re, im, red);
-        if (threadIdx.x == 0) { coef[2 * j] = re; coef[2 * j + 1] = im; }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (l == 0) { red[(w * n + j) * 2] = re; red[(w * n + j) * 2 + 1] = im; }
       }
       __syncthreads();
-      for (int q = threadIdx.x; q < g.Vb; q += blockDim.x) {
-        size_t b = LY::base(X * g.Vb + q, g.Vb);
-        for (int u = 6 * s; u < 6 * s + 6; ++u) {
-          double2* pi = reinterpret_cast<double2*>(lam + i * fstride) + b + (size_t)u * g.Vb;
-          double2 v = *pi;
-          for (int j = 0; j < i; ++j) {
-            double2 a = reinterpret_cast<const double2*>(lam + j * fstride)[b + (size_t)u * g.Vb];
-            double cr = coef[2 * j], ci = coef[2 * j + 1];
-            v.x -= cr * a.x - ci * a.y;
-            v.y -= cr * a.y + ci * a.x;
-          }
-          *pi = v;
-        }
+      for (int j = threadIdx.x; j < i; j += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int ww = 0; ww < nw; ++ww) { re += red[(ww * n + j) * 2]; im += red[(ww * n + j) * 2 + 1]; }
+        coef[2 * j] = re;
+        coef[2 * j + 1] = im;
       }
+      __syncthreads();
+      if (own)
+        for (int j = 0; j < i; ++j) {
+          const double cr = coef[2 * j], ci = coef[2 * j + 1];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            double2 a = *at(j, u);
+            v[u].x -= cr * a.x - ci * a.y;
+            v[u].y -= cr * a.y + ci * a.x;
+          }
+        }
       __syncthreads();
     }
     double nn = 0.0, dummy = 0.0;
-    for (int q = threadIdx.x; q < g.Vb; q += blockDim.x) {
-      size_t b = LY::base(X * g.Vb + q, g.Vb);
-      for (int u = 6 * s; u < 6 * s + 6; ++u) {
-        double2 v = reinterpret_cast<const double2*>(lam + i * fstride)[b + (size_t)u * g.Vb];
-        nn += v.x * v.x + v.y * v.y;
-      }
-    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) nn += v[u].x * v[u].x + v[u].y * v[u].y;
     block_sum2_all(nn, dummy, red);
-    double f = 1.0 / sqrt(nn);
-    for (int q = threadIdx.x; q < g.Vb; q += blockDim.x) {
-      size_t b = LY::base(X * g.Vb + q, g.Vb);
-      for (int u = 6 * s; u < 6 * s + 6; ++u) {
-        double2* pi = reinterpret_cast<double2*>(lam + i * fstride) + b + (size_t)u * g.Vb;
-        double2 v = *pi;
-        v.x *= f;
-        v.y *= f;
-        *pi = v;
-      }
-    }
+    const double f = 1.0 / sqrt(nn);
+    if (own)
+#pragma unroll
+      for (int u = 0; u < 6; ++u) *at(i, u) = make_double2(v[u].x * f, v[u].y * f);
     __syncthreads();
   }
 }
@@ -509,8 +512,8 @@ __global__ void k_conv_c(const RS* __restrict__ s, RD* __restrict__ d, size_t n)
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st) {
-  int threads = g.Vb >= 256 ? 256 : ((g.Vb + 31) / 32) * 32;
-  size_t smem = (2 * (threads / 32) + 2 * n) * sizeof(double);
+  int threads = ((g.Vb + 31) / 32) * 32;
+  size_t smem = ((size_t)2 * (threads / 32) * (n > 1 ? n : 1) + 2 * n) * sizeof(double);
   k_orthonormalise<<<dim3(g.nb, 2), threads, smem, st>>>(g, lam, n);
   ++g_launches;
   return cudaGetLastError();

@@ -428,6 +428,9 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(const double* __restri
 template <class R>
 __global__ void k_multi_axpy(PtrList<R> v, int k, const double* __restrict__ coef, double sign,
                              R* __restrict__ w, size_t n) {
+  __shared__ double cs[2 * MAXK];            // signed coefficients, loaded once per CTA
+  for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) cs[j] = sign * coef[j];
+  __syncthreads();
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   cpx<R>* wc = reinterpret_cast<cpx<R>*>(w);
@@ -435,9 +438,9 @@ __global__ void k_multi_axpy(PtrList<R> v, int k, const double* __restrict__ coe
     double re = wc[i].re, im = wc[i].im;
     for (int j = 0; j < k; ++j) {
       cpx<R> a = reinterpret_cast<const cpx<R>*>(v.p[j])[i];
-      double cr = sign * coef[2 * j], ci = sign * coef[2 * j + 1];
-      re += cr * (double)a.re - ci * (double)a.im;
-      im += cr * (double)a.im + ci * (double)a.re;
+      const double cr = cs[2 * j], ci = cs[2 * j + 1];
+      re = ::fma(cr, (double)a.re, ::fma(-ci, (double)a.im, re));
+      im = ::fma(cr, (double)a.im, ::fma(ci, (double)a.re, im));
     }
     wc[i] = mk((R)re, (R)im);
   }
@@ -452,7 +455,10 @@ __global__ void k_axpby(double a, const R* __restrict__ x, double b, R* __restri
 
 template <class R>
 __global__ void k_scale_inv_norm(const R* __restrict__ x, R* __restrict__ y, const double* s, size_t n) {
-  double f = 1.0 / sqrt(s[0]);
+  __shared__ double fs;                      // 1/sqrt(s) once per CTA (FP64 division is scarce)
+  if (threadIdx.x == 0) fs = 1.0 / sqrt(s[0]);
+  __syncthreads();
+  const double f = fs;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (; i < n; i += stride) y[i] = (R)((double)x[i] * f);

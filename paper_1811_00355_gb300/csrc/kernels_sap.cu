@@ -558,7 +558,7 @@ __device__ __forceinline__ f2 psum(const f2* P, int Vh, int k, int h) {
 __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_iters, int x_is_zero,
                                                   const float* __restrict__ b, float* __restrict__ x,
                                                   const float* __restrict__ gauge, const float* __restrict__ clov,
-                                                  const float* __restrict__ clov_inv) {
+                                                  const float* __restrict__ clov_inv, int* status) {
   using LYG = Layout<float, GAUGE_NR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
@@ -581,19 +581,32 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
   const int cb = sub >> 1, half = sub & 1;
   const int de = B * Vb + h, dO = B * Vb + Vh + h;
 
-  // stage links, A_ee and A_oo^-1 of the block
+  // stage the block's links, A_ee and A_oo^-1 with bulk asynchronous copies
+  // (one row of Vb or Vh 16-byte units each); they land while the residual,
+  // which reads global memory only, is computed
+  __shared__ __align__(8) uint64_t mbar;
+  if (t == 0) {
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
   {
-    const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
-    for (int i = t; i < LYG::NU * Vb; i += blockDim.x) {
-      int u = i / Vb, q = i - u * Vb;
-      sl[u * Vbp + q] = __ldg(src + i);
-    }
-    const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
-    const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
-    for (int i = t; i < 18 * Vh; i += blockDim.x) {
-      int u = i / Vh, hh = i - u * Vh;
-      Aee[i] = __ldg(ca + (size_t)u * Vb + hh);
-      Aoi[i] = __ldg(ci + (size_t)u * Vb + Vh + hh);
+    // 12 link rows + 18 A_ee rows + 18 A_oo^-1 rows, one copy per thread;
+    // the expected byte count is registered by thread 0 before any copy
+    const unsigned link_row = (unsigned)Vb * 16u, half_row = (unsigned)Vh * 16u;
+    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + 36u * half_row);
+    __syncthreads();
+    if (t < LYG::NU) {
+      const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
+      bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
+    } else if (t < LYG::NU + 18) {
+      const int u = t - LYG::NU;
+      const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
+      bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
+    } else if (t < LYG::NU + 36) {
+      const int u = t - LYG::NU - 18;
+      const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
+      bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
     }
   }
 
@@ -622,6 +635,16 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
         else re[i] = re[i] - v;
       }
       __syncthreads();
+    }
+  }
+  // the staged block must have landed (bounded wait; on time-out record
+  // DDAMG_ETIMEOUT, wait again for the copies in flight, and leave x alone)
+  {
+    const bool ok = mbar_wait_bounded(&mbar, 0, MBAR_POLL_LIMIT);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicExch(status, 6);
+      mbar_wait_bounded(&mbar, 0, MBAR_POLL_LIMIT);
+      return;
     }
   }
   // u_o = A_oo^-1 r_o
@@ -748,37 +771,38 @@ static size_t sap_fast_smem(const Geom& g) {
 
 static bool sap_fast_ok(const Geom& g) {
   const int Vh = g.Vb / 2;
-  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_fast_smem(g) <= 227 * 1024;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_fast_smem(g) <= 226 * 1024;
 }
 
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,
-                      const R* gauge, const R* clover, const R* clover_inv, int nrhs,
+                      const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
                       cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (sap_fast_ok(g)) {
-      static bool cfg = false;
-      if (!cfg) {
+      static size_t cfg = 0;
+      const size_t need = sap_fast_smem(g);
+      if (cfg < need) {
         cudaError_t e = cudaFuncSetAttribute(fast::k_sap_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+                                             (int)need);
         if (e != cudaSuccess) return e;
-        cfg = true;
+        cfg = need;
       }
       dim3 grid(g.nb / 2, nrhs);
       fast::k_sap_fast<<<grid, 2 * g.Vb, sap_fast_smem(g), st>>>(g, colour, mr_iters, x_is_zero ? 1 : 0, b, x,
-                                                                 gauge, clover, clover_inv);
+                                                                 gauge, clover, clover_inv, status);
       ++g_launches;
       return cudaGetLastError();
     }
   }
   int threads = sap_threads(g);
   size_t smem = sap_smem_bytes(g, sizeof(R));
-  static bool configured[2] = {false, false};
+  static size_t configured[2] = {0, 0};
   cudaError_t e;
-  if (!configured[sizeof(R) == 8]) {
-    e = cudaFuncSetAttribute(k_sap_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (configured[sizeof(R) == 8] < smem) {
+    e = cudaFuncSetAttribute(k_sap_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured[sizeof(R) == 8] = true;
+    configured[sizeof(R) == 8] = smem;
   }
   dim3 grid(g.nb / 2, nrhs);
   k_sap_sweep<R><<<grid, threads, smem, st>>>(g, colour, mr_iters, x_is_zero ? 1 : 0, b, x, gauge,
@@ -788,8 +812,8 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
 }
 
 template cudaError_t sap_sweep<float>(const Geom&, int, int, bool, const float*, float*, const float*,
-                                      const float*, const float*, int, cudaStream_t);
+                                      const float*, const float*, int, int*, cudaStream_t);
 template cudaError_t sap_sweep<double>(const Geom&, int, int, bool, const double*, double*,
-                                       const double*, const double*, const double*, int, cudaStream_t);
+                                       const double*, const double*, const double*, int, int*, cudaStream_t);
 
 }  // namespace ddamg
