@@ -40,6 +40,13 @@ WORKLOAD = dict(L=(16, 16, 16, 16), block=(4, 4, 4, 4), eps=0.25, seed=1, m0=-0.
 # operator once (self + 8 links on every site) plus A_oo^-1 on the odd sites.
 SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
 L2_BYTES = 129 * 2 ** 20
+# stencil bandwidth lattice: 32^3 x 64 (the lattice of the batched workload),
+# far larger than L2, links tiled from an 8^4 field of the same generator
+STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
+               n_v=24, reps=20)
+# compulsory bytes per site of one fine D apply: in and out spinor (24 reals
+# each), four two-row links (12 reals each), packed clover A (72 reals)
+D_REALS_PER_SITE = 24 + 24 + 4 * 12 + 72
 # outer-solver preconditioner calls of this workload (12 point sources), as
 # measured on the CUDA path; used only to scale the reference arm's sample
 REFERENCE_PRECOND_CALLS = 12 * 12
@@ -227,6 +234,10 @@ def run_ours(args):
         e2e = {"value": round(12 / statistics.mean(et) * world, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(U_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
 
+    sten = None
+    if rank == 0 and not args.no_stencils:
+        sten = stencils(P, torch, stream, pk, pk_kind)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         counts = {"precond_calls": sum(i["precond_calls"] for i in infos[-1])}
@@ -249,10 +260,74 @@ def run_ours(args):
                             "max_true_residual": max(i["true_residual"] for info in infos for i in info),
                             "step_seconds": [round(t, 4) for t in times]},
             "kernel_ms": {k: round(v[0], 3) for k, v in classes.items()},
+            "stencils": sten,
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _tiled(a, small, L):
+    """Periodic tiling of a per-site array of the small lattice onto L."""
+    sx, sy, sz, st = small
+    inner = a.shape[1:]
+    a = a.reshape((st, sz, sy, sx) + inner)
+    a = np.tile(a, (L[3] // st, L[2] // sz, L[1] // sy, L[0] // sx) + (1,) * len(inner))
+    return np.ascontiguousarray(a.reshape((-1,) + inner))
+
+
+def stencils(P, torch, stream, pk, pk_kind):
+    """Achieved HBM bandwidth of the fine D (FP32, FP64) and of the coarse
+    9-point stencil (FP32) on a lattice far larger than L2, from the
+    library's own per-kernel CUDA-event timing."""
+    import synthetic as syn
+    s = STENCIL
+    L = s["L"]
+    V = int(np.prod(L))
+    U = torch.from_numpy(_tiled(syn.gauge_field(s["tile"], s["eps"], s["seed"]), s["tile"], L)).cuda()
+    x = torch.from_numpy(_tiled(syn.gaussian_spinors(1, s["tile"], s["seed"] + 1)[0], s["tile"], L)).cuda()
+    params = P.default_params(L=L, sap_block=s["block"], n_v=s["n_v"], m0=s["m0"], csw=s["csw"],
+                              setup_iters=0, precision=P.FP32, seed=777)
+    h = P.DDAMG(params, U, stream=stream.cuda_stream)
+    out = {"lattice": "x".join(map(str, L)), "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind + " (burst copy)",
+           "timing": "CUDA events around each kernel launch, %d launches after warm-up" % s["reps"]}
+    try:
+        for name, prec, rs in (("dslash_f32", P.FP32, 4), ("dslash_f64", P.FP64, 8)):
+            for _ in range(3):
+                h.apply_D(x, prec)
+            h.reset_stats()
+            h.enable_kernel_timing(True)
+            for _ in range(s["reps"]):
+                h.apply_D(x, prec)
+            st = h.stats()
+            h.enable_kernel_timing(False)
+            us = 1e3 * st["dslash_ms"] / st["dslash_launches"]
+            byts = V * D_REALS_PER_SITE * rs
+            gbs = byts / (us * 1e-6) / 1e9
+            out[name] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
+                         "frac": round(gbs / pk["hbm_gbs"], 4)}
+        del x
+        h.run_setup()                      # device-drawn test vectors, SAP, orthonormalise, D_c
+        n2 = 2 * s["n_v"]
+        nx = h.NX
+        gen = np.random.default_rng(s["seed"] + 2)
+        xc = torch.from_numpy(gen.standard_normal((nx, n2)) + 1j * gen.standard_normal((nx, n2))).cuda()
+        for _ in range(3):
+            h.apply_coarse(xc, P.FP32)
+        h.reset_stats()
+        h.enable_kernel_timing(True)
+        for _ in range(s["reps"]):
+            h.apply_coarse(xc, P.FP32)
+        st = h.stats()
+        h.enable_kernel_timing(False)
+        us = 1e3 * st["coarse_apply_ms"] / st["coarse_apply_launches"]
+        byts = nx * (9 * n2 * n2 + 2 * n2) * 8
+        gbs = byts / (us * 1e-6) / 1e9
+        out["coarse_f32"] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
+                             "frac": round(gbs / pk["hbm_gbs"], 4), "n_v": s["n_v"]}
+    finally:
+        h.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -343,6 +418,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stencils", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -121,6 +121,8 @@ typedef struct {
   uint64_t coarse_launches;   /* launches of the coarse GMRES kernel         */
   double coarse_ms;
   size_t device_bytes;        /* device memory held by the handle            */
+  uint64_t coarse_apply_launches; /* launches of the coarse 9-point stencil  */
+  double coarse_apply_ms;         /* (ddamg_apply_coarse) and their time     */
 } ddamg_stats;
 
 /* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,

@@ -56,6 +56,7 @@ class Stats(C.Structure):
         ("kernel_launches", C.c_uint64), ("dslash_launches", C.c_uint64), ("dslash_ms", C.c_double),
         ("sap_launches", C.c_uint64), ("sap_ms", C.c_double),
         ("coarse_launches", C.c_uint64), ("coarse_ms", C.c_double), ("device_bytes", C.c_size_t),
+        ("coarse_apply_launches", C.c_uint64), ("coarse_apply_ms", C.c_double),
     ]
 
     def as_dict(self):

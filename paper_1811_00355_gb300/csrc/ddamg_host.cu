@@ -25,6 +25,7 @@ using cd = std::complex<double>;
 namespace {
 
 constexpr uint32_t NEG = 0x80000000u;
+constexpr int NCLS = 4;               // kernel timing classes
 
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -96,8 +97,9 @@ struct ddamg_ctx {
   // and device time; timers recorded outside graphs wait in `pending`
   bool timing = false;
   uint64_t launches0 = 0;
-  uint64_t n_cls[3] = {0, 0, 0};
-  double ms_cls[3] = {0.0, 0.0, 0.0};
+  // timing classes: 0 fine D, 1 SAP sweep, 2 coarse GMRES, 3 coarse stencil
+  uint64_t n_cls[NCLS] = {0, 0, 0, 0};
+  double ms_cls[NCLS] = {0.0, 0.0, 0.0, 0.0};
   std::vector<std::pair<int, Timer>> pending;
   std::vector<Timer> pool;
 
@@ -110,7 +112,7 @@ struct ddamg_ctx {
     cudaGraphExec_t exec = nullptr;
     std::vector<GraphTimer> timers;
     uint64_t launches = 0;
-    uint64_t n_cls[3] = {0, 0, 0};
+    uint64_t n_cls[NCLS] = {0, 0, 0, 0};
     int gen = -1;
     bool timing = false;
   };
@@ -651,8 +653,7 @@ ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& 
   CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c1, h->st));
   CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
   CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
-  CK(multi_axpy<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->st));
-  CK(norm2<double>(h->fw, NC, h->red, nn, h->st));
+  CK(multi_axpy_norm<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->red, nn, h->st));
   CK(cudaMemcpyAsync(h->h_pinned, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(scale_by_inv_norm<double>(h->fw, vk1, nn, N, h->st));
   return DDAMG_OK;
@@ -675,7 +676,8 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     }
     G.timers.clear();
     const uint64_t l0 = g_launches;
-    uint64_t c0[3] = {h->n_cls[0], h->n_cls[1], h->n_cls[2]};
+    uint64_t c0[NCLS];
+    for (int c = 0; c < NCLS; ++c) c0[c] = h->n_cls[c];
     // record on the handle's private stream (the caller's stream may be the
     // legacy default stream, which cannot be captured); replay on h->st
     cudaStream_t user = h->st;
@@ -692,7 +694,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     e = cudaStreamEndCapture(h->st, &graph);
     h->st = user;
     G.launches = g_launches - l0;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NCLS; ++c) {
       G.n_cls[c] = h->n_cls[c] - c0[c];
       h->n_cls[c] = c0[c];
     }
@@ -710,7 +712,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
   }
   CK(cudaGraphLaunch(G.exec, h->st));
   g_launches += G.launches;
-  for (int c = 0; c < 3; ++c) h->n_cls[c] += G.n_cls[c];
+  for (int c = 0; c < NCLS; ++c) h->n_cls[c] += G.n_cls[c];
   return DDAMG_OK;
 }
 
@@ -1259,7 +1261,9 @@ ddamg_status ddamg_apply_coarse(ddamg_handle h, int prec, int nrhs, const double
     TRY(need_tmp(h, nrhs, 6));
     size_t nc = (size_t)nrhs * h->g.nb * h->n2;
     TRY(coarse_in<R>(h, in, on_device, nc, (R*)h->tmp[0]));
-    CK(coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st));
+    CK(timed(h, 3, [&] {
+      return coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st);
+    }));
     return coarse_out<R>(h, (R*)h->tmp[1], nc, out, on_device);
   });
 }
@@ -1338,6 +1342,8 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   out->sap_ms = h->ms_cls[1];
   out->coarse_ms = h->ms_cls[2];
   out->device_bytes = h->bytes;
+  out->coarse_apply_launches = h->n_cls[3];
+  out->coarse_apply_ms = h->ms_cls[3];
   return DDAMG_OK;
 }
 
@@ -1346,7 +1352,7 @@ ddamg_status ddamg_reset_stats(ddamg_handle h) {
   CK(cudaStreamSynchronize(h->st));
   collect_pending(h);
   h->launches0 = g_launches;
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < NCLS; ++c) {
     h->n_cls[c] = 0;
     h->ms_cls[c] = 0.0;
   }

@@ -77,6 +77,10 @@ cudaError_t norm2(const R* w, size_t n, double* scratch, double* out, cudaStream
 template <class R>
 cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign, R* w,
                        size_t n, cudaStream_t st);
+// multi_axpy, then out[0] = ||w||^2 of the updated w (scratch as multi_dot)
+template <class R>
+cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
+                            double* scratch, double* out, cudaStream_t st);
 // y = a x + b y (real scalars)
 template <class R>
 cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t st);

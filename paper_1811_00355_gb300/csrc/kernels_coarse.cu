@@ -44,12 +44,28 @@ __device__ __forceinline__ void block_sum2_all(double& a, double& b, double* sh)
   __syncthreads();
 }
 
+// sum of (a, b) over a warp with five FP64 additions per lane instead of ten:
+// the halves trade one value each first.  Lane 0 returns the sum of a, lane
+// 16 the sum of b.
+__device__ __forceinline__ double warp_sum_pair(double a, double b) {
+  const bool up = (threadIdx.x & 16) != 0;
+  double keep = up ? b : a;
+  keep += __shfl_xor_sync(0xffffffffu, up ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return keep;
+}
+
 // ---------------------------------------------------------------------------
-// orthonormalisation: CTA per (aggregate, chirality), thread per site.
+// orthonormalisation: CTA per (aggregate, chirality), two sites per thread.
 // Classical Gram-Schmidt, two passes, FP64: for vector i every thread forms
 // its partial products with all earlier vectors j < i at once, and the CTA
 // reduces the i coefficients together (one barrier per pass, not per j).
+// Two sites per thread halve the share of FP64 additions spent in the
+// cross-thread sums, FP64 being GB300's scarce arithmetic.
 // ---------------------------------------------------------------------------
+constexpr int ORTHO_SITES = 2;
+
 __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
   extern __shared__ double osh[];          // red [warps][n][2], coef [n][2]
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -58,30 +74,39 @@ __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
   const int X = blockIdx.x, s = blockIdx.y;
   const size_t fstride = (size_t)g.V * SPINOR_NR;
   using LY = Layout<double, SPINOR_NR>;
-  const int q = threadIdx.x;
-  const bool own = q < g.Vb;
-  const size_t b = LY::base(X * g.Vb + (own ? q : 0), g.Vb);
-  auto at = [&](int j, int u) -> double2* {
-    return reinterpret_cast<double2*>(lam + j * fstride) + b + (size_t)(6 * s + u) * g.Vb;
+  bool own[ORTHO_SITES];
+  size_t base[ORTHO_SITES];
+#pragma unroll
+  for (int e = 0; e < ORTHO_SITES; ++e) {
+    const int q = threadIdx.x + e * blockDim.x;
+    own[e] = q < g.Vb;
+    base[e] = LY::base(X * g.Vb + (own[e] ? q : 0), g.Vb) + (size_t)6 * s * g.Vb;
+  }
+  auto at = [&](int j, int e, int u) -> double2* {
+    return reinterpret_cast<double2*>(lam + j * fstride) + base[e] + (size_t)u * g.Vb;
   };
   for (int i = 0; i < n; ++i) {
-    double2 v[6];
+    double2 v[ORTHO_SITES][6];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) v[u] = own ? *at(i, u) : make_double2(0.0, 0.0);
+    for (int e = 0; e < ORTHO_SITES; ++e)
+#pragma unroll
+      for (int u = 0; u < 6; ++u) v[e][u] = own[e] ? *at(i, e, u) : make_double2(0.0, 0.0);
     for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
         double re = 0.0, im = 0.0;
-        if (own) {
 #pragma unroll
-          for (int u = 0; u < 6; ++u) {
-            double2 a = *at(j, u);
-            re += a.x * v[u].x + a.y * v[u].y;
-            im += a.x * v[u].y - a.y * v[u].x;
+        for (int e = 0; e < ORTHO_SITES; ++e) {
+          if (own[e]) {
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              const double2 a = *at(j, e, u);
+              re = ::fma(a.x, v[e][u].x, ::fma(a.y, v[e][u].y, re));
+              im = ::fma(a.x, v[e][u].y, ::fma(-a.y, v[e][u].x, im));
+            }
           }
         }
-        re = warp_sum(re);
-        im = warp_sum(im);
-        if (l == 0) { red[(w * n + j) * 2] = re; red[(w * n + j) * 2 + 1] = im; }
+        const double r = warp_sum_pair(re, im);
+        if ((l & 15) == 0) red[(w * n + j) * 2 + (l >> 4)] = r;
       }
       __syncthreads();
       for (int j = threadIdx.x; j < i; j += blockDim.x) {
@@ -91,26 +116,34 @@ __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
         coef[2 * j + 1] = im;
       }
       __syncthreads();
-      if (own)
-        for (int j = 0; j < i; ++j) {
-          const double cr = coef[2 * j], ci = coef[2 * j + 1];
+      for (int j = 0; j < i; ++j) {
+        const double cr = coef[2 * j], ci = coef[2 * j + 1];
 #pragma unroll
-          for (int u = 0; u < 6; ++u) {
-            double2 a = *at(j, u);
-            v[u].x -= cr * a.x - ci * a.y;
-            v[u].y -= cr * a.y + ci * a.x;
+        for (int e = 0; e < ORTHO_SITES; ++e) {
+          if (own[e]) {
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              const double2 a = *at(j, e, u);
+              v[e][u].x = ::fma(-cr, a.x, ::fma(ci, a.y, v[e][u].x));
+              v[e][u].y = ::fma(-cr, a.y, ::fma(-ci, a.x, v[e][u].y));
+            }
           }
         }
+      }
       __syncthreads();
     }
     double nn = 0.0, dummy = 0.0;
 #pragma unroll
-    for (int u = 0; u < 6; ++u) nn += v[u].x * v[u].x + v[u].y * v[u].y;
+    for (int e = 0; e < ORTHO_SITES; ++e)
+#pragma unroll
+      for (int u = 0; u < 6; ++u) nn = ::fma(v[e][u].x, v[e][u].x, ::fma(v[e][u].y, v[e][u].y, nn));
     block_sum2_all(nn, dummy, red);
     const double f = 1.0 / sqrt(nn);
-    if (own)
 #pragma unroll
-      for (int u = 0; u < 6; ++u) *at(i, u) = make_double2(v[u].x * f, v[u].y * f);
+    for (int e = 0; e < ORTHO_SITES; ++e)
+      if (own[e])
+#pragma unroll
+        for (int u = 0; u < 6; ++u) *at(i, e, u) = make_double2(v[e][u].x * f, v[e][u].y * f);
     __syncthreads();
   }
 }
@@ -118,6 +151,28 @@ __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
 // ---------------------------------------------------------------------------
 // restriction: CTA per (aggregate, rhs)
 // ---------------------------------------------------------------------------
+// sum of 16 values over a warp as a reduce-scatter: 16 shuffles instead of
+// 80; lane l ends with the total of value (l >> 1) & 15
+template <class R>
+__device__ __forceinline__ R warp_reduce_scatter16(R (&v)[16]) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int lev = 0; lev < 4; ++lev) {
+    const int half = 8 >> lev, off = 16 >> lev;
+    const bool up = (l & off) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const R send = up ? v[k] : v[k + half];
+      const R keep = up ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// restriction b_c(X, s, i) = <lambda_i restricted to (X, s), b> (Eq. 3): CTA
+// per (aggregate, rhs); test vectors in groups of four, each site's b loaded
+// once per group, the group's 16 sums reduced by a reduce-scatter
 template <class R>
 __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __restrict__ b,
                            cpx<R>* __restrict__ bc) {
@@ -126,28 +181,34 @@ __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const size_t fstride = (size_t)g.V * SPINOR_NR;
   const R* bb = b + rhs * fstride;
-  for (int i = 0; i < n; ++i) {
-    cpx<R> a2[2] = {mk(R(0), R(0)), mk(R(0), R(0))};   // s = 0, 1
+  for (int i0 = 0; i0 < n; i0 += 4) {
+    R acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = R(0);
     for (int q = threadIdx.x; q < g.Vb; q += blockDim.x) {
-      int d = X * g.Vb + q;
-      Spinor<R> L, B;
-      load_spinor<R>(lam + i * fstride, d, g.Vb, L);
+      const int d = X * g.Vb + q;
+      Spinor<R> B;
       load_spinor<R>(bb, d, g.Vb, B);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) fmac(a2[k / 6], L.c[k], B.c[k]);
-    }
-    double a[4];
+      for (int ii = 0; ii < 4; ++ii) {
+        if (i0 + ii < n) {
+          Spinor<R> L;
+          load_spinor<R>(lam + (i0 + ii) * fstride, d, g.Vb, L);
+          cpx<R> a0 = mk(R(0), R(0)), a1 = mk(R(0), R(0));
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      a[2 * k] = warp_sum_t<R>(a2[k].re);
-      a[2 * k + 1] = warp_sum_t<R>(a2[k].im);
-    }
-    if (l == 0) {
-      for (int s = 0; s < 2; ++s) {
-        rsh[(w * 2 * n + s * n + i) * 2] = a[2 * s];
-        rsh[(w * 2 * n + s * n + i) * 2 + 1] = a[2 * s + 1];
+          for (int k = 0; k < 6; ++k) fmac(a0, L.c[k], B.c[k]);
+#pragma unroll
+          for (int k = 6; k < 12; ++k) fmac(a1, L.c[k], B.c[k]);
+          acc[4 * ii] += a0.re;
+          acc[4 * ii + 1] += a0.im;
+          acc[4 * ii + 2] += a1.re;
+          acc[4 * ii + 3] += a1.im;
+        }
       }
     }
+    const R tot = warp_reduce_scatter16<R>(acc);
+    const int vi = (l >> 1) & 15, ii = vi >> 2, sc = (vi >> 1) & 1, ri = vi & 1;
+    if ((l & 1) == 0 && i0 + ii < n) rsh[(w * 2 * n + sc * n + i0 + ii) * 2 + ri] = (double)tot;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < 2 * n; r += blockDim.x) {
@@ -512,7 +573,7 @@ __global__ void k_conv_c(const RS* __restrict__ s, RD* __restrict__ d, size_t n)
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st) {
-  int threads = ((g.Vb + 31) / 32) * 32;
+  int threads = (((g.Vb + ORTHO_SITES - 1) / ORTHO_SITES + 31) / 32) * 32;
   size_t smem = ((size_t)2 * (threads / 32) * (n > 1 ? n : 1) + 2 * n) * sizeof(double);
   k_orthonormalise<<<dim3(g.nb, 2), threads, smem, st>>>(g, lam, n);
   ++g_launches;

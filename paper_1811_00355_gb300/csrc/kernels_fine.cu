@@ -384,28 +384,64 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
   __syncthreads();
 }
 
+// FP64 arithmetic is the scarce resource of these kernels (GB300 issues two
+// FP64 lanes per clock per SM against 128 FP32 lanes), so they are written to
+// spend it on the products: vectors are taken in groups of DOT_J, each
+// thread sums many elements before any cross-thread step, and the CTA
+// reduction transposes the partial sums through shared memory so that every
+// value is reduced by one warp instead of every warp reducing every value.
+constexpr int DOT_J = 4;
+
+// acc[2 jj + (0, 1)] += <v_{j0 + jj}, w> over this thread's elements, jj < NJ
+template <class R, int NJ>
+__device__ __forceinline__ void dot_group(const PtrList<R>& v, int j0, const cpx<R>* __restrict__ wc, size_t lo,
+                                          size_t hi, double (&acc)[2 * DOT_J]) {
+  for (size_t i = lo + threadIdx.x; i < hi; i += RED_TPB) {
+    const cpx<R> b = wc[i];
+    const double br = (double)b.re, bi = (double)b.im;
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const cpx<R> a = reinterpret_cast<const cpx<R>*>(v.p[j0 + jj])[i];
+      const double ar = (double)a.re, ai = (double)a.im;
+      acc[2 * jj] = ::fma(ar, br, ::fma(ai, bi, acc[2 * jj]));
+      acc[2 * jj + 1] = ::fma(ar, bi, ::fma(-ai, br, acc[2 * jj + 1]));
+    }
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(RED_TPB) k_multi_dot_partial(PtrList<R> v, int k,
                                                                const R* __restrict__ w, size_t n,
                                                                double* __restrict__ part) {
-  __shared__ double sh[2 * (RED_TPB / 32)];
-  size_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  size_t lo = blockIdx.x * chunk;
-  size_t hi = lo + chunk < n ? lo + chunk : n;
+  __shared__ double sh[2 * DOT_J][RED_TPB];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk;
+  const size_t hi = lo + chunk < n ? lo + chunk : n;
   const cpx<R>* wc = reinterpret_cast<const cpx<R>*>(w);
-  for (int j = 0; j < k; ++j) {
-    const cpx<R>* vc = reinterpret_cast<const cpx<R>*>(v.p[j]);
-    double re = 0.0, im = 0.0;
-    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      cpx<R> a = vc[i], b = wc[i];
-      re += (double)a.re * (double)b.re + (double)a.im * (double)b.im;
-      im += (double)a.re * (double)b.im - (double)a.im * (double)b.re;
+  const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
+  for (int j0 = 0; j0 < k; j0 += DOT_J) {
+    const int nj = k - j0 < DOT_J ? k - j0 : DOT_J;
+    double acc[2 * DOT_J];
+#pragma unroll
+    for (int q = 0; q < 2 * DOT_J; ++q) acc[q] = 0.0;
+    static_assert(DOT_J == 4, "the dispatch below covers groups of up to four");
+    switch (nj) {
+      case 4: dot_group<R, 4>(v, j0, wc, lo, hi, acc); break;
+      case 3: dot_group<R, 3>(v, j0, wc, lo, hi, acc); break;
+      case 2: dot_group<R, 2>(v, j0, wc, lo, hi, acc); break;
+      default: dot_group<R, 1>(v, j0, wc, lo, hi, acc); break;
     }
-    block_sum2(re, im, sh);
-    if (threadIdx.x == 0) {
-      part[((size_t)j * gridDim.x + blockIdx.x) * 2] = re;
-      part[((size_t)j * gridDim.x + blockIdx.x) * 2 + 1] = im;
+#pragma unroll
+    for (int q = 0; q < 2 * DOT_J; ++q) sh[q][t] = acc[q];
+    __syncthreads();
+    for (int q = wid; q < 2 * nj; q += RED_TPB / 32) {
+      double sum = 0.0;
+#pragma unroll
+      for (int u = 0; u < RED_TPB / 32; ++u) sum += sh[q][lane + 32 * u];
+      sum = warp_sum(sum);
+      if (lane == 0) part[((size_t)(j0 + (q >> 1)) * gridDim.x + blockIdx.x) * 2 + (q & 1)] = sum;
     }
+    __syncthreads();
   }
 }
 
@@ -425,24 +461,59 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(const double* __restri
   }
 }
 
+// w -= sum_j coef_j v_j (coef scaled by sign); with part != nullptr also the
+// CTA partial sums of ||w_new||^2 (slot layout of k_multi_dot_partial, k = 1)
 template <class R>
-__global__ void k_multi_axpy(PtrList<R> v, int k, const double* __restrict__ coef, double sign,
-                             R* __restrict__ w, size_t n) {
+__global__ void __launch_bounds__(RED_TPB) k_multi_axpy(PtrList<R> v, int k, const double* __restrict__ coef,
+                                                        double sign, R* __restrict__ w, size_t n,
+                                                        double* __restrict__ part) {
   __shared__ double cs[2 * MAXK];            // signed coefficients, loaded once per CTA
+  __shared__ double sh[RED_TPB / 32];
   for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) cs[j] = sign * coef[j];
   __syncthreads();
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk;
+  const size_t hi = lo + chunk < n ? lo + chunk : n;
   cpx<R>* wc = reinterpret_cast<cpx<R>*>(w);
-  for (; i < n; i += stride) {
-    double re = wc[i].re, im = wc[i].im;
-    for (int j = 0; j < k; ++j) {
-      cpx<R> a = reinterpret_cast<const cpx<R>*>(v.p[j])[i];
-      const double cr = cs[2 * j], ci = cs[2 * j + 1];
-      re = ::fma(cr, (double)a.re, ::fma(-ci, (double)a.im, re));
-      im = ::fma(cr, (double)a.im, ::fma(ci, (double)a.re, im));
+  double nn = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += RED_TPB) {
+    double re = (double)wc[i].re, im = (double)wc[i].im;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      cpx<R> a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = reinterpret_cast<const cpx<R>*>(v.p[j + u])[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double cr = cs[2 * (j + u)], ci = cs[2 * (j + u) + 1];
+        const double ar = (double)a[u].re, ai = (double)a[u].im;
+        re = ::fma(cr, ar, ::fma(-ci, ai, re));
+        im = ::fma(cr, ai, ::fma(ci, ar, im));
+      }
     }
-    wc[i] = mk((R)re, (R)im);
+    for (; j < k; ++j) {
+      const cpx<R> a = reinterpret_cast<const cpx<R>*>(v.p[j])[i];
+      const double cr = cs[2 * j], ci = cs[2 * j + 1];
+      const double ar = (double)a.re, ai = (double)a.im;
+      re = ::fma(cr, ar, ::fma(-ci, ai, re));
+      im = ::fma(cr, ai, ::fma(ci, ar, im));
+    }
+    const cpx<R> o = mk((R)re, (R)im);
+    wc[i] = o;
+    if (part) nn = ::fma((double)o.re, (double)o.re, ::fma((double)o.im, (double)o.im, nn));
+  }
+  if (part) {
+    nn = warp_sum(nn);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nn;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double s2 = threadIdx.x < RED_TPB / 32 ? sh[threadIdx.x] : 0.0;
+      s2 = warp_sum(s2);
+      if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s2;
+        part[2 * blockIdx.x + 1] = 0.0;
+      }
+    }
   }
 }
 
@@ -609,10 +680,19 @@ cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign
   if (k > MAXK) return cudaErrorInvalidValue;
   PtrList<R> pl;
   for (int j = 0; j < k; ++j) pl.p[j] = v[j];
-  unsigned nb = nblk(n, 256);
-  if (nb > 4096) nb = 4096;
-  k_multi_axpy<R><<<nb, 256, 0, st>>>(pl, k, coef, sign, w, n);
+  k_multi_axpy<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, nullptr);
   ++g_launches;
+  return cudaGetLastError();
+}
+template <class R>
+cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
+                            double* scratch, double* out, cudaStream_t st) {
+  if (k > MAXK) return cudaErrorInvalidValue;
+  PtrList<R> pl;
+  for (int j = 0; j < k; ++j) pl.p[j] = v[j];
+  k_multi_axpy<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, scratch);
+  k_reduce_final<<<1, RED_TPB, 0, st>>>(scratch, RED_CTAS, out);
+  g_launches += 2;
   return cudaGetLastError();
 }
 template <class R>
@@ -667,6 +747,8 @@ template cudaError_t multi_axpy<float>(const float* const*, int, const double*, 
                                        cudaStream_t);
 template cudaError_t multi_axpy<double>(const double* const*, int, const double*, double, double*,
                                         size_t, cudaStream_t);
+template cudaError_t multi_axpy_norm<double>(const double* const*, int, const double*, double, double*,
+                                             size_t, double*, double*, cudaStream_t);
 template cudaError_t axpby<float>(double, const float*, double, float*, size_t, cudaStream_t);
 template cudaError_t axpby<double>(double, const double*, double, double*, size_t, cudaStream_t);
 template cudaError_t scale_by_inv_norm<float>(const float*, float*, const double*, size_t, cudaStream_t);

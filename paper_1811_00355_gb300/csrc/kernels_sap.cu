@@ -517,9 +517,16 @@ __device__ __forceinline__ void hop_local(const int16_t* __restrict__ bnbr, cons
   }
 }
 
-// hop phase inside the block: P[mu][k][h] for site q = qoff + h, values from buf
-__device__ __forceinline__ void hop_phase(const int16_t* bnbr, const float4* sl, const f2* buf, int Vb, int Vbp,
-                                          int Vh, int qoff, int mu, int h, f2* P) {
+// hop phase inside the block: P[mu][k][h] for site q = qoff + h, values from
+// the buffer at byte offset buf_off of the dynamic shared memory, partials at
+// p_off
+__device__ __forceinline__ void hop_phase(const int16_t* __restrict__ bnbr, int Vb, int buf_off, int p_off, int qoff,
+                                       int mu, int h) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Vh = Vb / 2, Vbp = Vb + LPAD;
+  const float4* sl = reinterpret_cast<const float4*>(smem_raw);
+  const f2* buf = reinterpret_cast<const f2*>(smem_raw + buf_off);
+  f2* P = reinterpret_cast<f2*>(smem_raw + p_off);
   Spinor<float> acc;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
@@ -578,6 +585,9 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
   const int t = threadIdx.x;
   const int mu = t / Vh, h = t - mu * Vh;      // hop phases
   const int sub = mu;                          // site phases: spin sub of site h
+  const int offE = (int)(reinterpret_cast<unsigned char*>(E) - smem_raw);
+  const int offO = (int)(reinterpret_cast<unsigned char*>(O) - smem_raw);
+  const int offP = (int)(reinterpret_cast<unsigned char*>(P) - smem_raw);
   const int cb = sub >> 1, half = sub & 1;
   const int de = B * Vb + h, dO = B * Vb + Vh + h;
 
@@ -661,7 +671,7 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
   }
   __syncthreads();
   // rhs_e = r_e + 1/2 hop(u_o)
-  hop_phase(g.bnbr, sl, O, Vb, Vbp, Vh, 0, mu, h, P);
+  hop_phase(g.bnbr, Vb, offO, offP, 0, mu, h);
   __syncthreads();
   f2 res[3], xe[3];
 #pragma unroll
@@ -676,7 +686,7 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
     for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = res[i];
     __syncthreads();
     // odd: w = A_oo^-1 (-1/2 hop(res))
-    hop_phase(g.bnbr, sl, E, Vb, Vbp, Vh, Vh, mu, h, P);
+    hop_phase(g.bnbr, Vb, offE, offP, Vh, mu, h);
     __syncthreads();
     {
       f2 v6[6], w[3];
@@ -688,7 +698,7 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
     }
     __syncthreads();
     // even: p = A_ee res + 1/2 hop(w)
-    hop_phase(g.bnbr, sl, O, Vb, Vbp, Vh, 0, mu, h, P);
+    hop_phase(g.bnbr, Vb, offO, offP, 0, mu, h);
     __syncthreads();
     f2 pv[3];
     float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
@@ -722,7 +732,7 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
 #pragma unroll
   for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = xe[i];
   __syncthreads();
-  hop_phase(g.bnbr, sl, E, Vb, Vbp, Vh, Vh, mu, h, P);
+  hop_phase(g.bnbr, Vb, offE, offP, Vh, mu, h);
   __syncthreads();
   f2 eo[3];
   {
