@@ -100,6 +100,13 @@ typedef struct {
   int max_outer_iter;  /* FGMRES iteration cap per right-hand side          */
   uint64_t seed;       /* seed of the initial random test vectors           */
   size_t hbm_budget;   /* device-memory admission limit in bytes, 0 = none  */
+  double outer_refine; /* FP32 inner precision only: if > 0, the FGMRES
+                          operator products D z_k (z_k = M v_k, an FP32
+                          result) are taken in FP32 and a cycle restarts from
+                          the FP64 true residual r = b - D x once its
+                          recurrence residual fell by this factor (iterative
+                          refinement); the basis, Gram-Schmidt and r stay
+                          FP64.  0 = D z_k in FP64, restart only at m.      */
 } ddamg_params;
 
 typedef struct {
@@ -126,7 +133,7 @@ typedef struct {
 } ddamg_stats;
 
 /* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,
- * coarse tol 5e-2, FP32 inner precision, restart 30). */
+ * coarse tol 5e-2, FP32 inner precision, restart 30, outer_refine 1e-5). */
 DDAMG_API void ddamg_default_params(ddamg_params *p);
 
 /* Name of a status code (static string). */

@@ -36,7 +36,7 @@ class Params(C.Structure):
         ("setup_iters", C.c_int), ("n_sap", C.c_int), ("mr_iters", C.c_int),
         ("coarse_tol", C.c_double), ("coarse_restart", C.c_int), ("coarse_max_iter", C.c_int),
         ("precision", C.c_int), ("outer_restart", C.c_int), ("max_outer_iter", C.c_int),
-        ("seed", C.c_uint64), ("hbm_budget", C.c_size_t),
+        ("seed", C.c_uint64), ("hbm_budget", C.c_size_t), ("outer_refine", C.c_double),
     ]
 
 

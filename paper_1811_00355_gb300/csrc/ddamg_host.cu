@@ -6,6 +6,7 @@
 // driven from the host with one device-to-host read per iteration; the
 // preconditioner M (Eq. 5), the SAP smoother and the coarse solve run as
 // kernels without host synchronisation.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -88,6 +89,7 @@ struct ddamg_ctx {
   // outer FGMRES
   double* fV = nullptr;          // (m+1) fields
   double* fZ = nullptr;          // m fields
+  float* fZ32 = nullptr;         // m FP32 fields (iterative-refinement mode)
   double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fw = nullptr;
   void* fin = nullptr;           // inner-precision in/out for M
   void* fout = nullptr;
@@ -202,6 +204,7 @@ ddamg_status validate(const ddamg_params* p, std::string& why) {
   if (!is_prec(p->precision)) return bad("precision must be DDAMG_FP64 or DDAMG_FP32");
   if (p->outer_restart < 1 || p->outer_restart > 62 || p->max_outer_iter < 1)
     return bad("outer_restart in [1, 62], max_outer_iter >= 1");
+  if (!(p->outer_refine >= 0.0 && p->outer_refine < 1.0)) return bad("outer_refine in [0, 1)");
   if (!std::isfinite(p->m0) || !std::isfinite(p->csw)) return bad("m0 and csw must be finite");
   return DDAMG_OK;
 }
@@ -609,11 +612,16 @@ ddamg_status precond_to_f64(ddamg_ctx* h, const double* v, double* z) {
   return from_inner<float>(h, fout, z, 1);
 }
 
+// FGMRES as iterative refinement: FP32 operator products in the Arnoldi
+// process, FP64 basis, Gram-Schmidt and true residuals
+bool refine_mode(const ddamg_ctx* h) { return h->p.precision == DDAMG_FP32 && h->p.outer_refine > 0.0; }
+
 ddamg_status alloc_outer(ddamg_ctx* h) {
   if (h->fV) return DDAMG_OK;
   const int m = h->p.outer_restart;
   TRY(dalloc_t(h, &h->fV, (size_t)(m + 1) * h->V24));
-  TRY(dalloc_t(h, &h->fZ, (size_t)m * h->V24));
+  if (refine_mode(h)) TRY(dalloc_t(h, &h->fZ32, (size_t)m * h->V24));
+  else TRY(dalloc_t(h, &h->fZ, (size_t)m * h->V24));
   TRY(dalloc_t(h, &h->fx, h->V24));
   TRY(dalloc_t(h, &h->fb, h->V24));
   TRY(dalloc_t(h, &h->fr, h->V24));
@@ -639,14 +647,24 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
 // The device work of one outer iteration k: z_k = M v_k, w = D z_k, two
 // classical Gram-Schmidt passes (the preconditioned direction is nearly in
 // the Krylov space, so the first pass always cancels most of w), ||w||^2,
-// the coefficients to pinned host memory, v_{k+1} = w / ||w||.
+// the coefficients to pinned host memory, v_{k+1} = w / ||w||.  In the
+// iterative-refinement mode z_k stays FP32 (it is an FP32 result of M) and
+// D z_k is taken in FP32 before w joins the FP64 basis.
 template <class R>
 ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlist, double* vk, double* zk,
                                double* vk1) {
   const int m = h->p.outer_restart;
   const size_t N = h->V24, NC = N / 2;
-  TRY(precond_to_f64<R>(h, vk, zk));
-  TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->fw, 1));
+  if (refine_mode(h)) {
+    float* z32 = h->fZ32 + (size_t)k * N;
+    TRY(to_inner<float>(h, vk, (float*)h->fin, 1));
+    TRY(op_M<float>(h, (float*)h->fin, z32, 1));
+    TRY(op_dslash<float>(h, DSLASH_D, z32, nullptr, (float*)h->fout, 1));
+    TRY(from_inner<float>(h, (float*)h->fout, h->fw, 1));
+  } else {
+    TRY(precond_to_f64<R>(h, vk, zk));
+    TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->fw, 1));
+  }
   double* c1 = h->dots;
   double* c2 = h->dots + 2 * (m + 2);
   double* nn = h->dots + 4 * (m + 2);
@@ -732,11 +750,16 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
   const size_t NC = N / 2;          // complex
   double* V = h->fV;
   double* Z = h->fZ;
+  const bool refine = refine_mode(h);
   auto Vk = [&](int k) { return V + (size_t)k * N; };
-  auto Zk = [&](int k) { return Z + (size_t)k * N; };
+  auto Zk = [&](int k) { return refine ? nullptr : Z + (size_t)k * N; };
   std::vector<const double*> vlist(m + 1), zlist(m);
+  std::vector<const float*> zlist32(m);
   for (int k = 0; k <= m; ++k) vlist[k] = Vk(k);
-  for (int k = 0; k < m; ++k) zlist[k] = Zk(k);
+  for (int k = 0; k < m; ++k) {
+    zlist[k] = Zk(k);
+    zlist32[k] = refine ? h->fZ32 + (size_t)k * N : nullptr;
+  }
   int iters = 0, restarts = 0, calls = 0;
   CK(cudaMemsetAsync(h->fx, 0, N * 8, h->st));
   CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
@@ -758,6 +781,10 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
     std::fill(g.begin(), g.end(), cd(0));
     g[0] = beta;
     int kdone = 0;
+    // a refinement cycle ends once its recurrence residual fell by
+    // outer_refine: beyond that the FP32 operator products, not the
+    // iteration, limit the residual the recurrence can trust
+    const double cycle_stop = std::max(tol * bnorm, refine ? h->p.outer_refine * beta : 0.0);
     for (int k = 0; k < m; ++k) {
       TRY(run_iteration<R>(h, k, vlist, Vk(k), Zk(k), Vk(k + 1)));
       ++calls;
@@ -791,7 +818,7 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       g[k] = cs[k] * g[k];
       ++iters;
       kdone = k + 1;
-      if (std::abs(g[k + 1]) <= tol * bnorm || iters >= h->p.max_outer_iter || hn == 0.0) break;
+      if (std::abs(g[k + 1]) <= cycle_stop || iters >= h->p.max_outer_iter || hn == 0.0) break;
     }
     for (int i = kdone - 1; i >= 0; --i) {
       cd acc = g[i];
@@ -803,7 +830,8 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       host[2 * j + 1] = y[j].imag();
     }
     CK(cudaMemcpyAsync(h->d_coef, host, 2 * kdone * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    CK(multi_axpy<double>(zlist.data(), kdone, h->d_coef, 1.0, h->fx, NC, h->st));
+    if (refine) CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kdone, h->d_coef, 1.0, h->fx, 1, h->st));
+    else CK(multi_axpy<double>(zlist.data(), kdone, h->d_coef, 1.0, h->fx, NC, h->st));
     // true residual
     TRY(op_dslash<double>(h, DSLASH_RES, h->fx, h->fb, h->fr, 1));
     CK(norm2<double>(h->fr, NC, h->red, h->dots, h->st));
@@ -962,6 +990,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->max_outer_iter = 1000;
   p->seed = 1;
   p->hbm_budget = 0;
+  p->outer_refine = 1e-5;
 }
 
 const char* ddamg_status_string(ddamg_status s) {

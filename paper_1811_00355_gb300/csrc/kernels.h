@@ -81,6 +81,10 @@ cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign
 template <class R>
 cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
                             double* scratch, double* out, cudaStream_t st);
+// nf FP64 spinor fields w += sum_j coef[j] * v_j with FP32 spinor fields v_j
+// (each precision in its own device layout; FP64 arithmetic)
+cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, double sign,
+                                    double* w, int nf, cudaStream_t st);
 // y = a x + b y (real scalars)
 template <class R>
 cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t st);

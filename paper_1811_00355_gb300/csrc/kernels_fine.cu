@@ -517,6 +517,49 @@ __global__ void __launch_bounds__(RED_TPB) k_multi_axpy(PtrList<R> v, int k, con
   }
 }
 
+// FP64 spinor fields w += sum_j coef_j v_j with FP32 spinor fields v_j.  The
+// two precisions lay a block out in 16-byte units of different width (12
+// double2 or 6 float4 per site), so complex component c of local site q of
+// block B sits at (B 12 + c) Vb + q in w and at 2 ((B 6 + c / 2) Vb + q) + c % 2
+// in v_j.
+__global__ void __launch_bounds__(RED_TPB) k_multi_axpy_f32(PtrList<float> v, int k, const double* __restrict__ coef,
+                                                            double sign, double* __restrict__ w, size_t n, int Vb) {
+  __shared__ double cs[2 * MAXK];
+  for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) cs[j] = sign * coef[j];
+  __syncthreads();
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk;
+  const size_t hi = lo + chunk < n ? lo + chunk : n;
+  cpx<double>* wc = reinterpret_cast<cpx<double>*>(w);
+  const size_t per_block = (size_t)12 * Vb;
+  for (size_t i = lo + threadIdx.x; i < hi; i += RED_TPB) {
+    const size_t B = i / per_block;
+    const int rem = (int)(i - B * per_block);
+    const int c = rem / Vb, q = rem - c * Vb;
+    const size_t i32 = 2 * ((B * 6 + (size_t)(c >> 1)) * Vb + q) + (c & 1);
+    double re = wc[i].re, im = wc[i].im;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      cpx<float> a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = reinterpret_cast<const cpx<float>*>(v.p[j + u])[i32];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double cr = cs[2 * (j + u)], ci = cs[2 * (j + u) + 1];
+        re = ::fma(cr, (double)a[u].re, ::fma(-ci, (double)a[u].im, re));
+        im = ::fma(cr, (double)a[u].im, ::fma(ci, (double)a[u].re, im));
+      }
+    }
+    for (; j < k; ++j) {
+      const cpx<float> a = reinterpret_cast<const cpx<float>*>(v.p[j])[i32];
+      const double cr = cs[2 * j], ci = cs[2 * j + 1];
+      re = ::fma(cr, (double)a.re, ::fma(-ci, (double)a.im, re));
+      im = ::fma(cr, (double)a.im, ::fma(ci, (double)a.re, im));
+    }
+    wc[i] = mk(re, im);
+  }
+}
+
 template <class R>
 __global__ void k_axpby(double a, const R* __restrict__ x, double b, R* __restrict__ y, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -693,6 +736,16 @@ cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double
   k_multi_axpy<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, scratch);
   k_reduce_final<<<1, RED_TPB, 0, st>>>(scratch, RED_CTAS, out);
   g_launches += 2;
+  return cudaGetLastError();
+}
+cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, double sign,
+                                    double* w, int nf, cudaStream_t st) {
+  if (k > MAXK) return cudaErrorInvalidValue;
+  PtrList<float> pl;
+  for (int j = 0; j < k; ++j) pl.p[j] = v[j];
+  const size_t n = (size_t)nf * g.V * (SPINOR_NR / 2);
+  k_multi_axpy_f32<<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, g.Vb);
+  ++g_launches;
   return cudaGetLastError();
 }
 template <class R>

@@ -254,6 +254,26 @@ def test_solve_full_workload_point_sources():
         assert res <= 1e-10, (k, res, info[k])
 
 
+@pytest.mark.parametrize("refine", [0.0, 1e-3, 1e-5])
+def test_solve_fp32_refinement_modes(refine):
+    """FP32 inner solver: with outer_refine > 0 the FGMRES operator products
+    are FP32 and cycles restart from the FP64 true residual; with 0 they are
+    FP64.  Every mode reaches a true residual <= 1e-10 (oracle's D)."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1, outer_refine=refine)
+    s.run_setup()
+    op = oracle_op(L, eps, seed, m0, csw)
+    rhs = syn.gaussian_spinors(3, L, 31)
+    x, info = s.solve(rhs, 1e-10)
+    for k in range(3):
+        res = rel(op.apply(t(x[k])).numpy(), rhs[k])
+        assert res <= 1e-10, (k, res, info[k])
+        assert info[k]["converged"] == 1 and info[k]["true_residual"] <= 1e-10
+        if refine >= 1e-3:
+            assert info[k]["restarts"] >= 2, info[k]
+    s.close()
+
+
 def test_random_vectors_match_philox_definition():
     P = _P()
     s = make(SMALL, 0)
