@@ -176,6 +176,21 @@ DDAMG_API ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double *rhs,
                          double *x, int on_device, double tol,
                          ddamg_solve_info *info);
 
+/* Solve the nrhs systems D x_k = rhs_k (nrhs <= 64) together.  Every right-
+ * hand side has its own FGMRES -- basis, Hessenberg matrix, restarts and
+ * convergence test, with the arithmetic of ddamg_solve -- but the iterations
+ * of the batch advance in lockstep, so each application of M (Eq. 5), of D
+ * and of the Gram-Schmidt reductions runs once for the whole batch, through
+ * multi-right-hand-side kernels and the coarse GMRES with the right-hand
+ * sides in lockstep.  The paper solves its 12 spin-colour sources one at a
+ * time; batching them is this library's addition.  Arguments, layouts and
+ * status codes as ddamg_solve; info[k].coarse_iters and precond_calls count
+ * the whole batch, seconds is the batch's wall time.  Device memory grows by
+ * about nrhs * (2 restart + 8) fine fields on first use. */
+DDAMG_API ddamg_status ddamg_solve_batched(ddamg_handle h, int nrhs, const double *rhs,
+                                 double *x, int on_device, double tol,
+                                 ddamg_solve_info *info);
+
 /* ---- single steps of the method, for checking and benchmarking ---------- */
 
 /* out = D in (Wilson-clover operator above) in the given precision. */

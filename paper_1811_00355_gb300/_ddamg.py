@@ -76,6 +76,7 @@ SIGNATURES = {
     "ddamg_run_setup": (_I, [_H, _P, _I]),
     "ddamg_update_mass": (_I, [_H, _D, _D]),
     "ddamg_solve": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(SolveInfo)]),
+    "ddamg_solve_batched": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(SolveInfo)]),
     "ddamg_apply_D": (_I, [_H, _I, _I, _P, _P, _I]),
     "ddamg_apply_clover": (_I, [_H, _I, _I, _I, _P, _P, _I]),
     "ddamg_get_clover": (_I, [_H, _I, _P]),
@@ -215,6 +216,17 @@ class DDAMG:
         pi, dev = _ptr(rhs)
         po, _ = _ptr(x)
         st = self.lib.ddamg_solve(self.h, n, pi, po, dev, tol, info)
+        if not (allow_noconv and st == 4):
+            self._check(st)
+        return x, [i.as_dict() for i in info]
+
+    def solve_batched(self, rhs, tol=1e-10, allow_noconv=False):
+        n = self._nrhs(rhs)
+        x = self._fine_out(rhs, n).reshape(rhs.shape)
+        info = (SolveInfo * n)()
+        pi, dev = _ptr(rhs)
+        po, _ = _ptr(x)
+        st = self.lib.ddamg_solve_batched(self.h, n, pi, po, dev, tol, info)
         if not (allow_noconv and st == 4):
             self._check(st)
         return x, [i.as_dict() for i in info]

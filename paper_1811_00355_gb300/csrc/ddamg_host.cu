@@ -90,6 +90,16 @@ struct ddamg_ctx {
   double* fV = nullptr;          // (m+1) fields
   double* fZ = nullptr;          // m fields
   float* fZ32 = nullptr;         // m FP32 fields (iterative-refinement mode)
+  // batched solve: blocks of bcap fields (one per right-hand side)
+  int bcap = 0;
+  size_t bbytes = 0;             // bytes of the one batch allocation
+  unsigned char* bmem = nullptr;
+  double* bV = nullptr;          // (m+1) blocks
+  void* bZ = nullptr;            // m blocks (FP32 in refinement mode, else FP64)
+  double *bx = nullptr, *bb = nullptr, *br = nullptr, *bw = nullptr;
+  void *bin = nullptr, *bout = nullptr;   // inner-precision staging
+  double* bsmall = nullptr;      // coefficients and norms of the batch
+  double* h_bpinned = nullptr;
   double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fw = nullptr;
   void* fin = nullptr;           // inner-precision in/out for M
   void* fout = nullptr;
@@ -166,6 +176,18 @@ ddamg_status dalloc(ddamg_ctx* h, void** p, size_t bytes) {
   h->bytes += bytes;
   return DDAMG_OK;
 }
+// release one allocation made by dalloc
+void dfree(ddamg_ctx* h, void* p, size_t bytes) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      h->allocs.erase(h->allocs.begin() + i);
+      cudaFree(p);
+      h->bytes -= bytes;
+      return;
+    }
+}
+
 template <class T>
 ddamg_status dalloc_t(ddamg_ctx* h, T** p, size_t count) {
   void* v = nullptr;
@@ -830,7 +852,7 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       host[2 * j + 1] = y[j].imag();
     }
     CK(cudaMemcpyAsync(h->d_coef, host, 2 * kdone * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    if (refine) CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kdone, h->d_coef, 1.0, h->fx, 1, h->st));
+    if (refine) CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kdone, h->d_coef, 0, 1.0, h->fx, 1, h->st));
     else CK(multi_axpy<double>(zlist.data(), kdone, h->d_coef, 1.0, h->fx, NC, h->st));
     // true residual
     TRY(op_dslash<double>(h, DSLASH_RES, h->fx, h->fb, h->fr, 1));
@@ -854,6 +876,238 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
     info->converged = converged ? 1 : 0;
   }
   if (!converged) return fail(h, DDAMG_ENOCONV, "FGMRES reached max_outer_iter (residual %.3e)", beta / bnorm);
+  return DDAMG_OK;
+}
+
+// ---- batched outer FGMRES -------------------------------------------------------
+// Every right-hand side keeps its own FGMRES (basis, Hessenberg matrix,
+// Givens rotations, restarts, convergence); the iterations of the batch run in
+// lockstep so that M, D and the Gram-Schmidt reductions act on all of them in
+// one launch each (multi-right-hand-side kernels, the coarse GMRES with the
+// right-hand sides in lockstep).  A right-hand side that has converged keeps
+// being carried (its results are no longer used) until the batch finishes.
+constexpr int MAX_BATCH = 64;
+
+size_t batch_small_len(int m, int nb) { return (size_t)nb * (4 * (m + 2) + 2 + 2 * (m + 1) + 2); }
+
+ddamg_status alloc_batch(ddamg_ctx* h, int nb) {
+  if (h->bcap >= nb) return DDAMG_OK;
+  if (h->bmem) {
+    dfree(h, h->bmem, h->bbytes);
+    h->bmem = nullptr;
+    h->bcap = 0;
+  }
+  const int m = h->p.outer_restart;
+  const size_t F = h->V24 * sizeof(double);            // one FP64 field
+  const size_t zf = refine_mode(h) ? F / 2 : F;
+  const size_t small = batch_small_len(m, nb) * sizeof(double);
+  const size_t bytes = (size_t)nb * ((m + 1) * F + m * zf + 4 * F + 2 * F) + small + 256;
+  void* p = nullptr;
+  TRY(dalloc(h, &p, bytes));
+  h->bmem = (unsigned char*)p;
+  h->bbytes = bytes;
+  unsigned char* q = h->bmem;
+  auto take = [&](size_t b) { unsigned char* r = q; q += b; return r; };
+  h->bV = (double*)take((size_t)nb * (m + 1) * F);
+  h->bZ = take((size_t)nb * m * zf);
+  h->bx = (double*)take(nb * F);
+  h->bb = (double*)take(nb * F);
+  h->br = (double*)take(nb * F);
+  h->bw = (double*)take(nb * F);
+  h->bin = take(nb * F);
+  h->bout = take(nb * F);
+  h->bsmall = (double*)take(small);
+  if (h->h_bpinned) cudaFreeHost(h->h_bpinned);
+  h->h_bpinned = nullptr;
+  CK(cudaHostAlloc(&h->h_bpinned, small, cudaHostAllocDefault));
+  h->bcap = nb;
+  return DDAMG_OK;
+}
+
+template <class R>
+ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* info) {
+  const int m = h->p.outer_restart;
+  const size_t N = h->V24, NC = N / 2;
+  const bool refine = refine_mode(h);
+  const size_t blk = (size_t)nb * N;                      // reals of one block of nb fields
+  double* V = h->bV;
+  auto Vk = [&](int k) { return V + (size_t)k * blk; };
+  float* Z32 = (float*)h->bZ;
+  double* Z64 = (double*)h->bZ;
+  std::vector<const double*> vlist(m + 1), zlist(m);
+  std::vector<const float*> zlist32(m);
+  for (int k = 0; k <= m; ++k) vlist[k] = Vk(k);
+  for (int k = 0; k < m; ++k) {
+    zlist[k] = Z64 + (size_t)k * blk;
+    zlist32[k] = Z32 + (size_t)k * blk;
+  }
+  // device small buffers: c1 | c2 (nb x 2(m+2) each) | nn (2 nb) | coef (nb x 2(m+1)) | norms (2 nb)
+  double* c1 = h->bsmall;
+  double* c2 = c1 + (size_t)nb * 2 * (m + 2);
+  double* nn = c2 + (size_t)nb * 2 * (m + 2);
+  double* coef = nn + 2 * nb;
+  double* norms = coef + (size_t)nb * 2 * (m + 1);
+  double* hp = h->h_bpinned;
+
+  CK(cudaMemsetAsync(h->bx, 0, nb * N * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
+  CK(norm2_batched<double>(h->bb, NC, nb, NC, h->red, norms, h->st));
+  CK(cudaMemcpyAsync(hp, norms, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::vector<double> bnorm(nb), beta(nb), cstop(nb), cs((size_t)nb * m);
+  std::vector<cd> Hc((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m), y(m);
+  std::vector<int> done(nb, 0), iters(nb, 0), restarts(nb, 0), kdone(nb, 0), open(nb, 0);
+  for (int r = 0; r < nb; ++r) {
+    bnorm[r] = std::sqrt(hp[2 * r]);
+    if (!std::isfinite(bnorm[r])) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: norm is not finite", r);
+    beta[r] = bnorm[r];
+    done[r] = bnorm[r] == 0.0;
+  }
+  CK(cudaMemcpyAsync(h->br, h->bb, nb * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(norms, hp, 2 * nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  int calls = 0, total = 0;
+  auto all_done = [&] {
+    for (int r = 0; r < nb; ++r)
+      if (!done[r]) return false;
+    return true;
+  };
+  while (!all_done() && total < h->p.max_outer_iter) {
+    // V_0 = r / beta for every right-hand side (norms holds beta^2)
+    CK(scale_by_inv_norm_batched<double>(h->br, Vk(0), norms, N, nb, h->st));
+    for (int r = 0; r < nb; ++r) {
+      std::fill(g.begin() + (size_t)r * (m + 1), g.begin() + (size_t)(r + 1) * (m + 1), cd(0));
+      g[(size_t)r * (m + 1)] = beta[r];
+      kdone[r] = 0;
+      open[r] = !done[r];
+      cstop[r] = std::max(tol * bnorm[r], refine ? h->p.outer_refine * beta[r] : 0.0);
+    }
+    int k = 0;
+    for (; k < m; ++k) {
+      // z_k = M v_k and w = D z_k for the whole batch
+      if (refine) {
+        float* zk = Z32 + (size_t)k * blk;
+        TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+        TRY(op_M<float>(h, (float*)h->bin, zk, nb));
+        TRY(op_dslash<float>(h, DSLASH_D, zk, nullptr, (float*)h->bout, nb));
+        TRY(from_inner<float>(h, (float*)h->bout, h->bw, nb));
+      } else {
+        double* zk = Z64 + (size_t)k * blk;
+        if constexpr (sizeof(R) == 8) {
+          TRY(op_M<double>(h, Vk(k), zk, nb));
+        } else {
+          TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+          TRY(op_M<float>(h, (float*)h->bin, (float*)h->bout, nb));
+          TRY(from_inner<float>(h, (float*)h->bout, zk, nb));
+        }
+        TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
+      }
+      ++calls;
+      // two classical Gram-Schmidt passes per right-hand side, ||w||, v_{k+1}
+      const int kk = k + 1;
+      CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c1, h->st));
+      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr, h->st));
+      CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
+      CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+      CK(scale_by_inv_norm_batched<double>(h->bw, Vk(k + 1), nn, N, nb, h->st));
+      CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      const double* h1 = hp;
+      const double* h2 = hp + (size_t)nb * 2 * (m + 2);
+      const double* hn2 = h2 + (size_t)nb * 2 * (m + 2);
+      bool any_open = false;
+      for (int r = 0; r < nb; ++r) {
+        if (!open[r]) continue;
+        std::vector<cd> col(k + 2);
+        for (int j = 0; j <= k; ++j)
+          col[j] = cd(h1[2 * (r * kk + j)] + h2[2 * (r * kk + j)], h1[2 * (r * kk + j) + 1] + h2[2 * (r * kk + j) + 1]);
+        const double hn = std::sqrt(hn2[2 * r]);
+        if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the basis norm", r);
+        col[k + 1] = hn;
+        double* csr = cs.data() + (size_t)r * m;
+        cd* snr = sn.data() + (size_t)r * m;
+        cd* gr = g.data() + (size_t)r * (m + 1);
+        for (int j = 0; j < k; ++j) {
+          cd t = csr[j] * col[j] + snr[j] * col[j + 1];
+          col[j + 1] = -std::conj(snr[j]) * col[j] + csr[j] * col[j + 1];
+          col[j] = t;
+        }
+        double a1 = std::abs(col[k]), a2 = std::abs(col[k + 1]);
+        if (a2 == 0.0) { csr[k] = 1.0; snr[k] = 0.0; }
+        else if (a1 == 0.0) { csr[k] = 0.0; snr[k] = std::conj(col[k + 1]) / a2; col[k] = a2; }
+        else {
+          double rho = std::hypot(a1, a2);
+          cd ph = col[k] / a1;
+          csr[k] = a1 / rho;
+          snr[k] = ph * std::conj(col[k + 1]) / rho;
+          col[k] = ph * rho;
+        }
+        for (int j = 0; j <= k; ++j) Hc[((size_t)r * (m + 1) + j) * m + k] = col[j];
+        gr[k + 1] = -std::conj(snr[k]) * gr[k];
+        gr[k] = csr[k] * gr[k];
+        ++iters[r];
+        kdone[r] = k + 1;
+        if (std::abs(gr[k + 1]) <= cstop[r] || iters[r] >= h->p.max_outer_iter || hn == 0.0) open[r] = 0;
+        any_open |= open[r] != 0;
+      }
+      ++total;
+      if (!any_open || total >= h->p.max_outer_iter) break;
+    }
+    // x_r += Z_r y_r (zero coefficients beyond each right-hand side's kdone)
+    int kmax = 0;
+    std::vector<double> cf((size_t)nb * 2 * (m + 1), 0.0);
+    for (int r = 0; r < nb; ++r) {
+      if (done[r] || kdone[r] == 0) continue;
+      const int kd = kdone[r];
+      kmax = std::max(kmax, kd);
+      const cd* gr = g.data() + (size_t)r * (m + 1);
+      for (int i = kd - 1; i >= 0; --i) {
+        cd acc = gr[i];
+        for (int j = i + 1; j < kd; ++j) acc -= Hc[((size_t)r * (m + 1) + i) * m + j] * y[j];
+        y[i] = acc / Hc[((size_t)r * (m + 1) + i) * m + i];
+      }
+      for (int j = 0; j < kd; ++j) {
+        cf[(size_t)r * 2 * (m + 1) + 2 * j] = y[j].real();
+        cf[(size_t)r * 2 * (m + 1) + 2 * j + 1] = y[j].imag();
+      }
+    }
+    if (kmax > 0) {
+      CK(cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      if (refine)
+        CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, nb, h->st));
+      else
+        CK(multi_axpy_batched<double>(zlist.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, NC, nb, NC, nullptr,
+                                      nullptr, h->st));
+    }
+    // FP64 true residuals
+    TRY(op_dslash<double>(h, DSLASH_RES, h->bx, h->bb, h->br, nb));
+    CK(norm2_batched<double>(h->br, NC, nb, NC, h->red, norms, h->st));
+    CK(cudaMemcpyAsync(hp, norms, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int r = 0; r < nb; ++r) {
+      if (done[r]) continue;
+      beta[r] = std::sqrt(hp[2 * r]);
+      ++restarts[r];
+      if (!std::isfinite(beta[r])) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the residual", r);
+      if (beta[r] <= tol * bnorm[r] || iters[r] >= h->p.max_outer_iter) done[r] = 1;
+    }
+  }
+  TRY(check_status(h));
+  int cit = 0;
+  CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
+  bool all_conv = true;
+  for (int r = 0; r < nb; ++r) {
+    const bool conv = bnorm[r] == 0.0 || beta[r] <= tol * bnorm[r];
+    all_conv &= conv;
+    if (info) {
+      info[r].outer_iters = iters[r];
+      info[r].restarts = restarts[r];
+      info[r].coarse_iters = cit;
+      info[r].precond_calls = calls;
+      info[r].true_residual = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+      info[r].converged = conv ? 1 : 0;
+    }
+  }
+  if (!all_conv) return fail(h, DDAMG_ENOCONV, "FGMRES reached max_outer_iter for part of the batch");
   return DDAMG_OK;
 }
 
@@ -1137,6 +1391,28 @@ ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double* rhs, double* x,
     if (info) info[k] = inf;
   }
   return worst;
+}
+
+ddamg_status ddamg_solve_batched(ddamg_handle h, int nrhs, const double* rhs, double* x, int on_device, double tol,
+                                 ddamg_solve_info* info) {
+  if (!h) return DDAMG_EINVAL;
+  if (nrhs < 0 || nrhs > MAX_BATCH || (nrhs > 0 && (!rhs || !x)))
+    return fail(h, DDAMG_EINVAL, "nrhs must be in [0, %d] with buffers", MAX_BATCH);
+  if (!(tol > 0.0)) return fail(h, DDAMG_EINVAL, "tol must be > 0");
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "run the setup first");
+  if (nrhs == 0) return DDAMG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  TRY(alloc_batch(h, nrhs));
+  TRY(need_tmp(h, nrhs, 6));
+  TRY(import_fields<double>(h, rhs, on_device, nrhs, h->bb));
+  ddamg_status s = h->p.precision == DDAMG_FP64 ? fgmres_batched<double>(h, nrhs, tol, info)
+                                                : fgmres_batched<float>(h, nrhs, tol, info);
+  if (s != DDAMG_OK && s != DDAMG_ENOCONV) return s;
+  TRY(export_fields<double>(h, h->bx, nrhs, x, on_device));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info)
+    for (int r = 0; r < nrhs; ++r) info[r].seconds = secs;
+  return s;
 }
 
 ddamg_status ddamg_apply_D(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
@@ -1426,6 +1702,7 @@ void ddamg_destroy(ddamg_handle h) {
     }
   }
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->h_bpinned) cudaFreeHost(h->h_bpinned);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   delete h;
 }

@@ -81,10 +81,28 @@ cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign
 template <class R>
 cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
                             double* scratch, double* out, cudaStream_t st);
-// nf FP64 spinor fields w += sum_j coef[j] * v_j with FP32 spinor fields v_j
-// (each precision in its own device layout; FP64 arithmetic)
-cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, double sign,
-                                    double* w, int nf, cudaStream_t st);
+// nf FP64 spinor fields w_r += sum_j coef[r cstride + j] * v_j,r with FP32
+// spinor fields v_j,r = v_j + r (each precision in its own device layout)
+cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, int cstride,
+                                    double sign, double* w, int nf, cudaStream_t st);
+// ---- batches of nb right-hand sides: vector j of right-hand side r is
+// v[j] + r * rstride (complex numbers); results per r follow one another
+// out[2 (r k + j)] = <v_j,r, w_r>
+template <class R>
+cudaError_t multi_dot_batched(const R* const* v, int k, const R* w, size_t n, int nb, size_t rstride,
+                              double* scratch, double* out, cudaStream_t st);
+// out[2 r] = ||w_r||^2
+template <class R>
+cudaError_t norm2_batched(const R* w, size_t n, int nb, size_t rstride, double* scratch, double* out,
+                          cudaStream_t st);
+// w_r += sign sum_j coef[r cstride + 2 j] v_j,r; with norms != nullptr also
+// norms[2 r] = ||w_r||^2 after the update
+template <class R>
+cudaError_t multi_axpy_batched(const R* const* v, int k, const double* coef, int cstride, double sign, R* w,
+                               size_t n, int nb, size_t rstride, double* scratch, double* norms, cudaStream_t st);
+// y_r = x_r / sqrt(s[2 r]) for nb consecutive fields of n reals (0 if s = 0)
+template <class R>
+cudaError_t scale_by_inv_norm_batched(const R* x, R* y, const double* s, size_t n, int nb, cudaStream_t st);
 // y = a x + b y (real scalars)
 template <class R>
 cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t st);

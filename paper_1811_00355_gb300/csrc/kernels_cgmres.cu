@@ -31,7 +31,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
-constexpr int NRMAX = 8;
+constexpr int NRMAX = 12;
 constexpr long long SPIN_LIMIT = 1ll << 24;
 
 __device__ __forceinline__ cpx<float> ldc(const cpx<float>* p) {
@@ -692,7 +692,8 @@ const void* kernel_for(int NR) {
     case 1: return (const void*)k_cgmres<R, 1>;
     case 2: return (const void*)k_cgmres<R, 2>;
     case 4: return (const void*)k_cgmres<R, 4>;
-    default: return (const void*)k_cgmres<R, 8>;
+    case 8: return (const void*)k_cgmres<R, 8>;
+    default: return (const void*)k_cgmres<R, 12>;
   }
 }
 
@@ -706,13 +707,16 @@ struct Choice {
 // attribute is set only when it changes
 template <class R>
 cudaError_t smem_attr(int NR, size_t bytes) {
-  static size_t current[4] = {0, 0, 0, 0};
-  size_t& c = current[NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : 3];
+  static size_t current[5] = {0, 0, 0, 0, 0};
+  size_t& c = current[NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4];
   if (c == bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel_for<R>(NR), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) c = bytes;
   return e;
 }
+
+// widest lockstep group for nrhs right-hand sides (instances 1, 2, 4, 8, 12)
+inline int first_nr(int nrhs) { return nrhs >= 12 ? 12 : nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1; }
 
 template <class R>
 Choice choose_uncached(const Geom& g, int n2, int m, int nrhs);
@@ -729,7 +733,7 @@ Choice choose(const Geom& g, int n2, int m, int nrhs) {
   static int used = 0;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int first = nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+  const int first = first_nr(nrhs);
   for (int i = 0; i < used; ++i) {
     const Entry& e = cache[i];
     if (e.dev == dev && e.nb == g.nb && e.n2 == n2 && e.m == m && e.first == first) return e.c;
@@ -747,8 +751,7 @@ Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int NE = g.nb / 2;
   Choice best{};
-  int first = nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
-  for (int NR = first; NR >= 1; NR /= 2) {
+  for (int NR = first_nr(nrhs); NR >= 1; NR = NR == 12 ? 8 : NR / 2) {
     for (int pass = 0; pass < 2; ++pass) {
       const bool local = pass == 0;
       // grid: as many CTAs as fit (two per SM at most), each owning >= 1 site

@@ -409,15 +409,21 @@ __device__ __forceinline__ void dot_group(const PtrList<R>& v, int j0, const cpx
   }
 }
 
+// right-hand side r = blockIdx.y of a batch: vectors and w start r * rstride
+// complex numbers further, its partial sums k * gridDim.x slots further
 template <class R>
 __global__ void __launch_bounds__(RED_TPB) k_multi_dot_partial(PtrList<R> v, int k,
                                                                const R* __restrict__ w, size_t n,
-                                                               double* __restrict__ part) {
+                                                               double* __restrict__ part, size_t rstride) {
   __shared__ double sh[2 * DOT_J][RED_TPB];
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk;
   const size_t hi = lo + chunk < n ? lo + chunk : n;
-  const cpx<R>* wc = reinterpret_cast<const cpx<R>*>(w);
+  const size_t roff = blockIdx.y * rstride;
+  if (roff)
+    for (int j = 0; j < k; ++j) v.p[j] += 2 * roff;
+  part += (size_t)blockIdx.y * k * gridDim.x * 2;
+  const cpx<R>* wc = reinterpret_cast<const cpx<R>*>(w) + roff;
   const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
   for (int j0 = 0; j0 < k; j0 += DOT_J) {
     const int nj = k - j0 < DOT_J ? k - j0 : DOT_J;
@@ -463,18 +469,26 @@ __global__ void __launch_bounds__(RED_TPB) k_reduce_final(const double* __restri
 
 // w -= sum_j coef_j v_j (coef scaled by sign); with part != nullptr also the
 // CTA partial sums of ||w_new||^2 (slot layout of k_multi_dot_partial, k = 1)
+// batched as k_multi_dot_partial: right-hand side r = blockIdx.y takes its
+// coefficients r * cstride doubles further and its norm partials gridDim.x
+// slots further
 template <class R>
 __global__ void __launch_bounds__(RED_TPB) k_multi_axpy(PtrList<R> v, int k, const double* __restrict__ coef,
                                                         double sign, R* __restrict__ w, size_t n,
-                                                        double* __restrict__ part) {
+                                                        double* __restrict__ part, size_t rstride, int cstride) {
   __shared__ double cs[2 * MAXK];            // signed coefficients, loaded once per CTA
   __shared__ double sh[RED_TPB / 32];
+  coef += (size_t)blockIdx.y * cstride;
   for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) cs[j] = sign * coef[j];
   __syncthreads();
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk;
   const size_t hi = lo + chunk < n ? lo + chunk : n;
-  cpx<R>* wc = reinterpret_cast<cpx<R>*>(w);
+  const size_t roff = blockIdx.y * rstride;
+  if (roff)
+    for (int j = 0; j < k; ++j) v.p[j] += 2 * roff;
+  if (part) part += (size_t)blockIdx.y * gridDim.x * 2;
+  cpx<R>* wc = reinterpret_cast<cpx<R>*>(w) + roff;
   double nn = 0.0;
   for (size_t i = lo + threadIdx.x; i < hi; i += RED_TPB) {
     double re = (double)wc[i].re, im = (double)wc[i].im;
@@ -522,15 +536,20 @@ __global__ void __launch_bounds__(RED_TPB) k_multi_axpy(PtrList<R> v, int k, con
 // double2 or 6 float4 per site), so complex component c of local site q of
 // block B sits at (B 12 + c) Vb + q in w and at 2 ((B 6 + c / 2) Vb + q) + c % 2
 // in v_j.
+// (field r = blockIdx.y of a batch: its own coefficients, cstride apart)
 __global__ void __launch_bounds__(RED_TPB) k_multi_axpy_f32(PtrList<float> v, int k, const double* __restrict__ coef,
-                                                            double sign, double* __restrict__ w, size_t n, int Vb) {
+                                                            double sign, double* __restrict__ w, size_t n, int Vb,
+                                                            int cstride) {
   __shared__ double cs[2 * MAXK];
+  coef += (size_t)blockIdx.y * cstride;
   for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) cs[j] = sign * coef[j];
   __syncthreads();
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk;
   const size_t hi = lo + chunk < n ? lo + chunk : n;
-  cpx<double>* wc = reinterpret_cast<cpx<double>*>(w);
+  const size_t roff = (size_t)blockIdx.y * n;          // complex numbers per field
+  for (int j = 0; j < k; ++j) v.p[j] += 2 * roff;
+  cpx<double>* wc = reinterpret_cast<cpx<double>*>(w) + roff;
   const size_t per_block = (size_t)12 * Vb;
   for (size_t i = lo + threadIdx.x; i < hi; i += RED_TPB) {
     const size_t B = i / per_block;
@@ -567,12 +586,19 @@ __global__ void k_axpby(double a, const R* __restrict__ x, double b, R* __restri
   for (; i < n; i += stride) y[i] = (R)(a * (double)x[i] + b * (double)y[i]);
 }
 
+// y = x / sqrt(s) for field r = blockIdx.y of a batch (n reals per field,
+// s[2 r]); a zero norm gives y = 0
 template <class R>
 __global__ void k_scale_inv_norm(const R* __restrict__ x, R* __restrict__ y, const double* s, size_t n) {
   __shared__ double fs;                      // 1/sqrt(s) once per CTA (FP64 division is scarce)
-  if (threadIdx.x == 0) fs = 1.0 / sqrt(s[0]);
+  if (threadIdx.x == 0) {
+    const double q = s[2 * blockIdx.y];
+    fs = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+  }
   __syncthreads();
   const double f = fs;
+  x += (size_t)blockIdx.y * n;
+  y += (size_t)blockIdx.y * n;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (; i < n; i += stride) y[i] = (R)((double)x[i] * f);
@@ -701,16 +727,27 @@ cudaError_t dslash(const Geom& g, int mode, const R* x, const R* b, R* y, const 
 
 size_t reduce_scratch_len(int k) { return (size_t)k * RED_CTAS * 2; }
 
+static unsigned batch_ctas(int nb) {
+  const int c = RED_CTAS / (nb > 0 ? nb : 1);
+  return (unsigned)(c > 0 ? c : 1);
+}
+
+template <class R>
+cudaError_t multi_dot_batched(const R* const* v, int k, const R* w, size_t n, int nb, size_t rstride,
+                              double* scratch, double* out, cudaStream_t st) {
+  if (k > MAXK || k < 1 || nb < 1) return cudaErrorInvalidValue;
+  PtrList<R> pl;
+  for (int j = 0; j < k; ++j) pl.p[j] = v[j];
+  const unsigned C = batch_ctas(nb);
+  k_multi_dot_partial<R><<<dim3(C, nb), RED_TPB, 0, st>>>(pl, k, w, n, scratch, rstride);
+  k_reduce_final<<<nb * k, RED_TPB, 0, st>>>(scratch, (int)C, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
 template <class R>
 cudaError_t multi_dot(const R* const* v, int k, const R* w, size_t n, double* scratch, double* out,
                       cudaStream_t st) {
-  if (k > MAXK) return cudaErrorInvalidValue;
-  PtrList<R> pl;
-  for (int j = 0; j < k; ++j) pl.p[j] = v[j];
-  k_multi_dot_partial<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, w, n, scratch);
-  k_reduce_final<<<k, RED_TPB, 0, st>>>(scratch, RED_CTAS, out);
-  g_launches += 2;
-  return cudaGetLastError();
+  return multi_dot_batched<R>(v, k, w, n, 1, 0, scratch, out, st);
 }
 template <class R>
 cudaError_t norm2(const R* w, size_t n, double* scratch, double* out, cudaStream_t st) {
@@ -718,33 +755,45 @@ cudaError_t norm2(const R* w, size_t n, double* scratch, double* out, cudaStream
   return multi_dot<R>(v, 1, w, n, scratch, out, st);
 }
 template <class R>
-cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
-                       cudaStream_t st) {
-  if (k > MAXK) return cudaErrorInvalidValue;
+cudaError_t norm2_batched(const R* w, size_t n, int nb, size_t rstride, double* scratch, double* out,
+                          cudaStream_t st) {
+  const R* v[1] = {w};
+  return multi_dot_batched<R>(v, 1, w, n, nb, rstride, scratch, out, st);
+}
+template <class R>
+cudaError_t multi_axpy_batched(const R* const* v, int k, const double* coef, int cstride, double sign, R* w,
+                               size_t n, int nb, size_t rstride, double* scratch, double* norms,
+                               cudaStream_t st) {
+  if (k > MAXK || k < 1 || nb < 1) return cudaErrorInvalidValue;
   PtrList<R> pl;
   for (int j = 0; j < k; ++j) pl.p[j] = v[j];
-  k_multi_axpy<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, nullptr);
+  const unsigned C = batch_ctas(nb);
+  k_multi_axpy<R><<<dim3(C, nb), RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, norms ? scratch : nullptr, rstride,
+                                                   cstride);
   ++g_launches;
+  if (norms) {
+    k_reduce_final<<<nb, RED_TPB, 0, st>>>(scratch, (int)C, norms);
+    ++g_launches;
+  }
   return cudaGetLastError();
+}
+template <class R>
+cudaError_t multi_axpy(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
+                       cudaStream_t st) {
+  return multi_axpy_batched<R>(v, k, coef, 0, sign, w, n, 1, 0, nullptr, nullptr, st);
 }
 template <class R>
 cudaError_t multi_axpy_norm(const R* const* v, int k, const double* coef, double sign, R* w, size_t n,
                             double* scratch, double* out, cudaStream_t st) {
-  if (k > MAXK) return cudaErrorInvalidValue;
-  PtrList<R> pl;
-  for (int j = 0; j < k; ++j) pl.p[j] = v[j];
-  k_multi_axpy<R><<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, scratch);
-  k_reduce_final<<<1, RED_TPB, 0, st>>>(scratch, RED_CTAS, out);
-  g_launches += 2;
-  return cudaGetLastError();
+  return multi_axpy_batched<R>(v, k, coef, 0, sign, w, n, 1, 0, scratch, out, st);
 }
-cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, double sign,
-                                    double* w, int nf, cudaStream_t st) {
-  if (k > MAXK) return cudaErrorInvalidValue;
+cudaError_t multi_axpy_f32_into_f64(const Geom& g, const float* const* v, int k, const double* coef, int cstride,
+                                    double sign, double* w, int nf, cudaStream_t st) {
+  if (k > MAXK || k < 1 || nf < 1) return cudaErrorInvalidValue;
   PtrList<float> pl;
   for (int j = 0; j < k; ++j) pl.p[j] = v[j];
-  const size_t n = (size_t)nf * g.V * (SPINOR_NR / 2);
-  k_multi_axpy_f32<<<RED_CTAS, RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, g.Vb);
+  const size_t n = (size_t)g.V * (SPINOR_NR / 2);
+  k_multi_axpy_f32<<<dim3(batch_ctas(nf), nf), RED_TPB, 0, st>>>(pl, k, coef, sign, w, n, g.Vb, cstride);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -757,12 +806,17 @@ cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t s
   return cudaGetLastError();
 }
 template <class R>
-cudaError_t scale_by_inv_norm(const R* x, R* y, const double* s, size_t n, cudaStream_t st) {
-  unsigned nb = nblk(n, 256);
-  if (nb > 4096) nb = 4096;
-  k_scale_inv_norm<R><<<nb, 256, 0, st>>>(x, y, s, n);
+cudaError_t scale_by_inv_norm_batched(const R* x, R* y, const double* s, size_t n, int nb, cudaStream_t st) {
+  unsigned c = nblk(n, 256);
+  const unsigned cap = 4096 / (nb > 0 ? nb : 1) > 0 ? 4096 / (nb > 0 ? nb : 1) : 1;
+  if (c > cap) c = cap;
+  k_scale_inv_norm<R><<<dim3(c, nb), 256, 0, st>>>(x, y, s, n);
   ++g_launches;
   return cudaGetLastError();
+}
+template <class R>
+cudaError_t scale_by_inv_norm(const R* x, R* y, const double* s, size_t n, cudaStream_t st) {
+  return scale_by_inv_norm_batched<R>(x, y, s, n, 1, st);
 }
 
 cudaError_t random_spinors(const Geom& g, uint64_t seed, int n, double* dev64, cudaStream_t st) {
@@ -802,6 +856,13 @@ template cudaError_t multi_axpy<double>(const double* const*, int, const double*
                                         size_t, cudaStream_t);
 template cudaError_t multi_axpy_norm<double>(const double* const*, int, const double*, double, double*,
                                              size_t, double*, double*, cudaStream_t);
+template cudaError_t multi_dot_batched<double>(const double* const*, int, const double*, size_t, int, size_t,
+                                               double*, double*, cudaStream_t);
+template cudaError_t norm2_batched<double>(const double*, size_t, int, size_t, double*, double*, cudaStream_t);
+template cudaError_t multi_axpy_batched<double>(const double* const*, int, const double*, int, double, double*,
+                                                size_t, int, size_t, double*, double*, cudaStream_t);
+template cudaError_t scale_by_inv_norm_batched<double>(const double*, double*, const double*, size_t, int,
+                                                       cudaStream_t);
 template cudaError_t axpby<float>(double, const float*, double, float*, size_t, cudaStream_t);
 template cudaError_t axpby<double>(double, const double*, double, double*, size_t, cudaStream_t);
 template cudaError_t scale_by_inv_norm<float>(const float*, float*, const double*, size_t, cudaStream_t);

@@ -274,6 +274,46 @@ def test_solve_fp32_refinement_modes(refine):
     s.close()
 
 
+@pytest.mark.parametrize("prec,refine", [(1, 1e-5), (1, 0.0), (0, 0.0)])
+def test_solve_batched_matches_one_at_a_time(prec, refine):
+    """The lockstep batch gives every right-hand side its own FGMRES: each
+    solution reaches the tolerance by the oracle's D, and equals the
+    one-at-a-time solution within what the two stopping points allow."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, prec, outer_refine=refine)
+    s.run_setup()
+    op = oracle_op(L, eps, seed, m0, csw)
+    rhs = np.concatenate([syn.gaussian_spinors(3, L, 41), syn.point_sources(L)[:2]])
+    xb, ib = s.solve_batched(np.ascontiguousarray(rhs), 1e-10)
+    xs, is_ = s.solve(np.ascontiguousarray(rhs), 1e-10)
+    for k in range(rhs.shape[0]):
+        res = rel(op.apply(t(xb[k])).numpy(), rhs[k])
+        assert res <= 1e-10 and ib[k]["converged"] == 1, (k, res, ib[k])
+        assert abs(ib[k]["outer_iters"] - is_[k]["outer_iters"]) <= 3, (ib[k], is_[k])
+        assert rel(xb[k], xs[k]) < 1e-6
+    s.close()
+
+
+def test_solve_batched_edge_cases():
+    """A zero right-hand side in the batch gives x = 0; a batch of one equals
+    the single solve; more than 64 is rejected before any device work."""
+    P = _P()
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1)
+    s.run_setup()
+    rhs = syn.gaussian_spinors(2, L, 43)
+    rhs[1] = 0
+    x, info = s.solve_batched(rhs, 1e-10)
+    assert np.all(x[1] == 0) and info[1]["converged"] == 1
+    x1, _ = s.solve_batched(np.ascontiguousarray(rhs[:1]), 1e-10)
+    xs, _ = s.solve(np.ascontiguousarray(rhs[:1]), 1e-10)
+    assert rel(x1[0], xs[0]) < 1e-12
+    with pytest.raises(P.DDAMGError) as e:
+        s.solve_batched(np.zeros((65,) + rhs.shape[1:], np.complex128), 1e-10)
+    assert e.value.status == 1
+    s.close()
+
+
 def test_random_vectors_match_philox_definition():
     P = _P()
     s = make(SMALL, 0)
