@@ -234,6 +234,10 @@ def run_ours(args):
         e2e = {"value": round(12 / statistics.mean(et) * world, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(U_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
 
+    var = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        var = variants(P, torch, stream, U_dev, b_dev, args.steps, flush)
+
     sten = None
     if rank == 0 and not args.no_stencils:
         sten = stencils(P, torch, stream, pk, pk_kind)
@@ -260,11 +264,84 @@ def run_ours(args):
                             "max_true_residual": max(i["true_residual"] for info in infos for i in info),
                             "step_seconds": [round(t, 4) for t in times]},
             "kernel_ms": {k: round(v[0], 3) for k, v in classes.items()},
+            "variants": var,
             "stencils": sten,
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def variants(P, torch, stream, U_dev, b_dev, steps, flush):
+    """The same 12-RHS workload (setup + 12 point sources to 1e-10) in two
+    other forms: the 12 sources solved together in one lockstep batch (FP32
+    inner solver), and the plain single-RHS form with an FP64 inner solver."""
+    w = WORKLOAD
+    out = {}
+    for name, prec, batched, n in (("batched_f32", P.FP32, True, steps), ("single_f64", P.FP64, False, 1)):
+        params = workload_params(P)
+        params.precision = prec
+        s = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
+        solve = s.solve_batched if batched else s.solve
+        try:
+            s.run_setup()
+            solve(b_dev, w["tol"])
+            times, infos = [], []
+            for _ in range(n):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.run_setup()
+                x, info = solve(b_dev, w["tol"])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                infos.append(info)
+            for info in infos:
+                for i in info:
+                    if not (i["converged"] and i["true_residual"] <= w["tol"]):
+                        raise RuntimeError(f"{name}: a solve missed the tolerance: {i}")
+            out[name] = {"value": round(12 * n / sum(times), 3), "unit": UNIT, "steps": n,
+                         "ms_per_step": round(1e3 * sum(times) / n, 2),
+                         "dtype": "f32+f64" if prec == P.FP32 else "f64",
+                         "outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in infos[-1]),
+                         "max_true_residual": max(i["true_residual"] for info in infos for i in info)}
+        finally:
+            s.close()
+    # the paper's second-mass use of a setup: keep the test vectors, change
+    # m0 (heavier quark), rebuild the clover term and D_c, solve again
+    params = workload_params(P)
+    s = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
+    try:
+        s.run_setup()
+        m_new = w["m0"] + 0.1
+        s.update_mass(m_new, w["csw"])
+        s.solve_batched(b_dev, w["tol"])
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.update_mass(m_new, w["csw"])
+        e1.record(stream)
+        x, info = s.solve_batched(b_dev, w["tol"])
+        e2.record(stream)
+        torch.cuda.synchronize()
+        for i in info:
+            if not (i["converged"] and i["true_residual"] <= w["tol"]):
+                raise RuntimeError(f"new-mass solve missed the tolerance: {i}")
+        t_up = e0.elapsed_time(e1) / 1e3
+        t_all = e0.elapsed_time(e2) / 1e3
+        out["new_mass_batched_f32"] = {"value": round(12 / t_all, 3), "unit": UNIT, "m0": m_new,
+                                       "update_ms": round(1e3 * t_up, 2), "ms_per_step": round(1e3 * t_all, 2),
+                                       "outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in info),
+                                       "max_true_residual": max(i["true_residual"] for i in info)}
+    finally:
+        s.close()
+    return out
 
 
 def _tiled(a, small, L):
@@ -419,6 +496,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stencils", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -32,7 +32,7 @@ constexpr int TPB = 256;
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
 constexpr int NRMAX = 12;
-constexpr long long SPIN_LIMIT = 1ll << 24;
+constexpr long long SPIN_LIMIT = 1ll << 21;   // polls of about an L2 round trip each
 
 __device__ __forceinline__ cpx<float> ldc(const cpx<float>* p) {
   float2 t = __ldcg(reinterpret_cast<const float2*>(p));
@@ -50,28 +50,43 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
+// Grid barrier on a counter that only grows during a launch (zeroed before
+// it): at its e-th barrier every CTA adds 1 and waits until the counter
+// reaches e * gridDim.x.  The arrival is a fence followed by a relaxed
+// reduction (no reply awaited), the wait an acquire load, so a barrier costs
+// about one L2 round trip after the last arrival.  The wait is bounded (about
+// a second); on time-out the CTA records DDAMG_ETIMEOUT and leaves, and the
+// CTAs still waiting for it then time out at this or their next barrier.
+__device__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__shared__ unsigned bar_epoch;       // barriers passed by this CTA in this launch
+
+// thread 0 zeroes the count at kernel entry (a __syncthreads must follow
+// before the first barrier)
+__device__ void grid_barrier_reset() {
+  if (threadIdx.x == 0) bar_epoch = 0;
+}
+
 __device__ bool grid_barrier(unsigned* bar, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    unsigned my = *gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
+    const unsigned target = (++bar_epoch) * gridDim.x;
+    __threadfence();                 // the CTA's writes (ordered by the bar.sync above) first
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == my) {
-        if (++spins > SPIN_LIMIT) { atomicExch(status, 6); ok = 0; break; }
-        __nanosleep(32);
+    long long spins = 0;
+    while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+      if (++spins > SPIN_LIMIT) {
+        atomicExch(status, 6);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
-    if (*(volatile int*)status != 0) ok = 0;
     ok_s = ok;
   }
   __syncthreads();
@@ -254,6 +269,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   __shared__ int exn[NR];      // explicit norm needed (FP32 path)
 
   const int G = gridDim.x;
+  grid_barrier_reset();
   const int lo = min(NE, (int)blockIdx.x * a.per);
   const int hi = min(NE, lo + a.per);
   const int nown = hi - lo;
