@@ -40,6 +40,10 @@ WORKLOAD = dict(L=(16, 16, 16, 16), block=(4, 4, 4, 4), eps=0.25, seed=1, m0=-0.
 # operator once (self + 8 links on every site) plus A_oo^-1 on the odd sites.
 SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
 L2_BYTES = 129 * 2 ** 20
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the
+# committed ncu capture profiles/k_cgmres_16x4_workload.md (single-RHS coarse
+# solve of the first timed solve); None for a kernel without a current capture
+TRAFFIC_BYTES_PER_LAUNCH = {"coarse_gmres": 29_881_088 + 41_984}
 # stencil bandwidth lattice: 32^3 x 64 (the lattice of the batched workload),
 # far larger than L2, links tiled from an 8^4 field of the same generator
 STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
@@ -198,7 +202,7 @@ def run_ours(args):
     dom = max(classes, key=lambda k: classes[k][0])
     ms, n = classes[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": None, "traffic": None, "peak_kind": pk_kind + " (burst copy)",
+            "frac": None, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "peak_kind": pk_kind + " (burst copy)",
             "share_of_step": round(ms / (1e3 * T / world) if T else 0.0, 3)}
     if dom == "sap_sweep" and n:
         per_launch = (V // 2) * SAP_BYTES_PER_SITE
