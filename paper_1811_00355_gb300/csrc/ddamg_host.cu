@@ -72,6 +72,7 @@ struct ddamg_ctx {
   bool have_coarse = false;
   void* Dc = nullptr;
   void* Ainv = nullptr;
+  void* AD = nullptr;             // A_oo^-1 D_c hop blocks of the odd coarse sites
   void* cwork = nullptr;
   int* d_iters = nullptr;        // per-rhs coarse iterations
   int* d_iters_acc = nullptr;    // running total
@@ -498,6 +499,7 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   CoarseSolveArgs a;
   a.Dc = h->Dc;
   a.Ainv = h->Ainv;
+  a.AinvD = h->AD;
   a.n = h->p.n_v;
   a.tol = tol;
   a.restart = h->p.coarse_restart;
@@ -545,6 +547,7 @@ ddamg_status alloc_coarse(ddamg_ctx* h) {
   const size_t n2 = h->n2;
   TRY(dalloc(h, &h->Dc, (size_t)h->g.nb * 9 * n2 * n2 * 2 * rs));
   TRY(dalloc(h, &h->Ainv, (size_t)h->g.nb * n2 * n2 * 2 * rs));
+  TRY(dalloc(h, &h->AD, (size_t)(h->g.nb / 2) * 8 * n2 * n2 * 2 * rs));
   TRY(dalloc(h, &h->cwork, coarse_gmres_work_bytes(h->g, h->p.n_v, h->p.coarse_restart, rs)));
   return DDAMG_OK;
 }
@@ -565,9 +568,11 @@ ddamg_status build_coarse_op(ddamg_ctx* h) {
   if (h->p.precision == DDAMG_FP32) {
     CK(assemble_coarse<float>(h->g, h->lam32, h->p.n_v, h->g32, h->A32, (float*)h->Dc, h->st));
     CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
+    CK(premultiply_odd<float>(h->g, (float*)h->Dc, (float*)h->Ainv, h->p.n_v, (float*)h->AD, h->st));
   } else {
     CK(assemble_coarse<double>(h->g, h->lam64, h->p.n_v, h->g64, h->A64, (double*)h->Dc, h->st));
     CK(invert_self_blocks<double>(h->g, (double*)h->Dc, h->p.n_v, (double*)h->Ainv, h->d_status, h->st));
+    CK(premultiply_odd<double>(h->g, (double*)h->Dc, (double*)h->Ainv, h->p.n_v, (double*)h->AD, h->st));
   }
   int sing = 0;
   CK(cudaMemcpyAsync(&sing, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -1202,6 +1207,7 @@ ddamg_status coarse_solve_noalloc_impl(ddamg_ctx* h, int nrhs, const double* in,
   CoarseSolveArgs a;
   a.Dc = h->Dc;
   a.Ainv = h->Ainv;
+  a.AinvD = h->AD;
   a.n = h->p.n_v;
   a.tol = tol;
   a.restart = h->p.coarse_restart;

@@ -148,6 +148,11 @@ cudaError_t assemble_coarse(const Geom& g, const R* lam, int n, const R* gauge,
 template <class R>
 cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* singular,
                                cudaStream_t st);
+// AD[ko][d - 1] = A_oo^-1(X) D_c[X][d] for the odd coarse sites X = codd[ko]
+// and d = 1..8 (column-major, FP64 accumulation): the odd half of the
+// even-odd Schur complement becomes one block product per site
+template <class R>
+cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R* AD, cudaStream_t st);
 // nblocks column-major blocks -> row-major complex doubles (host layout)
 template <class R>
 cudaError_t coarse_export(const R* Dc, int n, size_t nblocks, double* out, cudaStream_t st);
@@ -168,6 +173,7 @@ cudaError_t coarse_to_f64(const R* src, double* dst, size_t ncomplex, cudaStream
 struct CoarseSolveArgs {
   const void* Dc;
   const void* Ainv;
+  const void* AinvD;   // A_oo^-1 D_c[X][d], d = 1..8, per odd site (premultiply_odd)
   int n;            // test vectors (2n components per coarse site)
   double tol;
   int restart;      // <= 64

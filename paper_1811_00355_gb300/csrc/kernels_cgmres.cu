@@ -28,7 +28,10 @@ namespace ddamg {
 
 namespace {
 
-constexpr int TPB = 256;
+constexpr int TPB = 512;
+// partial-sum groups of mrhs_matvec (the plan's mvp buffer): more column
+// chunks for few right-hand sides, fewer where the buffer grows with NR
+__host__ __device__ constexpr int mvp_groups(int NR) { return NR >= 8 ? 9 : 18; }
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
 constexpr int NRMAX = 12;
@@ -71,13 +74,22 @@ __device__ void grid_barrier_reset() {
   if (threadIdx.x == 0) bar_epoch = 0;
 }
 
-__device__ bool grid_barrier(unsigned* bar, int* status) {
-  __shared__ int ok_s;
+// Split form: grid_arrive publishes this CTA's writes and counts it in;
+// grid_wait returns once every CTA has arrived.  Between the two a CTA may do
+// work that touches only its own shared memory and registers.
+__device__ void grid_arrive(unsigned* bar) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned target = (++bar_epoch) * gridDim.x;
+    ++bar_epoch;
     __threadfence();                 // the CTA's writes (ordered by the bar.sync above) first
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+  }
+}
+
+__device__ bool grid_wait(unsigned* bar, int* status) {
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    const unsigned target = bar_epoch * gridDim.x;
     int ok = 1;
     long long spins = 0;
     while ((int)(ld_acquire_gpu(bar) - target) < 0) {
@@ -91,6 +103,11 @@ __device__ bool grid_barrier(unsigned* bar, int* status) {
   }
   __syncthreads();
   return ok_s != 0;
+}
+
+__device__ bool grid_barrier(unsigned* bar, int* status) {
+  grid_arrive(bar);
+  return grid_wait(bar, status);
 }
 
 // shared-memory plan, identical on host and device
@@ -126,7 +143,7 @@ __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, 
     lb = g;
   }
   p.sv = put((size_t)NR * 9 * n2 * c);
-  p.mvp = put((size_t)9 * NR * n2 * c);
+  p.mvp = put((size_t)mvp_groups(NR) * NR * n2 * c);
   p.tmp = put((size_t)NR * n2 * c);
   p.hc = put((size_t)NR * 2 * (m + 1) * 8);
   p.h2 = put((size_t)NR * 2 * (m + 1) * 8);
@@ -153,6 +170,7 @@ struct CGA {
   Geom g;
   const cpx<R>* Dc;
   const cpx<R>* Ainv;
+  const cpx<R>* AD;    // [odd site][8] A_oo^-1 D_c blocks
   int n2;
   double tol;
   int m;
@@ -183,21 +201,28 @@ struct CGA {
 // loaded entry to all NR vectors.  The column range is split into CC chunks
 // when there are few directions.  Partials land in mvp[unit-group][r][row] and
 // are summed in a fixed order.
+// (M holds the blocks of directions d0 .. d1 - 1 from its start when
+// m_from_d0 is set, else the blocks of directions 0 .. d1 - 1)
 template <class R, int NR>
 __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const cpx<R>* sv, int d0, int d1,
-                                            int n2, cpx<R>* mvp, cpx<R>* out, int out_stride) {
+                                            int n2, cpx<R>* mvp, cpx<R>* out, int out_stride,
+                                            bool m_from_d0 = false) {
   using T = typename U16<R>::T;
   constexpr int RPU = 16 / (2 * sizeof(R));
   const int NP = n2 / RPU;
   const int ND = d1 - d0;
-  const int CC = ND >= 8 ? 1 : 8 / ND;
+  // column chunks: enough units for every thread, at most mvp_groups(NR) groups
+  int CC = (int)blockDim.x / (ND * NP);
+  if (CC * ND > mvp_groups(NR)) CC = mvp_groups(NR) / ND;
+  if (CC < 1) CC = 1;
+  if (CC > n2) CC = n2;
   const int CW = (n2 + CC - 1) / CC;
   const int units = ND * CC * NP;
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
     const int grp = u / NP, j = u - grp * NP;
     const int dd = grp / CC, cc = grp - dd * CC, d = d0 + dd;
     const int c0 = cc * CW, c1 = min(n2, c0 + CW);
-    const T* col = reinterpret_cast<const T*>(M + (size_t)d * n2 * n2) + j;
+    const T* col = reinterpret_cast<const T*>(M + (size_t)(m_from_d0 ? d - d0 : d) * n2 * n2) + j;
     cpx<R> acc[NR][RPU];
 #pragma unroll
     for (int r = 0; r < NR; ++r)
@@ -266,6 +291,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   int* tot = reinterpret_cast<int*>(sm + P.tot);          // iterations so far
   int* conv = reinterpret_cast<int*>(sm + P.conv);        // converged (or gave up)
   __shared__ int any_s;
+  __shared__ int any_act_s;
   __shared__ int exn[NR];      // explicit norm needed (FP32 path)
 
   const int G = gridDim.x;
@@ -291,18 +317,13 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
     }
     __syncthreads();
   };
-  // odd phase: to[r][ko] = A_oo^-1 sum_{d>=1} Dc[X][d] src[r][nbr]
+  // odd phase: to[r][ko] = sum_{d>=1} (A_oo^-1 Dc[X][d]) src[r][nbr]
   auto phase_odd = [&](const cpx<R>* src) {
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
       stage_odd(X, src);
-      mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, 1, 9, n2, mvp, tmp, n2);
-      for (int idx = tx; idx < NR * n2; idx += TPB) {
-        const int r = idx / n2, c = idx - r * n2;
-        sv[(r * 9) * n2 + c] = tmp[idx];
-      }
-      __syncthreads();
-      mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, a.to + (size_t)ko * n2, (int)vstr);
+      mrhs_matvec<R, NR>(a.AD + (size_t)ko * 8 * n2 * n2, sv, 1, 9, n2, mvp, a.to + (size_t)ko * n2, (int)vstr,
+                         true);
     }
   };
   // even phase: out[r][kk] = (self ? A_ee v : 0) - sum_{d>=1} Dc[X][d] to[r][nbr] (+ bsrc)
@@ -368,6 +389,31 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           const int j = pr / NR, r = pr - j * NR;
           dst[(size_t)r * dstride + 2 * j] = re;
           dst[(size_t)r * dstride + 2 * j + 1] = im;
+        }
+      }
+    }
+    __syncthreads();
+  };
+
+  // gather(kcount, false, hc, dstride) and gather_norm_slot(kcount, hn) in
+  // one pass: one round of L2 loads instead of two
+  auto gather_dots_norm = [&](int kcount, A* dst, int dstride, A* hn) {
+    const int pairs = (kcount + 1) * NR;
+    for (int pr = wid; pr < pairs; pr += NW) {
+      A re = 0, im = 0;
+      for (int c = lane; c < G; c += 32) {
+        re += (A)__ldcg(a.part + ((size_t)pr * G + c) * 2);
+        im += (A)__ldcg(a.part + ((size_t)pr * G + c) * 2 + 1);
+      }
+      re = wsum(re);
+      im = wsum(im);
+      if (lane == 0) {
+        const int j = pr / NR, r = pr - j * NR;
+        if (j < kcount) {
+          dst[(size_t)r * dstride + 2 * j] = re;
+          dst[(size_t)r * dstride + 2 * j + 1] = im;
+        } else {
+          hn[r] = re;                  // squared norm (real)
         }
       }
     }
@@ -475,87 +521,9 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         phase_odd(a.wg);
         if (!grid_barrier(a.bar, a.status)) return;
         phase_even(V + (size_t)k * NR * L, true, wl, nullptr);
-        if constexpr (sizeof(R) == 4) {
-          // FP32: one classical Gram-Schmidt pass whose reduction also carries
-          // ||w||^2, so ||w_new||^2 = ||w||^2 - sum_j |h_j|^2 (Pythagoras); an
-          // explicit norm is taken only if that difference has cancelled
-          partial(k + 1, false);
-          partial_norm_slot(k + 1);
-          if (!grid_barrier(a.bar, a.status)) return;
-          gather(k + 1, false, hc, 2 * (m + 1));
-          gather_norm_slot(k + 1, hnv);
-          if (tx < NR) {
-            const A* hr = hc + (size_t)tx * 2 * (m + 1);
-            A s2 = hnv[tx];
-            for (int j = 0; j <= k; ++j) s2 -= hr[2 * j] * hr[2 * j] + hr[2 * j + 1] * hr[2 * j + 1];
-            exn[tx] = (act[tx] && !(s2 > A(1e-3) * hnv[tx])) ? 1 : 0;
-            hnv[tx] = s2 > A(0) ? s2 : A(0);
-          }
-          __syncthreads();
-          for (int idx = tx; idx < NR * Lo; idx += TPB) {
-            const int r = idx / Lo, e = idx - r * Lo;
-            if (!act[r]) continue;
-            cpx<R> w0 = wl[(size_t)r * L + e];
-            const A* hr = hc + (size_t)r * 2 * (m + 1);
-            for (int j = 0; j <= k; ++j) {
-              cpx<R> v = Vk(j, r)[e];
-              cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
-              w0 = w0 - c * v;
-            }
-            wl[(size_t)r * L + e] = w0;
-            a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
-          }
-          if (tx == 0) {
-            int any = 0;
-            for (int r = 0; r < NR; ++r) any |= exn[r];
-            any_s = any;
-          }
-          __syncthreads();
-          // this barrier publishes the neighbours' w for the next odd phase
-          if (any_s) {
-            partial(1, true);
-            if (!grid_barrier(a.bar, a.status)) return;
-            gather(1, true, h2, 1);
-            if (tx < NR && exn[tx]) hnv[tx] = h2[tx];
-            __syncthreads();
-          } else {
-            if (!grid_barrier(a.bar, a.status)) return;
-          }
-        } else {
-          // FP64: classical Gram-Schmidt with one re-orthogonalisation pass
-          for (int pass = 0; pass < 2; ++pass) {
-            partial(k + 1, false);
-            if (!grid_barrier(a.bar, a.status)) return;
-            A* hh = pass == 0 ? hc : h2;
-            gather(k + 1, false, hh, 2 * (m + 1));
-            for (int idx = tx; idx < NR * Lo; idx += TPB) {
-              const int r = idx / Lo, e = idx - r * Lo;
-              if (!act[r]) continue;
-              cpx<R> w0 = wl[(size_t)r * L + e];
-              const A* hr = hh + (size_t)r * 2 * (m + 1);
-              for (int j = 0; j <= k; ++j) {
-                cpx<R> v = Vk(j, r)[e];
-                cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
-                w0 = w0 - c * v;
-              }
-              wl[(size_t)r * L + e] = w0;
-              if (pass == 1) a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
-            }
-            if (pass == 1 && tx < NR)
-              for (int j = 0; j <= k; ++j) {
-                hc[(size_t)tx * 2 * (m + 1) + 2 * j] += h2[(size_t)tx * 2 * (m + 1) + 2 * j];
-                hc[(size_t)tx * 2 * (m + 1) + 2 * j + 1] += h2[(size_t)tx * 2 * (m + 1) + 2 * j + 1];
-              }
-            __syncthreads();
-          }
-          // ||w||: this barrier also publishes the neighbours' w for the next odd phase
-          partial(1, true);
-          if (!grid_barrier(a.bar, a.status)) return;
-          gather(1, true, hnv, 1);
-        }
-        // Givens per right-hand side (thread r), V_{k+1} = w / h
-        if (tx < NR && act[tx]) {
-          const int r = tx;
+        // Givens rotation of right-hand side r's new Hessenberg column (one
+        // thread), new residual estimate, scale 1/h of V_{k+1}, convergence
+        auto givens = [&](int r) {
           const A hn = sqrt(hnv[r]);
           A* col = hc + (size_t)r * 2 * (m + 1);   // this column of the Hessenberg matrix
           col[2 * (k + 1)] = hn;
@@ -599,19 +567,117 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           scl[r] = hn > A(0) ? A(1) / hn : A(0);
           hnv[r] = hn;
           if (res <= (A)a.tol * bnorm[r] || hn == A(0) || tot[r] >= a.max_iter) act[r] = 0;
+        };
+        if constexpr (sizeof(R) == 4) {
+          // FP32: one classical Gram-Schmidt pass whose reduction also carries
+          // ||w||^2, so ||w_new||^2 = ||w||^2 - sum_j |h_j|^2 (Pythagoras); an
+          // explicit norm is taken only if that difference has cancelled
+          partial(k + 1, false);
+          partial_norm_slot(k + 1);
+          if (!grid_barrier(a.bar, a.status)) return;
+          gather_dots_norm(k + 1, hc, 2 * (m + 1), hnv);
+          if (tx < NR) {
+            const A* hr = hc + (size_t)tx * 2 * (m + 1);
+            A s2 = hnv[tx];
+            for (int j = 0; j <= k; ++j) s2 -= hr[2 * j] * hr[2 * j] + hr[2 * j + 1] * hr[2 * j + 1];
+            exn[tx] = (act[tx] && !(s2 > A(1e-3) * hnv[tx])) ? 1 : 0;
+            hnv[tx] = s2 > A(0) ? s2 : A(0);
+          }
+          __syncthreads();
+          if (tx == 0) {
+            int any = 0;
+            for (int r = 0; r < NR; ++r) any |= exn[r];
+            any_s = any;
+          }
+          for (int idx = tx; idx < NR * Lo; idx += TPB) {
+            const int r = idx / Lo, e = idx - r * Lo;
+            if (!act[r]) continue;
+            cpx<R> w0 = wl[(size_t)r * L + e];
+            const A* hr = hc + (size_t)r * 2 * (m + 1);
+            for (int j = 0; j <= k; ++j) {
+              cpx<R> v = Vk(j, r)[e];
+              cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
+              w0 = w0 - c * v;
+            }
+            wl[(size_t)r * L + e] = w0;
+            a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
+          }
+          __syncthreads();
+          if (any_s) {
+            partial(1, true);
+            if (!grid_barrier(a.bar, a.status)) return;
+            gather(1, true, h2, 1);
+            if (tx < NR && exn[tx]) hnv[tx] = h2[tx];
+            __syncthreads();
+            if (tx < NR && act[tx]) givens(tx);
+            __syncthreads();
+          } else {
+            // publish w for the next odd phase; the Givens step and the new
+            // basis vector are local work done while the other CTAs arrive
+            grid_arrive(a.bar);
+            if (tx < NR && act[tx]) givens(tx);
+            __syncthreads();
+          }
+          for (int idx = tx; idx < NR * Lo; idx += TPB) {
+            const int r = idx / Lo, e = idx - r * Lo;
+            Vk(k + 1, r)[e] = (R)scl[r] * wl[(size_t)r * L + e];
+          }
+          if (tx == 0) {
+            int any = 0;
+            for (int r = 0; r < NR; ++r) any |= act[r];
+            any_act_s = any;
+          }
+          if (!any_s) {
+            if (!grid_wait(a.bar, a.status)) return;
+          } else {
+            __syncthreads();
+          }
+          if (!any_act_s) break;
+        } else {
+          // FP64: classical Gram-Schmidt with one re-orthogonalisation pass
+          for (int pass = 0; pass < 2; ++pass) {
+            partial(k + 1, false);
+            if (!grid_barrier(a.bar, a.status)) return;
+            A* hh = pass == 0 ? hc : h2;
+            gather(k + 1, false, hh, 2 * (m + 1));
+            for (int idx = tx; idx < NR * Lo; idx += TPB) {
+              const int r = idx / Lo, e = idx - r * Lo;
+              if (!act[r]) continue;
+              cpx<R> w0 = wl[(size_t)r * L + e];
+              const A* hr = hh + (size_t)r * 2 * (m + 1);
+              for (int j = 0; j <= k; ++j) {
+                cpx<R> v = Vk(j, r)[e];
+                cpx<R> c = mk((R)hr[2 * j], (R)hr[2 * j + 1]);
+                w0 = w0 - c * v;
+              }
+              wl[(size_t)r * L + e] = w0;
+              if (pass == 1) a.wg[r * vstr + (size_t)lo * n2 + e] = w0;
+            }
+            if (pass == 1 && tx < NR)
+              for (int j = 0; j <= k; ++j) {
+                hc[(size_t)tx * 2 * (m + 1) + 2 * j] += h2[(size_t)tx * 2 * (m + 1) + 2 * j];
+                hc[(size_t)tx * 2 * (m + 1) + 2 * j + 1] += h2[(size_t)tx * 2 * (m + 1) + 2 * j + 1];
+              }
+            __syncthreads();
+          }
+          // ||w||: this barrier also publishes the neighbours' w for the next odd phase
+          partial(1, true);
+          if (!grid_barrier(a.bar, a.status)) return;
+          gather(1, true, hnv, 1);
+          if (tx < NR && act[tx]) givens(tx);
+          __syncthreads();
+          for (int idx = tx; idx < NR * Lo; idx += TPB) {
+            const int r = idx / Lo, e = idx - r * Lo;
+            Vk(k + 1, r)[e] = (R)scl[r] * wl[(size_t)r * L + e];
+          }
+          if (tx == 0) {
+            int any = 0;
+            for (int r = 0; r < NR; ++r) any |= act[r];
+            any_act_s = any;
+          }
+          __syncthreads();
+          if (!any_act_s) break;
         }
-        __syncthreads();
-        for (int idx = tx; idx < NR * Lo; idx += TPB) {
-          const int r = idx / Lo, e = idx - r * Lo;
-          Vk(k + 1, r)[e] = (R)scl[r] * wl[(size_t)r * L + e];
-        }
-        if (tx == 0) {
-          int any = 0;
-          for (int r = 0; r < NR; ++r) any |= act[r];
-          any_s = any;
-        }
-        __syncthreads();
-        if (!any_s) break;
       }
       // y = R^-1 g ; x_e += V y   (every right-hand side of this cycle)
       if (tx < NR && !conv[tx]) {
@@ -827,6 +893,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.g = g;
   a.Dc = reinterpret_cast<const cpx<R>*>(ca.Dc);
   a.Ainv = reinterpret_cast<const cpx<R>*>(ca.Ainv);
+  a.AD = reinterpret_cast<const cpx<R>*>(ca.AinvD);
   a.n2 = n2;
   a.tol = ca.tol;
   a.m = ca.restart;

@@ -545,6 +545,35 @@ __global__ void k_coarse_apply(Geom g, const cpx<R>* __restrict__ Dc, int n2, co
                 part);
 }
 
+// C = A B for one odd site X and direction d (column-major 2n x 2n blocks)
+template <class R>
+__global__ void k_premultiply_odd(Geom g, const cpx<R>* __restrict__ Dc, const cpx<R>* __restrict__ Ainv, int n2,
+                                  cpx<R>* __restrict__ AD) {
+  extern __shared__ __align__(16) unsigned char psh[];
+  cpx<R>* As = reinterpret_cast<cpx<R>*>(psh);
+  cpx<R>* Bs = As + n2 * n2;
+  const int ko = blockIdx.x, d = blockIdx.y + 1;
+  const int X = g.codd[ko];
+  const cpx<R>* A = Ainv + (size_t)X * n2 * n2;
+  const cpx<R>* B = Dc + ((size_t)X * 9 + d) * n2 * n2;
+  for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
+    As[i] = A[i];
+    Bs[i] = B[i];
+  }
+  __syncthreads();
+  cpx<R>* C = AD + ((size_t)ko * 8 + (d - 1)) * n2 * n2;
+  for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
+    const int r = i % n2, c = i / n2;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < n2; ++k) {
+      const cpx<R> a = As[k * n2 + r], b = Bs[c * n2 + k];
+      re += (double)a.re * (double)b.re - (double)a.im * (double)b.im;
+      im += (double)a.re * (double)b.im + (double)a.im * (double)b.re;
+    }
+    C[i] = mk((R)re, (R)im);
+  }
+}
+
 template <class R>
 __global__ void k_coarse_export(const cpx<R>* __restrict__ src, double* __restrict__ dst, int n2, size_t nblocks) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -633,6 +662,19 @@ cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* 
 }
 
 template <class R>
+cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R* AD, cudaStream_t st) {
+  const int n2 = 2 * n;
+  const size_t smem = (size_t)2 * n2 * n2 * sizeof(cpx<R>);
+  cudaError_t e = cudaFuncSetAttribute(k_premultiply_odd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_premultiply_odd<R><<<dim3(g.nb / 2, 8), 256, smem, st>>>(g, reinterpret_cast<const cpx<R>*>(Dc),
+                                                           reinterpret_cast<const cpx<R>*>(Ainv), n2,
+                                                           reinterpret_cast<cpx<R>*>(AD));
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs, cudaStream_t st) {
   int n2 = 2 * n;
   size_t smem = (size_t)18 * n2 * sizeof(cpx<R>);
@@ -680,6 +722,7 @@ template cudaError_t coarse_export<double>(const double*, int, size_t, double*, 
   template cudaError_t assemble_coarse<R>(const Geom&, const R*, int, const R*, const R*, R*,           \
                                           cudaStream_t);                                                \
   template cudaError_t invert_self_blocks<R>(const Geom&, const R*, int, R*, int*, cudaStream_t);       \
+  template cudaError_t premultiply_odd<R>(const Geom&, const R*, const R*, int, R*, cudaStream_t);      \
   template cudaError_t coarse_apply<R>(const Geom&, const R*, int, const R*, R*, int, cudaStream_t);    \
   template cudaError_t coarse_from_f64<R>(const double*, R*, size_t, cudaStream_t);                     \
   template cudaError_t coarse_to_f64<R>(const R*, double*, size_t, cudaStream_t);                       \
