@@ -36,8 +36,7 @@ WORKLOAD = dict(L=(16, 16, 16, 16), block=(4, 4, 4, 4), eps=0.25, seed=1, m0=-0.
                 n_v=20, setup_iters=4, n_sap=4, mr_iters=4, coarse_tol=5e-2, tol=1e-10)
 # algorithmic (compulsory) bytes per site of one launch of each timed kernel,
 # FP32 storage with two-row links: SAP sweep reads b, x, 4 links, A, A^-1 and
-# writes x on its blocks; the coarse GMRES iteration streams the coarse
-# operator once (self + 8 links on every site) plus A_oo^-1 on the odd sites.
+# writes x on its blocks (the coarse GMRES bytes are computed below).
 SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the
@@ -158,7 +157,6 @@ def run_ours(args):
         raise RuntimeError(f"warm-up solves did not converge: {bad}")
 
     solver.reset_stats()
-    solver.enable_kernel_timing(True)
     times = []
     infos = []
     if world > 1:
@@ -178,6 +176,15 @@ def run_ours(args):
             infos.append(info)
     if world > 1:
         dist.barrier()
+    torch.cuda.synchronize()
+    launches = solver.stats()["kernel_launches"]
+    # per-kernel device times for the roofline line come from one more step
+    # with CUDA events around every timed launch (events between kernels
+    # also serialise them, so this step is not part of the timed value)
+    solver.reset_stats()
+    solver.enable_kernel_timing(True)
+    flush.fill_(1.0)
+    step()
     torch.cuda.synchronize()
     st = solver.stats()
     solver.enable_kernel_timing(False)
@@ -203,7 +210,7 @@ def run_ours(args):
     ms, n = classes[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": None, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(dom), "peak_kind": pk_kind + " (burst copy)",
-            "share_of_step": round(ms / (1e3 * T / world) if T else 0.0, 3)}
+            "share_of_step": round(ms / (1e3 * T / args.steps) if T else 0.0, 3)}
     if dom == "sap_sweep" and n:
         per_launch = (V // 2) * SAP_BYTES_PER_SITE
         achieved = per_launch / (ms / n * 1e-3) / 1e9
@@ -212,7 +219,9 @@ def run_ours(args):
     elif dom == "coarse_gmres" and n:
         nx = V // 256
         n2 = 2 * w["n_v"]
-        per_iter = nx * 9 * n2 * n2 * 8 + (nx // 2) * n2 * n2 * 8
+        # one iteration streams the 9 blocks of D_c of every even site and the
+        # 8 premultiplied blocks A_oo^-1 D_c of every odd site (FP32 complex)
+        per_iter = (nx // 2) * (9 + 8) * n2 * n2 * 8
         its = sum(i["coarse_iters"] for info in infos for i in info)
         per_launch = per_iter * its / max(1, sum(i["precond_calls"] for info in infos for i in info))
         achieved = per_launch / (ms / n * 1e-3) / 1e9
@@ -261,7 +270,7 @@ def run_ours(args):
                                    "4 setup iters, 12 point sources one at a time, tol 1e-10",
                        "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(st["kernel_launches"]), "clocks": clk.summary(),
+            "gpu_launches": int(launches), "clocks": clk.summary(),
             "solve_stats": {"outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in infos[-1]),
                             "precond_calls": sum(i["precond_calls"] for i in infos[-1]),
                             "coarse_iters": sum(i["coarse_iters"] for i in infos[-1]),

@@ -456,20 +456,24 @@ __global__ void __launch_bounds__(512) k_sap_sweep(Geom g, int colour, int mr_it
 }
 
 // ---------------------------------------------------------------------------
-// FP32 sweep with warp-uniform directions (Schwarz blocks whose half volume is
-// a multiple of 32).  Hop phases: thread (mu, h) = (t / Vh, t % Vh) applies
-// the two hops of direction mu at site h of one parity, with the compile-time
-// projectors, and writes its 12-component partial to P[mu][12][Vh].  Site
-// phases: thread (sub, h) owns spin sub of site h, sums the four partials and
-// applies its three rows of the chiral clover block (staged in shared
-// memory together with the block's links).
+// FP32 sweep for Schwarz blocks whose half volume is a multiple of 32: the
+// thread layout and hop code of k_sap_sweep (four threads per site, one
+// runtime direction each, partial sums combined by warp shuffles), with
+//  * the block's links -- and, when SC, its A_ee and A_oo^-1 -- staged into
+//    shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier)
+//    that land while the residual is computed from global memory;
+//  * each thread's block-internal neighbour indices held in registers;
+//  * a programmatic-dependent-launch prologue: barrier set-up and the staging
+//    copies (links and clover are read-only during a solve) are issued before
+//    griddepcontrol.wait, so they overlap the previous sweep's tail.
+// SC = false reads the clover rows from global memory instead (half the
+// shared memory).
 // ---------------------------------------------------------------------------
-namespace fast {
+namespace stg {
 
 using f2 = cpx<float>;
 
-// packed Hermitian rows [3 half, 3 half + 3) of a chiral block times v6; P36 in
-// smem as [9 float4][Vh] starting at site h
+// own 3 rows of a staged chiral block ([9][Vh] float4, site h) times v6
 __device__ __forceinline__ void rows3(const float4* Ablk, int Vh, int h, int half, const f2 v6[6], f2 y[3]) {
   float P[36];
 #pragma unroll
@@ -482,118 +486,66 @@ __device__ __forceinline__ void rows3(const float4* Ablk, int Vh, int h, int hal
 #pragma unroll
   for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
 }
-// same, with the block read from global memory (clover field, device site d)
-__device__ __forceinline__ void rows3_g(const float* clov, int d, int Vb, int cb, int half, const f2 v6[6], f2 y[3]) {
-  float P[36];
-  load_units<float, CLOVER_NR>(clov, d, Vb, cb * 9, 9, P);
-  f2 y6[6];
-  herm6<float>(P, v6, y6);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
-}
 
-template <int MU>
-__device__ __forceinline__ void hop_local(const int16_t* __restrict__ bnbr, const float4* sl, const f2* buf,
-                                          int Vb, int Vbp, int Vh, int q, Spinor<float>& acc) {
+// hop_block with the neighbour indices already known (-1: outside the block)
+__device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, const f2* buf, int Vbp, int Vh, int q,
+                                            int sub, f2 out[3]) {
+  Spinor<float> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
+  const Dir<float> dr = make_dir<float>(sub);
   f2 hh[2][3], y[2][3];
   Spinor<float> nb;
-  int qf = __ldg(bnbr + (2 * MU) * Vb + q);
   if (qf >= 0) {
     smem_spinor<float>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
-    project<MU, -1>(nb, hh);
+    project_rt<float>(nb, dr, -1.f, hh);
     Link<float> U;
-    smem_link<float>(sl, Vbp, q, MU, U);
+    smem_link<float>(sl, Vbp, q, sub, U);
     su3_mul(U, hh, y);
-    accumulate<MU, -1>(acc, y, 1.f);
+    accumulate_rt<float>(acc, y, dr, -1.f, 1.f);
   }
-  int qb = __ldg(bnbr + (2 * MU + 1) * Vb + q);
   if (qb >= 0) {
     smem_spinor<float>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
-    project<MU, +1>(nb, hh);
+    project_rt<float>(nb, dr, 1.f, hh);
     Link<float> U;
-    smem_link<float>(sl, Vbp, qb, MU, U);
+    smem_link<float>(sl, Vbp, qb, sub, U);
     su3_mul_dag(U, hh, y);
-    accumulate<MU, +1>(acc, y, 1.f);
+    accumulate_rt<float>(acc, y, dr, 1.f, 1.f);
   }
+  reduce_scatter<float>(acc, sub, out);
 }
 
-// hop phase inside the block: P[mu][k][h] for site q = qoff + h, values from
-// the buffer at byte offset buf_off of the dynamic shared memory, partials at
-// p_off
-__device__ __forceinline__ void hop_phase(const int16_t* __restrict__ bnbr, int Vb, int buf_off, int p_off, int qoff,
-                                       int mu, int h) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int Vh = Vb / 2, Vbp = Vb + LPAD;
-  const float4* sl = reinterpret_cast<const float4*>(smem_raw);
-  const f2* buf = reinterpret_cast<const f2*>(smem_raw + buf_off);
-  f2* P = reinterpret_cast<f2*>(smem_raw + p_off);
-  Spinor<float> acc;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
-  const int q = qoff + h;
-  switch (mu) {
-    case 0: hop_local<0>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
-    case 1: hop_local<1>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
-    case 2: hop_local<2>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
-    default: hop_local<3>(bnbr, sl, buf, Vb, Vbp, Vh, q, acc); break;
-  }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) P[(mu * 12 + k) * Vh + h] = acc.c[k];
-}
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// global hop phase (residual): full neighbourhood, device site d
-__device__ __forceinline__ void hop_phase_g(const Geom& g, const float* x, const float* gauge, int d, int mu,
-                                            int h, int Vh, f2* P) {
-  Spinor<float> acc;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
-  switch (mu) {
-    case 0: hop_dir<0>(g, x, gauge, d, acc); break;
-    case 1: hop_dir<1>(g, x, gauge, d, acc); break;
-    case 2: hop_dir<2>(g, x, gauge, d, acc); break;
-    default: hop_dir<3>(g, x, gauge, d, acc); break;
-  }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) P[(mu * 12 + k) * Vh + h] = acc.c[k];
-}
-
-// sum over directions of component k of site h
-__device__ __forceinline__ f2 psum(const f2* P, int Vh, int k, int h) {
-  return (P[(0 * 12 + k) * Vh + h] + P[(1 * 12 + k) * Vh + h]) + (P[(2 * 12 + k) * Vh + h] + P[(3 * 12 + k) * Vh + h]);
-}
-
-__global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_iters, int x_is_zero,
-                                                  const float* __restrict__ b, float* __restrict__ x,
-                                                  const float* __restrict__ gauge, const float* __restrict__ clov,
-                                                  const float* __restrict__ clov_inv, int* status) {
+template <bool SC>
+__global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
+                                                 const float* __restrict__ b, float* __restrict__ x,
+                                                 const float* __restrict__ gauge, const float* __restrict__ clov,
+                                                 const float* __restrict__ clov_inv, int* status) {
   using LYG = Layout<float, GAUGE_NR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
   float4* sl = reinterpret_cast<float4*>(smem_raw);                    // [12][Vb + LPAD]
-  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh]
-  float4* Aoi = Aee + 18 * Vh;                                          // [2 cb][9][Vh]
-  f2* E = reinterpret_cast<f2*>(Aoi + 18 * Vh);                         // [12][Vh]
+  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh] (SC)
+  float4* Aoi = Aee + (SC ? 18 * Vh : 0);                               // [2 cb][9][Vh] (SC)
+  f2* E = reinterpret_cast<f2*>(Aoi + (SC ? 18 * Vh : 0));              // [12][Vh]
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
-  f2* RO = O + 12 * Vh;                                                 // [12][Vh]
-  f2* P = RO + 12 * Vh;                                                 // [4][12][Vh]
-  float* red = reinterpret_cast<float*>(P + 48 * Vh);                   // [3 * warps + 3]
+  float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
 
   const int B = block_of_colour(g, colour, blockIdx.x);
   const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
   b += off;
   x += off;
   const int t = threadIdx.x;
-  const int mu = t / Vh, h = t - mu * Vh;      // hop phases
-  const int sub = mu;                          // site phases: spin sub of site h
-  const int offE = (int)(reinterpret_cast<unsigned char*>(E) - smem_raw);
-  const int offO = (int)(reinterpret_cast<unsigned char*>(O) - smem_raw);
-  const int offP = (int)(reinterpret_cast<unsigned char*>(P) - smem_raw);
+  const int h = t >> 2, sub = t & 3;
   const int cb = sub >> 1, half = sub & 1;
   const int de = B * Vb + h, dO = B * Vb + Vh + h;
+  // block-internal neighbours of this thread's direction, even and odd site
+  const int qf_e = __ldg(g.bnbr + (2 * sub) * Vb + h), qb_e = __ldg(g.bnbr + (2 * sub + 1) * Vb + h);
+  const int qf_o = __ldg(g.bnbr + (2 * sub) * Vb + Vh + h), qb_o = __ldg(g.bnbr + (2 * sub + 1) * Vb + Vh + h);
 
-  // stage the block's links, A_ee and A_oo^-1 with bulk asynchronous copies
-  // (one row of Vb or Vh 16-byte units each); they land while the residual,
-  // which reads global memory only, is computed
+  // stage the block's links (and A_ee, A_oo^-1) with bulk asynchronous copies
   __shared__ __align__(8) uint64_t mbar;
   if (t == 0) {
     mbar_init(&mbar, 1);
@@ -601,50 +553,49 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
   }
   __syncthreads();
   {
-    // 12 link rows + 18 A_ee rows + 18 A_oo^-1 rows, one copy per thread;
-    // the expected byte count is registered by thread 0 before any copy
     const unsigned link_row = (unsigned)Vb * 16u, half_row = (unsigned)Vh * 16u;
-    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + 36u * half_row);
+    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + (SC ? 36u * half_row : 0u));
     __syncthreads();
     if (t < LYG::NU) {
       const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
       bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
-    } else if (t < LYG::NU + 18) {
+    } else if (SC && t < LYG::NU + 18) {
       const int u = t - LYG::NU;
       const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
       bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
-    } else if (t < LYG::NU + 36) {
+    } else if (SC && t < LYG::NU + 36) {
       const int u = t - LYG::NU - 18;
       const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
       bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
     }
   }
+  // b and x may still be written by the previous kernel of the stream
+  grid_dependency_wait();
 
-  // residual r = b - D x on both parities (own components)
+  // residual r = b - D x on the own components of both sites
   f2 re[3], ro[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    re[i] = ld_comp(b, comp_off<float>(de, Vb, 3 * sub + i));
-    ro[i] = ld_comp(b, comp_off<float>(dO, Vb, 3 * sub + i));
-  }
-  if (!x_is_zero) {
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-      const int d = par ? dO : de;
-      hop_phase_g(g, x, gauge, d, mu, h, Vh, P);
-      __syncthreads();
-      f2 x6[6], ax[3];
+  for (int par = 0; par < 2; ++par) {
+    const int d = par ? dO : de;
+    f2 r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r[i] = ld_comp(b, comp_off<float>(d, Vb, 3 * sub + i));
+    if (!x_is_zero) {
+      f2 hop[3], x6[6], ax[3];
+      hop_global<float>(g, x, gauge, d, sub, hop);
 #pragma unroll
       for (int i = 0; i < 6; ++i) x6[i] = ld_comp(x, comp_off<float>(d, Vb, 6 * cb + i));
-      rows3_g(clov, d, Vb, cb, half, x6, ax);
+      clover_rows<float>(clov, d, Vb, sub, x6, ax);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        f2 hs = psum(P, Vh, 3 * sub + i, h);
-        f2 v = mk(ax[i].re - 0.5f * hs.re, ax[i].im - 0.5f * hs.im);
-        if (par) ro[i] = ro[i] - v;
-        else re[i] = re[i] - v;
+        r[i].re -= ax[i].re - 0.5f * hop[i].re;
+        r[i].im -= ax[i].im - 0.5f * hop[i].im;
       }
-      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (par) ro[i] = r[i];
+      else re[i] = r[i];
     }
   }
   // the staged block must have landed (bounded wait; on time-out record
@@ -657,97 +608,93 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
       return;
     }
   }
+  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) {
+    if constexpr (SC) rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, y);
+    else clover_rows<float>(clov_inv, dO, Vb, sub, v6, y);
+  };
+  auto aee_rows = [&](const f2 v6[6], f2 y[3]) {
+    if constexpr (SC) rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, y);
+    else clover_rows<float>(clov, de, Vb, sub, v6, y);
+  };
   // u_o = A_oo^-1 r_o
-#pragma unroll
-  for (int i = 0; i < 3; ++i) RO[(3 * sub + i) * Vh + h] = ro[i];
-  __syncthreads();
   {
     f2 v6[6], u[3];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) v6[i] = RO[(6 * cb + i) * Vh + h];
-    rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, u);
+    chiral6<float>(ro, sub, v6);
+    ainv_rows(v6, u);
 #pragma unroll
     for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = u[i];
   }
   __syncthreads();
   // rhs_e = r_e + 1/2 hop(u_o)
-  hop_phase(g.bnbr, Vb, offO, offP, 0, mu, h);
-  __syncthreads();
   f2 res[3], xe[3];
+  {
+    f2 tt[3];
+    hop_block_q(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    f2 hs = psum(P, Vh, 3 * sub + i, h);
-    res[i] = mk(fmaf(0.5f, hs.re, re[i].re), fmaf(0.5f, hs.im, re[i].im));
-    xe[i] = mk(0.f, 0.f);
+    for (int i = 0; i < 3; ++i) {
+      res[i] = mk(fmaf(0.5f, tt[i].re, re[i].re), fmaf(0.5f, tt[i].im, re[i].im));
+      xe[i] = mk(0.f, 0.f);
+    }
   }
-
   for (int it = 0; it < mr_iters; ++it) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = res[i];
     __syncthreads();
-    // odd: w = A_oo^-1 (-1/2 hop(res))
-    hop_phase(g.bnbr, Vb, offE, offP, Vh, mu, h);
-    __syncthreads();
-    {
-      f2 v6[6], w[3];
+    {  // odd: w = A_oo^-1 (-1/2 hop(res))
+      f2 tt[3], v6[6], w[3];
+      hop_block_q(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) v6[i] = -0.5f * psum(P, Vh, 6 * cb + i, h);
-      rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, w);
+      for (int i = 0; i < 3; ++i) tt[i] = -0.5f * tt[i];
+      chiral6<float>(tt, sub, v6);
+      ainv_rows(v6, w);
 #pragma unroll
       for (int i = 0; i < 3; ++i) O[(3 * sub + i) * Vh + h] = w[i];
     }
     __syncthreads();
-    // even: p = A_ee res + 1/2 hop(w)
-    hop_phase(g.bnbr, Vb, offO, offP, 0, mu, h);
-    __syncthreads();
-    f2 pv[3];
     float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
-    {
-      f2 v6[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) v6[i] = E[(6 * cb + i) * Vh + h];
-      rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, pv);
+    f2 p[3];
+    {  // even: p = A_ee res + 1/2 hop(w)
+      f2 tt[3], v6[6];
+      chiral6<float>(res, sub, v6);
+      aee_rows(v6, p);
+      hop_block_q(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        f2 hs = psum(P, Vh, 3 * sub + i, h);
-        pv[i] = mk(fmaf(0.5f, hs.re, pv[i].re), fmaf(0.5f, hs.im, pv[i].im));
-        pr_re += pv[i].re * res[i].re + pv[i].im * res[i].im;
-        pr_im += pv[i].re * res[i].im - pv[i].im * res[i].re;
-        pp_r += pv[i].re * pv[i].re + pv[i].im * pv[i].im;
+        p[i] = mk(fmaf(0.5f, tt[i].re, p[i].re), fmaf(0.5f, tt[i].im, p[i].im));
+        pr_re += p[i].re * res[i].re + p[i].im * res[i].im;
+        pr_im += p[i].re * res[i].im - p[i].im * res[i].re;
+        pp_r += p[i].re * p[i].re + p[i].im * p[i].im;
       }
     }
     float dre, dim, pp;
     block_sum3<float>(pr_re, pr_im, pp_r, dre, dim, pp, red);
     if (pp > 0.f) {
-      f2 a = mk(dre / pp, dim / pp);
+      const f2 a = mk(dre / pp, dim / pp);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         fma(xe[i], a, res[i]);
-        res[i] = res[i] - a * pv[i];
+        res[i] = res[i] - a * p[i];
       }
     }
   }
-
+  // the next sweep may start its prologue
+  launch_dependents();
   // e_o = A_oo^-1 (r_o + 1/2 hop(e_e))
 #pragma unroll
   for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = xe[i];
   __syncthreads();
-  hop_phase(g.bnbr, Vb, offE, offP, Vh, mu, h);
-  __syncthreads();
   f2 eo[3];
   {
-    f2 v6[6];
+    f2 tt[3], v6[6];
+    hop_block_q(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      f2 hs = psum(P, Vh, 6 * cb + i, h);
-      f2 r0 = RO[(6 * cb + i) * Vh + h];
-      v6[i] = mk(fmaf(0.5f, hs.re, r0.re), fmaf(0.5f, hs.im, r0.im));
-    }
-    rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, eo);
+    for (int i = 0; i < 3; ++i) tt[i] = mk(fmaf(0.5f, tt[i].re, ro[i].re), fmaf(0.5f, tt[i].im, ro[i].im));
+    chiral6<float>(tt, sub, v6);
+    ainv_rows(v6, eo);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    size_t oe = comp_off<float>(de, Vb, 3 * sub + i), oo = comp_off<float>(dO, Vb, 3 * sub + i);
+    const size_t oe = comp_off<float>(de, Vb, 3 * sub + i), oo = comp_off<float>(dO, Vb, 3 * sub + i);
     f2 ve = xe[i], vo = eo[i];
     if (!x_is_zero) {
       ve = ve + ld_comp(x, oe);
@@ -758,7 +705,7 @@ __global__ void __launch_bounds__(512) k_sap_fast(Geom g, int colour, int mr_ite
   }
 }
 
-}  // namespace fast
+}  // namespace stg
 
 }  // namespace
 
@@ -770,18 +717,46 @@ size_t sap_smem_bytes(const Geom& g, int real_size) {
   return units * 16 + bufs + 100 * sizeof(double);
 }
 
-static size_t sap_fast_smem(const Geom& g) {
+static size_t sap_stg_smem(const Geom& g, bool stage_clover) {
   const int Vh = g.Vb / 2;
-  size_t bytes = (size_t)12 * (g.Vb + LPAD) * 16;   // links
-  bytes += (size_t)2 * 18 * Vh * 16;                // A_ee, A_oo^-1
-  bytes += (size_t)(3 * 12 + 48) * Vh * 8;          // E, O, RO, P
+  size_t bytes = (size_t)12 * (g.Vb + LPAD) * 16;               // links
+  if (stage_clover) bytes += (size_t)2 * 18 * Vh * 16;          // A_ee, A_oo^-1
+  bytes += (size_t)24 * Vh * 8;                                 // E, O
   bytes += 100 * sizeof(double);
   return bytes;
 }
 
-static bool sap_fast_ok(const Geom& g) {
+static bool sap_stg_ok(const Geom& g) {
   const int Vh = g.Vb / 2;
-  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_fast_smem(g) <= 226 * 1024;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g, true) <= 226 * 1024;
+}
+
+template <bool SC>
+static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const float* b, float* x,
+                              const float* gauge, const float* clover, const float* clover_inv, int nrhs,
+                              int* status, cudaStream_t st) {
+  static size_t cfg = 0;
+  const size_t need = sap_stg_smem(g, SC);
+  if (cfg < need) {
+    cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e != cudaSuccess) return e;
+    cfg = need;
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(g.nb / 2, nrhs);
+  lc.blockDim = dim3(2 * g.Vb);
+  lc.dynamicSmemBytes = need;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // prologue overlaps the previous kernel
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const int zero = x_is_zero ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg<SC>, g, colour, mr_iters, zero, b, x, gauge, clover,
+                                     clover_inv, status);
+  ++g_launches;
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <class R>
@@ -789,20 +764,10 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
                       cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
-    if (sap_fast_ok(g)) {
-      static size_t cfg = 0;
-      const size_t need = sap_fast_smem(g);
-      if (cfg < need) {
-        cudaError_t e = cudaFuncSetAttribute(fast::k_sap_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)need);
-        if (e != cudaSuccess) return e;
-        cfg = need;
-      }
-      dim3 grid(g.nb / 2, nrhs);
-      fast::k_sap_fast<<<grid, 2 * g.Vb, sap_fast_smem(g), st>>>(g, colour, mr_iters, x_is_zero ? 1 : 0, b, x,
-                                                                 gauge, clover, clover_inv, status);
-      ++g_launches;
-      return cudaGetLastError();
+    if (sap_stg_ok(g)) {
+      // (SC = false leaves the clover in L1/L2 for half the shared memory, but
+      // 512 threads at 128 registers fill an SM's register file anyway)
+      return launch_stg<true>(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, st);
     }
   }
   int threads = sap_threads(g);
