@@ -39,10 +39,11 @@ WORKLOAD = dict(L=(16, 16, 16, 16), block=(4, 4, 4, 4), eps=0.25, seed=1, m0=-0.
 # writes x on its blocks (the coarse GMRES bytes are computed below).
 SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
 L2_BYTES = 129 * 2 ** 20
-# DRAM bytes (read + write) of one launch of the dominant kernel, from the
-# committed ncu capture profiles/k_cgmres_16x4_workload.md (single-RHS coarse
-# solve of the first timed solve); None for a kernel without a current capture
-TRAFFIC_BYTES_PER_LAUNCH = {"coarse_gmres": 29_881_088 + 41_984}
+# DRAM bytes (read + write) of one launch of each timed kernel class, from
+# the committed ncu captures profiles/k_sap_stg_16x4_workload.md (a
+# single-RHS sweep) and profiles/k_cgmres_16x4_workload.md (a single-RHS
+# coarse solve); a class without a current capture reports None
+TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": 18_978_048 + 512, "coarse_gmres": 42_860_544 + 12_544}
 # stencil bandwidth lattice: 32^3 x 64 (the lattice of the batched workload),
 # far larger than L2, links tiled from an 8^4 field of the same generator
 STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
