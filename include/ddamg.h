@@ -130,6 +130,8 @@ typedef struct {
   size_t device_bytes;        /* device memory held by the handle            */
   uint64_t coarse_apply_launches; /* launches of the coarse 9-point stencil  */
   double coarse_apply_ms;         /* (ddamg_apply_coarse) and their time     */
+  uint64_t reorth_passes;         /* second Gram-Schmidt passes the outer
+                                     FGMRES needed (refinement mode)         */
 } ddamg_stats;
 
 /* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,

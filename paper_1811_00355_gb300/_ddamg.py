@@ -57,6 +57,7 @@ class Stats(C.Structure):
         ("sap_launches", C.c_uint64), ("sap_ms", C.c_double),
         ("coarse_launches", C.c_uint64), ("coarse_ms", C.c_double), ("device_bytes", C.c_size_t),
         ("coarse_apply_launches", C.c_uint64), ("coarse_apply_ms", C.c_double),
+        ("reorth_passes", C.c_uint64),
     ]
 
     def as_dict(self):

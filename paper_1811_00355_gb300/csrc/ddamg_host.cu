@@ -133,6 +133,7 @@ struct ddamg_ctx {
   int gen = 0;                          // bumped whenever buffers move
   std::vector<GraphTimer>* capture_timers = nullptr;
   double* h_pinned = nullptr;           // device-to-host landing buffer
+  uint64_t reorth = 0;                  // second Gram-Schmidt passes ordered by the host
   cudaStream_t cap_st = nullptr;        // private stream used only to record graphs
 };
 
@@ -695,14 +696,32 @@ ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& 
   double* c1 = h->dots;
   double* c2 = h->dots + 2 * (m + 2);
   double* nn = h->dots + 4 * (m + 2);
-  CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c1, h->st));
-  CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
-  CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
-  CK(multi_axpy_norm<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->red, nn, h->st));
+  if (refine_mode(h)) {
+    // one classical Gram-Schmidt pass; its reduction also carries ||w||^2
+    // so that the host can order a second pass when the first cancelled
+    // most of w (fgmres)
+    const double* keep = vlist[k + 1];
+    vlist[k + 1] = h->fw;
+    CK(multi_dot<double>(vlist.data(), k + 2, h->fw, NC, h->red, c1, h->st));
+    vlist[k + 1] = keep;
+    CK(multi_axpy_norm<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->red, nn, h->st));
+  } else {
+    CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c1, h->st));
+    CK(multi_axpy<double>(vlist.data(), k + 1, c1, -1.0, h->fw, NC, h->st));
+    CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
+    CK(multi_axpy_norm<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->red, nn, h->st));
+  }
   CK(cudaMemcpyAsync(h->h_pinned, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(scale_by_inv_norm<double>(h->fw, vk1, nn, N, h->st));
   return DDAMG_OK;
 }
+
+// In the refinement mode a second Gram-Schmidt pass is needed only when the
+// first one cancelled most of w: below this ratio ||w_after||^2 / ||w||^2
+// (orthogonality lost per pass is about eps ||w|| / ||w_after||; a cycle ends
+// after a relative reduction of 1e-5 or m iterations, and restarts from the
+// FP64 true residual)
+constexpr double REORTH_RATIO = 1e-2;
 
 // Launch iteration k from its CUDA graph (captured on first use, and again
 // whenever buffers moved or kernel timing was switched).
@@ -819,9 +838,26 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       collect_graph(h, k);
       const double* hp = h->h_pinned;
       std::vector<cd> col(k + 2);
-      for (int j = 0; j <= k; ++j)
-        col[j] = cd(hp[2 * j] + hp[2 * (m + 2) + 2 * j], hp[2 * j + 1] + hp[2 * (m + 2) + 2 * j + 1]);
-      const double n_after = hp[4 * (m + 2)];
+      double n_after = hp[4 * (m + 2)];
+      if (refine) {
+        for (int j = 0; j <= k; ++j) col[j] = cd(hp[2 * j], hp[2 * j + 1]);
+        const double n_before = hp[2 * (k + 1)];
+        if (n_after < REORTH_RATIO * n_before) {
+          double* c2 = h->dots + 2 * (m + 2);
+          double* nn = h->dots + 4 * (m + 2);
+          CK(multi_dot<double>(vlist.data(), k + 1, h->fw, NC, h->red, c2, h->st));
+          CK(multi_axpy_norm<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->red, nn, h->st));
+          CK(cudaMemcpyAsync(host, c2, (2 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+          CK(scale_by_inv_norm<double>(h->fw, Vk(k + 1), nn, N, h->st));
+          CK(cudaStreamSynchronize(h->st));
+          for (int j = 0; j <= k; ++j) col[j] += cd(host[2 * j], host[2 * j + 1]);
+          n_after = host[2 * (m + 2)];
+          ++h->reorth;
+        }
+      } else {
+        for (int j = 0; j <= k; ++j)
+          col[j] = cd(hp[2 * j] + hp[2 * (m + 2) + 2 * j], hp[2 * j + 1] + hp[2 * (m + 2) + 2 * j + 1]);
+      }
       const double hn = std::sqrt(n_after);
       if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the FGMRES basis norm");
       col[k + 1] = hn;
@@ -1007,15 +1043,38 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
         TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
       }
       ++calls;
-      // two classical Gram-Schmidt passes per right-hand side, ||w||, v_{k+1}
+      // classical Gram-Schmidt per right-hand side (two passes; in the
+      // refinement mode one, plus a second when the first cancelled most of
+      // some w -- as in fgmres), ||w||, v_{k+1}
       const int kk = k + 1;
-      CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c1, h->st));
-      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr, h->st));
-      CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
-      CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+      const int kd1 = refine ? kk + 1 : kk;     // first-pass dots (+ ||w||^2 in the refinement mode)
+      const double* keep = vlist[k + 1];
+      if (refine) vlist[k + 1] = h->bw;
+      CK(multi_dot_batched<double>(vlist.data(), kd1, h->bw, NC, nb, NC, h->red, c1, h->st));
+      vlist[k + 1] = keep;
+      bool second = !refine;
+      if (refine) {
+        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kd1, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+        CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        const double* hn2 = hp + (size_t)nb * 4 * (m + 2);
+        for (int r = 0; r < nb; ++r)
+          if (open[r] && hn2[2 * r] < REORTH_RATIO * hp[2 * (r * kd1 + kk)]) second = true;
+        if (second) ++h->reorth;
+      } else {
+        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr,
+                                      h->st));
+      }
+      if (second) {
+        CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
+        CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+      }
       CK(scale_by_inv_norm_batched<double>(h->bw, Vk(k + 1), nn, N, nb, h->st));
-      CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
+      if (second) {
+        CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->st));
+        CK(cudaStreamSynchronize(h->st));
+      }
       const double* h1 = hp;
       const double* h2 = hp + (size_t)nb * 2 * (m + 2);
       const double* hn2 = h2 + (size_t)nb * 2 * (m + 2);
@@ -1023,8 +1082,10 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
       for (int r = 0; r < nb; ++r) {
         if (!open[r]) continue;
         std::vector<cd> col(k + 2);
-        for (int j = 0; j <= k; ++j)
-          col[j] = cd(h1[2 * (r * kk + j)] + h2[2 * (r * kk + j)], h1[2 * (r * kk + j) + 1] + h2[2 * (r * kk + j) + 1]);
+        for (int j = 0; j <= k; ++j) {
+          col[j] = cd(h1[2 * (r * kd1 + j)], h1[2 * (r * kd1 + j) + 1]);
+          if (second) col[j] += cd(h2[2 * (r * kk + j)], h2[2 * (r * kk + j) + 1]);
+        }
         const double hn = std::sqrt(hn2[2 * r]);
         if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the basis norm", r);
         col[k + 1] = hn;
@@ -1655,6 +1716,7 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   out->device_bytes = h->bytes;
   out->coarse_apply_launches = h->n_cls[3];
   out->coarse_apply_ms = h->ms_cls[3];
+  out->reorth_passes = h->reorth;
   return DDAMG_OK;
 }
 
@@ -1663,6 +1725,7 @@ ddamg_status ddamg_reset_stats(ddamg_handle h) {
   CK(cudaStreamSynchronize(h->st));
   collect_pending(h);
   h->launches0 = g_launches;
+  h->reorth = 0;
   for (int c = 0; c < NCLS; ++c) {
     h->n_cls[c] = 0;
     h->ms_cls[c] = 0.0;

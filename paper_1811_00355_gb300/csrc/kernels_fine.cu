@@ -579,11 +579,13 @@ __global__ void __launch_bounds__(RED_TPB) k_multi_axpy_f32(PtrList<float> v, in
   }
 }
 
+// y = a x + b y in the field's own precision (FP32 fields stay off the
+// narrow FP64 pipe)
 template <class R>
-__global__ void k_axpby(double a, const R* __restrict__ x, double b, R* __restrict__ y, size_t n) {
+__global__ void k_axpby(R a, const R* __restrict__ x, R b, R* __restrict__ y, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; i < n; i += stride) y[i] = (R)(a * (double)x[i] + b * (double)y[i]);
+  for (; i < n; i += stride) y[i] = a * x[i] + b * y[i];
 }
 
 // y = x / sqrt(s) for field r = blockIdx.y of a batch (n reals per field,
@@ -801,7 +803,7 @@ template <class R>
 cudaError_t axpby(double a, const R* x, double b, R* y, size_t n, cudaStream_t st) {
   unsigned nb = nblk(n, 256);
   if (nb > 4096) nb = 4096;
-  k_axpby<R><<<nb, 256, 0, st>>>(a, x, b, y, n);
+  k_axpby<R><<<nb, 256, 0, st>>>((R)a, x, (R)b, y, n);
   ++g_launches;
   return cudaGetLastError();
 }
