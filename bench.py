@@ -252,6 +252,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_variants:
         var = variants(P, torch, stream, U_dev, b_dev, args.steps, flush)
 
+    srv = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        srv = serving(P, torch, stream)
+
     sten = None
     if rank == 0 and not args.no_stencils:
         sten = stencils(P, torch, stream, pk, pk_kind)
@@ -279,6 +283,7 @@ def run_ours(args):
                             "step_seconds": [round(t, 4) for t in times]},
             "kernel_ms": {k: round(v[0], 3) for k, v in classes.items()},
             "variants": var,
+            "serving": srv,
             "stencils": sten,
         }
         print(json.dumps(line))
@@ -356,6 +361,82 @@ def variants(P, torch, stream, U_dev, b_dev, steps, flush):
     finally:
         s.close()
     return out
+
+
+# serving stream: resident gauge configurations (lattice, eps, m0, csw drawn
+# once from eps in [0.2, 0.3], m0 in [-0.4, -0.2], csw in [1.0, 1.5] with a
+# fixed seed), Poisson arrivals, 1-12 Gaussian or point-source right-hand
+# sides per request at tol 1e-8 or 1e-10.  The lattices stop at 16^4 and the
+# rate is below the GPU's service rate for this mix, so that the stream is
+# served in a few seconds rather than queueing without bound.
+SERVING = dict(lattices=((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)), requests=40, rate_hz=8.0,
+               seed=2024, max_batch=12, restart=16)
+
+
+def serving(P, torch, stream):
+    """p50 / p99 latency (submit to results on the host) and solves/s of a
+    Poisson request stream through the library's serving loop."""
+    import threading
+    import synthetic as syn
+    sv = SERVING
+    gen = np.random.default_rng(sv["seed"])
+    srv = P.Server(max_batch=sv["max_batch"], stream=stream.cuda_stream)
+    cfgs = []
+    try:
+        for i, L in enumerate(sv["lattices"]):
+            eps, m0, csw = gen.uniform(0.2, 0.3), gen.uniform(-0.4, -0.2), gen.uniform(1.0, 1.5)
+            p = P.default_params(L=L, sap_block=(4, 4, 4, 4), n_v=20, m0=m0, csw=csw, precision=P.FP32,
+                                 outer_restart=sv["restart"])
+            cid = srv.add_config(p, syn.gauge_field(L, eps, 11 + i))
+            cfgs.append({"L": "x".join(map(str, L)), "eps": round(eps, 3), "m0": round(m0, 3),
+                         "csw": round(csw, 3), "id": cid})
+        # requests drawn up front (host inputs are part of the request)
+        reqs = []
+        for k in range(sv["requests"]):
+            c = cfgs[int(gen.integers(len(cfgs)))]
+            L = tuple(int(v) for v in c["L"].split("x"))
+            n = int(gen.integers(1, 13))
+            tol = 1e-8 if gen.random() < 0.5 else 1e-10
+            if gen.random() < 0.5:
+                rhs = syn.gaussian_spinors(n, L, 1000 + k)
+            else:
+                rhs = np.ascontiguousarray(syn.point_sources(L)[:n])
+            reqs.append((c["id"], rhs, tol, float(gen.exponential(1.0 / sv["rate_hz"]))))
+        # warm: every config set up once (resident afterwards)
+        for c in cfgs:
+            L = tuple(int(v) for v in c["L"].split("x"))
+            srv.wait(srv.submit(c["id"], syn.gaussian_spinors(1, L, 7), 1e-8))
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def feed():
+            for k, (cid, rhs, tol, gap) in enumerate(reqs):
+                time.sleep(gap)
+                ids[k] = srv.submit(cid, rhs, tol)
+
+        th = threading.Thread(target=feed)
+        th.start()
+        lat, batch_req, nrhs = [], [], 0
+        for k in range(len(reqs)):
+            while ids[k] is None:
+                time.sleep(0.0005)
+            x, info, ri = srv.wait(ids[k])
+            if not all(i["converged"] for i in info):
+                raise RuntimeError(f"serving: request {k} did not converge: {info}")
+            lat.append(ri["latency_seconds"])
+            batch_req.append(ri["batch_requests"])
+            nrhs += reqs[k][1].shape[0]
+        th.join()
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    lat = np.array(lat)
+    return {"p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "solves_per_s": round(nrhs / wall, 3), "requests": len(lat), "rhs": nrhs,
+            "arrival_rate_hz": sv["rate_hz"], "mean_requests_per_batch": round(float(np.mean(batch_req)), 2),
+            "configs": [{k: v for k, v in c.items() if k != "id"} for c in cfgs],
+            "note": "latency = submit to results in host memory; setups done before the stream (resident)"}
 
 
 def _tiled(a, small, L):
@@ -511,6 +592,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stencils", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -305,6 +305,56 @@ DDAMG_API ddamg_status ddamg_random_vectors(ddamg_handle h, uint64_t seed, int n
 DDAMG_API const char *ddamg_last_error(ddamg_handle h);
 DDAMG_API void ddamg_destroy(ddamg_handle h);
 
+/* ---- serving: continuous batching over resident gauge configurations ----
+ * Not in the paper.  A server owns several gauge configurations ("configs"),
+ * each with its own handle, setup and coarse operator kept resident in
+ * device memory, and one worker thread that runs the solves.  Requests
+ * (a config, nrhs right-hand sides, a tolerance) are submitted without
+ * blocking and queue up; whenever the worker is free it takes the config of
+ * the oldest waiting request and every waiting request of that config, in
+ * arrival order, up to max_batch right-hand sides, and solves them as one
+ * lockstep batch (ddamg_solve_batched, tolerance the smallest of the batch),
+ * so requests that arrive while others run join the next batch.  A config
+ * is set up on its first use; admission is by device-memory footprint: if
+ * setting up a config would exceed hbm_budget, idle configs are released
+ * (least recently used first) and set up again on their next request; a
+ * config that cannot fit even alone fails its requests with DDAMG_ENOMEM.
+ * Host buffers only; rhs and x of a request belong to the caller and must
+ * stay valid until ddamg_server_wait returns for it. */
+typedef struct ddamg_server *ddamg_server_handle;
+
+typedef struct {
+  ddamg_status status;    /* of the batch that solved this request           */
+  int batch_rhs;          /* right-hand sides in that batch                   */
+  int batch_requests;     /* requests in that batch                           */
+  int setup_run;          /* 1 if the batch had to set the config up first    */
+  double queue_seconds;   /* submit -> start of its batch                     */
+  double latency_seconds; /* submit -> results copied back                    */
+} ddamg_request_info;
+
+/* hbm_budget in bytes (0 = none), 1 <= max_batch <= 64; cuda_stream as in
+ * ddamg_create (NULL = a stream the server creates). */
+DDAMG_API ddamg_status ddamg_server_create(size_t hbm_budget, int max_batch, void *cuda_stream,
+                                 ddamg_server_handle *out);
+/* Register a gauge configuration (host FP64 links, layout of ddamg_create,
+ * copied); its id is returned in *config_id.  No device work yet. */
+DDAMG_API ddamg_status ddamg_server_add_config(ddamg_server_handle s, const ddamg_params *p,
+                                     const double *gauge, int *config_id);
+/* Queue a request of nrhs (1..max_batch) host right-hand sides; returns at
+ * once with its id. */
+DDAMG_API ddamg_status ddamg_server_submit(ddamg_server_handle s, int config_id, int nrhs,
+                                 const double *rhs, double *x, double tol,
+                                 ddamg_solve_info *info, uint64_t *request_id);
+/* Block until the request has completed; its per-RHS records were written
+ * to the info array given at submit, *rinfo (nullable) gets the request's
+ * record.  Returns the request's status. */
+DDAMG_API ddamg_status ddamg_server_wait(ddamg_server_handle s, uint64_t request_id,
+                               ddamg_request_info *rinfo);
+/* Device memory currently held by the server's resident configs. */
+DDAMG_API ddamg_status ddamg_server_device_bytes(ddamg_server_handle s, size_t *bytes);
+/* Finish the queued requests, stop the worker, release everything. */
+DDAMG_API void ddamg_server_destroy(ddamg_server_handle s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,16 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RequestInfo(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("batch_rhs", C.c_int), ("batch_requests", C.c_int), ("setup_run", C.c_int),
+        ("queue_seconds", C.c_double), ("latency_seconds", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -100,6 +110,12 @@ SIGNATURES = {
     "ddamg_enable_kernel_timing": (_I, [_H, _I]),
     "ddamg_random_vectors": (_I, [_H, C.c_uint64, _I, _P]),
     "ddamg_last_error": (C.c_char_p, [_H]),
+    "ddamg_server_create": (_I, [C.c_size_t, _I, _P, C.POINTER(_H)]),
+    "ddamg_server_add_config": (_I, [_H, C.POINTER(Params), _P, C.POINTER(_I)]),
+    "ddamg_server_submit": (_I, [_H, _I, _I, _P, _P, _D, _P, C.POINTER(C.c_uint64)]),
+    "ddamg_server_wait": (_I, [_H, C.c_uint64, C.POINTER(RequestInfo)]),
+    "ddamg_server_device_bytes": (_I, [_H, C.POINTER(C.c_size_t)]),
+    "ddamg_server_destroy": (None, [_H]),
     "ddamg_destroy": (None, [_H]),
 }
 
@@ -377,3 +393,67 @@ class DDAMG:
 
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ddamg_enable_kernel_timing(self.h, int(on)))
+
+
+class Server:
+    """Continuous-batching request loop over resident gauge configurations
+    (ddamg_server_*): submit returns at once, wait blocks for one request."""
+
+    def __init__(self, hbm_budget=0, max_batch=12, stream=None):
+        self.lib = load()
+        h = _H()
+        st = C.c_void_p(stream) if stream else None
+        status = self.lib.ddamg_server_create(hbm_budget, max_batch, st, C.byref(h))
+        if status != 0:
+            raise DDAMGError(status, self.lib.ddamg_status_string(status).decode())
+        self.h = h
+        self.V = {}
+        self._live = {}
+
+    def _check(self, status):
+        if status != 0:
+            raise DDAMGError(status, self.lib.ddamg_status_string(status).decode())
+
+    def add_config(self, params: Params, gauge) -> int:
+        gauge = np.ascontiguousarray(gauge, dtype=np.complex128)
+        cid = _I()
+        self._check(self.lib.ddamg_server_add_config(self.h, C.byref(params), C.c_void_p(gauge.ctypes.data),
+                                                     C.byref(cid)))
+        self.V[cid.value] = int(np.prod(list(params.L)))
+        return cid.value
+
+    def submit(self, config_id, rhs, tol=1e-10) -> int:
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        n = rhs.shape[0] if rhs.ndim == 4 else 1
+        x = np.empty_like(rhs)
+        info = (SolveInfo * n)()
+        rid = C.c_uint64()
+        self._check(self.lib.ddamg_server_submit(self.h, config_id, n, C.c_void_p(rhs.ctypes.data),
+                                                 C.c_void_p(x.ctypes.data), tol, C.cast(info, C.c_void_p),
+                                                 C.byref(rid)))
+        self._live[rid.value] = (rhs, x, info)     # buffers stay alive until wait
+        return rid.value
+
+    def wait(self, request_id, allow_noconv=False):
+        ri = RequestInfo()
+        status = self.lib.ddamg_server_wait(self.h, request_id, C.byref(ri))
+        rhs, x, info = self._live.pop(request_id)
+        if not (allow_noconv and status == 4):
+            self._check(status)
+        return x, [i.as_dict() for i in info], ri.as_dict()
+
+    def device_bytes(self) -> int:
+        b = C.c_size_t()
+        self._check(self.lib.ddamg_server_device_bytes(self.h, C.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ddamg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -49,9 +49,10 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header(lib):
     """Compile a tiny C program against the header and compare struct sizes
     with the ctypes mirrors."""
-    from paper_1811_00355_gb300._ddamg import Params, SolveInfo, Stats
-    src = ('#include "ddamg.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu\\n",'
-           ' sizeof(ddamg_params), sizeof(ddamg_solve_info), sizeof(ddamg_stats));return 0;}\n')
+    from paper_1811_00355_gb300._ddamg import Params, RequestInfo, SolveInfo, Stats
+    src = ('#include "ddamg.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu %zu\\n",'
+           ' sizeof(ddamg_params), sizeof(ddamg_solve_info), sizeof(ddamg_stats),'
+           ' sizeof(ddamg_request_info));return 0;}\n')
     tmp = os.path.join(ROOT, "paper_1811_00355_gb300", "_build")
     os.makedirs(tmp, exist_ok=True)
     c = os.path.join(tmp, "sizes.c")
@@ -59,7 +60,7 @@ def test_struct_sizes_match_header(lib):
     open(c, "w").write(src)
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
     sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
-    assert sizes == [C.sizeof(Params), C.sizeof(SolveInfo), C.sizeof(Stats)]
+    assert sizes == [C.sizeof(Params), C.sizeof(SolveInfo), C.sizeof(Stats), C.sizeof(RequestInfo)]
 
 
 def _create(lib, **kw):
@@ -96,3 +97,13 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.ddamg_solve(None, 1, None, None, 0, 1e-10, None) == 1
     assert lib.ddamg_apply_D(None, 0, 1, None, None, 0) == 1
     lib.ddamg_destroy(None)
+
+
+def test_server_rejects_invalid_arguments_before_device_work(lib):
+    """The serving API validates its arguments before touching the GPU."""
+    h = C.c_void_p()
+    assert lib.ddamg_server_create(0, 0, None, C.byref(h)) == 1          # max_batch < 1
+    assert lib.ddamg_server_create(0, 65, None, C.byref(h)) == 1         # max_batch > 64
+    assert lib.ddamg_server_create(0, 12, None, None) == 1
+    assert lib.ddamg_server_wait(None, 1, None) == 1
+    assert lib.ddamg_server_submit(None, 0, 1, None, None, 1e-10, None, None) == 1
