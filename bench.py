@@ -369,7 +369,7 @@ def variants(P, torch, stream, U_dev, b_dev, steps, flush):
 # sides per request at tol 1e-8 or 1e-10.  The lattices stop at 16^4 and the
 # rate is below the GPU's service rate for this mix, so that the stream is
 # served in a few seconds rather than queueing without bound.
-SERVING = dict(lattices=((8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16)), requests=40, rate_hz=8.0,
+SERVING = dict(lattices=((8, 8, 8, 8), (8, 8, 8, 16), (16, 16, 16, 16)), requests=40, rate_hz=8.0,
                seed=2024, max_batch=12, restart=16)
 
 
