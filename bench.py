@@ -206,6 +206,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = solver.stats()
     solver.enable_kernel_timing(False)
+    hist_f, hist_r = solver.history()
+    flops = {"model": "theoretical real flops of the method's arithmetic (ddamg_get_history)",
+             "setup_mflop_per_site": round(st["setup_flops"] / V / 1e6, 3),
+             "solve_mflop_per_site": round(st["solve_flops"] / 12 / V / 1e6, 3),
+             "last_solve_history": [[round(float(f), 3), float("%.3g" % r)] for f, r in zip(hist_f, hist_r)]}
     for info in infos:
         for i in info:
             if not (i["converged"] and i["true_residual"] <= w["tol"]):
@@ -295,6 +300,7 @@ def run_ours(args):
                             "max_true_residual": max(i["true_residual"] for info in infos for i in info),
                             "step_seconds": [round(t, 4) for t in times]},
             "kernel_ms": {k: round(v[0], 3) for k, v in classes.items()},
+            "flops": flops,
             "variants": var,
             "serving": srv,
             "stencils": sten,

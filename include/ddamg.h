@@ -132,6 +132,9 @@ typedef struct {
   double coarse_apply_ms;         /* (ddamg_apply_coarse) and their time     */
   uint64_t reorth_passes;         /* second Gram-Schmidt passes the outer
                                      FGMRES needed (refinement mode)         */
+  double setup_flops;             /* theoretical flops of the adaptive setups */
+  double solve_flops;             /* and of the solves (model of
+                                     ddamg_get_history) since the last reset  */
 } ddamg_stats;
 
 /* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,
@@ -296,6 +299,19 @@ DDAMG_API ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats *out);
 DDAMG_API ddamg_status ddamg_reset_stats(ddamg_handle h);
 /* Record CUDA events around the timed kernels (default off). */
 DDAMG_API ddamg_status ddamg_enable_kernel_timing(ddamg_handle h, int enable);
+
+/* Residual history of the last right-hand side of ddamg_solve (the axes of
+ * the paper's Fig. 3): after every outer iteration the cumulative
+ * theoretical cost in MFLOP per lattice site and the relative residual
+ * (the recurrence estimate; at every restart the FP64 true residual).
+ * Entry 0 is (0, 1).  *n receives the history length; at most cap entries
+ * are written.  Cost model: real flops of the arithmetic (complex
+ * multiply-add 8), per site 1320 for the Wilson hops, 552 for the two 6x6
+ * clover blocks, 48 to combine; SAP, restriction / prolongation, coarse
+ * GMRES (counted from its actual iterations) and Gram-Schmidt by their
+ * operation counts. */
+DDAMG_API ddamg_status ddamg_get_history(ddamg_handle h, int cap, double *mflop_per_site,
+                               double *rel_residual, int *n);
 
 /* Fill n_v * V spinor fields with the device generator's initial vectors
  * for seed (host buffer), for checking the generator. */

@@ -57,7 +57,7 @@ class Stats(C.Structure):
         ("sap_launches", C.c_uint64), ("sap_ms", C.c_double),
         ("coarse_launches", C.c_uint64), ("coarse_ms", C.c_double), ("device_bytes", C.c_size_t),
         ("coarse_apply_launches", C.c_uint64), ("coarse_apply_ms", C.c_double),
-        ("reorth_passes", C.c_uint64),
+        ("reorth_passes", C.c_uint64), ("setup_flops", C.c_double), ("solve_flops", C.c_double),
     ]
 
     def as_dict(self):
@@ -109,6 +109,7 @@ SIGNATURES = {
     "ddamg_reset_stats": (_I, [_H]),
     "ddamg_enable_kernel_timing": (_I, [_H, _I]),
     "ddamg_random_vectors": (_I, [_H, C.c_uint64, _I, _P]),
+    "ddamg_get_history": (_I, [_H, _I, _P, _P, C.POINTER(_I)]),
     "ddamg_last_error": (C.c_char_p, [_H]),
     "ddamg_server_create": (_I, [C.c_size_t, _I, _P, C.POINTER(_H)]),
     "ddamg_server_add_config": (_I, [_H, C.POINTER(Params), _P, C.POINTER(_I)]),
@@ -387,6 +388,17 @@ class DDAMG:
         s = Stats()
         self._check(self.lib.ddamg_get_stats(self.h, C.byref(s)))
         return s.as_dict()
+
+    def history(self):
+        """(MFLOP/site, relative residual) after every outer iteration of the
+        last right-hand side of solve()."""
+        n = _I()
+        self._check(self.lib.ddamg_get_history(self.h, 0, None, None, C.byref(n)))
+        f = np.empty(n.value)
+        r = np.empty(n.value)
+        self._check(self.lib.ddamg_get_history(self.h, n.value, C.c_void_p(f.ctypes.data),
+                                               C.c_void_p(r.ctypes.data), C.byref(n)))
+        return f, r
 
     def reset_stats(self):
         self._check(self.lib.ddamg_reset_stats(self.h))

@@ -125,6 +125,7 @@ struct ddamg_ctx {
     cudaGraphExec_t exec = nullptr;
     std::vector<GraphTimer> timers;
     uint64_t launches = 0;
+    double flops = 0.0;                 // model flops of one replay
     uint64_t n_cls[NCLS] = {0, 0, 0, 0};
     int gen = -1;
     bool timing = false;
@@ -134,6 +135,12 @@ struct ddamg_ctx {
   std::vector<GraphTimer>* capture_timers = nullptr;
   double* h_pinned = nullptr;           // device-to-host landing buffer
   uint64_t reorth = 0;                  // second Gram-Schmidt passes ordered by the host
+  // theoretical flop counts (model below): [0] setup, [1] solves; fphase
+  // selects the counter; a captured graph keeps its own share
+  double flops[2] = {0.0, 0.0};
+  int fphase = 1;
+  int* d_cit = nullptr;                 // coarse iterations of each outer iteration
+  std::vector<double> hist_flops, hist_res;   // last single-RHS solve
   cudaStream_t cap_st = nullptr;        // private stream used only to record graphs
 };
 
@@ -434,6 +441,51 @@ void collect_pending(ddamg_ctx* h) {
   h->pending.clear();
 }
 
+// ---- theoretical flop model -------------------------------------------------------
+// Real flops of the method's arithmetic, counted per unit of work (complex
+// multiply-add 8, complex add 2, real multiply-add 2), independent of how a
+// kernel schedules it.  Per site: the Wilson hopping term 1320 (spin-projected
+// form), the two 6x6 Hermitian clover blocks 552, combining 48 (24 more for a
+// residual b - D x).
+constexpr double F_HOP = 1320.0, F_CLOV = 552.0, F_D = F_HOP + F_CLOV + 48.0, F_RES = F_D + 24.0;
+
+void addf(ddamg_ctx* h, double f) { h->flops[h->fphase] += f; }
+// one SAP colour sweep of one right-hand side (sites of the colour: V/2)
+double flops_sap_sweep(const ddamg_ctx* h, bool x_is_zero) {
+  const double V = (double)h->g.V, q = V / 4.0;          // even (odd) sites of the colour
+  double f = q * (F_CLOV + F_HOP + 24.0);               // u_o = A^-1 r_o, rhs_e
+  f += h->p.mr_iters * q * ((F_HOP + 24.0 + F_CLOV) + (F_CLOV + F_HOP + 24.0 + 336.0));
+  f += q * (F_HOP + 24.0 + F_CLOV);                     // e_o
+  if (!x_is_zero) f += V / 2.0 * (F_RES + 24.0);        // residual, x += e
+  return f;
+}
+// restriction or prolongation of one right-hand side
+double flops_rp(const ddamg_ctx* h) { return (double)h->g.V * 12.0 * h->p.n_v * 8.0; }
+// coarse GMRES: fixed part of one solve (odd elimination, right-hand side,
+// back-substitution) and one iteration (Schur product, Gram-Schmidt with
+// about 10 basis vectors, update), per right-hand side
+double flops_coarse_fixed(const ddamg_ctx* h) {
+  const double ne = h->g.nb / 2.0, n2 = 2.0 * h->p.n_v;
+  return ne * (1.0 + 8.0 + 9.0) * n2 * n2 * 8.0;
+}
+double flops_coarse_iter(const ddamg_ctx* h) {
+  const double ne = h->g.nb / 2.0, n2 = 2.0 * h->p.n_v;
+  return ne * ((8.0 + 9.0) * n2 * n2 + 26.0 * n2) * 8.0;
+}
+// FP64 Gram-Schmidt pass over kv basis vectors (dots and update), one field
+double flops_gs_pass(const ddamg_ctx* h, int kv) { return (double)h->g.V * 12.0 * kv * 16.0; }
+// per-aggregate orthonormalisation (classical Gram-Schmidt twice, norms)
+double flops_ortho(const ddamg_ctx* h) {
+  const double n = h->p.n_v, V = h->g.V;
+  return V * 6.0 * 2.0 * (n * (n - 1.0) * 16.0 + n * 8.0);
+}
+// D_c assembly (D applied to the 2 n chirality-projected test vectors and
+// contracted with them), self-block inverses, premultiplied odd blocks
+double flops_build(const ddamg_ctx* h) {
+  const double n2 = 2.0 * h->p.n_v, V = h->g.V, nb = h->g.nb;
+  return n2 * V * F_D + V * 12.0 * n2 * n2 * 8.0 + nb * n2 * n2 * n2 * 8.0 + nb / 2.0 * 8.0 * n2 * n2 * n2 * 8.0;
+}
+
 // ---- in/out of fields -----------------------------------------------------------
 // host/device FP64 lexicographic -> device field of precision R (nf fields)
 template <class R>
@@ -474,6 +526,7 @@ template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 // ---- operators on device fields ---------------------------------------------------
 template <class R>
 ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
+  addf(h, (double)nf * h->g.V * (mode == DSLASH_RES ? F_RES : mode == DSLASH_CLOVER ? F_CLOV : F_D));
   CK(timed(h, 0, [&] {
     return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
   }));
@@ -487,6 +540,7 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf) {
   for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
     for (int c = 0; c < 2; ++c) {
       bool zero = cyc == 0 && c == 0;
+      addf(h, nf * flops_sap_sweep(h, zero));
       CK(timed(h, 1, [&] {
         return sap_sweep<R>(h->g, c, h->p.mr_iters, zero, b, x, gauge_of<R>(h), clov_of<R>(h, false),
                             clov_of<R>(h, true), nf, h->d_status, h->st);
@@ -505,6 +559,7 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   a.tol = tol;
   a.restart = h->p.coarse_restart;
   a.max_iter = h->p.coarse_max_iter;
+  addf(h, nf * flops_coarse_fixed(h));   // iterations are added when their counts are read
   CK(timed(h, 2, [&] {
     return coarse_gmres<R>(h->g, a, bc, xc, nf, h->cwork, iters_dev, h->d_iters_acc, h->d_status, h->st);
   }));
@@ -514,15 +569,16 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
 // out = M in  (Eq. 5): x1 = P D_c^-1 R in; out = x1 + SAP(in - D x1)
 // uses tmp[0..3]
 template <class R>
-ddamg_status op_M(ddamg_ctx* h, const R* in, R* out, int nf) {
+ddamg_status op_M(ddamg_ctx* h, const R* in, R* out, int nf, int* cit_dev = nullptr) {
   TRY(need_tmp(h, nf, 6));
   R* r1 = (R*)h->tmp[0];
   R* e = (R*)h->tmp[1];
   R* bc = (R*)h->tmp[2];
   R* xc = (R*)h->tmp[3];
   const int n = h->p.n_v;
+  addf(h, 2.0 * nf * flops_rp(h) + nf * 2.0 * h->V24);
   CK(restrict_op<R>(h->g, lam_of<R>(h), n, in, bc, nf, h->st));
-  TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, nullptr));
+  TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, cit_dev));
   CK(prolong_op<R>(h->g, lam_of<R>(h), n, xc, out, nf, false, h->st));
   TRY(op_dslash<R>(h, DSLASH_RES, out, in, r1, nf));
   TRY(op_sap<R>(h, r1, e, nf));
@@ -566,6 +622,7 @@ ddamg_status build_coarse_op(ddamg_ctx* h) {
   TRY(alloc_coarse(h));
   TRY(sync_lam32(h));
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+  addf(h, flops_build(h));
   if (h->p.precision == DDAMG_FP32) {
     CK(assemble_coarse<float>(h->g, h->lam32, h->p.n_v, h->g32, h->A32, (float*)h->Dc, h->st));
     CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
@@ -605,10 +662,24 @@ ddamg_status from_inner(ddamg_ctx* h, const R* src, double* dst, int nf) {
 }
 
 // ---- adaptive setup -----------------------------------------------------------------
+// coarse GMRES iterations accumulated on the device since the last call
+ddamg_status coarse_iters_since(ddamg_ctx* h, int* its) {
+  int acc = 0;
+  CK(cudaMemcpyAsync(&acc, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
+  *its = acc;
+  return DDAMG_OK;
+}
+
 template <class R>
 ddamg_status setup_impl(ddamg_ctx* h) {
   const int n = h->p.n_v;
   TRY(need_tmp(h, n, 6));
+  int its = 0;
+  TRY(coarse_iters_since(h, &its));
+  h->fphase = 0;
+  struct Back { ddamg_ctx* h; ~Back() { h->fphase = 1; } } back{h};
   R* a = (R*)h->tmp[4];
   R* b = (R*)h->tmp[5];
   // lambda_i <- SAP(lambda_i)
@@ -616,6 +687,7 @@ ddamg_status setup_impl(ddamg_ctx* h) {
   TRY(op_sap<R>(h, a, b, n));
   TRY(from_inner<R>(h, b, h->lam64, n));
   for (int it = 0; it < h->p.setup_iters; ++it) {
+    addf(h, flops_ortho(h));
     CK(orthonormalise(h->g, h->lam64, n, h->st));
     TRY(build_coarse_op(h));
     // lambda_i <- M lambda_i
@@ -624,19 +696,22 @@ ddamg_status setup_impl(ddamg_ctx* h) {
     TRY(from_inner<R>(h, b, h->lam64, n));
     TRY(check_status(h));
   }
+  addf(h, flops_ortho(h));
   CK(orthonormalise(h->g, h->lam64, n, h->st));
   TRY(build_coarse_op(h));
+  TRY(coarse_iters_since(h, &its));
+  addf(h, its * flops_coarse_iter(h));
   return check_status(h);
 }
 
 // ---- outer FGMRES (FP64) -----------------------------------------------------------
 template <class R>
-ddamg_status precond_to_f64(ddamg_ctx* h, const double* v, double* z) {
-  if (sizeof(R) == 8) return op_M<double>(h, v, z, 1);
+ddamg_status precond_to_f64(ddamg_ctx* h, const double* v, double* z, int* cit_dev) {
+  if (sizeof(R) == 8) return op_M<double>(h, v, z, 1, cit_dev);
   float* fin = (float*)h->fin;
   float* fout = (float*)h->fout;
   TRY(to_inner<float>(h, v, fin, 1));
-  TRY(op_M<float>(h, fin, fout, 1));
+  TRY(op_M<float>(h, fin, fout, 1, cit_dev));
   return from_inner<float>(h, fout, z, 1);
 }
 
@@ -657,6 +732,7 @@ ddamg_status alloc_outer(ddamg_ctx* h) {
   TRY(dalloc(h, &h->fin, h->V24 * sizeof(double)));
   TRY(dalloc(h, &h->fout, h->V24 * sizeof(double)));
   TRY(dalloc_t(h, &h->d_coef, (size_t)2 * (m + 1)));
+  TRY(dalloc_t(h, &h->d_cit, (size_t)m));
   if (!h->h_pinned) CK(cudaHostAlloc(&h->h_pinned, (6 * 64 + 16) * sizeof(double), cudaHostAllocDefault));
   h->graphs.resize(m);
   return DDAMG_OK;
@@ -686,16 +762,17 @@ ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& 
   if (refine_mode(h)) {
     float* z32 = h->fZ32 + (size_t)k * N;
     TRY(to_inner<float>(h, vk, (float*)h->fin, 1));
-    TRY(op_M<float>(h, (float*)h->fin, z32, 1));
+    TRY(op_M<float>(h, (float*)h->fin, z32, 1, h->d_cit + k));
     TRY(op_dslash<float>(h, DSLASH_D, z32, nullptr, (float*)h->fout, 1));
     TRY(from_inner<float>(h, (float*)h->fout, h->fw, 1));
   } else {
-    TRY(precond_to_f64<R>(h, vk, zk));
+    TRY(precond_to_f64<R>(h, vk, zk, h->d_cit + k));
     TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->fw, 1));
   }
   double* c1 = h->dots;
   double* c2 = h->dots + 2 * (m + 2);
   double* nn = h->dots + 4 * (m + 2);
+  addf(h, (refine_mode(h) ? 1 : 2) * flops_gs_pass(h, k + 1) + 2.0 * flops_gs_pass(h, 1));
   if (refine_mode(h)) {
     // one classical Gram-Schmidt pass; its reduction also carries ||w||^2
     // so that the host can order a second pass when the first cancelled
@@ -740,6 +817,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     }
     G.timers.clear();
     const uint64_t l0 = g_launches;
+    const double f0 = h->flops[h->fphase];
     uint64_t c0[NCLS];
     for (int c = 0; c < NCLS; ++c) c0[c] = h->n_cls[c];
     // record on the handle's private stream (the caller's stream may be the
@@ -758,6 +836,8 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     e = cudaStreamEndCapture(h->st, &graph);
     h->st = user;
     G.launches = g_launches - l0;
+    G.flops = h->flops[h->fphase] - f0;
+    h->flops[h->fphase] = f0;
     for (int c = 0; c < NCLS; ++c) {
       G.n_cls[c] = h->n_cls[c] - c0[c];
       h->n_cls[c] = c0[c];
@@ -776,6 +856,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
   }
   CK(cudaGraphLaunch(G.exec, h->st));
   g_launches += G.launches;
+  addf(h, G.flops);
   for (int c = 0; c < NCLS; ++c) h->n_cls[c] += G.n_cls[c];
   return DDAMG_OK;
 }
@@ -809,6 +890,13 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
   int iters = 0, restarts = 0, calls = 0;
   CK(cudaMemsetAsync(h->fx, 0, N * 8, h->st));
   CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
+  // history of this solve: model flops (coarse iterations added per cycle,
+  // from their counts) against the relative residual
+  const double f_start = h->flops[h->fphase];
+  double f_coarse = 0.0;
+  h->hist_flops.assign(1, 0.0);
+  h->hist_res.assign(1, 1.0);
+  std::vector<double> f_iter(m);
   // ||b||
   double host[6 * 64 + 16];
   CK(norm2<double>(h->fb, NC, h->red, h->dots, h->st));
@@ -853,6 +941,7 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
           for (int j = 0; j <= k; ++j) col[j] += cd(host[2 * j], host[2 * j + 1]);
           n_after = host[2 * (m + 2)];
           ++h->reorth;
+          addf(h, flops_gs_pass(h, k + 1) + flops_gs_pass(h, 1));
         }
       } else {
         for (int j = 0; j <= k; ++j)
@@ -881,7 +970,18 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       g[k] = cs[k] * g[k];
       ++iters;
       kdone = k + 1;
+      f_iter[k] = h->flops[h->fphase] - f_start;
+      h->hist_res.push_back(std::abs(g[k + 1]) / (bnorm > 0 ? bnorm : 1.0));
       if (std::abs(g[k + 1]) <= cycle_stop || iters >= h->p.max_outer_iter || hn == 0.0) break;
+    }
+    {  // coarse iterations of this cycle's preconditioner calls -> history flops
+      std::vector<int> cits(kdone);
+      CK(cudaMemcpyAsync(cits.data(), h->d_cit, kdone * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      for (int j = 0; j < kdone; ++j) {
+        f_coarse += cits[j] * flops_coarse_iter(h);
+        h->hist_flops.push_back(f_iter[j] + f_coarse);
+      }
     }
     for (int i = kdone - 1; i >= 0; --i) {
       cd acc = g[i];
@@ -893,6 +993,7 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
       host[2 * j + 1] = y[j].imag();
     }
     CK(cudaMemcpyAsync(h->d_coef, host, 2 * kdone * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    addf(h, (double)h->g.V * 12.0 * kdone * 8.0 + flops_gs_pass(h, 1));
     if (refine) CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kdone, h->d_coef, 0, 1.0, h->fx, 1, h->st));
     else CK(multi_axpy<double>(zlist.data(), kdone, h->d_coef, 1.0, h->fx, NC, h->st));
     // true residual
@@ -904,10 +1005,14 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
     ++restarts;
     if (!std::isfinite(beta)) return fail(h, DDAMG_ENUMERIC, "NaN or Inf in the true residual");
     converged = beta <= tol * bnorm;
+    // the FP64 true residual replaces the recurrence estimate of the cycle's end
+    h->hist_flops.push_back(h->flops[h->fphase] - f_start + f_coarse);
+    h->hist_res.push_back(bnorm > 0 ? beta / bnorm : 0.0);
   }
   TRY(check_status(h));
   int cit = 0;
   CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
+  addf(h, cit * flops_coarse_iter(h));
   if (info) {
     info->outer_iters = iters;
     info->restarts = restarts;
@@ -1069,6 +1174,7 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
         CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
         CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
       }
+      addf(h, nb * ((second ? 2.0 : 1.0) * flops_gs_pass(h, kk) + 2.0 * flops_gs_pass(h, 1)));
       CK(scale_by_inv_norm_batched<double>(h->bw, Vk(k + 1), nn, N, nb, h->st));
       if (second) {
         CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1137,6 +1243,7 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
       }
     }
     if (kmax > 0) {
+      addf(h, nb * ((double)h->g.V * 12.0 * kmax * 8.0 + flops_gs_pass(h, 1)));
       CK(cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
       if (refine)
         CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, nb, h->st));
@@ -1160,6 +1267,7 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
   TRY(check_status(h));
   int cit = 0;
   CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
+  addf(h, cit * flops_coarse_iter(h));
   bool all_conv = true;
   for (int r = 0; r < nb; ++r) {
     const bool conv = bnorm[r] == 0.0 || beta[r] <= tol * bnorm[r];
@@ -1717,6 +1825,19 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   out->coarse_apply_launches = h->n_cls[3];
   out->coarse_apply_ms = h->ms_cls[3];
   out->reorth_passes = h->reorth;
+  out->setup_flops = h->flops[0];
+  out->solve_flops = h->flops[1];
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_get_history(ddamg_handle h, int cap, double* mflop_per_site, double* rel_residual, int* n) {
+  if (!h || cap < 0 || !n || (cap > 0 && (!mflop_per_site || !rel_residual))) return DDAMG_EINVAL;
+  const int len = (int)std::min(h->hist_flops.size(), h->hist_res.size());
+  *n = len;
+  for (int i = 0; i < std::min(cap, len); ++i) {
+    mflop_per_site[i] = h->hist_flops[i] / h->g.V / 1e6;
+    rel_residual[i] = h->hist_res[i];
+  }
   return DDAMG_OK;
 }
 
@@ -1726,6 +1847,7 @@ ddamg_status ddamg_reset_stats(ddamg_handle h) {
   collect_pending(h);
   h->launches0 = g_launches;
   h->reorth = 0;
+  h->flops[0] = h->flops[1] = 0.0;
   for (int c = 0; c < NCLS; ++c) {
     h->n_cls[c] = 0;
     h->ms_cls[c] = 0.0;

@@ -149,7 +149,7 @@ template <class R>
 cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* singular,
                                cudaStream_t st);
 // AD[ko][d - 1] = A_oo^-1(X) D_c[X][d] for the odd coarse sites X = codd[ko]
-// and d = 1..8 (column-major, FP64 accumulation): the odd half of the
+// and d = 1..8 (column-major, accumulated in R): the odd half of the
 // even-odd Schur complement becomes one block product per site
 template <class R>
 cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R* AD, cudaStream_t st);

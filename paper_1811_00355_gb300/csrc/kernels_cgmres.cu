@@ -115,13 +115,15 @@ struct Plan {
   size_t V, x, rl, w, sv, mvp, tmp;                                    // cpx offsets (bytes)
   size_t hc, h2, Rf, cs, sn, gv, yv, beta, bnorm, hn, scale;           // double offsets
   size_t act, kd, tot, conv;                                            // int offsets
+  size_t Mres;         // resident D_c blocks of the CTA's even site (0: none)
   size_t bytes;        // total shared memory
   size_t local_bytes;  // V + x + rl + w (moved to global when too large)
 };
 
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
 
-__host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, bool local_in_smem) {
+__host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, bool local_in_smem,
+                                          bool resident = false) {
   Plan p;
   const size_t c = 2 * (size_t)rs;
   size_t o = 0;
@@ -160,6 +162,7 @@ __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, 
   p.kd = put((size_t)NR * 4);
   p.tot = put((size_t)NR * 4);
   p.conv = put((size_t)NR * 4);
+  p.Mres = resident ? put((size_t)9 * n2 * n2 * c) : 0;
   p.bytes = o;
   p.local_bytes = lb;
   return p;
@@ -182,6 +185,7 @@ struct CGA {
   int NE;
   int per;
   int local_in_smem;
+  int resident;      // the CTA keeps its even site's D_c blocks in shared memory
   cpx<R>* wg;        // [NR][NE][n2]
   cpx<R>* to;        // [NR][NE][n2]
   cpx<R>* xg;        // [NR][NE][n2]
@@ -203,7 +207,8 @@ struct CGA {
 // are summed in a fixed order.
 // (M holds the blocks of directions d0 .. d1 - 1 from its start when
 // m_from_d0 is set, else the blocks of directions 0 .. d1 - 1)
-template <class R, int NR>
+// (M in shared memory when SM: plain loads instead of the read-only path)
+template <class R, int NR, bool SM = false>
 __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const cpx<R>* sv, int d0, int d1,
                                             int n2, cpx<R>* mvp, cpx<R>* out, int out_stride,
                                             bool m_from_d0 = false) {
@@ -230,7 +235,9 @@ __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const 
       for (int q = 0; q < RPU; ++q) acc[r][q] = mk(R(0), R(0));
 #pragma unroll 8
     for (int c = c0; c < c1; ++c) {
-      T mm = __ldg(col + (size_t)c * NP);
+      T mm;
+      if constexpr (SM) mm = col[(size_t)c * NP];
+      else mm = __ldg(col + (size_t)c * NP);
       cpx<R> e0, e1;
       if constexpr (RPU == 2) { e0 = mk((R)mm.x, (R)mm.y); e1 = mk((R)mm.z, (R)mm.w); }
       else { e0 = mk((R)mm.x, (R)mm.y); e1 = e0; }
@@ -266,7 +273,8 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   using A = R;
   const int n2 = a.n2, m = a.m, NE = a.NE;
   const int L = a.per * n2;
-  const Plan P = make_plan(NR, L, n2, m, sizeof(R), a.local_in_smem != 0);
+  const Plan P = make_plan(NR, L, n2, m, sizeof(R), a.local_in_smem != 0, a.resident != 0);
+  cpx<R>* Mres = reinterpret_cast<cpx<R>*>(sm + P.Mres);   // [9][n2][n2] when resident
   unsigned char* lbase = a.local_in_smem ? sm : a.lglob + (size_t)blockIdx.x * a.lstride;
   cpx<R>* V = reinterpret_cast<cpx<R>*>(lbase + P.V);     // [m+1][NR][L]
   cpx<R>* xl = reinterpret_cast<cpx<R>*>(lbase + P.x);    // [NR][L]
@@ -298,6 +306,13 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   grid_barrier_reset();
   const int lo = min(NE, (int)blockIdx.x * a.per);
   const int hi = min(NE, lo + a.per);
+  if (a.resident && lo < hi) {      // one even site per CTA: its nine blocks, once per launch
+    using T = typename U16<R>::T;
+    const T* src = reinterpret_cast<const T*>(a.Dc + (size_t)a.g.ceven[lo] * 9 * n2 * n2);
+    T* dst = reinterpret_cast<T*>(Mres);
+    const int units = 9 * n2 * n2 * (int)sizeof(cpx<R>) / 16;
+    for (int i = threadIdx.x; i < units; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
   const int nown = hi - lo;
   const int Lo = nown * n2;          // owned local elements
   const size_t vstr = (size_t)NE * n2;
@@ -338,7 +353,10 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         sv[idx] = v;
       }
       __syncthreads();
-      mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, self ? 0 : 1, 9, n2, mvp, out + kk * n2, L);
+      if (a.resident)
+        mrhs_matvec<R, NR, true>(Mres, sv, self ? 0 : 1, 9, n2, mvp, out + kk * n2, L);
+      else
+        mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, self ? 0 : 1, 9, n2, mvp, out + kk * n2, L);
       if (bsrc) {
         for (int idx = tx; idx < NR * n2; idx += TPB) {
           const int r = idx / n2, c = idx - r * n2;
@@ -767,6 +785,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
 }
 
 constexpr size_t SMEM_BUDGET = 200 * 1024;
+constexpr size_t SMEM_RESIDENT_MAX = 224 * 1024;   // with resident blocks: one CTA per SM
 
 template <class R>
 const void* kernel_for(int NR) {
@@ -783,6 +802,7 @@ struct Choice {
   int NR, G, per;
   bool local;
   Plan plan;
+  bool resident;
 };
 
 // current dynamic shared-memory limit of each kernel instance, so that the
@@ -839,14 +859,23 @@ Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
       // grid: as many CTAs as fit (two per SM at most), each owning >= 1 site
       for (int per = 1; per <= NE; ++per) {
         int G = (NE + per - 1) / per;
+        const void* fn = kernel_for<R>(NR);
+        int occ = 0;
+        if (per == 1 && local) {
+          // one even site per CTA, its D_c blocks resident in shared memory
+          Plan pr = make_plan(NR, n2, n2, m, sizeof(R), true, true);
+          if (pr.bytes <= SMEM_RESIDENT_MAX && smem_attr<R>(NR, pr.bytes) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, pr.bytes) == cudaSuccess &&
+              occ >= 1 && G <= occ * sms)
+            return Choice{NR, G, per, true, pr, true};
+          cudaGetLastError();
+        }
         Plan p = make_plan(NR, per * n2, n2, m, sizeof(R), local);
         if (p.bytes > SMEM_BUDGET) break;
-        int occ = 0;
-        const void* fn = kernel_for<R>(NR);
         if (smem_attr<R>(NR, p.bytes) != cudaSuccess) break;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, p.bytes);
         if (occ < 1) break;
-        if (G <= occ * sms) return Choice{NR, G, per, local, p};
+        if (G <= occ * sms) return Choice{NR, G, per, local, p, false};
       }
     }
   }
@@ -905,6 +934,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.NE = g.nb / 2;
   a.per = ch.per;
   a.local_in_smem = ch.local ? 1 : 0;
+  a.resident = ch.resident ? 1 : 0;
   const size_t NE = a.NE;
   const size_t vec = (size_t)NRMAX * NE * n2;
   unsigned char* w8 = reinterpret_cast<unsigned char*>(work);

@@ -57,14 +57,15 @@ __device__ __forceinline__ double warp_sum_pair(double a, double b) {
 }
 
 // ---------------------------------------------------------------------------
-// orthonormalisation: CTA per (aggregate, chirality), two sites per thread.
+// orthonormalisation: CTA per (aggregate, chirality), ORTHO_SITES sites per
+// thread.
 // Classical Gram-Schmidt, two passes, FP64: for vector i every thread forms
 // its partial products with all earlier vectors j < i at once, and the CTA
 // reduces the i coefficients together (one barrier per pass, not per j).
-// Two sites per thread halve the share of FP64 additions spent in the
+// Several sites per thread cut the share of FP64 additions spent in the
 // cross-thread sums, FP64 being GB300's scarce arithmetic.
 // ---------------------------------------------------------------------------
-constexpr int ORTHO_SITES = 2;
+constexpr int ORTHO_SITES = 4;
 
 __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
   extern __shared__ double osh[];          // red [warps][n][2], coef [n][2]
@@ -562,15 +563,12 @@ __global__ void k_premultiply_odd(Geom g, const cpx<R>* __restrict__ Dc, const c
   }
   __syncthreads();
   cpx<R>* C = AD + ((size_t)ko * 8 + (d - 1)) * n2 * n2;
+  // accumulated in the blocks' own precision (FP32 blocks stay off the FP64 pipe)
   for (int i = threadIdx.x; i < n2 * n2; i += blockDim.x) {
     const int r = i % n2, c = i / n2;
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < n2; ++k) {
-      const cpx<R> a = As[k * n2 + r], b = Bs[c * n2 + k];
-      re += (double)a.re * (double)b.re - (double)a.im * (double)b.im;
-      im += (double)a.re * (double)b.im + (double)a.im * (double)b.re;
-    }
-    C[i] = mk((R)re, (R)im);
+    cpx<R> acc = mk(R(0), R(0));
+    for (int k = 0; k < n2; ++k) fma(acc, As[k * n2 + r], Bs[c * n2 + k]);
+    C[i] = acc;
   }
 }
 

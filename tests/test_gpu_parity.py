@@ -294,6 +294,28 @@ def test_solve_batched_matches_one_at_a_time(prec, refine):
     s.close()
 
 
+def test_residual_history_and_flop_model():
+    """The history of the last solve starts at (0, 1), its cost grows, it has
+    one entry per outer iteration plus one per restart, and it ends at the
+    FP64 true residual; the model's setup and solve flops are positive."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1)
+    s.reset_stats()
+    s.run_setup()
+    rhs = syn.gaussian_spinors(1, L, 52)
+    x, info = s.solve(rhs, 1e-10)
+    f, r = s.history()
+    assert f[0] == 0.0 and r[0] == 1.0
+    assert np.all(np.diff(f) >= 0.0) and f[-1] > 0.0
+    assert len(f) == 1 + info[0]["outer_iters"] + info[0]["restarts"]
+    assert r[-1] == pytest.approx(info[0]["true_residual"], rel=1e-12)
+    st = s.stats()
+    assert st["setup_flops"] > 0.0 and st["solve_flops"] > 0.0
+    # the solve's cost in the history equals the counter (one right-hand side)
+    assert f[-1] * 1e6 * np.prod(L) == pytest.approx(st["solve_flops"], rel=1e-9)
+    s.close()
+
+
 def test_solve_batched_edge_cases():
     """A zero right-hand side in the batch gives x = 0; a batch of one equals
     the single solve; more than 64 is rejected before any device work."""
