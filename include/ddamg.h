@@ -172,11 +172,15 @@ DDAMG_API ddamg_status ddamg_run_setup(ddamg_handle h, const double *init_vector
  * rebuild the clover term, its inverse and D_c. */
 DDAMG_API ddamg_status ddamg_update_mass(ddamg_handle h, double m0, double csw);
 
-/* Solve D x_k = rhs_k (k < nrhs) to ||b - D x|| <= tol ||b|| in FP64 with
- * FGMRES preconditioned by M (Sec. 2), one right-hand side at a time, from a
- * zero start.  rhs and x are nrhs spinor fields (host or device).  info
- * (nullable) receives nrhs records.  Returns DDAMG_ENOCONV if a right-hand
- * side hit max_outer_iter (its best x and residual are still written). */
+/* Solve D x_k = rhs_k (k < nrhs) to ||b - D x|| <= tol ||b|| (checked on the
+ * FP64 true residual) with FGMRES preconditioned by M (Sec. 2), one
+ * right-hand side at a time, from a zero start.  The FGMRES basis, its
+ * Gram-Schmidt and the residuals are FP64; with the FP32 inner precision and
+ * outer_refine > 0 the operator products D z_k are FP32 and cycles restart
+ * from the FP64 true residual (ddamg_params.outer_refine).  rhs and x are
+ * nrhs spinor fields (host or device).  info (nullable) receives nrhs
+ * records.  Returns DDAMG_ENOCONV if a right-hand side hit max_outer_iter
+ * (its best x and residual are still written). */
 DDAMG_API ddamg_status ddamg_solve(ddamg_handle h, int nrhs, const double *rhs,
                          double *x, int on_device, double tol,
                          ddamg_solve_info *info);
