@@ -246,25 +246,36 @@ def run_ours(args):
         roof.update(achieved=round(achieved, 1), frac=round(achieved / pk["hbm_gbs"], 4),
                     algorithmic_bytes_per_launch=int(per_launch), avg_launch_us=round(1e3 * ms / n, 2))
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: one handle kept
+    # across configurations (as a production loop would); every step uploads
+    # its links and right-hand sides from pinned host memory, runs the setup
+    # and the 12 solves, and reads the solutions back into pinned host memory
     e2e = None
     if not args.no_e2e:
         solver.close()
         torch.cuda.synchronize()
-        x_host = np.empty_like(b_host)
+        U_pin = torch.from_numpy(U_host).pin_memory().numpy()
+        b_pin = torch.from_numpy(b_host).pin_memory().numpy()
+        x_pin = torch.empty(b_host.shape, dtype=torch.complex128).pin_memory().numpy()
+        s2 = P.DDAMG(params, U_pin, stream=stream.cuda_stream)
         et = []
-        for k in range(max(1, min(args.steps, 3)) + 1):
-            t0 = time.perf_counter()
-            s2 = P.DDAMG(params, U_host, stream=stream.cuda_stream)
-            s2.run_setup()
-            xh, inf = s2.solve(b_host, w["tol"])
+        try:
+            for k in range(max(1, min(args.steps, 3)) + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s2.set_gauge(U_pin)
+                s2.run_setup()
+                xh, inf = s2.solve(b_pin, w["tol"], out=x_pin)
+                t1 = time.perf_counter()
+                if k:
+                    et.append(t1 - t0)
+                if not all(i["converged"] for i in inf):
+                    raise RuntimeError(f"end-to-end solve missed the tolerance: {inf}")
+        finally:
             s2.close()
-            t1 = time.perf_counter()
-            if k:
-                et.append(t1 - t0)
         e2e = {"value": round(job_throughput(12, 1, world, job_seconds(statistics.mean(et), world, "cuda")), 3),
-               "unit": UNIT,
-               "h2d_bytes_per_step": int(U_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+               "unit": UNIT, "h2d_bytes_per_step": int(U_host.nbytes + b_host.nbytes),
+               "d2h_bytes_per_step": int(x_pin.nbytes)}
 
     var = None
     if rank == 0 and world == 1 and not args.no_variants:

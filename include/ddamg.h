@@ -168,6 +168,15 @@ DDAMG_API ddamg_status ddamg_setup(const ddamg_params *p, const double *gauge,
 DDAMG_API ddamg_status ddamg_run_setup(ddamg_handle h, const double *init_vectors,
                              int on_device);
 
+/* Replace the links of an existing handle (same lattice; host or device,
+ * layout of ddamg_create; checked for SU(3) as there) and rebuild the clover
+ * term.  The setup belongs to the old links: solves need ddamg_run_setup
+ * first (DDAMG_ESTATE otherwise).  Reuses every device buffer, so a
+ * sequence of gauge configurations costs no allocation.  After a
+ * DDAMG_EINVAL (links not SU(3)) the handle holds no valid links until a
+ * successful ddamg_set_gauge. */
+DDAMG_API ddamg_status ddamg_set_gauge(ddamg_handle h, const double *gauge, int on_device);
+
 /* Change m0 / csw keeping the test vectors (the paper's "new kappa", Sec. 4):
  * rebuild the clover term, its inverse and D_c. */
 DDAMG_API ddamg_status ddamg_update_mass(ddamg_handle h, double m0, double csw);

@@ -85,6 +85,7 @@ SIGNATURES = {
     "ddamg_create": (_I, [C.POINTER(Params), _P, _I, _P, C.POINTER(_H)]),
     "ddamg_setup": (_I, [C.POINTER(Params), _P, _I, _P, C.POINTER(_H)]),
     "ddamg_run_setup": (_I, [_H, _P, _I]),
+    "ddamg_set_gauge": (_I, [_H, _P, _I]),
     "ddamg_update_mass": (_I, [_H, _D, _D]),
     "ddamg_solve": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(SolveInfo)]),
     "ddamg_solve_batched": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(SolveInfo)]),
@@ -224,12 +225,16 @@ class DDAMG:
             p, dev = _ptr(init)
             self._check(self.lib.ddamg_run_setup(self.h, p, dev))
 
+    def set_gauge(self, gauge):
+        p, dev = _ptr(gauge)
+        self._check(self.lib.ddamg_set_gauge(self.h, p, dev))
+
     def update_mass(self, m0, csw):
         self._check(self.lib.ddamg_update_mass(self.h, m0, csw))
 
-    def solve(self, rhs, tol=1e-10, allow_noconv=False):
+    def solve(self, rhs, tol=1e-10, allow_noconv=False, out=None):
         n = self._nrhs(rhs)
-        x = self._fine_out(rhs, n).reshape(rhs.shape)
+        x = self._fine_out(rhs, n).reshape(rhs.shape) if out is None else out
         info = (SolveInfo * n)()
         pi, dev = _ptr(rhs)
         po, _ = _ptr(x)
@@ -238,9 +243,9 @@ class DDAMG:
             self._check(st)
         return x, [i.as_dict() for i in info]
 
-    def solve_batched(self, rhs, tol=1e-10, allow_noconv=False):
+    def solve_batched(self, rhs, tol=1e-10, allow_noconv=False, out=None):
         n = self._nrhs(rhs)
-        x = self._fine_out(rhs, n).reshape(rhs.shape)
+        x = self._fine_out(rhs, n).reshape(rhs.shape) if out is None else out
         info = (SolveInfo * n)()
         pi, dev = _ptr(rhs)
         po, _ = _ptr(x)

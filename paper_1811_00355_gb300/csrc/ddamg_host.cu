@@ -1501,6 +1501,24 @@ ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_
   return DDAMG_OK;
 }
 
+ddamg_status ddamg_set_gauge(ddamg_handle h, const double* gauge, int on_device) {
+  if (!h || !gauge) return DDAMG_EINVAL;
+  const size_t V = h->g.V;
+  CK(cudaMemcpyAsync(h->d_gauge_lex, gauge, V * 72 * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemsetAsync(h->d_dev, 0, sizeof(unsigned long long), h->st));
+  CK(import_gauge(h->g, h->d_gauge_lex, h->g64, h->g32, h->d_dev, h->st));
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, h->d_dev, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  double dev;
+  std::memcpy(&dev, &bits, sizeof dev);
+  h->have_coarse = false;           // the clover term, test vectors and D_c belong to the old links
+  if (!(dev <= 1e-9)) return fail(h, DDAMG_EINVAL, "gauge links are not SU(3): max deviation %.3e", dev);
+  CK(build_clover(h->g, h->d_gauge_lex, h->p.m0, h->p.csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  return DDAMG_OK;
+}
+
 ddamg_status ddamg_run_setup(ddamg_handle h, const double* init, int on_device) {
   if (!h) return DDAMG_EINVAL;
   const int n = h->p.n_v;

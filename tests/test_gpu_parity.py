@@ -12,7 +12,7 @@ import torch
 import synthetic as syn
 from oracle.coarse import (Aggregation, CoarseOperator, coarse_operator,
                            orthonormalise, prolong, restrict)
-from oracle.dirac import pack_hermitian, chiral_blocks
+from oracle.dirac import WilsonClover, chiral_blocks, pack_hermitian
 from oracle.lattice import index_maps
 from oracle.solver import Params, TwoLevelMG
 from tests.gpu_common import (FULL, MID, SMALL, TOL32, TOL64, make, oracle_op, rel,
@@ -291,6 +291,55 @@ def test_solve_batched_matches_one_at_a_time(prec, refine):
         assert res <= 1e-10 and ib[k]["converged"] == 1, (k, res, ib[k])
         assert abs(ib[k]["outer_iters"] - is_[k]["outer_iters"]) <= 3, (ib[k], is_[k])
         assert rel(xb[k], xs[k]) < 1e-6
+    s.close()
+
+
+def test_update_mass_keeps_vectors_and_rebuilds_operators():
+    """ddamg_update_mass (the paper's second mass on one setup): D equals the
+    oracle's D at the new (m0, csw), the test vectors are unchanged, D_c is
+    P^H D' P with them, and a solve at the new mass reaches 1e-10."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 0)
+    s.run_setup()
+    lam_before = s.get_test_vectors()
+    m1, c1 = m0 + 0.1, csw + 0.2
+    s.update_mass(m1, c1)
+    op1 = oracle_op(L, eps, seed, m1, c1)
+    x = syn.gaussian_spinors(1, L, 60)
+    assert rel(s.apply_D(x)[0], op1.apply(t(x[0])).numpy()) < TOL64
+    lam = s.get_test_vectors()
+    assert np.array_equal(lam, lam_before)
+    agg = Aggregation(op1.geom, b)
+    Dc = coarse_operator(op1, t(lam), agg)
+    assert rel(s.get_coarse_op(), Dc.numpy()) < 1e-12
+    xs, info = s.solve(x, 1e-10)
+    assert rel(op1.apply(t(xs[0])).numpy(), x[0]) <= 1e-10
+    s.close()
+
+
+def test_set_gauge_replaces_links_and_needs_a_new_setup():
+    """ddamg_set_gauge: D follows the new links, a solve before the new setup
+    is refused, one after it reaches 1e-10, and non-SU(3) links are rejected."""
+    P = _P()
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1)
+    s.run_setup()
+    U2 = syn.gauge_field(L, 0.2, seed + 7)
+    s.set_gauge(U2)
+    op2 = WilsonClover(t(U2), L, m0, csw)
+    x = syn.gaussian_spinors(1, L, 61)
+    assert rel(s.apply_D(x, P.FP64)[0], op2.apply(t(x[0])).numpy()) < TOL64
+    with pytest.raises(P.DDAMGError) as e:
+        s.solve(x, 1e-10)
+    assert e.value.status == 7
+    s.run_setup()
+    xs, info = s.solve(x, 1e-10)
+    assert rel(op2.apply(t(xs[0])).numpy(), x[0]) <= 1e-10
+    bad = U2.copy()
+    bad[0, 0] *= 1.5
+    with pytest.raises(P.DDAMGError) as e:
+        s.set_gauge(bad)
+    assert e.value.status == 1
     s.close()
 
 
