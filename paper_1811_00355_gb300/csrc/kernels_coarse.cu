@@ -172,8 +172,10 @@ __device__ __forceinline__ R warp_reduce_scatter16(R (&v)[16]) {
 }
 
 // restriction b_c(X, s, i) = <lambda_i restricted to (X, s), b> (Eq. 3): CTA
-// per (aggregate, rhs); test vectors in groups of four, each site's b loaded
-// once per group, the group's 16 sums reduced by a reduce-scatter
+// per (aggregate, rhs, slice); test vectors in groups of four, the groups
+// dealt round-robin to gridDim.z slices (more CTAs for a single right-hand
+// side), each site's b loaded once per group, the group's 16 sums reduced by
+// a reduce-scatter
 template <class R>
 __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __restrict__ b,
                            cpx<R>* __restrict__ bc) {
@@ -182,7 +184,7 @@ __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const size_t fstride = (size_t)g.V * SPINOR_NR;
   const R* bb = b + rhs * fstride;
-  for (int i0 = 0; i0 < n; i0 += 4) {
+  for (int i0 = 4 * blockIdx.z; i0 < n; i0 += 4 * gridDim.z) {
     R acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = R(0);
@@ -213,6 +215,8 @@ __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __
   }
   __syncthreads();
   for (int r = threadIdx.x; r < 2 * n; r += blockDim.x) {
+    const int i = r < n ? r : r - n;
+    if (((i >> 2) % gridDim.z) != blockIdx.z) continue;   // another slice's vector
     double re = 0.0, im = 0.0;
     for (int ww = 0; ww < nw; ++ww) {
       re += rsh[(ww * 2 * n + r) * 2];
@@ -237,6 +241,7 @@ __global__ void k_prolong(Geom g, const R* __restrict__ lam, int n, const cpx<R>
   Spinor<R> acc;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc.c[k] = mk(R(0), R(0));
+#pragma unroll 4
   for (int i = 0; i < n; ++i) {
     Spinor<R> L;
     load_spinor<R>(lam + i * fstride, d, g.Vb, L);
@@ -611,7 +616,9 @@ template <class R>
 cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs, cudaStream_t st) {
   int threads = g.Vb >= 256 ? 256 : ((g.Vb + 31) / 32) * 32;
   size_t smem = (size_t)(threads / 32) * 2 * n * 2 * sizeof(double);
-  k_restrict<R><<<dim3(g.nb, nrhs), threads, smem, st>>>(g, lam, n, b, reinterpret_cast<cpx<R>*>(bc));
+  // a single right-hand side leaves SMs idle with one CTA per aggregate
+  const int slices = (nrhs == 1 && n >= 8) ? 2 : 1;
+  k_restrict<R><<<dim3(g.nb, nrhs, slices), threads, smem, st>>>(g, lam, n, b, reinterpret_cast<cpx<R>*>(bc));
   ++g_launches;
   return cudaGetLastError();
 }
