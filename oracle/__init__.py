@@ -1,7 +1,8 @@
 """CPU oracle for the 2-level DD-alpha-AMG Wilson-clover hot path (TEST INFRASTRUCTURE).
 
-This package is a plain, slow, FP64 NumPy restatement of what the paper's
-method computes, written to check the CUDA library against.  It is test
+This package is a plain, slow, FP64 restatement (PyTorch CPU tensors,
+complex128) of what the paper's method computes, written to check the CUDA
+library against.  It is test
 infrastructure only: the tests, the smoke check and the benchmark's CPU
 baseline leg may import it; the library never does, and it shares no code,
 tables or constants with the CUDA path.
