@@ -43,7 +43,7 @@ L2_BYTES = 129 * 2 ** 20
 # the committed ncu captures profiles/k_sap_stg_16x4_workload.md (a
 # single-RHS sweep) and profiles/k_cgmres_16x4_workload.md (a single-RHS
 # coarse solve); a class without a current capture reports None
-TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": 18_978_048 + 512, "coarse_gmres": 42_860_544 + 12_544}
+TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": 18_978_048 + 512, "coarse_gmres": 42_879_232 + 10_240}
 # stencil bandwidth lattice: 32^3 x 64 (the lattice of the batched workload),
 # far larger than L2, links tiled from an 8^4 field of the same generator
 STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
