@@ -107,6 +107,10 @@ typedef struct {
                           recurrence residual fell by this factor (iterative
                           refinement); the basis, Gram-Schmidt and r stay
                           FP64.  0 = D z_k in FP64, restart only at m.      */
+  int half_vectors;    /* FP32 inner precision only: 1 = the test vectors
+                          that R and P (Eq. 3, 4) read are stored in FP16
+                          (FP32 arithmetic), and D_c is assembled from the
+                          same rounded vectors; 0 = FP32 vectors            */
 } ddamg_params;
 
 typedef struct {

@@ -37,6 +37,7 @@ class Params(C.Structure):
         ("coarse_tol", C.c_double), ("coarse_restart", C.c_int), ("coarse_max_iter", C.c_int),
         ("precision", C.c_int), ("outer_restart", C.c_int), ("max_outer_iter", C.c_int),
         ("seed", C.c_uint64), ("hbm_budget", C.c_size_t), ("outer_refine", C.c_double),
+        ("half_vectors", C.c_int),
     ]
 
 

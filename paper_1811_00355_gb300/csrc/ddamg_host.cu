@@ -73,6 +73,7 @@ struct ddamg_ctx {
   void* Dc = nullptr;
   void* Ainv = nullptr;
   void* AD = nullptr;             // A_oo^-1 D_c hop blocks of the odd coarse sites
+  void* lam16 = nullptr;          // FP16 test vectors of R and P (half_vectors)
   void* cwork = nullptr;
   int* d_iters = nullptr;        // per-rhs coarse iterations
   int* d_iters_acc = nullptr;    // running total
@@ -236,6 +237,8 @@ ddamg_status validate(const ddamg_params* p, std::string& why) {
   if (p->outer_restart < 1 || p->outer_restart > 62 || p->max_outer_iter < 1)
     return bad("outer_restart in [1, 62], max_outer_iter >= 1");
   if (!(p->outer_refine >= 0.0 && p->outer_refine < 1.0)) return bad("outer_refine in [0, 1)");
+  if (p->half_vectors != 0 && (p->half_vectors != 1 || p->precision != DDAMG_FP32))
+    return bad("half_vectors is 0, or 1 with the FP32 inner precision");
   if (!std::isfinite(p->m0) || !std::isfinite(p->csw)) return bad("m0 and csw must be finite");
   return DDAMG_OK;
 }
@@ -523,6 +526,20 @@ template <class R> const R* lam_of(ddamg_ctx* h);
 template <> const float* lam_of<float>(ddamg_ctx* h) { return h->lam32; }
 template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 
+// R and P of the inner solver (FP16 test vectors when half_vectors is set)
+template <class R>
+cudaError_t restrict_inner(ddamg_ctx* h, const R* in, R* bc, int nf) {
+  if constexpr (sizeof(R) == 4)
+    if (h->p.half_vectors) return restrict_op_h(h->g, h->lam16, h->p.n_v, in, bc, nf, h->st);
+  return restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, in, bc, nf, h->st);
+}
+template <class R>
+cudaError_t prolong_inner(ddamg_ctx* h, const R* xc, R* out, int nf) {
+  if constexpr (sizeof(R) == 4)
+    if (h->p.half_vectors) return prolong_op_h(h->g, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
+  return prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, xc, out, nf, false, h->st);
+}
+
 // ---- operators on device fields ---------------------------------------------------
 template <class R>
 ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
@@ -577,9 +594,9 @@ ddamg_status op_M(ddamg_ctx* h, const R* in, R* out, int nf, int* cit_dev = null
   R* xc = (R*)h->tmp[3];
   const int n = h->p.n_v;
   addf(h, 2.0 * nf * flops_rp(h) + nf * 2.0 * h->V24);
-  CK(restrict_op<R>(h->g, lam_of<R>(h), n, in, bc, nf, h->st));
+  CK(restrict_inner<R>(h, in, bc, nf));
   TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, cit_dev));
-  CK(prolong_op<R>(h->g, lam_of<R>(h), n, xc, out, nf, false, h->st));
+  CK(prolong_inner<R>(h, xc, out, nf));
   TRY(op_dslash<R>(h, DSLASH_RES, out, in, r1, nf));
   TRY(op_sap<R>(h, r1, e, nf));
   CK(axpby<R>(1.0, e, 1.0, out, nf * h->V24, h->st));
@@ -613,9 +630,15 @@ ddamg_status sync_lam32(ddamg_ctx* h) {
   if (h->p.precision == DDAMG_FP32) {
     if (!h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
     CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    if (h->p.half_vectors) {
+      if (!h->lam16) TRY(dalloc(h, &h->lam16, (size_t)h->p.n_v * h->V24 * 2));
+      CK(round_vectors_half(h->lam32, h->lam16, (size_t)h->p.n_v * h->V24, h->st));
+    }
   }
   return DDAMG_OK;
 }
+
+
 
 ddamg_status build_coarse_op(ddamg_ctx* h) {
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
@@ -1420,6 +1443,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->seed = 1;
   p->hbm_budget = 0;
   p->outer_refine = 1e-5;
+  p->half_vectors = 0;
 }
 
 const char* ddamg_status_string(ddamg_status s) {
@@ -1730,7 +1754,7 @@ ddamg_status ddamg_restrict(ddamg_handle h, int prec, int nrhs, const double* in
     if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
     TRY(need_tmp(h, nrhs, 6));
     TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[0]));
-    CK(restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st));
+    CK(restrict_inner<R>(h, (R*)h->tmp[0], (R*)h->tmp[1], nrhs));
     return coarse_out<R>(h, (R*)h->tmp[1], (size_t)nrhs * h->g.nb * h->n2, out, on_device);
   });
 }
@@ -1744,7 +1768,7 @@ ddamg_status ddamg_prolong(ddamg_handle h, int prec, int nrhs, const double* in,
     if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
     TRY(need_tmp(h, nrhs, 6));
     TRY(coarse_in<R>(h, in, on_device, (size_t)nrhs * h->g.nb * h->n2, (R*)h->tmp[0]));
-    CK(prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, false, h->st));
+    CK(prolong_inner<R>(h, (R*)h->tmp[0], (R*)h->tmp[1], nrhs));
     return export_fields<R>(h, (R*)h->tmp[1], nrhs, out, on_device);
   });
 }

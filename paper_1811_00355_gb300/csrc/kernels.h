@@ -135,6 +135,13 @@ template <class R>
 cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs,
                         cudaStream_t st);
 // x (+)= P x_c
+// the same with FP16 test vectors (FP32 layout, 8-byte units), FP32 arithmetic
+cudaError_t restrict_op_h(const Geom& g, const void* lam16, int n, const float* b, float* bc, int nrhs,
+                          cudaStream_t st);
+cudaError_t prolong_op_h(const Geom& g, const void* lam16, int n, const float* xc, float* x, int nrhs,
+                         bool accumulate, cudaStream_t st);
+// lam16 = FP16(lam32) and lam32 = FP32(lam16) (n reals)
+cudaError_t round_vectors_half(float* lam32, void* lam16, size_t n, cudaStream_t st);
 template <class R>
 cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs,
                        bool accumulate, cudaStream_t st);

@@ -9,6 +9,8 @@
 //     stopped at a relative residual of the even-site Schur system (Sec. 2).
 // Aggregates coincide with the Schwarz blocks: aggregate X owns the device
 // sites [X Vb, (X+1) Vb).
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -150,6 +152,41 @@ __global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
 }
 
 // ---------------------------------------------------------------------------
+// test vectors as R and P read them: in the field's precision, or (FP32
+// arithmetic) stored in FP16 in the FP32 field layout with 8-byte units
+// (four halves, two complex numbers, per unit)
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void load_lam(const R* lam, int d, int Vb, Spinor<R>& s) {
+  load_spinor<R>(lam, d, Vb, s);
+}
+__device__ __forceinline__ void load_lam(const __half* lam, int d, int Vb, Spinor<float>& s) {
+  using LY = Layout<float, SPINOR_NR>;
+  const size_t b = LY::base(d, Vb);
+  const uint2* p = reinterpret_cast<const uint2*>(lam);
+#pragma unroll
+  for (int u = 0; u < LY::NU; ++u) {
+    const uint2 w = __ldg(p + b + (size_t)u * Vb);
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+    s.c[2 * u] = mk(f0.x, f0.y);
+    s.c[2 * u + 1] = mk(f1.x, f1.y);
+  }
+}
+
+// FP16 copy of FP32 test vectors, and the FP32 vectors rounded to the same
+// values (so that D_c is assembled from exactly the P that R and P apply)
+__global__ void k_round_half(float* __restrict__ lam32, __half* __restrict__ lam16, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) {
+    const __half h = __float2half_rn(lam32[i]);
+    lam16[i] = h;
+    lam32[i] = __half2float(h);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // restriction: CTA per (aggregate, rhs)
 // ---------------------------------------------------------------------------
 // sum of 16 values over a warp as a reduce-scatter: 16 shuffles instead of
@@ -176,8 +213,8 @@ __device__ __forceinline__ R warp_reduce_scatter16(R (&v)[16]) {
 // dealt round-robin to gridDim.z slices (more CTAs for a single right-hand
 // side), each site's b loaded once per group, the group's 16 sums reduced by
 // a reduce-scatter
-template <class R>
-__global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __restrict__ b,
+template <class R, class S>
+__global__ void k_restrict(Geom g, const S* __restrict__ lam, int n, const R* __restrict__ b,
                            cpx<R>* __restrict__ bc) {
   extern __shared__ double rsh[];    // [warps][2n][2]
   const int X = blockIdx.x, rhs = blockIdx.y;
@@ -196,7 +233,7 @@ __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __
       for (int ii = 0; ii < 4; ++ii) {
         if (i0 + ii < n) {
           Spinor<R> L;
-          load_spinor<R>(lam + (i0 + ii) * fstride, d, g.Vb, L);
+          load_lam(lam + (i0 + ii) * fstride, d, g.Vb, L);
           cpx<R> a0 = mk(R(0), R(0)), a1 = mk(R(0), R(0));
 #pragma unroll
           for (int k = 0; k < 6; ++k) fmac(a0, L.c[k], B.c[k]);
@@ -229,8 +266,8 @@ __global__ void k_restrict(Geom g, const R* __restrict__ lam, int n, const R* __
 // ---------------------------------------------------------------------------
 // prolongation: thread per (site, rhs)
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void k_prolong(Geom g, const R* __restrict__ lam, int n, const cpx<R>* __restrict__ xc,
+template <class R, class S>
+__global__ void k_prolong(Geom g, const S* __restrict__ lam, int n, const cpx<R>* __restrict__ xc,
                           R* __restrict__ x, int accumulate) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
   int rhs = blockIdx.y;
@@ -244,7 +281,7 @@ __global__ void k_prolong(Geom g, const R* __restrict__ lam, int n, const cpx<R>
 #pragma unroll 4
   for (int i = 0; i < n; ++i) {
     Spinor<R> L;
-    load_spinor<R>(lam + i * fstride, d, g.Vb, L);
+    load_lam(lam + i * fstride, d, g.Vb, L);
     cpx<R> c0 = c[i], c1 = c[n + i];
 #pragma unroll
     for (int k = 0; k < 12; ++k) fma(acc.c[k], k < 6 ? c0 : c1, L.c[k]);
@@ -612,22 +649,48 @@ cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <class R>
-cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs, cudaStream_t st) {
+template <class R, class S>
+static cudaError_t restrict_launch(const Geom& g, const S* lam, int n, const R* b, R* bc, int nrhs,
+                                   cudaStream_t st) {
   int threads = g.Vb >= 256 ? 256 : ((g.Vb + 31) / 32) * 32;
   size_t smem = (size_t)(threads / 32) * 2 * n * 2 * sizeof(double);
   // a single right-hand side leaves SMs idle with one CTA per aggregate
   const int slices = (nrhs == 1 && n >= 8) ? 2 : 1;
-  k_restrict<R><<<dim3(g.nb, nrhs, slices), threads, smem, st>>>(g, lam, n, b, reinterpret_cast<cpx<R>*>(bc));
+  k_restrict<R, S><<<dim3(g.nb, nrhs, slices), threads, smem, st>>>(g, lam, n, b, reinterpret_cast<cpx<R>*>(bc));
+  ++g_launches;
+  return cudaGetLastError();
+}
+template <class R, class S>
+static cudaError_t prolong_launch(const Geom& g, const S* lam, int n, const R* xc, R* x, int nrhs, bool accumulate,
+                                  cudaStream_t st) {
+  k_prolong<R, S><<<dim3(nblk(g.V, 128), nrhs), 128, 0, st>>>(
+      g, lam, n, reinterpret_cast<const cpx<R>*>(xc), x, accumulate ? 1 : 0);
   ++g_launches;
   return cudaGetLastError();
 }
 
 template <class R>
+cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs, cudaStream_t st) {
+  return restrict_launch<R, R>(g, lam, n, b, bc, nrhs, st);
+}
+template <class R>
 cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs, bool accumulate,
                        cudaStream_t st) {
-  k_prolong<R><<<dim3(nblk(g.V, 128), nrhs), 128, 0, st>>>(
-      g, lam, n, reinterpret_cast<const cpx<R>*>(xc), x, accumulate ? 1 : 0);
+  return prolong_launch<R, R>(g, lam, n, xc, x, nrhs, accumulate, st);
+}
+cudaError_t restrict_op_h(const Geom& g, const void* lam16, int n, const float* b, float* bc, int nrhs,
+                          cudaStream_t st) {
+  return restrict_launch<float, __half>(g, reinterpret_cast<const __half*>(lam16), n, b, bc, nrhs, st);
+}
+cudaError_t prolong_op_h(const Geom& g, const void* lam16, int n, const float* xc, float* x, int nrhs,
+                         bool accumulate, cudaStream_t st) {
+  return prolong_launch<float, __half>(g, reinterpret_cast<const __half*>(lam16), n, xc, x, nrhs, accumulate, st);
+}
+cudaError_t round_vectors_half(float* lam32, void* lam16, size_t n, cudaStream_t st) {
+  unsigned nb = nblk(n, 256);
+  if (nb > 4096) nb = 4096;
+  if (!nb) return cudaSuccess;
+  k_round_half<<<nb, 256, 0, st>>>(lam32, reinterpret_cast<__half*>(lam16), n);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -343,6 +343,40 @@ def test_set_gauge_replaces_links_and_needs_a_new_setup():
     s.close()
 
 
+def test_half_vectors_restrict_prolong_and_coarse_operator():
+    """FP16 storage of the test vectors (half_vectors): R, P and D_c against
+    the oracle's FP64 vectors within the 2e-2 of half-precision storage."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    op = oracle_op(L, eps, seed, m0, csw)
+    agg = Aggregation(op.geom, b)
+    lam = orthonormalise(t(syn.gaussian_spinors(n_v, L, 62)), agg)
+    s = make(MID, 1, half_vectors=1)
+    s.set_test_vectors(np.ascontiguousarray(lam.numpy()))
+    s.build_coarse()
+    x = syn.gaussian_spinors(2, L, 63)
+    got = s.restrict(x, 1)
+    ref = restrict(lam, agg, t(x)).numpy()
+    assert rel(got, ref) < 2e-2
+    xc = np.ascontiguousarray(ref)
+    got = s.prolong(xc, 1)
+    assert rel(got, prolong(lam, agg, t(xc)).numpy()) < 2e-2
+    assert rel(s.get_coarse_op(), coarse_operator(op, lam, agg).numpy()) < 2e-2
+    s.close()
+
+
+def test_half_vectors_solve_reaches_tolerance():
+    """With FP16 test vectors the FP64 outer FGMRES still reaches 1e-10."""
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1, half_vectors=1)
+    s.run_setup()
+    op = oracle_op(L, eps, seed, m0, csw)
+    rhs = syn.gaussian_spinors(2, L, 64)
+    x, info = s.solve(rhs, 1e-10)
+    for k in range(2):
+        assert rel(op.apply(t(x[k])).numpy(), rhs[k]) <= 1e-10, info[k]
+    s.close()
+
+
 def test_residual_history_and_flop_model():
     """The history of the last solve starts at (0, 1), its cost grows, it has
     one entry per outer iteration plus one per restart, and it ends at the
