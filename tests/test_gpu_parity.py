@@ -377,6 +377,47 @@ def test_half_vectors_solve_reaches_tolerance():
     s.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_odd_number_of_test_vectors(prec):
+    """n_v = 5 (the paper's even-n restriction is a tiling artefact): D_c and
+    the coarse stencil match the oracle, and a solve reaches 1e-10."""
+    L, b, eps, m0, csw, _, seed = MID
+    n_v = 5
+    cfg = (L, b, eps, m0, csw, n_v, seed)
+    op = oracle_op(L, eps, seed, m0, csw)
+    agg = Aggregation(op.geom, b)
+    lam = orthonormalise(t(syn.gaussian_spinors(n_v, L, 65)), agg)
+    s = make(cfg, prec)
+    s.set_test_vectors(np.ascontiguousarray(lam.numpy()))
+    s.build_coarse()
+    Dc = coarse_operator(op, lam, agg)
+    tol = 1e-12 if prec == 0 else TOL32
+    assert rel(s.get_coarse_op(), Dc.numpy()) < tol
+    rng = np.random.default_rng(66)
+    x = rng.standard_normal((1, agg.NX, 2 * n_v)) + 1j * rng.standard_normal((1, agg.NX, 2 * n_v))
+    got = s.apply_coarse(x, prec)
+    ref = CoarseOperator(Dc, agg.coarse).apply(t(x)).numpy()
+    assert rel(got, ref) < (TOL64 if prec == 0 else TOL32)
+    s.run_setup()
+    rhs = syn.gaussian_spinors(1, L, 67)
+    xs, info = s.solve(rhs, 1e-10)
+    assert rel(op.apply(t(xs[0])).numpy(), rhs[0]) <= 1e-10
+    s.close()
+
+
+def test_zero_and_empty_right_hand_sides():
+    """b = 0 gives x = 0 at once; a call with no right-hand side does nothing."""
+    L = MID[0]
+    s = make(MID, 1)
+    s.run_setup()
+    x, info = s.solve(np.zeros((1,) + syn.gaussian_spinors(1, L, 1).shape[1:], np.complex128), 1e-10)
+    assert np.all(x == 0) and info[0]["converged"] == 1 and info[0]["outer_iters"] == 0
+    empty = np.zeros((0, int(np.prod(L)), 4, 3), np.complex128)
+    xe, ie = s.solve(empty, 1e-10)
+    assert xe.shape == empty.shape and ie == []
+    s.close()
+
+
 def test_residual_history_and_flop_model():
     """The history of the last solve starts at (0, 1), its cost grows, it has
     one entry per outer iteration plus one per restart, and it ends at the
