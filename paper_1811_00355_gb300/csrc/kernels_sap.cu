@@ -459,15 +459,13 @@ __global__ void __launch_bounds__(512) k_sap_sweep(Geom g, int colour, int mr_it
 // FP32 sweep for Schwarz blocks whose half volume is a multiple of 32: the
 // thread layout and hop code of k_sap_sweep (four threads per site, one
 // runtime direction each, partial sums combined by warp shuffles), with
-//  * the block's links -- and, when SC, its A_ee and A_oo^-1 -- staged into
+//  * the block's links, A_ee and A_oo^-1 staged into
 //    shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier)
 //    that land while the residual is computed from global memory;
 //  * each thread's block-internal neighbour indices held in registers;
 //  * a programmatic-dependent-launch prologue: barrier set-up and the staging
 //    copies (links and clover are read-only during a solve) are issued before
 //    griddepcontrol.wait, so they overlap the previous sweep's tail.
-// SC = false reads the clover rows from global memory instead (half the
-// shared memory).
 // ---------------------------------------------------------------------------
 namespace stg {
 
@@ -518,7 +516,6 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, co
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <bool SC>
 __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
                                                  const float* __restrict__ b, float* __restrict__ x,
                                                  const float* __restrict__ gauge, const float* __restrict__ clov,
@@ -527,9 +524,9 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
   float4* sl = reinterpret_cast<float4*>(smem_raw);                    // [12][Vb + LPAD]
-  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh] (SC)
-  float4* Aoi = Aee + (SC ? 18 * Vh : 0);                               // [2 cb][9][Vh] (SC)
-  f2* E = reinterpret_cast<f2*>(Aoi + (SC ? 18 * Vh : 0));              // [12][Vh]
+  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh]
+  float4* Aoi = Aee + 18 * Vh;                                          // [2 cb][9][Vh]
+  f2* E = reinterpret_cast<f2*>(Aoi + 18 * Vh);                         // [12][Vh]
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
   float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
 
@@ -554,16 +551,16 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   __syncthreads();
   {
     const unsigned link_row = (unsigned)Vb * 16u, half_row = (unsigned)Vh * 16u;
-    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + (SC ? 36u * half_row : 0u));
+    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + 36u * half_row);
     __syncthreads();
     if (t < LYG::NU) {
       const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
       bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
-    } else if (SC && t < LYG::NU + 18) {
+    } else if (t < LYG::NU + 18) {
       const int u = t - LYG::NU;
       const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
       bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
-    } else if (SC && t < LYG::NU + 36) {
+    } else if (t < LYG::NU + 36) {
       const int u = t - LYG::NU - 18;
       const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
       bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
@@ -608,14 +605,8 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       return;
     }
   }
-  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) {
-    if constexpr (SC) rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, y);
-    else clover_rows<float>(clov_inv, dO, Vb, sub, v6, y);
-  };
-  auto aee_rows = [&](const f2 v6[6], f2 y[3]) {
-    if constexpr (SC) rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, y);
-    else clover_rows<float>(clov, de, Vb, sub, v6, y);
-  };
+  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, y); };
+  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, y); };
   // u_o = A_oo^-1 r_o
   {
     f2 v6[6], u[3];
@@ -717,10 +708,10 @@ size_t sap_smem_bytes(const Geom& g, int real_size) {
   return units * 16 + bufs + 100 * sizeof(double);
 }
 
-static size_t sap_stg_smem(const Geom& g, bool stage_clover) {
+static size_t sap_stg_smem(const Geom& g) {
   const int Vh = g.Vb / 2;
   size_t bytes = (size_t)12 * (g.Vb + LPAD) * 16;               // links
-  if (stage_clover) bytes += (size_t)2 * 18 * Vh * 16;          // A_ee, A_oo^-1
+  bytes += (size_t)2 * 18 * Vh * 16;                            // A_ee, A_oo^-1
   bytes += (size_t)24 * Vh * 8;                                 // E, O
   bytes += 100 * sizeof(double);
   return bytes;
@@ -728,17 +719,16 @@ static size_t sap_stg_smem(const Geom& g, bool stage_clover) {
 
 static bool sap_stg_ok(const Geom& g) {
   const int Vh = g.Vb / 2;
-  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g, true) <= 226 * 1024;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g) <= 226 * 1024;
 }
 
-template <bool SC>
 static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const float* b, float* x,
                               const float* gauge, const float* clover, const float* clover_inv, int nrhs,
                               int* status, cudaStream_t st) {
   static size_t cfg = 0;
-  const size_t need = sap_stg_smem(g, SC);
+  const size_t need = sap_stg_smem(g);
   if (cfg < need) {
-    cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e != cudaSuccess) return e;
     cfg = need;
   }
@@ -753,7 +743,7 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
   lc.attrs = at;
   lc.numAttrs = 1;
   const int zero = x_is_zero ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg<SC>, g, colour, mr_iters, zero, b, x, gauge, clover,
+  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg, g, colour, mr_iters, zero, b, x, gauge, clover,
                                      clover_inv, status);
   ++g_launches;
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -765,9 +755,7 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
                       cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (sap_stg_ok(g)) {
-      // (SC = false leaves the clover in L1/L2 for half the shared memory, but
-      // 512 threads at 128 registers fill an SM's register file anyway)
-      return launch_stg<true>(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, st);
+      return launch_stg(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, st);
     }
   }
   int threads = sap_threads(g);
