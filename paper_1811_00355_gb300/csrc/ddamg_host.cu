@@ -7,6 +7,7 @@
 // preconditioner M (Eq. 5), the SAP smoother and the coarse solve run as
 // kernels without host synchronisation.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,6 +28,9 @@ namespace {
 
 constexpr uint32_t NEG = 0x80000000u;
 constexpr int NCLS = 4;               // kernel timing classes
+// slot of h->dots / h->h_pinned that an outer iteration's graph copies to the
+// host last: the host waits for it instead of synchronising the stream
+constexpr int DONE_SLOT = 6 * 64 + 8;
 
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -812,7 +816,30 @@ ddamg_status enqueue_iteration(ddamg_ctx* h, int k, std::vector<const double*>& 
     CK(multi_axpy_norm<double>(vlist.data(), k + 1, c2, -1.0, h->fw, NC, h->red, nn, h->st));
   }
   CK(cudaMemcpyAsync(h->h_pinned, h->dots, (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->h_pinned + DONE_SLOT, h->dots + DONE_SLOT, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(scale_by_inv_norm<double>(h->fw, vk1, nn, N, h->st));
+  return DDAMG_OK;
+}
+
+// Wait until iteration k's coefficients have reached the host: poll the slot
+// its graph copies last (stream order makes the coefficient copy complete
+// first), so that the host works on the Givens step while the graph's last
+// kernel still runs.  Falls back to a stream synchronisation after about a
+// second, and when kernel timing needs the graph's events.
+ddamg_status wait_coefficients(ddamg_ctx* h) {
+  if (h->timing) {
+    CK(cudaStreamSynchronize(h->st));
+    return DDAMG_OK;
+  }
+  volatile double* flag = h->h_pinned + DONE_SLOT;
+  const auto t0 = std::chrono::steady_clock::now();
+  while (*flag != 1.0) {
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(1)) {
+      CK(cudaStreamSynchronize(h->st));
+      break;
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
   return DDAMG_OK;
 }
 
@@ -943,10 +970,11 @@ ddamg_status fgmres(ddamg_ctx* h, double tol, ddamg_solve_info* info) {
     // iteration, limit the residual the recurrence can trust
     const double cycle_stop = std::max(tol * bnorm, refine ? h->p.outer_refine * beta : 0.0);
     for (int k = 0; k < m; ++k) {
+      *(volatile double*)(h->h_pinned + DONE_SLOT) = 0.0;
       TRY(run_iteration<R>(h, k, vlist, Vk(k), Zk(k), Vk(k + 1)));
       ++calls;
-      CK(cudaStreamSynchronize(h->st));
-      collect_graph(h, k);
+      TRY(wait_coefficients(h));
+      if (h->timing) collect_graph(h, k);
       const double* hp = h->h_pinned;
       std::vector<cd> col(k + 2);
       double n_after = hp[4 * (m + 2)];
@@ -1499,6 +1527,11 @@ ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_
     TRY(dalloc_t(h, &h->d_status, 1));
     TRY(dalloc_t(h, &h->red, reduce_scratch_len(64)));
     TRY(dalloc_t(h, &h->dots, (size_t)6 * 64 + 16));
+    {
+      const double one = 1.0;
+      CK(cudaMemcpyAsync(h->dots + DONE_SLOT, &one, sizeof one, cudaMemcpyHostToDevice, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
     TRY(dalloc_t(h, &h->lam64, (size_t)p->n_v * h->V24));
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(h->d_dev, 0, sizeof(unsigned long long), h->st));
