@@ -232,6 +232,32 @@ class DDAMG:
 
     def update_mass(self, m0, csw):
         self._check(self.lib.ddamg_update_mass(self.h, m0, csw))
+        self.p.m0, self.p.csw = m0, csw
+
+    # the geometry a saved setup must match to be loaded
+    _SETUP_KEYS = ("L", "sap_block", "agg_block", "n_v")
+
+    def save_setup(self, path):
+        """Write the setup's test vectors (orthonormal per aggregate and
+        chirality, FP64) with the geometry and mass they belong to to an .npz
+        file.  The links are not saved: they are the caller's input."""
+        meta = {k: np.array(list(getattr(self.p, k)) if k != "n_v" else [self.p.n_v], np.int64)
+                for k in self._SETUP_KEYS}
+        np.savez(path, vectors=self.get_test_vectors(), m0=self.p.m0, csw=self.p.csw, **meta)
+
+    def load_setup(self, path):
+        """Install test vectors written by save_setup in this handle and
+        assemble D_c from them with the handle's own links and mass (a saved
+        setup serves another mass as the mass update does).  The geometry
+        must match.  Returns the (m0, csw) the vectors were saved at."""
+        z = np.load(path)
+        for k in self._SETUP_KEYS:
+            want = list(getattr(self.p, k)) if k != "n_v" else [self.p.n_v]
+            if list(z[k]) != want:
+                raise DDAMGError(1, "saved setup has %s=%s, this handle %s" % (k, list(z[k]), want))
+        self.set_test_vectors(np.ascontiguousarray(z["vectors"]))
+        self.build_coarse()
+        return float(z["m0"]), float(z["csw"])
 
     def solve(self, rhs, tol=1e-10, allow_noconv=False, out=None):
         n = self._nrhs(rhs)

@@ -526,66 +526,56 @@ __global__ void k_invert_self(Geom g, const cpx<R>* __restrict__ Dc, int n2, cpx
 }
 
 // ---------------------------------------------------------------------------
-// coarse stencil building block (whole CTA):
-//   out[r] = scale * sum_{d in [d0,d1)} sum_c M_d[r][c] sv[d][c]
-// The 2n x 2n blocks are stored column-major (M_d[c][r] contiguous in r), so
-// a thread streams one (or two, FP32) rows with 16-byte loads down the
-// columns while neighbouring threads read neighbouring rows.  One partial
-// per direction lands in smem part[9][n2]; the sum over directions is taken
-// in a fixed order, so the result is bitwise reproducible.
+// coarse 9-point stencil (Eq. 2 applied): y(X) = sum_d D_c(X,d) x(nbr_d(X)).
+// The nine 2n x 2n blocks of a site are stored column-major and back to back,
+// so together they form one 2n x 18n matrix whose column dc = d*2n + c
+// multiplies x(nbr_d(X))[c].  A team of NP = 2n / RPU threads owns a site;
+// a thread owns RPU rows (two in FP32, one in FP64), streams them down all
+// 18n columns with 16-byte loads (neighbouring threads read neighbouring rows
+// of a column) and accumulates in registers.  Every byte of D_c is read once,
+// no partial sums go through shared memory and no thread idles while others
+// stream.  The gathered neighbour vectors sit in shared memory, one padded
+// copy per team so that the teams' broadcasts fall in different banks.  The
+// sum runs in a fixed order, so the result is bitwise reproducible.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ void cta_matvec(const cpx<R>* __restrict__ M, const cpx<R>* sv, int d0,
-                                           int d1, int n2, cpx<R>* out, R scale, bool add,
-                                           cpx<R>* part) {
+__global__ void k_coarse_apply(Geom g, const cpx<R>* __restrict__ Dc, int n2, int S,
+                               const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char csh[];
   using T = typename U16<R>::T;
   constexpr int RPU = 16 / (2 * sizeof(R));      // rows per 16-byte load
   const int NP = n2 / RPU;
-  const int units = (d1 - d0) * NP;
-  for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int dd = u / NP, j = u - dd * NP, d = d0 + dd;
-    const T* col = reinterpret_cast<const T*>(M + (size_t)d * n2 * n2) + j;
-    const cpx<R>* v = sv + d * n2;
-    cpx<R> a0 = mk(R(0), R(0)), a1 = mk(R(0), R(0));
-#pragma unroll 8
-    for (int c = 0; c < n2; ++c) {
-      T m = __ldg(col + (size_t)c * NP);
-      cpx<R> vc = v[c];
-      if constexpr (RPU == 2) {
-        fma(a0, mk((R)m.x, (R)m.y), vc);
-        fma(a1, mk((R)m.z, (R)m.w), vc);
-      } else {
-        fma(a0, mk((R)m.x, (R)m.y), vc);
-      }
+  const int NC = 9 * n2;                         // columns of the site's 2n x 18n matrix
+  const int team = threadIdx.x / NP, j = threadIdx.x - team * NP;
+  const int X = blockIdx.x * S + team;
+  const bool live = team < S && X < g.nb;
+  cpx<R>* sv = reinterpret_cast<cpx<R>*>(csh) + team * (NC + 1);
+  const size_t roff = (size_t)blockIdx.y * g.nb * n2;
+  if (live) {
+    const cpx<R>* xr = x + roff;
+    for (int idx = j; idx < NC; idx += NP) {
+      const int d = idx / n2, c = idx - d * n2;
+      sv[idx] = xr[(size_t)g.cnbr[d * g.nb + X] * n2 + c];
     }
-    part[dd * n2 + RPU * j] = a0;
-    if constexpr (RPU == 2) part[dd * n2 + RPU * j + 1] = a1;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < n2; r += blockDim.x) {
-    cpx<R> acc = mk(R(0), R(0));
-    for (int dd = 0; dd < d1 - d0; ++dd) acc = acc + part[dd * n2 + r];
-    acc = scale * acc;
-    out[r] = add ? out[r] + acc : acc;
+  if (!live) return;
+  const T* col = reinterpret_cast<const T*>(Dc + (size_t)X * NC * n2) + j;
+  cpx<R> a0 = mk(R(0), R(0)), a1 = mk(R(0), R(0));
+#pragma unroll 8
+  for (int c = 0; c < NC; ++c) {
+    const T m = __ldg(col + (size_t)c * NP);
+    const cpx<R> vc = sv[c];
+    if constexpr (RPU == 2) {
+      fma(a0, mk((R)m.x, (R)m.y), vc);
+      fma(a1, mk((R)m.z, (R)m.w), vc);
+    } else {
+      fma(a0, mk((R)m.x, (R)m.y), vc);
+    }
   }
-  __syncthreads();
-}
-
-template <class R>
-__global__ void k_coarse_apply(Geom g, const cpx<R>* __restrict__ Dc, int n2, const cpx<R>* __restrict__ x,
-                               cpx<R>* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char csh[];
-  cpx<R>* sv = reinterpret_cast<cpx<R>*>(csh);   // [9][n2]
-  cpx<R>* part = sv + 9 * n2;                    // [9][n2]
-  const int X = blockIdx.x, rhs = blockIdx.y;
-  const cpx<R>* xr = x + (size_t)rhs * g.nb * n2;
-  for (int idx = threadIdx.x; idx < 9 * n2; idx += blockDim.x) {
-    int d = idx / n2, c = idx - d * n2;
-    sv[idx] = xr[(size_t)g.cnbr[d * g.nb + X] * n2 + c];
-  }
-  __syncthreads();
-  cta_matvec<R>(Dc + (size_t)X * 9 * n2 * n2, sv, 0, 9, n2, y + ((size_t)rhs * g.nb + X) * n2, R(1), false,
-                part);
+  cpx<R>* out = y + roff + (size_t)X * n2 + RPU * j;
+  out[0] = a0;
+  if constexpr (RPU == 2) out[1] = a1;
 }
 
 // C = A B for one odd site X and direction d (column-major 2n x 2n blocks)
@@ -744,11 +734,19 @@ cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R*
 
 template <class R>
 cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs, cudaStream_t st) {
-  int n2 = 2 * n;
-  size_t smem = (size_t)18 * n2 * sizeof(cpx<R>);
-  k_coarse_apply<R><<<dim3(g.nb, nrhs), 128, smem, st>>>(g, reinterpret_cast<const cpx<R>*>(Dc), n2,
-                                                         reinterpret_cast<const cpx<R>*>(x),
-                                                         reinterpret_cast<cpx<R>*>(y));
+  const int n2 = 2 * n;
+  const int NP = n2 / (16 / (2 * (int)sizeof(R)));
+  // sites per CTA: the fewest that fill whole warps, at most 1024 threads
+  int S = 32;
+  while (S > 1 && (S / 2) * NP % 32 == 0) S /= 2;
+  while (S > 1 && S * NP > 1024) S /= 2;
+  const size_t smem = (size_t)S * (9 * n2 + 1) * sizeof(cpx<R>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_coarse_apply<R><<<dim3((g.nb + S - 1) / S, nrhs), S * NP, smem, st>>>(
+      g, reinterpret_cast<const cpx<R>*>(Dc), n2, S, reinterpret_cast<const cpx<R>*>(x), reinterpret_cast<cpx<R>*>(y));
   ++g_launches;
   return cudaGetLastError();
 }

@@ -317,6 +317,41 @@ def test_update_mass_keeps_vectors_and_rebuilds_operators():
     s.close()
 
 
+def test_saved_setup_loads_into_a_new_handle(tmp_path):
+    """A setup written with save_setup and loaded into a fresh handle on the
+    same links gives the same D_c and the same solve (the setup is a pure
+    function of the test vectors); loaded at another mass it serves that mass
+    as the mass update does; a setup of another geometry is refused."""
+    P = _P()
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, 1)
+    s.run_setup()
+    rhs = syn.gaussian_spinors(1, L, 68)
+    x0, info0 = s.solve(rhs, 1e-10)
+    Dc0 = s.get_coarse_op()
+    path = str(tmp_path / "setup.npz")
+    s.save_setup(path)
+    s.close()
+    s2 = make(MID, 1)
+    assert s2.load_setup(path) == (m0, csw)
+    assert np.array_equal(s2.get_coarse_op(), Dc0)
+    x1, info1 = s2.solve(rhs, 1e-10)
+    assert info1[0]["outer_iters"] == info0[0]["outer_iters"]
+    assert np.array_equal(x1, x0)
+    s2.close()
+    s3 = make(MID, 1)
+    s3.update_mass(m0 + 0.1, csw)
+    s3.load_setup(path)
+    op1 = oracle_op(L, eps, seed, m0 + 0.1, csw)
+    x2, _ = s3.solve(rhs, 1e-10)
+    assert rel(op1.apply(t(x2[0])).numpy(), rhs[0]) <= 1e-10
+    s3.close()
+    other = make(SMALL, 0)
+    with pytest.raises(P.DDAMGError):
+        other.load_setup(path)
+    other.close()
+
+
 def test_set_gauge_replaces_links_and_needs_a_new_setup():
     """ddamg_set_gauge: D follows the new links, a solve before the new setup
     is refused, one after it reaches 1e-10, and non-SU(3) links are rejected."""
