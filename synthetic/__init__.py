@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "volume", "rng", "gauge_field", "random_su3", "gaussian_spinors",
+    "volume", "rng", "gauge_field", "gauge_field_sliced", "random_su3", "gaussian_spinors",
     "point_sources", "Philox4x32",
 ]
 
@@ -72,6 +72,35 @@ def gauge_field(L, eps: float, seed: int) -> np.ndarray:
     """Near-unit SU(3) gauge field, complex128 ``[V][4][3][3]``."""
     V = volume(L)
     return np.ascontiguousarray(random_su3((V, 4), eps, rng(seed)))
+
+
+def _slice_links(args):
+    n_sites, eps, seed, t = args
+    g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(t)])))
+    return random_su3((n_sites, 4), eps, g)
+
+
+def gauge_field_sliced(L, eps: float, seed: int, workers: int = 0) -> np.ndarray:
+    """Near-unit SU(3) gauge field for large lattices, complex128 ``[V][4][3][3]``.
+
+    The same distribution as :func:`gauge_field`, drawn one time slice at a
+    time: the links of slice ``t`` come from PCG64 seeded with
+    ``SeedSequence([seed, t])``, so the field does not depend on how many
+    processes draw it.  ``workers > 1`` draws the slices in a pool of that
+    many spawned processes (spawned, so that a process that already uses a
+    GPU can call it).
+    """
+    L = tuple(int(v) for v in L)
+    per = L[0] * L[1] * L[2]
+    jobs = [(per, eps, seed, t) for t in range(L[3])]
+    if workers and workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_slice_links, jobs))
+    else:
+        parts = [_slice_links(j) for j in jobs]
+    return np.ascontiguousarray(np.concatenate(parts, axis=0))
 
 
 def unit_gauge(L) -> np.ndarray:
