@@ -626,9 +626,26 @@ def main():
     ap.add_argument("--no-stencils", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--stencils-only", action="store_true",
+                    help="time only the stencils (for profiler captures) and print their JSON")
+    ap.add_argument("--stencil-lattice", default=None,
+                    help="X,Y,Z,T of the stencil lattice (multiples of 8; default 32,32,32,64)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.stencil_lattice:
+        L = tuple(int(v) for v in args.stencil_lattice.split(","))
+        if len(L) != 4 or any(v % 8 for v in L):
+            raise SystemExit("--stencil-lattice wants four multiples of 8")
+        STENCIL["L"] = L
+    if args.stencils_only:
+        import torch
+        import paper_1811_00355_gb300 as P
+        torch.cuda.set_device(0)
+        P.load()
+        pk, pk_kind = peaks()
+        print(json.dumps({"stencils": stencils(P, torch, torch.cuda.current_stream(), pk, pk_kind)}))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
