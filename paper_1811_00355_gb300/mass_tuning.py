@@ -5,7 +5,8 @@ equations D^H D x = D^H b need more than N iterations to reach a relative
 residual ||b - D x|| / ||b|| <= tol" (a light quark, where the multigrid
 preconditioner matters).  This module measures that count with the library's
 own D (``DDAMG.apply_D``; D^H = g5 D g5 for the Wilson-clover operator) and
-scans m0 downward until the count exceeds N.  The scan estimates the count
+scans m0 downward until the count exceeds N (or, where no mass reaches N,
+to the mass of the largest count).  The scan estimates the count
 from a short run first: the CG coefficients of k iterations define the Lanczos
 tridiagonal matrix of D^H D, whose extreme eigenvalues bound its condition
 number kappa, and CG needs about sqrt(kappa)/2 * ln(2/tol) iterations.  The
@@ -89,34 +90,51 @@ def predicted_iterations(kappa, tol):
     return 0.5 * math.sqrt(kappa) * math.log(2.0 / tol)
 
 
-def scan_mass(h, b, target=5000, m0_start=-0.2, step=0.01, probe_iters=400, tol=1e-10,
-              m0_floor=-2.0, confirm=True, confirm_cap=None):
+def scan_mass(h, b, target=5000, m0_start=0.0, step=0.01, probe_iters=400, probe_tol=1e-6, tol=1e-10,
+              m0_floor=-2.0, patience=5, confirm=True, confirm_cap=None):
     """Lower m0 from m0_start in steps of `step` until the predicted CG count
-    of the normal equations exceeds `target`; then (if `confirm`) count it in
-    FP64, stepping further down while the count stays at or below target.
-    The handle's mass is changed (``update_mass``).  Returns a dict with the
-    chosen m0, the confirmed count and the scan's estimates."""
+    of the normal equations exceeds `target`.
+
+    Each probe runs at most `probe_iters` CG steps with the FP32 operator and
+    stops at the relative residual `probe_tol` (beyond the FP32 rounding
+    floor the coefficients carry no information).  Near-unit links and an
+    antiperiodic time direction keep the smallest singular value of D away
+    from zero, so the count has a maximum over m0 (the most critical mass)
+    that may lie below the target: once `patience` probes in a row stay
+    below the largest prediction, the scan has passed that maximum and
+    returns the mass of the largest prediction, with target_reached False.
+    If `confirm`, the count at the chosen mass is then taken in FP64 (at most
+    `confirm_cap` iterations).  The handle's mass is changed
+    (``update_mass``).  Returns a dict with the chosen m0, the scan's
+    estimates and the confirmed count."""
     csw = h.p.csw
     scan = []
     m0 = m0_start
-    while m0 >= m0_floor:
+    best_m0, best = m0_start, -1.0
+    behind = 0
+    reached = False
+    while m0 >= m0_floor - 1e-12:
         h.update_mass(m0, csw)
-        _, _, a, bt, _ = cg_normal_equations(h, b, tol=0.0, max_iter=probe_iters, precision=FP32)
+        _, _, a, bt, _ = cg_normal_equations(h, b, tol=probe_tol, max_iter=probe_iters, precision=FP32)
         lo, hi = lanczos_extremes(a, bt)
         pred = predicted_iterations(hi / lo, tol) if lo > 0 else float("inf")
-        scan.append({"m0": round(m0, 6), "lambda_min": lo, "lambda_max": hi, "predicted": pred})
+        scan.append({"m0": round(m0, 6), "lambda_min": lo, "lambda_max": hi, "predicted": pred,
+                     "probe_iters": len(a)})
+        if pred > best:
+            best_m0, best, behind = m0, pred, 0
+        else:
+            behind += 1
         if pred > target:
+            reached = True
+            break
+        if behind >= patience:
             break
         m0 -= step
-    out = {"m0": round(m0, 6), "scan": scan, "target": target}
-    if not confirm:
-        return out
-    cap = confirm_cap or 3 * target
-    while m0 >= m0_floor:
-        h.update_mass(m0, csw)
+    chosen = m0 if reached else best_m0
+    out = {"m0": round(chosen, 6), "target": target, "target_reached": reached, "scan": scan}
+    if confirm:
+        cap = confirm_cap or 3 * target
+        h.update_mass(chosen, csw)
         its, resid, _, _, _ = cg_normal_equations(h, b, tol=tol, max_iter=cap, precision=FP64)
-        out.update(m0=round(m0, 6), cg_iterations=its, cg_residual=resid, capped=its >= cap and resid > tol)
-        if its > target:
-            break
-        m0 -= step
+        out.update(cg_iterations=its, cg_residual=resid, capped=resid > tol)
     return out
