@@ -48,6 +48,12 @@ TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": 18_978_048 + 512, "coarse_gmres": 42_87
 # far larger than L2, links tiled from an 8^4 field of the same generator
 STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
                n_v=24, reps=20)
+# the 32^3 x 64 batched workload: 12 point sources in one lockstep batch,
+# n_v 24, FP32 inner solver with FP64 refinement; m0 = -0.125 is where the
+# unpreconditioned CG count of this ensemble peaks (mass_tuning.scan_mass on
+# the GPU: about 2100 iterations predicted there, no mass reaches 5000)
+LARGE = dict(L=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.125, csw=1.5, n_v=24,
+             outer_restart=10, tol=1e-10)
 # compulsory bytes per site of one fine D apply: in and out spinor (24 reals
 # each), four two-row links (12 reals each), packed clover A (72 reals)
 D_REALS_PER_SITE = 24 + 24 + 4 * 12 + 72
@@ -289,6 +295,13 @@ def run_ours(args):
     if rank == 0 and not args.no_stencils:
         sten = stencils(P, torch, stream, pk, pk_kind)
 
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        solver.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        large = large_batched()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         counts = {"precond_calls": sum(i["precond_calls"] for i in infos[-1])}
@@ -315,6 +328,7 @@ def run_ours(args):
             "variants": var,
             "serving": srv,
             "stencils": sten,
+            "batched_32x32x32x64": large,
         }
         print(json.dumps(line))
     if world > 1:
@@ -481,6 +495,67 @@ def _tiled(a, small, L):
     return np.ascontiguousarray(a.reshape((-1,) + inner))
 
 
+def large_batched():
+    """The 32^3 x 64 batched workload in a child process (its ~200 GB of
+    device memory and any failure stay out of this process); returns its
+    JSON object, or {"error": ...}."""
+    import subprocess
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--large-only"], cwd=ROOT,
+                           capture_output=True, text=True, timeout=400)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"error": "exit %d: %s" % (r.returncode, (r.stderr or r.stdout)[-400:])}
+        return json.loads(lines[-1])
+    except Exception as e:                      # noqa: BLE001 - reported in the JSON line
+        return {"error": repr(e)[:400]}
+
+
+def large_batched_child():
+    """Setup + the 12 point sources as one batch on 32^3 x 64, twice (the
+    first pass allocates the batch buffers); the second is timed with CUDA
+    events.  Prints one JSON object."""
+    import torch
+    import paper_1811_00355_gb300 as P
+    import synthetic as syn
+    s = LARGE
+    t0 = time.perf_counter()
+    U = syn.gauge_field_sliced(s["L"], s["eps"], s["seed"], workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    P.load()
+    stream = torch.cuda.current_stream()
+    U_dev = torch.from_numpy(U).cuda()
+    del U
+    b_dev = torch.from_numpy(syn.point_sources(s["L"])).cuda()
+    params = P.default_params(L=s["L"], sap_block=s["block"], n_v=s["n_v"], m0=s["m0"], csw=s["csw"],
+                              outer_restart=s["outer_restart"], precision=P.FP32)
+    h = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
+    try:
+        for _ in range(2):
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            h.run_setup()
+            ev[1].record(stream)
+            x, info = h.solve_batched(b_dev, s["tol"])
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+        setup_s = ev[0].elapsed_time(ev[1]) / 1e3
+        solve_s = ev[1].elapsed_time(ev[2]) / 1e3
+        ok = all(i["converged"] and i["true_residual"] <= s["tol"] for i in info)
+        out = {"value": round(12 / (setup_s + solve_s), 3), "unit": UNIT, "lattice": "32x32x32x64",
+               "m0": s["m0"], "csw": s["csw"], "eps": s["eps"], "n_v": s["n_v"], "rhs": "12 point sources, one batch",
+               "dtype": "f32+f64", "setup_s": round(setup_s, 3), "solve_s": round(solve_s, 3),
+               "outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in info),
+               "max_true_residual": max(i["true_residual"] for i in info), "all_converged": ok,
+               "device_GB": round(h.stats()["device_bytes"] / 1e9, 1), "gauge_generation_s": round(gen_s, 1),
+               "timing": "CUDA events, second of two passes"}
+    finally:
+        h.close()
+    print(json.dumps(out))
+
+
 def stencils(P, torch, stream, pk, pk_kind):
     """Achieved HBM bandwidth of the fine D (FP32, FP64) and of the coarse
     9-point stencil (FP32) on a lattice far larger than L2, from the
@@ -626,6 +701,8 @@ def main():
     ap.add_argument("--no-stencils", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^3 x 64 batched workload")
+    ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--stencils-only", action="store_true",
                     help="time only the stencils (for profiler captures) and print their JSON")
     ap.add_argument("--stencil-lattice", default=None,
@@ -638,6 +715,9 @@ def main():
         if len(L) != 4 or any(v % 8 for v in L):
             raise SystemExit("--stencil-lattice wants four multiples of 8")
         STENCIL["L"] = L
+    if args.large_only:
+        large_batched_child()
+        return
     if args.stencils_only:
         import torch
         import paper_1811_00355_gb300 as P
