@@ -20,10 +20,14 @@ solver to K computer", Sec. 2 "Algorithm" and Sec. 3):
   prolongation P (Eq. 3, Eq. 4), coarse operator (Eq. 2), coarse stencil and
   even-odd GMRES (Sec. 2);
 * :mod:`oracle.solver`   preconditioner M (Eq. 5), outer flexible GMRES,
-  adaptive setup (Sec. 2).
+  adaptive setup (Sec. 2);
+* :mod:`oracle.three_level`  the same construction applied once more to
+  D_c (the recursion Sec. 1 names as a merit, not run in the paper): level-2
+  Schwarz smoother, aggregation, D_cc = P2^H D_c P2, and the three-level M.
 
 Every function that is checked only by the invariants it must satisfy, and
 not against an independent value, says so.  The adaptive setup's output is
 "parity unpinned" as a unique result (it depends on rounding); it is pinned
-only through the invariants P^H P = 1 and D_c = P^H D P.
+only through the invariants P^H P = 1 and D_c = P^H D P.  The same holds for
+the level-2 setup of the three-level method (P2^H P2 = 1, D_cc = P2^H D_c P2).
 """
