@@ -107,3 +107,45 @@ def test_server_rejects_invalid_arguments_before_device_work(lib):
     assert lib.ddamg_server_create(0, 12, None, None) == 1
     assert lib.ddamg_server_wait(None, 1, None) == 1
     assert lib.ddamg_server_submit(None, 0, 1, None, None, 1e-10, None, None) == 1
+
+
+class _StubHandle:
+    """The part of a DDAMG handle that save_setup / load_setup use, with
+    the device calls replaced by host arrays (no GPU needed)."""
+
+    def __init__(self, P, L, n_v):
+        self._SETUP_KEYS = P.DDAMG._SETUP_KEYS
+        self.p = P.default_params(L=L, sap_block=(2, 2, 2, 2), n_v=n_v, m0=-0.2, csw=1.1)
+        self.V = int(np.prod(L))
+        self.vectors = None
+        self.built = False
+        rng = np.random.default_rng(1)
+        self._mine = rng.standard_normal((n_v, self.V, 4, 3)) + 1j * rng.standard_normal((n_v, self.V, 4, 3))
+
+    def get_test_vectors(self):
+        return self._mine
+
+    def set_test_vectors(self, v):
+        self.vectors = v
+
+    def build_coarse(self):
+        self.built = True
+
+
+def test_setup_file_round_trip_and_geometry_check(lib, tmp_path):
+    """save_setup writes the vectors with geometry and mass; load_setup gives
+    them back unchanged with that mass, and refuses another geometry before
+    any device call."""
+    import paper_1811_00355_gb300 as P
+    a = _StubHandle(P, (4, 4, 4, 4), 3)
+    path = str(tmp_path / "s.npz")
+    P.DDAMG.save_setup(a, path)
+    b = _StubHandle(P, (4, 4, 4, 4), 3)
+    b.p.m0 = 0.1
+    assert P.DDAMG.load_setup(b, path) == (-0.2, 1.1)
+    assert b.built and np.array_equal(b.vectors, a._mine)
+    for L, n_v in (((4, 4, 4, 8), 3), ((4, 4, 4, 4), 4)):
+        c = _StubHandle(P, L, n_v)
+        with pytest.raises(P.DDAMGError):
+            P.DDAMG.load_setup(c, path)
+        assert c.vectors is None and not c.built
