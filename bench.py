@@ -615,7 +615,6 @@ def _oracle_sample():
     """Time the oracle's operations on the 16^4 workload once each (seconds)."""
     import torch
     import synthetic as syn
-    from oracle.coarse import CoarseOperator, coarse_operator, orthonormalise
     from oracle.solver import Params, TwoLevelMG
     w = WORKLOAD
     L = w["L"]

@@ -7,7 +7,6 @@ import numpy as np
 import torch
 
 import synthetic as syn
-from oracle.coarse import Aggregation, CoarseOperator, coarse_operator, orthonormalise
 from oracle.dirac import WilsonClover
 from oracle.sap import SchwarzSmoother
 

@@ -12,7 +12,7 @@ import torch
 import synthetic as syn
 from oracle.coarse import (Aggregation, CoarseOperator, coarse_operator,
                            orthonormalise, prolong, restrict)
-from oracle.dirac import WilsonClover, chiral_blocks, pack_hermitian
+from oracle.dirac import WilsonClover
 from oracle.lattice import index_maps
 from oracle.solver import Params, TwoLevelMG
 from tests.gpu_common import (FULL, MID, SMALL, TOL32, TOL64, make, oracle_op, rel,

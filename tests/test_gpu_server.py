@@ -5,7 +5,6 @@ alone, and a device-memory budget that holds one configuration at a time
 releases and re-creates setups without changing results."""
 from __future__ import annotations
 
-import numpy as np
 import pytest
 
 import synthetic as syn
