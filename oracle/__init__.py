@@ -23,7 +23,10 @@ solver to K computer", Sec. 2 "Algorithm" and Sec. 3):
   adaptive setup (Sec. 2);
 * :mod:`oracle.three_level`  the same construction applied once more to
   D_c (the recursion Sec. 1 names as a merit, not run in the paper): level-2
-  Schwarz smoother, aggregation, D_cc = P2^H D_c P2, and the three-level M.
+  Schwarz smoother, aggregation, D_cc = P2^H D_c P2, and the three-level M;
+* :mod:`oracle.critical_mass`  the smallest singular value of D and the most
+  critical bare mass of a gauge field on a proxy lattice (a workload
+  parameter, not a step of the method).
 
 Every function that is checked only by the invariants it must satisfy, and
 not against an independent value, says so.  The adaptive setup's output is
