@@ -519,6 +519,8 @@ def large_batched_child():
     import paper_1811_00355_gb300 as P
     import synthetic as syn
     s = LARGE
+    if not torch.cuda.is_available():
+        raise SystemExit("no CUDA device")
     t0 = time.perf_counter()
     U = syn.gauge_field_sliced(s["L"], s["eps"], s["seed"], workers=min(16, os.cpu_count() or 1))
     gen_s = time.perf_counter() - t0
