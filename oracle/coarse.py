@@ -185,10 +185,14 @@ class CoarseOperator:
         return self.self_term(v) + self.hop(v)
 
     def dense(self) -> torch.Tensor:
+        """The stencil as a dense matrix: block (X, nbr_d(X)) collects
+        D_c[X, d] for every d (blocks whose neighbours coincide add up)."""
         n2 = self.Dc.shape[-1]
-        N = self.NX * n2
-        E = torch.eye(N, dtype=torch.complex128).reshape(N, self.NX, n2)
-        return self.apply(E).reshape(N, N).T
+        B = torch.zeros((self.NX, self.NX, n2, n2), dtype=torch.complex128)   # [X][Y][row][col]
+        rows = torch.arange(self.NX)
+        for d in range(9):
+            B.index_put_((rows, self.nbr[d]), self.Dc[:, d], accumulate=True)
+        return B.permute(0, 2, 1, 3).reshape(self.NX * n2, self.NX * n2)
 
     def solve(self, b, tol, restart, maxiter):
         """Even-odd preconditioned GMRES; returns ``(x, iterations)``."""
