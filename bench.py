@@ -57,9 +57,11 @@ LARGE = dict(L=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.125,
 # compulsory bytes per site of one fine D apply: in and out spinor (24 reals
 # each), four two-row links (12 reals each), packed clover A (72 reals)
 D_REALS_PER_SITE = 24 + 24 + 4 * 12 + 72
-# outer-solver preconditioner calls of this workload (12 point sources), as
-# measured on the CUDA path; used only to scale the reference arm's sample
-REFERENCE_PRECOND_CALLS = 12 * 12
+# outer-solver preconditioner calls of this workload (12 point sources) in
+# the oracle's arithmetic: the FP64 single-right-hand-side form of the CUDA
+# path (FP64 M and D, FGMRES(30), as the oracle) takes 20 outer iterations
+# per source; used only to scale the reference arm's sample
+REFERENCE_PRECOND_CALLS = 12 * 20
 
 
 def env_rank():
