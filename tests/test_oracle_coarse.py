@@ -7,25 +7,10 @@ import torch
 from oracle.coarse import (Aggregation, CoarseOperator, coarse_operator,
                            orthonormalise, prolong, restrict)
 from oracle.krylov import gmres
-from tests.oracle_fixtures import C128, dense_D, dot, rel, spinors, wilson
+from tests.oracle_fixtures import C128, dense_D, dense_P, dot, rel, spinors, wilson
 
 L = (4, 4, 4, 4)
 ARGS = (L, 0.3, 0, -0.2, 1.0)
-
-
-def _dense_P(lam, agg):
-    """Columns lambda_i(X, s) in coarse order (X, s*n + i), Eq. 1."""
-    n = lam.shape[0]
-    V = lam.shape[1]
-    P = torch.zeros((12 * V, agg.NX * 2 * n), dtype=C128)
-    for X in range(agg.NX):
-        sites = agg.sites[X]
-        for s in (0, 1):
-            for i in range(n):
-                v = torch.zeros((V, 4, 3), dtype=C128)
-                v[sites, 2 * s:2 * s + 2] = lam[i, sites, 2 * s:2 * s + 2]
-                P[:, X * 2 * n + s * n + i] = v.reshape(-1)
-    return P
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +18,7 @@ def setup4():
     op = wilson(*ARGS)
     agg = Aggregation(op.geom, (2, 2, 2, 2))
     lam = orthonormalise(spinors(4, L, 31), agg)
-    return op, agg, lam, _dense_P(lam, agg)
+    return op, agg, lam, dense_P(lam, agg)
 
 
 def test_orthonormal(setup4):
@@ -46,8 +31,8 @@ def test_orthonormalise_keeps_span():
     op = wilson(*ARGS)
     agg = Aggregation(op.geom, (2, 2, 2, 2))
     raw = spinors(4, L, 32)
-    Praw = _dense_P(raw, agg)
-    Q = _dense_P(orthonormalise(raw, agg), agg)
+    Praw = dense_P(raw, agg)
+    Q = dense_P(orthonormalise(raw, agg), agg)
     proj = Q @ (Q.conj().T @ Praw)
     assert rel(proj, Praw) < 1e-13
 
@@ -103,7 +88,7 @@ def test_coarse_operator_4x4_aggregates_larger_coarse_lattice():
     agg = Aggregation(op.geom, (2, 2, 2, 4))
     lam = orthonormalise(spinors(2, Lr, 35), agg)
     cop = CoarseOperator(coarse_operator(op, lam, agg), agg.coarse)
-    P = _dense_P(lam, agg)
+    P = dense_P(lam, agg)
     x = torch.randn(P.shape[1], dtype=torch.float64) + 1j * torch.randn(P.shape[1], dtype=torch.float64)
     fine = op.apply((P @ x).reshape(-1, 4, 3)).reshape(-1)
     expect = P.conj().T @ fine

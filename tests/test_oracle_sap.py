@@ -10,22 +10,10 @@ from __future__ import annotations
 import torch
 
 from oracle.sap import SchwarzSmoother
-from tests.oracle_fixtures import dense_D, rel, spinors, wilson
+from tests.oracle_fixtures import dense_block_inverse, dense_D, rel, spinors, wilson
 
 L = (4, 4, 4, 4)
 ARGS = (L, 0.3, 0, 0.3, 1.0)          # heavier mass: MR converges quickly
-
-
-def _dense_blocks(sm, D, c):
-    """K_c = sum_{B of colour c} I_B D_BB^-1 I_B^T as a dense matrix."""
-    n = D.shape[0]
-    K = torch.zeros_like(D)
-    for B in range(sm.blk.n_blocks):
-        if int(sm.blk.colour_of_block[B]) != c:
-            continue
-        idx = (sm.blk.sites[B][:, None] * 12 + torch.arange(12)).reshape(-1)
-        K[idx[:, None], idx[None, :]] = torch.linalg.inv(D[idx][:, idx])
-    return K
 
 
 def test_mr_converges_to_block_solve():
@@ -35,7 +23,7 @@ def test_mr_converges_to_block_solve():
     r = spinors(1, L, 21)[0]
     for c in (0, 1):
         e = sm.block_solve(r, c, 200)
-        K = _dense_blocks(sm, D, c)
+        K = dense_block_inverse(sm.blk, D, c)
         expect = (K @ r.reshape(-1)).reshape(r.shape)
         assert rel(e, expect) < 1e-12
 
@@ -63,7 +51,7 @@ def test_sap_matches_dense_multiplicative_schwarz():
     D = dense_D(*ARGS)
     sm = SchwarzSmoother(op, (2, 2, 2, 2))
     b = spinors(1, L, 23)[0]
-    K = [_dense_blocks(sm, D, c) for c in (0, 1)]
+    K = [dense_block_inverse(sm.blk, D, c) for c in (0, 1)]
     x = torch.zeros(D.shape[0], dtype=D.dtype)
     bv = b.reshape(-1)
     for _ in range(3):

@@ -8,7 +8,7 @@ import torch
 import synthetic as syn
 from oracle.coarse import CoarseOperator, coarse_operator
 from oracle.solver import Params, TwoLevelMG
-from tests.oracle_fixtures import C128, dense_D, rel, spinors, t
+from tests.oracle_fixtures import C128, dense_block_inverse, dense_D, dense_P, rel, spinors, t
 
 L = (4, 4, 4, 4)
 
@@ -67,10 +67,84 @@ def test_setup_improves_convergence(mg4):
     assert its_setup <= its_raw
 
 
-def test_preconditioner_is_eq5(mg4):
-    """M r = x1 + SAP(r - D x1) with x1 = P D_c^-1 R r: check the coarse part
-    is removed from the residual in the coarse space, R (r - D x1) ~ 0 up to the
-    coarse tolerance, and that M is a good approximate inverse."""
+# Eq. 5 in an exact mode: with the block solves run to convergence (MR on a
+# heavier mass) and the coarse system solved to rounding, M is the fixed linear
+# map  M = C + S (1 - D C),  C = P D_c^-1 P^H,  S the multiplicative Schwarz
+# smoother written with dense block inverses.  Both sides are formed from
+# dense matrices that share nothing with the oracle's stencil code.
+EXACT = dict(m0=0.3, n_v=4, n_sap=2, mr_iters=200, coarse_tol=1e-14, coarse_maxiter=4000, setup_iters=0)
+
+
+def _exact_mg(cls=TwoLevelMG):
+    mg = cls(t(syn.gauge_field(L, 0.3, 0)), _params(**EXACT))
+    mg.set_test_vectors(spinors(EXACT["n_v"], L, 70))
+    return mg
+
+
+def _dense_eq5(mg, r):
+    D = dense_D(L, 0.3, 0, EXACT["m0"], 1.0)
+    Pd = dense_P(mg.lam, mg.agg)
+    C = Pd @ torch.linalg.solve(Pd.conj().T @ D @ Pd, Pd.conj().T)
+    K = [dense_block_inverse(mg.sap.blk, D, c) for c in (0, 1)]
+
+    def schwarz(v):
+        x = torch.zeros_like(v)
+        for _ in range(EXACT["n_sap"]):
+            for c in (0, 1):
+                x = x + K[c] @ (v - D @ x)
+        return x
+
+    rv = r.reshape(-1)
+    x1 = C @ rv
+    return (x1 + schwarz(rv - D @ x1)).reshape(r.shape)
+
+
+class _PreSmoothing(TwoLevelMG):
+    """Planted mistake: smoothing before the coarse correction."""
+    def apply_M(self, r):
+        e = self.smoother(r)
+        return e + self.coarse_correction(r - self.op.apply(e))
+
+
+class _NoResidualUpdate(TwoLevelMG):
+    """Planted mistake: the smoother applied to r instead of r - D x1."""
+    def apply_M(self, r):
+        return self.coarse_correction(r) + self.smoother(r)
+
+
+class _WrongSign(TwoLevelMG):
+    """Planted mistake: r + D x1 as the smoother's right-hand side."""
+    def apply_M(self, r):
+        x1 = self.coarse_correction(r)
+        return x1 + self.smoother(r + self.op.apply(x1))
+
+
+class _CoarseOnly(TwoLevelMG):
+    """Planted mistake: the smoother term dropped."""
+    def apply_M(self, r):
+        return self.coarse_correction(r)
+
+
+def test_preconditioner_is_eq5_exactly():
+    """Eq. 5 with exact block and coarse solves equals the dense formula
+    C + S (1 - D C) to rounding."""
+    mg = _exact_mg()
+    r = spinors(1, L, 71)[0]
+    assert rel(mg.apply_M(r), _dense_eq5(mg, r)) < 1e-11
+
+
+@pytest.mark.parametrize("cls", [_PreSmoothing, _NoResidualUpdate, _WrongSign, _CoarseOnly])
+def test_eq5_pin_rejects_planted_mistakes(cls):
+    """Each plausible mistake in the preconditioner moves M r far from the
+    dense Eq. 5 (so the exact pin above would catch it)."""
+    mg = _exact_mg(cls)
+    r = spinors(1, L, 71)[0]
+    assert rel(mg.apply_M(r), _dense_eq5(mg, r)) > 1e-3
+
+
+def test_preconditioner_reduces_coarse_residual(mg4):
+    """At the method's coarse tolerance the coarse part is removed from the
+    residual up to 5e-2 (R (r - D x1) ~ 0), and M is a good approximate inverse."""
     r = spinors(1, L, 4)[0]
     from oracle.coarse import restrict
     x1 = mg4.coarse_correction(r)
