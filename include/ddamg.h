@@ -139,6 +139,10 @@ typedef struct {
   double setup_flops;             /* theoretical flops of the adaptive setups */
   double solve_flops;             /* and of the solves (model of
                                      ddamg_get_history) since the last reset  */
+  uint64_t restrict_launches;     /* launches of the restriction (Eq. 3)     */
+  double restrict_ms;
+  uint64_t prolong_launches;      /* launches of the prolongation (Eq. 4)    */
+  double prolong_ms;
 } ddamg_stats;
 
 /* Fill *p with the library defaults (4^4 blocks, n_v 20, N_SAP 4, 4 MR,
@@ -258,6 +262,38 @@ DDAMG_API ddamg_status ddamg_build_coarse(ddamg_handle h);
 
 /* Export D_c in the coarse-op layout (host buffer, NX*9*(2n)^2 complex). */
 DDAMG_API ddamg_status ddamg_get_coarse_op(ddamg_handle h, double *out);
+
+/* Install a coarse operator given in the coarse-op layout (host or device,
+ * NX*9*(2n)^2 complex doubles), stored in the inner precision, and invert
+ * its self blocks for the even-odd coarse solve (Sec. 2), as
+ * ddamg_build_coarse does for the D_c of Eq. 2.  For running the coarse
+ * stencil and solver on a given operator; the test vectors are left as they
+ * are.  DDAMG_ENUMERIC if a self block is singular. */
+DDAMG_API ddamg_status ddamg_set_coarse_op(ddamg_handle h, const double *dc, int on_device);
+
+/* Launch configuration the coarse GMRES (Sec. 2) uses for nrhs right-hand
+ * sides on this handle (chosen by the library from the coarse lattice, n_v,
+ * the restart length and the device's shared memory and SM count). */
+typedef struct {
+  int rhs_per_pass;      /* right-hand sides solved in lockstep per pass     */
+  int ctas;              /* CTAs of the cooperative launch                   */
+  int sites_per_cta;     /* even (and odd) coarse sites owned by each CTA    */
+  int krylov_in_shared;  /* 1: the CTA's Krylov-basis slices in shared memory,
+                            0: in global scratch                             */
+  int resident_blocks;   /* 1: the even site's nine D_c blocks stay in shared
+                            memory for the launch                            */
+  size_t shared_bytes;   /* dynamic shared memory per CTA                    */
+  size_t scratch_bytes;  /* global scratch the launch touches                */
+} ddamg_coarse_plan;
+DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan *out);
+
+/* Polls of the device-side bounded waits before they give up and the call
+ * returns DDAMG_ETIMEOUT: the SAP kernel's wait for its staged block and the
+ * coarse GMRES grid barrier (default about a second each).  polls >= 0 sets
+ * both (0: a wait gives up at its first unsuccessful poll, for exercising
+ * the time-out path); polls < 0 restores the defaults.  A wait that gives up
+ * leaves its outputs incomplete; the handle stays usable. */
+DDAMG_API ddamg_status ddamg_set_wait_limit(ddamg_handle h, int64_t polls);
 
 /* Eq. 3: out[X][s n + i] = <lambda_i(X,s)|in>; nrhs fine -> coarse. */
 DDAMG_API ddamg_status ddamg_restrict(ddamg_handle h, int precision, int nrhs,

@@ -29,12 +29,10 @@ def _givens(h1: complex, h2: complex):
     return a1 / rho, ph * h2.conjugate() / rho, ph * rho
 
 
-def gmres(apply_A, b, tol, restart, maxiter, precond=None):
-    """Solve ``A x = b`` from ``x = 0``.  Returns ``(x, iterations, converged)``.
-
-    ``precond`` (optional) is applied on the right, each basis vector may be
-    preconditioned differently (flexible GMRES).
-    """
+def gmres_steps(apply_A, b, tol, restart, maxiter, precond=None):
+    """Generator form of :func:`gmres`: yields the running iteration count
+    after every Arnoldi step and returns ``(x, iterations, converged)`` (as
+    the value of ``StopIteration``).  The arithmetic is that of gmres."""
     x = torch.zeros_like(b)
     bnorm = torch.linalg.vector_norm(b).item()
     if bnorm == 0.0:
@@ -76,6 +74,7 @@ def gmres(apply_A, b, tol, restart, maxiter, precond=None):
             g[k] = cs[k] * g[k]
             total += 1
             k_done = k + 1
+            yield total
             if abs(g[k + 1]) <= tol * bnorm or total >= maxiter or hn == 0:
                 break
         y = [0j] * k_done
@@ -87,3 +86,17 @@ def gmres(apply_A, b, tol, restart, maxiter, precond=None):
         for i in range(k_done):
             x = x + y[i] * Zb[i]
         r = b - apply_A(x)
+
+
+def gmres(apply_A, b, tol, restart, maxiter, precond=None):
+    """Solve ``A x = b`` from ``x = 0``.  Returns ``(x, iterations, converged)``.
+
+    ``precond`` (optional) is applied on the right, each basis vector may be
+    preconditioned differently (flexible GMRES).
+    """
+    it = gmres_steps(apply_A, b, tol, restart, maxiter, precond)
+    while True:
+        try:
+            next(it)
+        except StopIteration as done:
+            return done.value

@@ -31,7 +31,7 @@ import torch
 from .coarse import (Aggregation, CoarseOperator, coarse_operator,
                      orthonormalise, prolong, restrict)
 from .dirac import WilsonClover
-from .krylov import gmres
+from .krylov import gmres, gmres_steps
 from .sap import SchwarzSmoother
 
 
@@ -108,6 +108,12 @@ class TwoLevelMG:
         """Outer FGMRES preconditioned by M; returns ``(x, iterations, converged)``."""
         return gmres(self.op.apply, b, tol, self.p.outer_restart,
                      self.p.outer_maxiter, precond=self.apply_M)
+
+    def solve_steps(self, b, tol):
+        """:meth:`solve` as a generator that yields after every outer
+        iteration (for timing the solver one iteration at a time)."""
+        return gmres_steps(self.op.apply, b, tol, self.p.outer_restart,
+                           self.p.outer_maxiter, precond=self.apply_M)
 
     def true_residual(self, b, x):
         return (torch.linalg.vector_norm(b - self.op.apply(x))

@@ -59,6 +59,8 @@ class Stats(C.Structure):
         ("coarse_launches", C.c_uint64), ("coarse_ms", C.c_double), ("device_bytes", C.c_size_t),
         ("coarse_apply_launches", C.c_uint64), ("coarse_apply_ms", C.c_double),
         ("reorth_passes", C.c_uint64), ("setup_flops", C.c_double), ("solve_flops", C.c_double),
+        ("restrict_launches", C.c_uint64), ("restrict_ms", C.c_double),
+        ("prolong_launches", C.c_uint64), ("prolong_ms", C.c_double),
     ]
 
     def as_dict(self):
@@ -69,6 +71,17 @@ class RequestInfo(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("batch_rhs", C.c_int), ("batch_requests", C.c_int), ("setup_run", C.c_int),
         ("queue_seconds", C.c_double), ("latency_seconds", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CoarsePlan(C.Structure):
+    _fields_ = [
+        ("rhs_per_pass", C.c_int), ("ctas", C.c_int), ("sites_per_cta", C.c_int),
+        ("krylov_in_shared", C.c_int), ("resident_blocks", C.c_int),
+        ("shared_bytes", C.c_size_t), ("scratch_bytes", C.c_size_t),
     ]
 
     def as_dict(self):
@@ -106,6 +119,9 @@ SIGNATURES = {
     "ddamg_coarse_solve": (_I, [_H, _I, _I, _P, _P, _I, _D, _P]),
     "ddamg_coarse_solve_noalloc": (_I, [_H, _I, _P, _P, _D, _P]),
     "ddamg_apply_M": (_I, [_H, _I, _I, _P, _P, _I]),
+    "ddamg_set_coarse_op": (_I, [_H, _P, _I]),
+    "ddamg_get_coarse_plan": (_I, [_H, _I, C.POINTER(CoarsePlan)]),
+    "ddamg_set_wait_limit": (_I, [_H, C.c_int64]),
     "ddamg_get_index_maps": (_I, [_H, _P, _P, _P, _P, _P]),
     "ddamg_get_stats": (_I, [_H, C.POINTER(Stats)]),
     "ddamg_reset_stats": (_I, [_H]),
@@ -347,6 +363,23 @@ class DDAMG:
         out = np.empty((self.NX, 9, n2, n2), np.complex128)
         self._check(self.lib.ddamg_get_coarse_op(self.h, C.c_void_p(out.ctypes.data)))
         return out
+
+    def set_coarse_op(self, dc):
+        """Install a coarse operator ``[NX][9][2n][2n]`` (host or device) and
+        invert its self blocks."""
+        p, dev = _ptr(dc)
+        self._check(self.lib.ddamg_set_coarse_op(self.h, p, dev))
+
+    def coarse_plan(self, nrhs=1):
+        """Launch configuration of the coarse GMRES for nrhs right-hand sides."""
+        c = CoarsePlan()
+        self._check(self.lib.ddamg_get_coarse_plan(self.h, nrhs, C.byref(c)))
+        return c.as_dict()
+
+    def set_wait_limit(self, polls=-1):
+        """Polls of the device-side bounded waits before they give up
+        (0: at the first unsuccessful poll; negative: the defaults)."""
+        self._check(self.lib.ddamg_set_wait_limit(self.h, polls))
 
     def restrict(self, x, precision=FP64):
         n = self._nrhs(x)

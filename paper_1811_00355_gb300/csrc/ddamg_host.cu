@@ -27,7 +27,7 @@ using cd = std::complex<double>;
 namespace {
 
 constexpr uint32_t NEG = 0x80000000u;
-constexpr int NCLS = 4;               // kernel timing classes
+constexpr int NCLS = 6;               // kernel timing classes
 // slot of h->dots / h->h_pinned that an outer iteration's graph copies to the
 // host last: the host waits for it instead of synchronising the stream
 constexpr int DONE_SLOT = 6 * 64 + 8;
@@ -35,6 +35,11 @@ constexpr int DONE_SLOT = 6 * 64 + 8;
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
 };
+
+// polls before a device-side wait gives up (each poll about an L2 round
+// trip): about a second for a staged SAP block and for a grid barrier
+constexpr long long WAIT_SAP_DEFAULT = 1ll << 22;
+constexpr long long WAIT_GRID_DEFAULT = 1ll << 21;
 
 }  // namespace
 
@@ -115,9 +120,10 @@ struct ddamg_ctx {
   // and device time; timers recorded outside graphs wait in `pending`
   bool timing = false;
   uint64_t launches0 = 0;
-  // timing classes: 0 fine D, 1 SAP sweep, 2 coarse GMRES, 3 coarse stencil
-  uint64_t n_cls[NCLS] = {0, 0, 0, 0};
-  double ms_cls[NCLS] = {0.0, 0.0, 0.0, 0.0};
+  // timing classes: 0 fine D, 1 SAP sweep, 2 coarse GMRES, 3 coarse stencil,
+  // 4 restriction, 5 prolongation
+  uint64_t n_cls[NCLS] = {};
+  double ms_cls[NCLS] = {};
   std::vector<std::pair<int, Timer>> pending;
   std::vector<Timer> pool;
 
@@ -131,7 +137,7 @@ struct ddamg_ctx {
     std::vector<GraphTimer> timers;
     uint64_t launches = 0;
     double flops = 0.0;                 // model flops of one replay
-    uint64_t n_cls[NCLS] = {0, 0, 0, 0};
+    uint64_t n_cls[NCLS] = {};
     int gen = -1;
     bool timing = false;
   };
@@ -147,6 +153,11 @@ struct ddamg_ctx {
   int* d_cit = nullptr;                 // coarse iterations of each outer iteration
   std::vector<double> hist_flops, hist_res;   // last single-RHS solve
   cudaStream_t cap_st = nullptr;        // private stream used only to record graphs
+  // polls of the device-side bounded waits before they give up
+  // (ddamg_set_wait_limit): the SAP kernel's wait for its staged block and
+  // the coarse GMRES grid barrier
+  long long wait_sap = WAIT_SAP_DEFAULT;
+  long long wait_grid = WAIT_GRID_DEFAULT;
 };
 
 namespace {
@@ -533,15 +544,19 @@ template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 // R and P of the inner solver (FP16 test vectors when half_vectors is set)
 template <class R>
 cudaError_t restrict_inner(ddamg_ctx* h, const R* in, R* bc, int nf) {
-  if constexpr (sizeof(R) == 4)
-    if (h->p.half_vectors) return restrict_op_h(h->g, h->lam16, h->p.n_v, in, bc, nf, h->st);
-  return restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, in, bc, nf, h->st);
+  return timed(h, 4, [&] {
+    if constexpr (sizeof(R) == 4)
+      if (h->p.half_vectors) return restrict_op_h(h->g, h->lam16, h->p.n_v, in, bc, nf, h->st);
+    return restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, in, bc, nf, h->st);
+  });
 }
 template <class R>
 cudaError_t prolong_inner(ddamg_ctx* h, const R* xc, R* out, int nf) {
-  if constexpr (sizeof(R) == 4)
-    if (h->p.half_vectors) return prolong_op_h(h->g, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
-  return prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, xc, out, nf, false, h->st);
+  return timed(h, 5, [&] {
+    if constexpr (sizeof(R) == 4)
+      if (h->p.half_vectors) return prolong_op_h(h->g, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
+    return prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, xc, out, nf, false, h->st);
+  });
 }
 
 // ---- operators on device fields ---------------------------------------------------
@@ -564,7 +579,7 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf) {
       addf(h, nf * flops_sap_sweep(h, zero));
       CK(timed(h, 1, [&] {
         return sap_sweep<R>(h->g, c, h->p.mr_iters, zero, b, x, gauge_of<R>(h), clov_of<R>(h, false),
-                            clov_of<R>(h, true), nf, h->d_status, h->st);
+                            clov_of<R>(h, true), nf, h->d_status, h->wait_sap, h->st);
       }));
     }
   return DDAMG_OK;
@@ -580,6 +595,7 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   a.tol = tol;
   a.restart = h->p.coarse_restart;
   a.max_iter = h->p.coarse_max_iter;
+  a.wait_limit = h->wait_grid;
   addf(h, nf * flops_coarse_fixed(h));   // iterations are added when their counts are read
   CK(timed(h, 2, [&] {
     return coarse_gmres<R>(h->g, a, bc, xc, nf, h->cwork, iters_dev, h->d_iters_acc, h->d_status, h->st);
@@ -613,7 +629,8 @@ ddamg_status check_status(ddamg_ctx* h) {
   CK(cudaStreamSynchronize(h->st));
   if (st != 0) {
     cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
-    return fail(h, DDAMG_ETIMEOUT, "a device-side grid barrier gave up waiting (status %d)", st);
+    return fail(h, DDAMG_ETIMEOUT, "a bounded device-side wait (SAP staging or coarse grid barrier) gave up (status %d)",
+                st);
   }
   return DDAMG_OK;
 }
@@ -866,7 +883,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
       cudaEventDestroy(gt.t.b);
     }
     G.timers.clear();
-    const uint64_t l0 = g_launches;
+    const uint64_t l0 = LaunchCount::mine();
     const double f0 = h->flops[h->fphase];
     uint64_t c0[NCLS];
     for (int c = 0; c < NCLS; ++c) c0[c] = h->n_cls[c];
@@ -885,14 +902,14 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->st, &graph);
     h->st = user;
-    G.launches = g_launches - l0;
+    G.launches = LaunchCount::mine() - l0;
     G.flops = h->flops[h->fphase] - f0;
     h->flops[h->fphase] = f0;
     for (int c = 0; c < NCLS; ++c) {
       G.n_cls[c] = h->n_cls[c] - c0[c];
       h->n_cls[c] = c0[c];
     }
-    g_launches = l0;
+    g_launches.remove_mine(G.launches);
     if (s != DDAMG_OK) {
       if (graph) cudaGraphDestroy(graph);
       return s;
@@ -1385,25 +1402,18 @@ ddamg_status coarse_out(ddamg_ctx* h, const R* src, size_t nc, double* dst, int 
 constexpr size_t NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-unsigned char* g_noalloc_ptr[128] = {};   // device address of the array, per device
-
-// Once per device, with that device current: the array's name is only a
-// host-side stand-in, so its device address comes from cudaGetSymbolAddress.
+// The array's name is only a host-side stand-in: its device address comes
+// from cudaGetSymbolAddress, looked up on every call with the caller's device
+// current, so that it always belongs to the current context (a cached
+// address would go stale after cudaDeviceReset or under another context).
+// The first call on a device may load the library's device code (lazy
+// loading), so it must come before any stream capture.
 ddamg_status noalloc_scratch(ddamg_ctx* h, unsigned char** out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(h, DDAMG_EINVAL, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(h, DDAMG_ECUDA, "cudaGetSymbolAddress of the fixed scratch array failed: %s",
-                  cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = reinterpret_cast<unsigned char*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(h, DDAMG_ECUDA, "cudaGetSymbolAddress of the fixed scratch array failed: %s", cudaGetErrorString(e));
+  *out = reinterpret_cast<unsigned char*>(p);
   return DDAMG_OK;
 }
 
@@ -1412,7 +1422,8 @@ ddamg_status coarse_solve_noalloc_impl(ddamg_ctx* h, int nrhs, const double* in,
                                        int* iters) {
   const size_t nc = (size_t)nrhs * h->g.nb * h->n2;
   const size_t vec = (nc * 2 * sizeof(R) + 255) / 256 * 256;
-  const size_t work = coarse_gmres_exact_bytes<R>(h->g, h->p.n_v, h->p.coarse_restart, nrhs);
+  const CoarsePlan plan = coarse_gmres_plan<R>(h->g, h->p.n_v, h->p.coarse_restart, nrhs);
+  const size_t work = plan.work_bytes;
   if (work == 0) return fail(h, DDAMG_EINVAL, "no launch configuration for the coarse solve");
   const size_t need = 2 * vec + work;
   if (need > NOALLOC_SCRATCH_BYTES)
@@ -1432,8 +1443,9 @@ ddamg_status coarse_solve_noalloc_impl(ddamg_ctx* h, int nrhs, const double* in,
   a.tol = tol;
   a.restart = h->p.coarse_restart;
   a.max_iter = h->p.coarse_max_iter;
+  a.wait_limit = h->wait_grid;
   CK(coarse_from_f64<R>(in, bin, nc, h->st));
-  CK(coarse_gmres<R>(h->g, a, bin, xout, nrhs, wk, h->d_iters, nullptr, h->d_status, h->st));
+  CK(coarse_gmres<R>(h->g, a, bin, xout, nrhs, wk, h->d_iters, nullptr, h->d_status, h->st, &plan));
   CK(coarse_to_f64<R>(xout, out, nc, h->st));
   TRY(check_status(h));
   if (iters) CK(cudaMemcpyAsync(iters, h->d_iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -1711,7 +1723,7 @@ ddamg_status ddamg_block_solve(ddamg_handle h, int prec, int colour, int nrhs, c
     CK(cudaMemsetAsync(x, 0, nrhs * h->V24 * sizeof(R), h->st));
     ++h->n_cls[1];
     CK(sap_sweep<R>(h->g, colour, h->p.mr_iters, true, b, x, gauge_of<R>(h), clov_of<R>(h, false),
-                    clov_of<R>(h, true), nrhs, h->d_status, h->st));
+                    clov_of<R>(h, true), nrhs, h->d_status, h->wait_sap, h->st));
     TRY(check_status(h));
     return export_fields<R>(h, x, nrhs, out, on_device);
   });
@@ -1775,6 +1787,75 @@ ddamg_status ddamg_get_coarse_op(ddamg_handle h, double* out) {
   cudaFree(tmpd);
   h->allocs.pop_back();
   h->bytes -= 2 * nc * sizeof(double);
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_set_coarse_op(ddamg_handle h, const double* dc, int on_device) {
+  if (!h || !dc) return DDAMG_EINVAL;
+  TRY(alloc_coarse(h));
+  const size_t nblk = (size_t)h->g.nb * 9;
+  const size_t nc = nblk * h->n2 * h->n2;
+  const double* src = dc;
+  double* tmpd = nullptr;
+  if (!on_device) {
+    TRY(dalloc_t(h, &tmpd, 2 * nc));
+    CK(cudaMemcpyAsync(tmpd, dc, 2 * nc * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    src = tmpd;
+  }
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+  if (h->p.precision == DDAMG_FP32) {
+    CK(coarse_import<float>(src, h->p.n_v, nblk, (float*)h->Dc, h->st));
+    CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
+    CK(premultiply_odd<float>(h->g, (float*)h->Dc, (float*)h->Ainv, h->p.n_v, (float*)h->AD, h->st));
+  } else {
+    CK(coarse_import<double>(src, h->p.n_v, nblk, (double*)h->Dc, h->st));
+    CK(invert_self_blocks<double>(h->g, (double*)h->Dc, h->p.n_v, (double*)h->Ainv, h->d_status, h->st));
+    CK(premultiply_odd<double>(h->g, (double*)h->Dc, (double*)h->Ainv, h->p.n_v, (double*)h->AD, h->st));
+  }
+  int sing = 0;
+  CK(cudaMemcpyAsync(&sing, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (tmpd) {
+    cudaFree(tmpd);
+    h->allocs.pop_back();
+    h->bytes -= 2 * nc * sizeof(double);
+  }
+  if (sing) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
+    h->have_coarse = false;
+    return fail(h, DDAMG_ENUMERIC, "a coarse self block is singular");
+  }
+  h->have_coarse = true;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan* out) {
+  if (!h || !out || nrhs < 1) return DDAMG_EINVAL;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const CoarsePlan c = h->p.precision == DDAMG_FP64
+                           ? coarse_gmres_plan<double>(h->g, h->p.n_v, h->p.coarse_restart, nrhs)
+                           : coarse_gmres_plan<float>(h->g, h->p.n_v, h->p.coarse_restart, nrhs);
+  if (c.NR == 0) return fail(h, DDAMG_EINVAL, "no launch configuration for the coarse solve");
+  out->rhs_per_pass = c.NR;
+  out->ctas = c.G;
+  out->sites_per_cta = c.per;
+  out->krylov_in_shared = c.local_in_smem;
+  out->resident_blocks = c.resident;
+  out->shared_bytes = c.smem_bytes;
+  out->scratch_bytes = c.work_bytes;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_set_wait_limit(ddamg_handle h, int64_t polls) {
+  if (!h) return DDAMG_EINVAL;
+  if (polls < 0) {
+    h->wait_sap = WAIT_SAP_DEFAULT;
+    h->wait_grid = WAIT_GRID_DEFAULT;
+  } else {
+    h->wait_sap = polls;
+    h->wait_grid = polls;
+  }
   return DDAMG_OK;
 }
 
@@ -1889,7 +1970,7 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   if (!h || !out) return DDAMG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
   collect_pending(h);
-  out->kernel_launches = g_launches - h->launches0;
+  out->kernel_launches = g_launches.total() - h->launches0;
   out->dslash_launches = h->n_cls[0];
   out->sap_launches = h->n_cls[1];
   out->coarse_launches = h->n_cls[2];
@@ -1900,6 +1981,10 @@ ddamg_status ddamg_get_stats(ddamg_handle h, ddamg_stats* out) {
   out->coarse_apply_launches = h->n_cls[3];
   out->coarse_apply_ms = h->ms_cls[3];
   out->reorth_passes = h->reorth;
+  out->restrict_launches = h->n_cls[4];
+  out->restrict_ms = h->ms_cls[4];
+  out->prolong_launches = h->n_cls[5];
+  out->prolong_ms = h->ms_cls[5];
   out->setup_flops = h->flops[0];
   out->solve_flops = h->flops[1];
   return DDAMG_OK;
@@ -1920,7 +2005,7 @@ ddamg_status ddamg_reset_stats(ddamg_handle h) {
   if (!h) return DDAMG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
   collect_pending(h);
-  h->launches0 = g_launches;
+  h->launches0 = g_launches.total();
   h->reorth = 0;
   h->flops[0] = h->flops[1] = 0.0;
   for (int c = 0; c < NCLS; ++c) {

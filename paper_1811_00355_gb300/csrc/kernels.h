@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstddef>
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,8 +29,35 @@ struct Geom {
   const int* cpos;          // [nb] position of a coarse site in its parity list
 };
 
-// kernel launch counter (incremented by each launcher)
-extern uint64_t g_launches;
+// Kernel launch counter: every launcher adds its launches to the process
+// total (atomic, any host thread) and to a per-thread count, which lets a
+// thread that captures a CUDA graph tell its own captured launches apart.
+struct LaunchCount {
+  std::atomic<uint64_t> all{0};
+  static uint64_t& mine() {
+    static thread_local uint64_t m = 0;
+    return m;
+  }
+  void add(uint64_t n) {
+    all.fetch_add(n, std::memory_order_relaxed);
+    mine() += n;
+  }
+  // launches that were recorded into a graph, not run
+  void remove_mine(uint64_t n) {
+    all.fetch_sub(n, std::memory_order_relaxed);
+    mine() -= n;
+  }
+  LaunchCount& operator++() {
+    add(1);
+    return *this;
+  }
+  LaunchCount& operator+=(uint64_t n) {
+    add(n);
+    return *this;
+  }
+  uint64_t total() const { return all.load(std::memory_order_relaxed); }
+};
+extern LaunchCount g_launches;
 
 // ---- layout conversion ------------------------------------------------------
 // host layout (FP64 lexicographic, interleaved complex) <-> device fields
@@ -120,11 +148,12 @@ cudaError_t index_maps(const Geom& g, int* parity, int* block, int* colour, cuda
 // one colour of a Schwarz sweep on all blocks of that colour:
 //   r = b - D x (or r = b if x_is_zero), e = MR-even-odd block solve of r,
 //   x += e (x is overwritten with e if x_is_zero)
-// *status receives DDAMG_ETIMEOUT (6) if a bounded wait for staged data gives up
+// *status receives DDAMG_ETIMEOUT (6) if a bounded wait for staged data gives
+// up after wait_limit polls (the CTA then leaves x untouched)
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b,
                       R* x, const R* gauge, const R* clover, const R* clover_inv, int nrhs,
-                      int* status, cudaStream_t st);
+                      int* status, long long wait_limit, cudaStream_t st);
 size_t sap_smem_bytes(const Geom& g, int real_size);
 
 // ---- coarse grid ----------------------------------------------------------------
@@ -160,6 +189,9 @@ cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* 
 // even-odd Schur complement becomes one block product per site
 template <class R>
 cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R* AD, cudaStream_t st);
+// nblocks row-major complex doubles (host layout, device memory) -> column-major blocks
+template <class R>
+cudaError_t coarse_import(const double* src, int n, size_t nblocks, R* Dc, cudaStream_t st);
 // nblocks column-major blocks -> row-major complex doubles (host layout)
 template <class R>
 cudaError_t coarse_export(const R* Dc, int n, size_t nblocks, double* out, cudaStream_t st);
@@ -185,14 +217,29 @@ struct CoarseSolveArgs {
   double tol;
   int restart;      // <= 64
   int max_iter;
+  long long wait_limit;   // polls of a grid-barrier wait before it gives up (DDAMG_ETIMEOUT)
 };
+// launch configuration of the coarse GMRES for nrhs right-hand sides (all
+// zero if none exists): NR right-hand sides in lockstep per launch pass, G
+// CTAs owning `per` even and `per` odd coarse sites each, the Krylov slices
+// in shared memory (local_in_smem) or in global scratch, the even site's D_c
+// blocks resident in shared memory; dynamic shared memory per CTA and the
+// bytes of `work` the launch touches
+struct CoarsePlan {
+  int NR, G, per, local_in_smem, resident;
+  size_t smem_bytes, work_bytes;
+};
+template <class R>
+CoarsePlan coarse_gmres_plan(const Geom& g, int n, int restart, int nrhs);
 size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size);
 // bytes of `work` that coarse_gmres() touches for nrhs right-hand sides (0 if
 // no launch configuration exists)
 template <class R>
 size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs);
+// (sized: the plan the caller sized `work` for; the launch refuses any other)
 template <class R>
 cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& a, const R* b, R* x, int nrhs,
-                         void* work, int* iters, int* iters_acc, int* status, cudaStream_t st);
+                         void* work, int* iters, int* iters_acc, int* status, cudaStream_t st,
+                         const CoarsePlan* sized = nullptr);
 
 }  // namespace ddamg

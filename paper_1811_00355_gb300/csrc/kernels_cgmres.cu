@@ -20,6 +20,7 @@
 // deterministic (fixed trees).  Every barrier wait is bounded; on time-out
 // the kernel records DDAMG_ETIMEOUT (6) and returns.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -35,7 +36,6 @@ __host__ __device__ constexpr int mvp_groups(int NR) { return NR >= 8 ? 9 : 18; 
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
 constexpr int NRMAX = 12;
-constexpr long long SPIN_LIMIT = 1ll << 21;   // polls of about an L2 round trip each
 
 __device__ __forceinline__ cpx<float> ldc(const cpx<float>* p) {
   float2 t = __ldcg(reinterpret_cast<const float2*>(p));
@@ -86,14 +86,14 @@ __device__ void grid_arrive(unsigned* bar) {
   }
 }
 
-__device__ bool grid_wait(unsigned* bar, int* status) {
+__device__ bool grid_wait(unsigned* bar, int* status, long long limit) {
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
     const unsigned target = bar_epoch * gridDim.x;
     int ok = 1;
     long long spins = 0;
     while ((int)(ld_acquire_gpu(bar) - target) < 0) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > limit) {
         atomicExch(status, 6);
         ok = 0;
         break;
@@ -105,9 +105,9 @@ __device__ bool grid_wait(unsigned* bar, int* status) {
   return ok_s != 0;
 }
 
-__device__ bool grid_barrier(unsigned* bar, int* status) {
+__device__ bool grid_barrier(unsigned* bar, int* status, long long limit) {
   grid_arrive(bar);
-  return grid_wait(bar, status);
+  return grid_wait(bar, status, limit);
 }
 
 // shared-memory plan, identical on host and device
@@ -196,6 +196,7 @@ struct CGA {
   int* iters;
   int* iters_acc;
   int* status;
+  long long spin_limit;   // polls of a barrier wait before it gives up
 };
 
 // Multi-right-hand-side block product on one coarse site, whole CTA:
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       __syncthreads();
       mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, a.to + (size_t)ko * n2, (int)vstr);
     }
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
     // rhs_e = b_e - D_eo to ; x_e = 0 ; w = rhs_e
     phase_even(nullptr, false, rl, bb);
     for (int idx = tx; idx < NR * L; idx += TPB) {
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
     }
     __syncthreads();
     partial(1, true);
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
     gather(1, true, bnorm, 1);
     if (tx < NR) {
       bnorm[tx] = sqrt(bnorm[tx]);
@@ -533,11 +534,11 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         Vk(0, r)[e] = (R)scl[r] * v;
         if (e < Lo) a.wg[r * vstr + (size_t)lo * n2 + e] = v;
       }
-      if (!grid_barrier(a.bar, a.status)) return;
+      if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       for (int k = 0; k < m; ++k) {
         // w = S V_k: odd phase from the neighbours' unnormalised w (scale 1/h)
         phase_odd(a.wg);
-        if (!grid_barrier(a.bar, a.status)) return;
+        if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
         phase_even(V + (size_t)k * NR * L, true, wl, nullptr);
         // Givens rotation of right-hand side r's new Hessenberg column (one
         // thread), new residual estimate, scale 1/h of V_{k+1}, convergence
@@ -592,7 +593,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           // explicit norm is taken only if that difference has cancelled
           partial(k + 1, false);
           partial_norm_slot(k + 1);
-          if (!grid_barrier(a.bar, a.status)) return;
+          if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
           gather_dots_norm(k + 1, hc, 2 * (m + 1), hnv);
           if (tx < NR) {
             const A* hr = hc + (size_t)tx * 2 * (m + 1);
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           __syncthreads();
           if (any_s) {
             partial(1, true);
-            if (!grid_barrier(a.bar, a.status)) return;
+            if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
             gather(1, true, h2, 1);
             if (tx < NR && exn[tx]) hnv[tx] = h2[tx];
             __syncthreads();
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
             any_act_s = any;
           }
           if (!any_s) {
-            if (!grid_wait(a.bar, a.status)) return;
+            if (!grid_wait(a.bar, a.status, a.spin_limit)) return;
           } else {
             __syncthreads();
           }
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           // FP64: classical Gram-Schmidt with one re-orthogonalisation pass
           for (int pass = 0; pass < 2; ++pass) {
             partial(k + 1, false);
-            if (!grid_barrier(a.bar, a.status)) return;
+            if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
             A* hh = pass == 0 ? hc : h2;
             gather(k + 1, false, hh, 2 * (m + 1));
             for (int idx = tx; idx < NR * Lo; idx += TPB) {
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           }
           // ||w||: this barrier also publishes the neighbours' w for the next odd phase
           partial(1, true);
-          if (!grid_barrier(a.bar, a.status)) return;
+          if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
           gather(1, true, hnv, 1);
           if (tx < NR && act[tx]) givens(tx);
           __syncthreads();
@@ -729,10 +730,10 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         a.xg[r * vstr + (size_t)lo * n2 + e] = s;
       }
       if (tx < NR) scl[tx] = A(1);
-      if (!grid_barrier(a.bar, a.status)) return;
+      if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       // true residual w = rhs_e - S x_e
       phase_odd(a.xg);
-      if (!grid_barrier(a.bar, a.status)) return;
+      if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       phase_even(xl, true, wl, nullptr);
       for (int idx = tx; idx < NR * Lo; idx += TPB) {
         const int r = idx / Lo, e = idx - r * Lo;
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       if (tx < NR) act[tx] = conv[tx] ? 0 : 1;
       __syncthreads();
       partial(1, true);
-      if (!grid_barrier(a.bar, a.status)) return;
+      if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       gather(1, true, beta, 1);
       if (tx < NR && !conv[tx]) {
         beta[tx] = sqrt(beta[tx]);
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       a.xg[r * vstr + (size_t)lo * n2 + e] = xl[(size_t)r * L + e];
     }
     if (tx < NR) scl[tx] = -A(1);
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
       stage_odd(X, a.xg);
@@ -780,7 +781,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       if (a.iters) a.iters[r0 + tx] = tot[tx];
       if (a.iters_acc) atomicAdd(a.iters_acc, tot[tx]);
     }
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
   }
 }
 
@@ -805,12 +806,23 @@ struct Choice {
   bool resident;
 };
 
-// current dynamic shared-memory limit of each kernel instance, so that the
-// attribute is set only when it changes
+// Host state of the launch configurations: the dynamic shared-memory limit
+// last set on each kernel instance per device (cudaFuncSetAttribute acts on
+// the current device) and the cache of chosen configurations.  Several host
+// threads may solve on different handles at once, so both are guarded by one
+// mutex.
+std::mutex g_cfg_mu;
+
+constexpr int MAXDEV = 64;
+
+inline int nr_slot(int NR) { return NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4; }
+
+// caller holds g_cfg_mu
 template <class R>
-cudaError_t smem_attr(int NR, size_t bytes) {
-  static size_t current[5] = {0, 0, 0, 0, 0};
-  size_t& c = current[NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4];
+cudaError_t smem_attr_locked(int dev, int NR, size_t bytes) {
+  static size_t current[MAXDEV][5] = {};
+  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  size_t& c = current[dev][nr_slot(NR)];
   if (c == bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel_for<R>(NR), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) c = bytes;
@@ -821,7 +833,7 @@ cudaError_t smem_attr(int NR, size_t bytes) {
 inline int first_nr(int nrhs) { return nrhs >= 12 ? 12 : nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1; }
 
 template <class R>
-Choice choose_uncached(const Geom& g, int n2, int m, int nrhs);
+Choice choose_uncached(int dev, const Geom& g, int n2, int m, int nrhs);
 
 // launch configurations are cached: the occupancy queries behind them cost
 // far more host time than a coarse solve's launch
@@ -836,20 +848,20 @@ Choice choose(const Geom& g, int n2, int m, int nrhs) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int first = first_nr(nrhs);
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
   for (int i = 0; i < used; ++i) {
     const Entry& e = cache[i];
     if (e.dev == dev && e.nb == g.nb && e.n2 == n2 && e.m == m && e.first == first) return e.c;
   }
-  Choice c = choose_uncached<R>(g, n2, m, nrhs);
+  Choice c = choose_uncached<R>(dev, g, n2, m, nrhs);
   Entry e{dev, g.nb, n2, m, first, c};
   cache[used < 16 ? used++ : (dev + g.nb + first) % 16] = e;
   return c;
 }
 
 template <class R>
-Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
+Choice choose_uncached(int dev, const Geom& g, int n2, int m, int nrhs) {
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int NE = g.nb / 2;
   Choice best{};
@@ -864,7 +876,7 @@ Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
         if (per == 1 && local) {
           // one even site per CTA, its D_c blocks resident in shared memory
           Plan pr = make_plan(NR, n2, n2, m, sizeof(R), true, true);
-          if (pr.bytes <= SMEM_RESIDENT_MAX && smem_attr<R>(NR, pr.bytes) == cudaSuccess &&
+          if (pr.bytes <= SMEM_RESIDENT_MAX && smem_attr_locked<R>(dev, NR, pr.bytes) == cudaSuccess &&
               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, pr.bytes) == cudaSuccess &&
               occ >= 1 && G <= occ * sms)
             return Choice{NR, G, per, true, pr, true};
@@ -872,7 +884,7 @@ Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
         }
         Plan p = make_plan(NR, per * n2, n2, m, sizeof(R), local);
         if (p.bytes > SMEM_BUDGET) break;
-        if (smem_attr<R>(NR, p.bytes) != cudaSuccess) break;
+        if (smem_attr_locked<R>(dev, NR, p.bytes) != cudaSuccess) break;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, p.bytes);
         if (occ < 1) break;
         if (G <= occ * sms) return Choice{NR, G, per, local, p, false};
@@ -885,16 +897,32 @@ Choice choose_uncached(const Geom& g, int n2, int m, int nrhs) {
 }  // namespace
 
 template <class R>
-size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs) {
-  // the same layout as coarse_gmres() below, for the plan it would choose
+CoarsePlan coarse_gmres_plan(const Geom& g, int n, int restart, int nrhs) {
+  CoarsePlan out{};
+  if (restart > MAXM || restart < 1 || nrhs < 1) return out;
   Choice ch = choose<R>(g, 2 * n, restart, nrhs);
-  if (ch.NR == 0) return 0;
+  if (ch.NR == 0) return out;
+  out.NR = ch.NR;
+  out.G = ch.G;
+  out.per = ch.per;
+  out.local_in_smem = ch.local ? 1 : 0;
+  out.resident = ch.resident ? 1 : 0;
+  out.smem_bytes = ch.plan.bytes;
+  // the layout of coarse_gmres() below
   const size_t NE = g.nb / 2, n2 = 2 * n;
   size_t bytes = al16(3 * (size_t)NRMAX * NE * n2 * sizeof(cpx<R>));
   bytes += al16((size_t)(MAXM + 2) * NRMAX * NE * 2 * sizeof(double));
   bytes += 256;
   if (!ch.local) bytes += (size_t)ch.G * al16(ch.plan.local_bytes);
-  return bytes;
+  out.work_bytes = bytes;
+  return out;
+}
+template CoarsePlan coarse_gmres_plan<float>(const Geom&, int, int, int);
+template CoarsePlan coarse_gmres_plan<double>(const Geom&, int, int, int);
+
+template <class R>
+size_t coarse_gmres_exact_bytes(const Geom& g, int n, int restart, int nrhs) {
+  return coarse_gmres_plan<R>(g, n, restart, nrhs).work_bytes;
 }
 template size_t coarse_gmres_exact_bytes<float>(const Geom&, int, int, int);
 template size_t coarse_gmres_exact_bytes<double>(const Geom&, int, int, int);
@@ -913,11 +941,15 @@ size_t coarse_gmres_work_bytes(const Geom& g, int n, int restart, int real_size)
 
 template <class R>
 cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R* x, int nrhs, void* work,
-                         int* iters, int* iters_acc, int* status, cudaStream_t st) {
+                         int* iters, int* iters_acc, int* status, cudaStream_t st, const CoarsePlan* sized) {
   if (ca.restart > MAXM || ca.restart < 1 || nrhs < 1) return cudaErrorInvalidValue;
   const int n2 = 2 * ca.n;
   Choice ch = choose<R>(g, n2, ca.restart, nrhs);
   if (ch.NR == 0) return cudaErrorInvalidConfiguration;
+  // a caller that sized `work` for a plan must get exactly that plan
+  if (sized && (sized->NR != ch.NR || sized->G != ch.G || sized->per != ch.per ||
+                sized->local_in_smem != (ch.local ? 1 : 0) || sized->resident != (ch.resident ? 1 : 0)))
+    return cudaErrorInvalidValue;
   CGA<R> a;
   a.g = g;
   a.Dc = reinterpret_cast<const cpx<R>*>(ca.Dc);
@@ -951,10 +983,16 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.iters = iters;
   a.iters_acc = iters_acc;
   a.status = status;
+  a.spin_limit = ca.wait_limit;
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const void* fn = kernel_for<R>(ch.NR);
-  e = smem_attr<R>(ch.NR, ch.plan.bytes);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_cfg_mu);
+    e = smem_attr_locked<R>(dev, ch.NR, ch.plan.bytes);
+  }
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   cudaLaunchConfig_t cfg = {};
@@ -973,8 +1011,8 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
 }
 
 template cudaError_t coarse_gmres<float>(const Geom&, const CoarseSolveArgs&, const float*, float*, int, void*,
-                                         int*, int*, int*, cudaStream_t);
+                                         int*, int*, int*, cudaStream_t, const CoarsePlan*);
 template cudaError_t coarse_gmres<double>(const Geom&, const CoarseSolveArgs&, const double*, double*, int,
-                                          void*, int*, int*, int*, cudaStream_t);
+                                          void*, int*, int*, int*, cudaStream_t, const CoarsePlan*);
 
 }  // namespace ddamg

@@ -619,6 +619,20 @@ __global__ void k_coarse_export(const cpx<R>* __restrict__ src, double* __restri
   }
 }
 
+// row-major complex doubles (host layout) -> column-major blocks in R
+template <class R>
+__global__ void k_coarse_import(const double* __restrict__ src, cpx<R>* __restrict__ dst, int n2, size_t nblocks) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = nblocks * n2 * n2;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < total; i += stride) {
+    size_t blk = i / ((size_t)n2 * n2);
+    int e = (int)(i - blk * n2 * n2);
+    int r = e / n2, c = e - r * n2;
+    dst[blk * n2 * n2 + (size_t)c * n2 + r] = mk((R)src[2 * i], (R)src[2 * i + 1]);
+  }
+}
+
 template <class RD, class RS>
 __global__ void k_conv_c(const RS* __restrict__ s, RD* __restrict__ d, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -778,6 +792,14 @@ cudaError_t coarse_export(const R* Dc, int n, size_t nblocks, double* out, cudaS
   ++g_launches;
   return cudaGetLastError();
 }
+template <class R>
+cudaError_t coarse_import(const double* src, int n, size_t nblocks, R* Dc, cudaStream_t st) {
+  k_coarse_import<R><<<4096, 256, 0, st>>>(src, reinterpret_cast<cpx<R>*>(Dc), 2 * n, nblocks);
+  ++g_launches;
+  return cudaGetLastError();
+}
+template cudaError_t coarse_import<float>(const double*, int, size_t, float*, cudaStream_t);
+template cudaError_t coarse_import<double>(const double*, int, size_t, double*, cudaStream_t);
 template cudaError_t coarse_export<float>(const float*, int, size_t, double*, cudaStream_t);
 template cudaError_t coarse_export<double>(const double*, int, size_t, double*, cudaStream_t);
 

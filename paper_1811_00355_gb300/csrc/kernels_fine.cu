@@ -9,7 +9,7 @@
 
 namespace ddamg {
 
-uint64_t g_launches = 0;
+LaunchCount g_launches;
 
 namespace {
 

@@ -519,7 +519,8 @@ __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontr
 __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
                                                  const float* __restrict__ b, float* __restrict__ x,
                                                  const float* __restrict__ gauge, const float* __restrict__ clov,
-                                                 const float* __restrict__ clov_inv, int* status) {
+                                                 const float* __restrict__ clov_inv, int* status,
+                                                 long long wait_limit) {
   using LYG = Layout<float, GAUGE_NR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   // the staged block must have landed (bounded wait; on time-out record
   // DDAMG_ETIMEOUT, wait again for the copies in flight, and leave x alone)
   {
-    const bool ok = mbar_wait_bounded(&mbar, 0, MBAR_POLL_LIMIT);
+    const bool ok = mbar_wait_bounded(&mbar, 0, wait_limit);
     if (__syncthreads_or(!ok)) {
       if (t == 0) atomicExch(status, 6);
       mbar_wait_bounded(&mbar, 0, MBAR_POLL_LIMIT);
@@ -724,7 +725,7 @@ static bool sap_stg_ok(const Geom& g) {
 
 static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const float* b, float* x,
                               const float* gauge, const float* clover, const float* clover_inv, int nrhs,
-                              int* status, cudaStream_t st) {
+                              int* status, long long wait_limit, cudaStream_t st) {
   static size_t cfg = 0;
   const size_t need = sap_stg_smem(g);
   if (cfg < need) {
@@ -744,7 +745,7 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
   lc.numAttrs = 1;
   const int zero = x_is_zero ? 1 : 0;
   cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg, g, colour, mr_iters, zero, b, x, gauge, clover,
-                                     clover_inv, status);
+                                     clover_inv, status, wait_limit);
   ++g_launches;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -752,10 +753,11 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
-                      cudaStream_t st) {
+                      long long wait_limit, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (sap_stg_ok(g)) {
-      return launch_stg(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, st);
+      return launch_stg(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, wait_limit,
+                        st);
     }
   }
   int threads = sap_threads(g);
@@ -775,8 +777,9 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
 }
 
 template cudaError_t sap_sweep<float>(const Geom&, int, int, bool, const float*, float*, const float*,
-                                      const float*, const float*, int, int*, cudaStream_t);
+                                      const float*, const float*, int, int*, long long, cudaStream_t);
 template cudaError_t sap_sweep<double>(const Geom&, int, int, bool, const double*, double*,
-                                       const double*, const double*, const double*, int, int*, cudaStream_t);
+                                       const double*, const double*, const double*, int, int*, long long,
+                                       cudaStream_t);
 
 }  // namespace ddamg

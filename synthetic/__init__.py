@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "volume", "rng", "gauge_field", "gauge_field_sliced", "random_su3", "gaussian_spinors",
-    "point_sources", "Philox4x32",
+    "point_sources", "coarse_stencil", "Philox4x32",
 ]
 
 
@@ -128,6 +128,21 @@ def point_sources(L, site: int = 0) -> np.ndarray:
     for k in range(12):
         b[k, site, k // 3, k % 3] = 1.0
     return b
+
+
+def coarse_stencil(NX: int, n2: int, seed: int, diag: float = 4.0, hop: float = 0.15) -> np.ndarray:
+    """A 9-point coarse stencil with ``n2 x n2`` complex blocks, complex128
+    ``[NX][9][n2][n2]`` (block 0 the self block, 1 + 2 mu / 2 + 2 mu the
+    links to X + mu / X - mu): self blocks ``diag * 1`` plus Gaussian entries
+    of standard deviation ``hop / sqrt(n2)``, link blocks Gaussian with that
+    deviation.  The shape and the diagonal dominance of the coarse operator of
+    a massive Wilson-clover D, for exercising coarse solvers on large coarse
+    lattices without assembling one."""
+    g = rng(seed)
+    sd = hop / np.sqrt(n2)
+    B = sd * (g.standard_normal((NX, 9, n2, n2)) + 1j * g.standard_normal((NX, 9, n2, n2)))
+    B[:, 0] += diag * np.eye(n2)
+    return np.ascontiguousarray(B)
 
 
 class Philox4x32:

@@ -28,6 +28,23 @@ def rel(a, b) -> float:
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def maxrel(a, b) -> float:
+    """Largest element-wise deviation over the largest reference element.
+    An error confined to a few sites (one block face, one aggregate, the
+    hops across the time boundary) is not diluted by the size of the field
+    here, as it is in the norm-wise rel()."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def assert_close(a, b, tol, what=""):
+    """Norm-wise and element-wise relative errors both below tol."""
+    r, m = rel(a, b), maxrel(a, b)
+    assert r < tol and m < tol, f"{what} norm-wise {r:.3e}, element-wise {m:.3e}, bound {tol:.1e}"
+    return r, m
+
+
 def t(a) -> torch.Tensor:
     return torch.from_numpy(np.ascontiguousarray(a))
 

@@ -15,7 +15,7 @@ from oracle.coarse import (Aggregation, CoarseOperator, coarse_operator,
 from oracle.dirac import WilsonClover
 from oracle.lattice import index_maps
 from oracle.solver import Params, TwoLevelMG
-from tests.gpu_common import (FULL, MID, SMALL, TOL32, TOL64, make, oracle_op, rel,
+from tests.gpu_common import (FULL, MID, SMALL, TOL32, TOL64, assert_close, make, oracle_op, rel,
                               smoother, t)
 
 pytestmark = pytest.mark.gpu
@@ -47,8 +47,8 @@ def test_clover_packed_blocks(cfg):
     L, b, eps, m0, csw, n_v, seed = cfg
     s = make(cfg, _P().FP64)
     op = oracle_op(L, eps, seed, m0, csw)
-    assert rel(s.get_clover(False), op.packed_clover(False).numpy()) < TOL64
-    assert rel(s.get_clover(True), op.packed_clover(True).numpy()) < TOL64
+    assert_close(s.get_clover(False), op.packed_clover(False).numpy(), TOL64)
+    assert_close(s.get_clover(True), op.packed_clover(True).numpy(), TOL64)
 
 
 @pytest.mark.parametrize("cfg", [SMALL, MID, FULL])
@@ -62,7 +62,7 @@ def test_wilson_clover_D(cfg, prec):
     ref = op.apply(t(x)).numpy()
     tol = TOL64 if prec == 0 else TOL32
     for k in range(2):
-        assert rel(y[k], ref[k]) < tol
+        assert_close(y[k], ref[k], tol)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -72,8 +72,8 @@ def test_clover_and_inverse_apply(prec):
     op = oracle_op(L, eps, seed, m0, csw)
     x = syn.gaussian_spinors(1, L, 41)
     tol = TOL64 if prec == 0 else TOL32
-    assert rel(s.apply_clover(x, False, prec), op.site(t(x)).numpy()) < tol
-    assert rel(s.apply_clover(x, True, prec), op.site(t(x), inverse=True).numpy()) < tol
+    assert_close(s.apply_clover(x, False, prec), op.site(t(x)).numpy(), tol)
+    assert_close(s.apply_clover(x, True, prec), op.site(t(x), inverse=True).numpy(), tol)
 
 
 @pytest.mark.parametrize("cfg", [SMALL, MID])
@@ -87,7 +87,7 @@ def test_block_solve(cfg, prec):
         got = s.block_solve(r, c, prec)
         ref = sm.block_solve(t(r[0]), c, 4).numpy()
         tol = 1e-12 if prec == 0 else 5 * TOL32
-        assert rel(got[0], ref) < tol
+        assert_close(got[0], ref, tol)
         # zero on the blocks of the other colour
         other = sm.mask[1 - c, None].numpy().real.astype(bool)[:, 0, 0]
         assert np.abs(got[0][other]).max() == 0.0
@@ -103,7 +103,7 @@ def test_sap(cfg, prec):
     got = s.sap(r, prec)
     ref = sm.apply(t(r[0]), 4, 4).numpy()
     tol = 1e-12 if prec == 0 else 2e-5
-    assert rel(got[0], ref) < tol
+    assert_close(got[0], ref, tol)
 
 
 @pytest.mark.parametrize("cfg", [SMALL, MID])
@@ -115,7 +115,7 @@ def test_orthonormalise(cfg):
     s.orthonormalize()
     op = oracle_op(L, eps, seed, m0, csw)
     ref = orthonormalise(t(lam), Aggregation(op.geom, b)).numpy()
-    assert rel(s.get_test_vectors(), ref) < 1e-13
+    assert_close(s.get_test_vectors(), ref, 1e-13)
 
 
 @pytest.mark.parametrize("cfg", [SMALL, MID])
@@ -131,10 +131,10 @@ def test_restrict_prolong(cfg, prec):
     tol = TOL64 if prec == 0 else TOL32
     bc = s.restrict(x, prec)
     ref = restrict(lam, agg, t(x)).numpy()
-    assert rel(bc, ref) < tol
+    assert_close(bc, ref, tol)
     y = np.ascontiguousarray(ref)
     got = s.prolong(y, prec)
-    assert rel(got, prolong(lam, agg, t(y)).numpy()) < tol
+    assert_close(got, prolong(lam, agg, t(y)).numpy(), tol)
 
 
 @pytest.fixture(scope="module")
@@ -160,7 +160,7 @@ def test_coarse_operator(coarse_pair, prec):
     handles, lam, agg, cop = coarse_pair
     got = handles[prec].get_coarse_op()
     tol = 1e-12 if prec == 0 else TOL32
-    assert rel(got, cop.Dc.numpy()) < tol
+    assert_close(got, cop.Dc.numpy(), tol)
     for X in (0, 5, agg.NX - 1):
         assert rel(got[X], cop.Dc[X].numpy()) < 10 * tol
 
@@ -172,7 +172,7 @@ def test_coarse_stencil(coarse_pair, prec):
     x = rng.standard_normal((2, agg.NX, 2 * lam.shape[0])) + 1j * rng.standard_normal((2, agg.NX, 2 * lam.shape[0]))
     got = handles[prec].apply_coarse(x, prec)
     ref = cop.apply(t(x)).numpy()
-    assert rel(got, ref) < (TOL64 if prec == 0 else TOL32)
+    assert_close(got, ref, (TOL64 if prec == 0 else TOL32))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -186,14 +186,14 @@ def test_coarse_even_odd_gmres(coarse_pair, prec):
         xr, ir = cop.solve(t(b[k]), 5e-2, 30, 300)
         assert abs(int(its[k]) - ir) <= (0 if prec == 0 else 1)
         if prec == 0:
-            assert rel(x[k], xr.numpy()) < 1e-11
+            assert_close(x[k], xr.numpy(), 1e-11)
     # tight tolerance: the dense solve
     tol = 1e-12 if prec == 0 else 1e-5
     x, its = handles[prec].coarse_solve(b, tol, prec)
     Dd = cop.dense().numpy()
     for k in range(2):
         xd = np.linalg.solve(Dd, b[k].reshape(-1)).reshape(b[k].shape)
-        assert rel(x[k], xd) < (1e-10 if prec == 0 else 1e-4)
+        assert_close(x[k], xd, (1e-10 if prec == 0 else 1e-4))
 
 
 def test_preconditioner_M_fp64():
@@ -208,7 +208,7 @@ def test_preconditioner_M_fp64():
     r = syn.gaussian_spinors(1, L, 51)
     got = s.apply_M(r, 0)
     ref = mg.apply_M(t(r[0])).numpy()
-    assert rel(got[0], ref) < 1e-11
+    assert_close(got[0], ref, 1e-11)
 
 
 def test_setup_fp64_matches_oracle():
@@ -220,8 +220,8 @@ def test_setup_fp64_matches_oracle():
     s.run_setup(lam0)
     mg = TwoLevelMG(t(syn.gauge_field(L, eps, seed)), Params(L, b, b, n_v, m0, csw, setup_iters=3))
     mg.setup(t(lam0))
-    assert rel(s.get_test_vectors(), mg.lam.numpy()) < 1e-9
-    assert rel(s.get_coarse_op(), mg.cop.Dc.numpy()) < 1e-9
+    assert_close(s.get_test_vectors(), mg.lam.numpy(), 1e-9)
+    assert_close(s.get_coarse_op(), mg.cop.Dc.numpy(), 1e-9)
 
 
 def test_solve_small_fp64_matches_dense():
@@ -290,7 +290,7 @@ def test_solve_batched_matches_one_at_a_time(prec, refine):
         res = rel(op.apply(t(xb[k])).numpy(), rhs[k])
         assert res <= 1e-10 and ib[k]["converged"] == 1, (k, res, ib[k])
         assert abs(ib[k]["outer_iters"] - is_[k]["outer_iters"]) <= 3, (ib[k], is_[k])
-        assert rel(xb[k], xs[k]) < 1e-6
+        assert_close(xb[k], xs[k], 1e-6)
     s.close()
 
 
@@ -306,12 +306,12 @@ def test_update_mass_keeps_vectors_and_rebuilds_operators():
     s.update_mass(m1, c1)
     op1 = oracle_op(L, eps, seed, m1, c1)
     x = syn.gaussian_spinors(1, L, 60)
-    assert rel(s.apply_D(x)[0], op1.apply(t(x[0])).numpy()) < TOL64
+    assert_close(s.apply_D(x)[0], op1.apply(t(x[0])).numpy(), TOL64)
     lam = s.get_test_vectors()
     assert np.array_equal(lam, lam_before)
     agg = Aggregation(op1.geom, b)
     Dc = coarse_operator(op1, t(lam), agg)
-    assert rel(s.get_coarse_op(), Dc.numpy()) < 1e-12
+    assert_close(s.get_coarse_op(), Dc.numpy(), 1e-12)
     xs, info = s.solve(x, 1e-10)
     assert rel(op1.apply(t(xs[0])).numpy(), x[0]) <= 1e-10
     s.close()
@@ -363,7 +363,7 @@ def test_set_gauge_replaces_links_and_needs_a_new_setup():
     s.set_gauge(U2)
     op2 = WilsonClover(t(U2), L, m0, csw)
     x = syn.gaussian_spinors(1, L, 61)
-    assert rel(s.apply_D(x, P.FP64)[0], op2.apply(t(x[0])).numpy()) < TOL64
+    assert_close(s.apply_D(x, P.FP64)[0], op2.apply(t(x[0])).numpy(), TOL64)
     with pytest.raises(P.DDAMGError) as e:
         s.solve(x, 1e-10)
     assert e.value.status == 7
@@ -391,11 +391,11 @@ def test_half_vectors_restrict_prolong_and_coarse_operator():
     x = syn.gaussian_spinors(2, L, 63)
     got = s.restrict(x, 1)
     ref = restrict(lam, agg, t(x)).numpy()
-    assert rel(got, ref) < 2e-2
+    assert_close(got, ref, 2e-2)
     xc = np.ascontiguousarray(ref)
     got = s.prolong(xc, 1)
-    assert rel(got, prolong(lam, agg, t(xc)).numpy()) < 2e-2
-    assert rel(s.get_coarse_op(), coarse_operator(op, lam, agg).numpy()) < 2e-2
+    assert_close(got, prolong(lam, agg, t(xc)).numpy(), 2e-2)
+    assert_close(s.get_coarse_op(), coarse_operator(op, lam, agg).numpy(), 2e-2)
     s.close()
 
 
@@ -427,12 +427,12 @@ def test_odd_number_of_test_vectors(prec):
     s.build_coarse()
     Dc = coarse_operator(op, lam, agg)
     tol = 1e-12 if prec == 0 else TOL32
-    assert rel(s.get_coarse_op(), Dc.numpy()) < tol
+    assert_close(s.get_coarse_op(), Dc.numpy(), tol)
     rng = np.random.default_rng(66)
     x = rng.standard_normal((1, agg.NX, 2 * n_v)) + 1j * rng.standard_normal((1, agg.NX, 2 * n_v))
     got = s.apply_coarse(x, prec)
     ref = CoarseOperator(Dc, agg.coarse).apply(t(x)).numpy()
-    assert rel(got, ref) < (TOL64 if prec == 0 else TOL32)
+    assert_close(got, ref, (TOL64 if prec == 0 else TOL32))
     s.run_setup()
     rhs = syn.gaussian_spinors(1, L, 67)
     xs, info = s.solve(rhs, 1e-10)
@@ -488,7 +488,7 @@ def test_solve_batched_edge_cases():
     assert np.all(x[1] == 0) and info[1]["converged"] == 1
     x1, _ = s.solve_batched(np.ascontiguousarray(rhs[:1]), 1e-10)
     xs, _ = s.solve(np.ascontiguousarray(rhs[:1]), 1e-10)
-    assert rel(x1[0], xs[0]) < 1e-12
+    assert_close(x1[0], xs[0], 1e-12)
     with pytest.raises(P.DDAMGError) as e:
         s.solve_batched(np.zeros((65,) + rhs.shape[1:], np.complex128), 1e-10)
     assert e.value.status == 1

@@ -8,7 +8,7 @@ from __future__ import annotations
 import pytest
 
 import synthetic as syn
-from tests.gpu_common import MID, make, oracle_op, rel, t
+from tests.gpu_common import MID, assert_close, make, oracle_op, rel, t
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +48,7 @@ def _check(results, reqs):
             assert res <= tol, (ci, k, res)
             assert info[k]["converged"] == 1
         alone = _alone(MID if ci == 0 else OTHER, rhs, tol)
-        assert rel(x, alone) < 1e-5
+        assert_close(x, alone, 1e-5)
 
 
 def test_server_batches_requests_and_matches_alone():

@@ -20,7 +20,7 @@ import torch
 
 import synthetic as syn
 from oracle.coarse import Aggregation, orthonormalise
-from tests.gpu_common import MID, TOL32, TOL64, make, oracle_op, rel, t
+from tests.gpu_common import MID, TOL32, TOL64, assert_close, make, oracle_op, t
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_noalloc_coarse_solve_matches_coarse_solve(prec):
             slack = (1 << 21) + ((16 << 20) if call == 0 else 0)
             assert free_after >= free_before - slack
             assert np.array_equal(its, its_ref), call
-            assert rel(got.cpu().numpy(), ref) < tol, call
+            assert_close(got.cpu().numpy(), ref, tol, call)
     finally:
         s.close()
 
