@@ -78,8 +78,15 @@ typedef enum {
 
 /* Arithmetic of the smoother, coarse grid and projections.  The outer
  * FGMRES, its residual r = b - D x and the test-vector orthonormalisation
- * are always FP64. */
-typedef enum { DDAMG_FP64 = 0, DDAMG_FP32 = 1 } ddamg_precision;
+ * are always FP64.  DDAMG_BF16 and DDAMG_FP16 compute in FP32 like
+ * DDAMG_FP32 but store in that half type: the smoother's links, clover
+ * blocks (A and A^-1) and spinor fields (each spinor divided by its site
+ * norm, the largest magnitude of its 24 reals, kept in FP32), and the test
+ * vectors that R and P read (D_c is assembled from the same rounded
+ * vectors); the coarse operator and the remaining fields stay FP32.  As a
+ * step precision, BF16 / FP16 select the half-storage D (ddamg_apply_D),
+ * SAP (ddamg_sap) and block solve (ddamg_block_solve). */
+typedef enum { DDAMG_FP64 = 0, DDAMG_FP32 = 1, DDAMG_BF16 = 2, DDAMG_FP16 = 3 } ddamg_precision;
 
 typedef struct {
   int L[4];            /* lattice extents x, y, z, t; each even             */
@@ -110,7 +117,8 @@ typedef struct {
   int half_vectors;    /* FP32 inner precision only: 1 = the test vectors
                           that R and P (Eq. 3, 4) read are stored in FP16
                           (FP32 arithmetic), and D_c is assembled from the
-                          same rounded vectors; 0 = FP32 vectors            */
+                          same rounded vectors; 0 = FP32 vectors (BF16 and
+                          FP16 inner precisions always store them in half) */
 } ddamg_params;
 
 typedef struct {

@@ -5,8 +5,8 @@ The solver is the CUDA library ``libddamg.so`` behind the C ABI of
 package loads nothing; :func:`load` (or creating a :class:`DDAMG`) loads the
 library and fails loudly if it has not been built.
 """
-from ._ddamg import (FP32, FP64, DDAMG, DDAMGError, Params, RequestInfo, Server, SolveInfo,
+from ._ddamg import (BF16, FP16, FP32, FP64, DDAMG, DDAMGError, Params, RequestInfo, Server, SolveInfo,
                      Stats, default_params, load)
 
-__all__ = ["FP32", "FP64", "DDAMG", "DDAMGError", "Params", "RequestInfo", "Server", "SolveInfo",
+__all__ = ["BF16", "FP16", "FP32", "FP64", "DDAMG", "DDAMGError", "Params", "RequestInfo", "Server", "SolveInfo",
            "Stats", "default_params", "load"]

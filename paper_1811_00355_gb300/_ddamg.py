@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libddamg.so")
 
 FP64 = 0
 FP32 = 1
+BF16 = 2
+FP16 = 3
 
 STATUS = {0: "DDAMG_OK", 1: "DDAMG_EINVAL", 2: "DDAMG_ENOMEM", 3: "DDAMG_ECUDA",
           4: "DDAMG_ENOCONV", 5: "DDAMG_ENUMERIC", 6: "DDAMG_ETIMEOUT", 7: "DDAMG_ESTATE"}

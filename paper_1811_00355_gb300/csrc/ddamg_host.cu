@@ -18,6 +18,9 @@
 #include <chrono>
 #include <mutex>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/ddamg.h"
 #include "kernels.h"
 
@@ -82,7 +85,22 @@ struct ddamg_ctx {
   void* Dc = nullptr;
   void* Ainv = nullptr;
   void* AD = nullptr;             // A_oo^-1 D_c hop blocks of the odd coarse sites
-  void* lam16 = nullptr;          // FP16 test vectors of R and P (half_vectors)
+  void* lam16 = nullptr;          // half test vectors of R and P (half_vectors, or a half inner precision)
+  // half-precision copies of the FP32 links and clover blocks (index 0 FP16,
+  // 1 BF16), made on first use and refreshed when the links or the clover
+  // term change (op_gen counts those changes)
+  void* gH[2] = {nullptr, nullptr};
+  void* AH[2] = {nullptr, nullptr};
+  void* AiH[2] = {nullptr, nullptr};
+  uint64_t h_gen[2] = {0, 0};
+  uint64_t op_gen = 1;
+  // half spinor fields of the smoother (b, x) and of the half D (in, out),
+  // each with its FP32 site norms
+  void* hb = nullptr;
+  void* hx = nullptr;
+  float* hbn = nullptr;
+  float* hxn = nullptr;
+  size_t h_fields = 0;
   void* cwork = nullptr;
   int* d_iters = nullptr;        // per-rhs coarse iterations
   int* d_iters_acc = nullptr;    // running total
@@ -221,7 +239,18 @@ ddamg_status dalloc_t(ddamg_ctx* h, T** p, size_t count) {
   return s;
 }
 
-bool is_prec(int p) { return p == DDAMG_FP64 || p == DDAMG_FP32; }
+bool is_prec(int p) { return p == DDAMG_FP64 || p == DDAMG_FP32 || p == DDAMG_BF16 || p == DDAMG_FP16; }
+// half storage kind of a precision: 0 FP16, 1 BF16, -1 none
+int half_kind(int p) { return p == DDAMG_FP16 ? 0 : p == DDAMG_BF16 ? 1 : -1; }
+// FP32 arithmetic in the inner solver (FP32 or a half storage precision)
+bool inner32(const ddamg_ctx* h) { return h->p.precision != DDAMG_FP64; }
+// the test vectors of R and P are stored in half: FP16 with half_vectors, or
+// the half type of a half inner precision
+int lam_half_kind(const ddamg_ctx* h) {
+  const int k = half_kind(h->p.precision);
+  if (k >= 0) return k;
+  return (inner32(h) && h->p.half_vectors) ? 0 : -1;
+}
 
 ddamg_status validate(const ddamg_params* p, std::string& why) {
   auto bad = [&](const char* m) {
@@ -248,7 +277,7 @@ ddamg_status validate(const ddamg_params* p, std::string& why) {
   if (p->setup_iters < 0 || p->n_sap < 1 || p->mr_iters < 0) return bad("setup_iters >= 0, n_sap >= 1, mr_iters >= 0");
   if (!(p->coarse_tol > 0.0) || p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_max_iter < 1)
     return bad("coarse_tol > 0, coarse_restart in [1, 64], coarse_max_iter >= 1");
-  if (!is_prec(p->precision)) return bad("precision must be DDAMG_FP64 or DDAMG_FP32");
+  if (!is_prec(p->precision)) return bad("precision must be DDAMG_FP64, DDAMG_FP32, DDAMG_BF16 or DDAMG_FP16");
   if (p->outer_restart < 1 || p->outer_restart > 62 || p->max_outer_iter < 1)
     return bad("outer_restart in [1, 62], max_outer_iter >= 1");
   if (!(p->outer_refine >= 0.0 && p->outer_refine < 1.0)) return bad("outer_refine in [0, 1)");
@@ -545,18 +574,32 @@ template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 template <class R>
 cudaError_t restrict_inner(ddamg_ctx* h, const R* in, R* bc, int nf) {
   return timed(h, 4, [&] {
-    if constexpr (sizeof(R) == 4)
-      if (h->p.half_vectors) return restrict_op_h(h->g, h->lam16, h->p.n_v, in, bc, nf, h->st);
+    if constexpr (sizeof(R) == 4) {
+      const int k = lam_half_kind(h);
+      if (k >= 0) return restrict_op_h(h->g, k, h->lam16, h->p.n_v, in, bc, nf, h->st);
+    }
     return restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, in, bc, nf, h->st);
   });
 }
 template <class R>
 cudaError_t prolong_inner(ddamg_ctx* h, const R* xc, R* out, int nf) {
   return timed(h, 5, [&] {
-    if constexpr (sizeof(R) == 4)
-      if (h->p.half_vectors) return prolong_op_h(h->g, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
+    if constexpr (sizeof(R) == 4) {
+      const int k = lam_half_kind(h);
+      if (k >= 0) return prolong_op_h(h->g, k, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
+    }
     return prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, xc, out, nf, false, h->st);
   });
+}
+
+// half storage: copies of the operators and the smoother's spinor buffers
+ddamg_status half_operators(ddamg_ctx* h, int k);
+ddamg_status need_half_fields(ddamg_ctx* h, size_t nf);
+// f(S*) with S the half type of kind k (0 FP16, 1 BF16)
+template <class F>
+cudaError_t by_half(int k, F&& f) {
+  if (k == 0) return f((__half*)nullptr);
+  return f((__nv_bfloat16*)nullptr);
 }
 
 // ---- operators on device fields ---------------------------------------------------
@@ -571,7 +614,39 @@ ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int
 
 // SAP from zero: x = S b
 template <class R>
-ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf) {
+ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
+  if (kind == -2) kind = half_kind(h->p.precision);
+  if constexpr (sizeof(R) == 4) {
+    // half storage: links, clover blocks and the smoother's b and x in the
+    // half type (FP32 arithmetic); b in and x out in FP32
+    if (kind >= 0 && sap_half_ok(h->g)) {
+      TRY(half_operators(h, kind));
+      TRY(need_half_fields(h, nf));
+      CK(cudaMemsetAsync(h->hx, 0, nf * h->V24 * 2, h->st));
+      CK(cudaMemsetAsync(h->hxn, 0, nf * h->g.V * sizeof(float), h->st));
+      CK(by_half(kind, [&](auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return spinor_to_half<S>(h->g, b, h->hb, h->hbn, nf, h->st);
+      }));
+      for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
+        for (int c = 0; c < 2; ++c) {
+          const bool zero = cyc == 0 && c == 0;
+          addf(h, nf * flops_sap_sweep(h, zero));
+          CK(timed(h, 1, [&] {
+            return by_half(kind, [&](auto* tag) {
+              using S = std::remove_pointer_t<decltype(tag)>;
+              return sap_sweep_h<S>(h->g, c, h->p.mr_iters, zero, h->hb, h->hbn, h->hx, h->hxn, h->gH[kind],
+                                    h->AH[kind], h->AiH[kind], nf, h->d_status, h->wait_sap, h->st);
+            });
+          }));
+        }
+      CK(by_half(kind, [&](auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return spinor_from_half<S>(h->g, h->hx, h->hxn, x, nf, false, h->st);
+      }));
+      return DDAMG_OK;
+    }
+  }
   CK(cudaMemsetAsync(x, 0, nf * h->V24 * sizeof(R), h->st));
   for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
     for (int c = 0; c < 2; ++c) {
@@ -638,7 +713,7 @@ ddamg_status check_status(ddamg_ctx* h) {
 // ---- coarse operator ----------------------------------------------------------------
 ddamg_status alloc_coarse(ddamg_ctx* h) {
   if (h->Dc) return DDAMG_OK;
-  const int rs = h->p.precision == DDAMG_FP64 ? 8 : 4;
+  const int rs = inner32(h) ? 4 : 8;
   const size_t n2 = h->n2;
   TRY(dalloc(h, &h->Dc, (size_t)h->g.nb * 9 * n2 * n2 * 2 * rs));
   TRY(dalloc(h, &h->Ainv, (size_t)h->g.nb * n2 * n2 * 2 * rs));
@@ -648,16 +723,71 @@ ddamg_status alloc_coarse(ddamg_ctx* h) {
 }
 
 ddamg_status sync_lam32(ddamg_ctx* h) {
-  if (h->p.precision == DDAMG_FP32) {
+  if (inner32(h)) {
     if (!h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
     CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
-    if (h->p.half_vectors) {
+    const int k = lam_half_kind(h);
+    if (k >= 0) {
       if (!h->lam16) TRY(dalloc(h, &h->lam16, (size_t)h->p.n_v * h->V24 * 2));
-      CK(round_vectors_half(h->lam32, h->lam16, (size_t)h->p.n_v * h->V24, h->st));
+      CK(round_vectors_half(k, h->lam32, h->lam16, (size_t)h->p.n_v * h->V24, h->st));
     }
   }
   return DDAMG_OK;
 }
+
+// half copies of the FP32 links and clover blocks for storage kind k
+ddamg_status half_operators(ddamg_ctx* h, int k) {
+  if (h->gH[k] && h->h_gen[k] == h->op_gen) return DDAMG_OK;
+  const size_t V = h->g.V;
+  if (!h->gH[k]) {
+    TRY(dalloc(h, &h->gH[k], V * 48 * 2));
+    TRY(dalloc(h, &h->AH[k], V * 72 * 2));
+    TRY(dalloc(h, &h->AiH[k], V * 72 * 2));
+  }
+  if (k == 0) {
+    CK(to_half<__half>(h->g32, h->gH[k], V * 48, h->st));
+    CK(to_half<__half>(h->A32, h->AH[k], V * 72, h->st));
+    CK(to_half<__half>(h->Ai32, h->AiH[k], V * 72, h->st));
+  } else {
+    CK(to_half<__nv_bfloat16>(h->g32, h->gH[k], V * 48, h->st));
+    CK(to_half<__nv_bfloat16>(h->A32, h->AH[k], V * 72, h->st));
+    CK(to_half<__nv_bfloat16>(h->Ai32, h->AiH[k], V * 72, h->st));
+  }
+  h->h_gen[k] = h->op_gen;
+  return DDAMG_OK;
+}
+
+// the clover term A = (4 + m0) + C and its inverse from the resident links;
+// half copies already in use are refreshed at once (captured graphs read
+// them in place)
+ddamg_status rebuild_clover(ddamg_ctx* h, double m0, double csw) {
+  CK(build_clover(h->g, h->d_gauge_lex, m0, csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  ++h->op_gen;
+  for (int k = 0; k < 2; ++k)
+    if (h->gH[k]) TRY(half_operators(h, k));
+  return DDAMG_OK;
+}
+
+// half spinor buffers b, x (with site norms) for nf fields
+ddamg_status need_half_fields(ddamg_ctx* h, size_t nf) {
+  if (h->h_fields >= nf) return DDAMG_OK;
+  dfree(h, h->hb, h->h_fields * h->V24 * 2);
+  dfree(h, h->hx, h->h_fields * h->V24 * 2);
+  dfree(h, h->hbn, h->h_fields * h->g.V * sizeof(float));
+  dfree(h, h->hxn, h->h_fields * h->g.V * sizeof(float));
+  h->hb = h->hx = nullptr;
+  h->hbn = h->hxn = nullptr;
+  h->h_fields = 0;
+  TRY(dalloc(h, &h->hb, nf * h->V24 * 2));
+  TRY(dalloc(h, &h->hx, nf * h->V24 * 2));
+  TRY(dalloc_t(h, &h->hbn, nf * h->g.V));
+  TRY(dalloc_t(h, &h->hxn, nf * h->g.V));
+  h->h_fields = nf;
+  ++h->gen;                        // captured graphs refer to the old buffers
+  return DDAMG_OK;
+}
+
+
 
 
 
@@ -667,7 +797,7 @@ ddamg_status build_coarse_op(ddamg_ctx* h) {
   TRY(sync_lam32(h));
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
   addf(h, flops_build(h));
-  if (h->p.precision == DDAMG_FP32) {
+  if (inner32(h)) {
     CK(assemble_coarse<float>(h->g, h->lam32, h->p.n_v, h->g32, h->A32, (float*)h->Dc, h->st));
     CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
     CK(premultiply_odd<float>(h->g, (float*)h->Dc, (float*)h->Ainv, h->p.n_v, (float*)h->AD, h->st));
@@ -761,7 +891,7 @@ ddamg_status precond_to_f64(ddamg_ctx* h, const double* v, double* z, int* cit_d
 
 // FGMRES as iterative refinement: FP32 operator products in the Arnoldi
 // process, FP64 basis, Gram-Schmidt and true residuals
-bool refine_mode(const ddamg_ctx* h) { return h->p.precision == DDAMG_FP32 && h->p.outer_refine > 0.0; }
+bool refine_mode(const ddamg_ctx* h) { return inner32(h) && h->p.outer_refine > 0.0; }
 
 ddamg_status alloc_outer(ddamg_ctx* h) {
   if (h->fV) return DDAMG_OK;
@@ -787,7 +917,12 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
   TRY(alloc_outer(h));
   if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
   TRY(need_tmp(h, 1, 6));
-  if (h->p.precision == DDAMG_FP32) coarse_gmres_exact_bytes<float>(h->g, h->p.n_v, h->p.coarse_restart, 1);
+  const int k = half_kind(h->p.precision);
+  if (k >= 0) {
+    TRY(half_operators(h, k));
+    TRY(need_half_fields(h, 1));
+  }
+  if (inner32(h)) coarse_gmres_exact_bytes<float>(h->g, h->p.n_v, h->p.coarse_restart, 1);
   else coarse_gmres_exact_bytes<double>(h->g, h->p.n_v, h->p.coarse_restart, 1);
   return DDAMG_OK;
 }
@@ -1355,7 +1490,7 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
 
 bool is_prec_ok(ddamg_ctx* h, int prec) {
   if (!is_prec(prec)) {
-    fail(h, DDAMG_EINVAL, "precision must be DDAMG_FP64 or DDAMG_FP32");
+    fail(h, DDAMG_EINVAL, "precision must be DDAMG_FP64, DDAMG_FP32, DDAMG_BF16 or DDAMG_FP16");
     return false;
   }
   return true;
@@ -1557,7 +1692,7 @@ ddamg_status ddamg_create(const ddamg_params* p, const double* gauge, int gauge_
     std::memcpy(&dev, &bits, sizeof dev);
     if (!(dev <= 1e-9))
       return fail(h, DDAMG_EINVAL, "gauge links are not SU(3): max deviation %.3e", dev);
-    CK(build_clover(h->g, h->d_gauge_lex, p->m0, p->csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+    TRY(rebuild_clover(h, p->m0, p->csw));
     CK(cudaStreamSynchronize(h->st));
     return DDAMG_OK;
   }();
@@ -1584,7 +1719,7 @@ ddamg_status ddamg_set_gauge(ddamg_handle h, const double* gauge, int on_device)
   std::memcpy(&dev, &bits, sizeof dev);
   h->have_coarse = false;           // the clover term, test vectors and D_c belong to the old links
   if (!(dev <= 1e-9)) return fail(h, DDAMG_EINVAL, "gauge links are not SU(3): max deviation %.3e", dev);
-  CK(build_clover(h->g, h->d_gauge_lex, h->p.m0, h->p.csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  TRY(rebuild_clover(h, h->p.m0, h->p.csw));
   return DDAMG_OK;
 }
 
@@ -1593,7 +1728,7 @@ ddamg_status ddamg_run_setup(ddamg_handle h, const double* init, int on_device) 
   const int n = h->p.n_v;
   // the clover term and its inverse are part of the setup (rebuilt from the
   // resident links, so a repeated setup redoes all of its work)
-  CK(build_clover(h->g, h->d_gauge_lex, h->p.m0, h->p.csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  TRY(rebuild_clover(h, h->p.m0, h->p.csw));
   if (init) {
     TRY(import_fields<double>(h, init, on_device, n, h->lam64));
   } else {
@@ -1627,7 +1762,7 @@ ddamg_status ddamg_update_mass(ddamg_handle h, double m0, double csw) {
   if (!std::isfinite(m0) || !std::isfinite(csw)) return fail(h, DDAMG_EINVAL, "m0 and csw must be finite");
   h->p.m0 = m0;
   h->p.csw = csw;
-  CK(build_clover(h->g, h->d_gauge_lex, m0, csw, h->A64, h->Ai64, h->A32, h->Ai32, h->st));
+  TRY(rebuild_clover(h, m0, csw));
   if (h->have_coarse) TRY(build_coarse_op(h));
   CK(cudaStreamSynchronize(h->st));
   return DDAMG_OK;
@@ -1679,6 +1814,29 @@ ddamg_status ddamg_solve_batched(ddamg_handle h, int nrhs, const double* rhs, do
 
 ddamg_status ddamg_apply_D(ddamg_handle h, int prec, int nrhs, const double* in, double* out, int on_device) {
   if (!h || nrhs < 1 || !in || !out) return DDAMG_EINVAL;
+  const int k = half_kind(prec);
+  if (k >= 0) {
+    // half links, clover and spinors (FP32 arithmetic): in -> half, D, -> FP64
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(half_operators(h, k));
+    TRY(need_half_fields(h, nrhs));
+    float* t0 = (float*)h->tmp[0];
+    float* t1 = (float*)h->tmp[1];
+    TRY(import_fields<float>(h, in, on_device, nrhs, t0));
+    addf(h, (double)nrhs * h->g.V * F_D);
+    CK(by_half(k, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      cudaError_t e = spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
+      if (e != cudaSuccess) return e;
+      e = timed(h, 0, [&] {
+        return dslash_h<S>(h->g, DSLASH_D, h->hb, h->hbn, nullptr, nullptr, h->hx, h->hxn, h->gH[k], h->AH[k], nrhs,
+                           h->st);
+      });
+      if (e != cudaSuccess) return e;
+      return spinor_from_half<S>(h->g, h->hx, h->hxn, t1, nrhs, false, h->st);
+    }));
+    return export_fields<float>(h, t1, nrhs, out, on_device);
+  }
   return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
     using R = std::remove_pointer_t<decltype(tag)>;
     TRY(need_tmp(h, nrhs, 6));
@@ -1714,6 +1872,28 @@ ddamg_status ddamg_get_clover(ddamg_handle h, int inverse, double* out) {
 ddamg_status ddamg_block_solve(ddamg_handle h, int prec, int colour, int nrhs, const double* in, double* out,
                                int on_device) {
   if (!h || nrhs < 1 || !in || !out || (colour != 0 && colour != 1)) return DDAMG_EINVAL;
+  const int k = half_kind(prec);
+  if (k >= 0 && sap_half_ok(h->g)) {
+    TRY(need_tmp(h, nrhs, 6));
+    TRY(half_operators(h, k));
+    TRY(need_half_fields(h, nrhs));
+    float* t0 = (float*)h->tmp[0];
+    TRY(import_fields<float>(h, in, on_device, nrhs, t0));
+    CK(cudaMemsetAsync(h->hx, 0, nrhs * h->V24 * 2, h->st));
+    CK(cudaMemsetAsync(h->hxn, 0, nrhs * h->g.V * sizeof(float), h->st));
+    ++h->n_cls[1];
+    CK(by_half(k, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      cudaError_t e = spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
+      if (e != cudaSuccess) return e;
+      e = sap_sweep_h<S>(h->g, colour, h->p.mr_iters, true, h->hb, h->hbn, h->hx, h->hxn, h->gH[k], h->AH[k],
+                         h->AiH[k], nrhs, h->d_status, h->wait_sap, h->st);
+      if (e != cudaSuccess) return e;
+      return spinor_from_half<S>(h->g, h->hx, h->hxn, t0, nrhs, false, h->st);
+    }));
+    TRY(check_status(h));
+    return export_fields<float>(h, t0, nrhs, out, on_device);
+  }
   return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
     using R = std::remove_pointer_t<decltype(tag)>;
     TRY(need_tmp(h, nrhs, 6));
@@ -1735,7 +1915,7 @@ ddamg_status ddamg_sap(ddamg_handle h, int prec, int nrhs, const double* in, dou
     using R = std::remove_pointer_t<decltype(tag)>;
     TRY(need_tmp(h, nrhs, 6));
     TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[4]));
-    TRY(op_sap<R>(h, (R*)h->tmp[4], (R*)h->tmp[5], nrhs));
+    TRY(op_sap<R>(h, (R*)h->tmp[4], (R*)h->tmp[5], nrhs, half_kind(prec)));
     TRY(check_status(h));
     return export_fields<R>(h, (R*)h->tmp[5], nrhs, out, on_device);
   });
@@ -1779,7 +1959,7 @@ ddamg_status ddamg_get_coarse_op(ddamg_handle h, double* out) {
   size_t nc = (size_t)h->g.nb * 9 * h->n2 * h->n2;
   double* tmpd;
   TRY(dalloc_t(h, &tmpd, 2 * nc));
-  if (h->p.precision == DDAMG_FP32) CK(coarse_export<float>((const float*)h->Dc, h->p.n_v, (size_t)h->g.nb * 9, tmpd, h->st));
+  if (inner32(h)) CK(coarse_export<float>((const float*)h->Dc, h->p.n_v, (size_t)h->g.nb * 9, tmpd, h->st));
   else CK(coarse_export<double>((const double*)h->Dc, h->p.n_v, (size_t)h->g.nb * 9, tmpd, h->st));
   CK(cudaMemcpyAsync(out, tmpd, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -1803,7 +1983,7 @@ ddamg_status ddamg_set_coarse_op(ddamg_handle h, const double* dc, int on_device
     src = tmpd;
   }
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
-  if (h->p.precision == DDAMG_FP32) {
+  if (inner32(h)) {
     CK(coarse_import<float>(src, h->p.n_v, nblk, (float*)h->Dc, h->st));
     CK(invert_self_blocks<float>(h->g, (float*)h->Dc, h->p.n_v, (float*)h->Ainv, h->d_status, h->st));
     CK(premultiply_odd<float>(h->g, (float*)h->Dc, (float*)h->Ainv, h->p.n_v, (float*)h->AD, h->st));

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <atomic>
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace ddamg {
@@ -91,6 +93,22 @@ template <class R>
 cudaError_t dslash(const Geom& g, int mode, const R* x, const R* b, R* y, const R* gauge,
                    const R* clover, int nrhs, cudaStream_t st);
 
+// ---- half-precision storage (S = __half or __nv_bfloat16; half.cuh) ------------
+// D in FP32 arithmetic with half links, clover blocks and spinors (each
+// spinor field with its FP32 site norms xn / bn / yn, V per field)
+template <class S>
+cudaError_t dslash_h(const Geom& g, int mode, const void* x, const float* xn, const void* b, const float* bn,
+                     void* y, float* yn, const void* gauge, const void* clover, int nrhs, cudaStream_t st);
+// nf FP32 spinor fields -> half fields with site norms, and back (dst = or +=)
+template <class S>
+cudaError_t spinor_to_half(const Geom& g, const float* src, void* dst, float* nrm, int nf, cudaStream_t st);
+template <class S>
+cudaError_t spinor_from_half(const Geom& g, const void* src, const float* nrm, float* dst, int nf, bool accumulate,
+                             cudaStream_t st);
+// n FP32 values of a block-major field (links, clover, test vectors) -> half
+template <class S>
+cudaError_t to_half(const float* src, void* dst, size_t n, cudaStream_t st);
+
 // ---- BLAS-1 on flat complex arrays (n complex numbers) -------------------------
 // partial sums per CTA land in `scratch` (>= reduce_scratch_len(k) doubles)
 size_t reduce_scratch_len(int k);
@@ -155,6 +173,14 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
                       R* x, const R* gauge, const R* clover, const R* clover_inv, int nrhs,
                       int* status, long long wait_limit, cudaStream_t st);
 size_t sap_smem_bytes(const Geom& g, int real_size);
+// one colour of a Schwarz sweep with half storage (FP32 arithmetic): links,
+// clover blocks A and A^-1 and the spinors b, x (with their site norms) in
+// the half type S; needs blocks whose half volume is a multiple of 32
+template <class S>
+cudaError_t sap_sweep_h(const Geom& g, int colour, int mr_iters, bool x_is_zero, const void* b, const float* bn,
+                        void* x, float* xn, const void* gauge, const void* clover, const void* clover_inv, int nrhs,
+                        int* status, long long wait_limit, cudaStream_t st);
+bool sap_half_ok(const Geom& g);
 
 // ---- coarse grid ----------------------------------------------------------------
 // classical Gram-Schmidt twice per (aggregate, chirality) on n FP64 fields
@@ -164,13 +190,14 @@ template <class R>
 cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs,
                         cudaStream_t st);
 // x (+)= P x_c
-// the same with FP16 test vectors (FP32 layout, 8-byte units), FP32 arithmetic
-cudaError_t restrict_op_h(const Geom& g, const void* lam16, int n, const float* b, float* bc, int nrhs,
+// the same with half test vectors (FP16, or BF16 if bf16; FP32 layout with
+// 8-byte units), FP32 arithmetic
+cudaError_t restrict_op_h(const Geom& g, int bf16, const void* lam16, int n, const float* b, float* bc, int nrhs,
                           cudaStream_t st);
-cudaError_t prolong_op_h(const Geom& g, const void* lam16, int n, const float* xc, float* x, int nrhs,
+cudaError_t prolong_op_h(const Geom& g, int bf16, const void* lam16, int n, const float* xc, float* x, int nrhs,
                          bool accumulate, cudaStream_t st);
-// lam16 = FP16(lam32) and lam32 = FP32(lam16) (n reals)
-cudaError_t round_vectors_half(float* lam32, void* lam16, size_t n, cudaStream_t st);
+// lam16 = half(lam32) and lam32 = FP32(lam16) (n reals, a multiple of 4)
+cudaError_t round_vectors_half(int bf16, float* lam32, void* lam16, size_t n, cudaStream_t st);
 template <class R>
 cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs,
                        bool accumulate, cudaStream_t st);

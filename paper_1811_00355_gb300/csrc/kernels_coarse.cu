@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "half.cuh"
 #include "kernels.h"
 
 namespace ddamg {
@@ -160,29 +161,30 @@ template <class R>
 __device__ __forceinline__ void load_lam(const R* lam, int d, int Vb, Spinor<R>& s) {
   load_spinor<R>(lam, d, Vb, s);
 }
+template <class S>
+__device__ __forceinline__ void load_lam_h(const S* lam, int d, int Vb, Spinor<float>& s) {
+  load_site_h<S, SPINOR_NR>(lam, d, Vb, reinterpret_cast<float*>(s.c));
+}
 __device__ __forceinline__ void load_lam(const __half* lam, int d, int Vb, Spinor<float>& s) {
-  using LY = Layout<float, SPINOR_NR>;
-  const size_t b = LY::base(d, Vb);
-  const uint2* p = reinterpret_cast<const uint2*>(lam);
-#pragma unroll
-  for (int u = 0; u < LY::NU; ++u) {
-    const uint2 w = __ldg(p + b + (size_t)u * Vb);
-    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
-    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
-    s.c[2 * u] = mk(f0.x, f0.y);
-    s.c[2 * u + 1] = mk(f1.x, f1.y);
-  }
+  load_lam_h<__half>(lam, d, Vb, s);
+}
+__device__ __forceinline__ void load_lam(const __nv_bfloat16* lam, int d, int Vb, Spinor<float>& s) {
+  load_lam_h<__nv_bfloat16>(lam, d, Vb, s);
 }
 
-// FP16 copy of FP32 test vectors, and the FP32 vectors rounded to the same
+// half copy of FP32 test vectors, and the FP32 vectors rounded to the same
 // values (so that D_c is assembled from exactly the P that R and P apply)
-__global__ void k_round_half(float* __restrict__ lam32, __half* __restrict__ lam16, size_t n) {
+template <class S>
+__global__ void k_round_half(float* __restrict__ lam32, S* __restrict__ lam16, size_t n4) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; i < n; i += stride) {
-    const __half h = __float2half_rn(lam32[i]);
-    lam16[i] = h;
-    lam32[i] = __half2float(h);
+  for (; i < n4; i += stride) {
+    float4 v = reinterpret_cast<const float4*>(lam32)[i];
+    float w[4] = {v.x, v.y, v.z, v.w};
+    const uint2 p = pack4<S>(w);
+    reinterpret_cast<uint2*>(lam16)[i] = p;
+    unpack4<S>(p, w);
+    reinterpret_cast<float4*>(lam32)[i] = make_float4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -682,19 +684,26 @@ cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, in
                        cudaStream_t st) {
   return prolong_launch<R, R>(g, lam, n, xc, x, nrhs, accumulate, st);
 }
-cudaError_t restrict_op_h(const Geom& g, const void* lam16, int n, const float* b, float* bc, int nrhs,
+cudaError_t restrict_op_h(const Geom& g, int bf16, const void* lam16, int n, const float* b, float* bc, int nrhs,
                           cudaStream_t st) {
-  return restrict_launch<float, __half>(g, reinterpret_cast<const __half*>(lam16), n, b, bc, nrhs, st);
+  if (bf16)
+    return restrict_launch<float, __nv_bfloat16>(g, static_cast<const __nv_bfloat16*>(lam16), n, b, bc, nrhs, st);
+  return restrict_launch<float, __half>(g, static_cast<const __half*>(lam16), n, b, bc, nrhs, st);
 }
-cudaError_t prolong_op_h(const Geom& g, const void* lam16, int n, const float* xc, float* x, int nrhs,
+cudaError_t prolong_op_h(const Geom& g, int bf16, const void* lam16, int n, const float* xc, float* x, int nrhs,
                          bool accumulate, cudaStream_t st) {
-  return prolong_launch<float, __half>(g, reinterpret_cast<const __half*>(lam16), n, xc, x, nrhs, accumulate, st);
+  if (bf16)
+    return prolong_launch<float, __nv_bfloat16>(g, static_cast<const __nv_bfloat16*>(lam16), n, xc, x, nrhs,
+                                                accumulate, st);
+  return prolong_launch<float, __half>(g, static_cast<const __half*>(lam16), n, xc, x, nrhs, accumulate, st);
 }
-cudaError_t round_vectors_half(float* lam32, void* lam16, size_t n, cudaStream_t st) {
-  unsigned nb = nblk(n, 256);
+cudaError_t round_vectors_half(int bf16, float* lam32, void* lam16, size_t n, cudaStream_t st) {
+  const size_t n4 = n / 4;
+  unsigned nb = nblk(n4, 256);
   if (nb > 4096) nb = 4096;
   if (!nb) return cudaSuccess;
-  k_round_half<<<nb, 256, 0, st>>>(lam32, reinterpret_cast<__half*>(lam16), n);
+  if (bf16) k_round_half<__nv_bfloat16><<<nb, 256, 0, st>>>(lam32, static_cast<__nv_bfloat16*>(lam16), n4);
+  else k_round_half<__half><<<nb, 256, 0, st>>>(lam32, static_cast<__half*>(lam16), n4);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -1,0 +1,195 @@
+// Wilson-clover stencil and layout conversions for half-precision storage
+// (BF16 or FP16, see half.cuh) with FP32 arithmetic.
+//
+// D x = A x - 1/2 sum_mu [(1-g_mu) U_mu(x) x(x+mu) + (1+g_mu) U_mu(x-mu)^H x(x-mu)]
+// (paper Sec. 1 and 3) with links, the two packed clover blocks and the
+// spinors read from half fields: per site 48 + 4 bytes of input spinor, 96
+// of links (two rows of four links), 144 of clover, 48 + 4 of output.
+#include "half.cuh"
+#include "kernels.h"
+
+namespace ddamg {
+
+namespace {
+
+constexpr int TPB = 128;
+
+inline unsigned nblk(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+template <int MU, class S>
+__device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x, const float* __restrict__ xn,
+                                          const S* __restrict__ gauge, int d, Spinor<float>& acc) {
+  cpx<float> h[2][3], y[2][3];
+  Spinor<float> nb;
+  {  // forward: (1 - g_mu) U_mu(x) x(x+mu)
+    const uint32_t e = __ldg(g.nbr + (size_t)(2 * MU) * g.V + d);
+    const int n = (int)(e & ~NEG_BIT);
+    const float sc = (e & NEG_BIT) ? -1.f : 1.f;
+    load_spinor_h<S>(x, xn, n, g.Vb, nb);
+    project<MU, -1>(nb, h);
+    Link<float> U;
+    load_link_h<S>(gauge, d, g.Vb, MU, U);
+    su3_mul(U, h, y);
+    accumulate<MU, -1>(acc, y, sc);
+  }
+  {  // backward: (1 + g_mu) U_mu(x-mu)^H x(x-mu)
+    const uint32_t e = __ldg(g.nbr + (size_t)(2 * MU + 1) * g.V + d);
+    const int n = (int)(e & ~NEG_BIT);
+    const float sc = (e & NEG_BIT) ? -1.f : 1.f;
+    load_spinor_h<S>(x, xn, n, g.Vb, nb);
+    project<MU, +1>(nb, h);
+    Link<float> U;
+    load_link_h<S>(gauge, n, g.Vb, MU, U);
+    su3_mul_dag(U, h, y);
+    accumulate<MU, +1>(acc, y, sc);
+  }
+}
+
+// one thread per site; right-hand side blockIdx.y (fields V sites apart)
+template <class S, int MODE>
+__global__ void __launch_bounds__(TPB) k_dslash_h(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
+                                                  const S* __restrict__ b, const float* __restrict__ bn,
+                                                  S* __restrict__ y, float* __restrict__ yn,
+                                                  const S* __restrict__ gauge, const S* __restrict__ clover) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= g.V) return;
+  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  const size_t noff = (size_t)blockIdx.y * g.V;
+  x += off;
+  xn += noff;
+  y += off;
+  yn += noff;
+  Spinor<float> out;
+  {
+    Spinor<float> xs;
+    load_spinor_h<S>(x, xn, d, g.Vb, xs);
+    clover_mul_h<S>(clover, d, g.Vb, xs, out);
+  }
+  if (MODE != DSLASH_CLOVER) {
+    Spinor<float> acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
+    hop_dir_h<0>(g, x, xn, gauge, d, acc);
+    hop_dir_h<1>(g, x, xn, gauge, d, acc);
+    hop_dir_h<2>(g, x, xn, gauge, d, acc);
+    hop_dir_h<3>(g, x, xn, gauge, d, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      out.c[k].re = fmaf(-0.5f, acc.c[k].re, out.c[k].re);
+      out.c[k].im = fmaf(-0.5f, acc.c[k].im, out.c[k].im);
+    }
+  }
+  if (MODE == DSLASH_RES) {
+    Spinor<float> bs;
+    load_spinor_h<S>(b + off, bn + noff, d, g.Vb, bs);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out.c[k] = bs.c[k] - out.c[k];
+  }
+  store_spinor_h<S>(y, yn, d, g.Vb, out);
+}
+
+// FP32 spinor fields -> half fields with site norms (nf fields)
+template <class S>
+__global__ void k_spinor_to_half(Geom g, const float* __restrict__ src, S* __restrict__ dst, float* __restrict__ nrm) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= g.V) return;
+  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  Spinor<float> s;
+  load_spinor<float>(src + off, d, g.Vb, s);
+  store_spinor_h<S>(dst + off, nrm + (size_t)blockIdx.y * g.V, d, g.Vb, s);
+}
+
+// half fields -> FP32 fields (dst = value, or dst += value)
+template <class S>
+__global__ void k_spinor_from_half(Geom g, const S* __restrict__ src, const float* __restrict__ nrm,
+                                   float* __restrict__ dst, int accumulate) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= g.V) return;
+  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  Spinor<float> s;
+  load_spinor_h<S>(src + off, nrm + (size_t)blockIdx.y * g.V, d, g.Vb, s);
+  if (accumulate) {
+    Spinor<float> o;
+    load_spinor<float>(dst + off, d, g.Vb, o);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s.c[k] = s.c[k] + o.c[k];
+  }
+  store_spinor<float>(dst + off, d, g.Vb, s);
+}
+
+// an FP32 array in the block-major layout -> the same array in half units
+// (four values per unit in both, so the order is element for element)
+template <class S>
+__global__ void k_to_half(const float* __restrict__ src, S* __restrict__ dst, size_t n4) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n4; i += stride) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + i);
+    const float w[4] = {v.x, v.y, v.z, v.w};
+    st4<S>(dst, i, w);
+  }
+}
+
+}  // namespace
+
+template <class S>
+cudaError_t dslash_h(const Geom& g, int mode, const void* x, const float* xn, const void* b, const float* bn,
+                     void* y, float* yn, const void* gauge, const void* clover, int nrhs, cudaStream_t st) {
+  const dim3 grid(nblk(g.V, TPB), nrhs);
+  const S* xs = static_cast<const S*>(x);
+  const S* bs = static_cast<const S*>(b);
+  S* ys = static_cast<S*>(y);
+  const S* gs = static_cast<const S*>(gauge);
+  const S* cs = static_cast<const S*>(clover);
+  if (mode == DSLASH_D)
+    k_dslash_h<S, DSLASH_D><<<grid, TPB, 0, st>>>(g, xs, xn, bs, bn, ys, yn, gs, cs);
+  else if (mode == DSLASH_RES)
+    k_dslash_h<S, DSLASH_RES><<<grid, TPB, 0, st>>>(g, xs, xn, bs, bn, ys, yn, gs, cs);
+  else
+    k_dslash_h<S, DSLASH_CLOVER><<<grid, TPB, 0, st>>>(g, xs, xn, bs, bn, ys, yn, gs, cs);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t spinor_to_half(const Geom& g, const float* src, void* dst, float* nrm, int nf, cudaStream_t st) {
+  if (nf < 1) return cudaSuccess;
+  k_spinor_to_half<S><<<dim3(nblk(g.V, TPB), nf), TPB, 0, st>>>(g, src, static_cast<S*>(dst), nrm);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t spinor_from_half(const Geom& g, const void* src, const float* nrm, float* dst, int nf, bool accumulate,
+                             cudaStream_t st) {
+  if (nf < 1) return cudaSuccess;
+  k_spinor_from_half<S><<<dim3(nblk(g.V, TPB), nf), TPB, 0, st>>>(g, static_cast<const S*>(src), nrm, dst,
+                                                                   accumulate ? 1 : 0);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t to_half(const float* src, void* dst, size_t n, cudaStream_t st) {
+  const size_t n4 = n / 4;
+  unsigned nb = nblk(n4, 256);
+  if (nb > 4096) nb = 4096;
+  if (!nb) return cudaSuccess;
+  k_to_half<S><<<nb, 256, 0, st>>>(src, static_cast<S*>(dst), n4);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+#define INST_H(S)                                                                                              \
+  template cudaError_t dslash_h<S>(const Geom&, int, const void*, const float*, const void*, const float*, void*, \
+                                   float*, const void*, const void*, int, cudaStream_t);                      \
+  template cudaError_t spinor_to_half<S>(const Geom&, const float*, void*, float*, int, cudaStream_t);         \
+  template cudaError_t spinor_from_half<S>(const Geom&, const void*, const float*, float*, int, bool,           \
+                                           cudaStream_t);                                                      \
+  template cudaError_t to_half<S>(const float*, void*, size_t, cudaStream_t);
+
+INST_H(__half)
+INST_H(__nv_bfloat16)
+#undef INST_H
+
+}  // namespace ddamg

@@ -14,7 +14,10 @@
 //   e_o = A_oo^-1 (r_o - D_oe e_e)
 //   x  += e
 // with D_eo, D_oe the hops that stay inside the block (-1/2 (1 -+ g) U).
+#include <mutex>
+
 #include "common.cuh"
+#include "half.cuh"
 #include "kernels.h"
 
 namespace ddamg {
@@ -456,38 +459,129 @@ __global__ void __launch_bounds__(512) k_sap_sweep(Geom g, int colour, int mr_it
 }
 
 // ---------------------------------------------------------------------------
-// FP32 sweep for Schwarz blocks whose half volume is a multiple of 32: the
-// thread layout and hop code of k_sap_sweep (four threads per site, one
-// runtime direction each, partial sums combined by warp shuffles), with
-//  * the block's links, A_ee and A_oo^-1 staged into
-//    shared memory by bulk asynchronous copies (cp.async.bulk + mbarrier)
-//    that land while the residual is computed from global memory;
+// Staged sweep (FP32 arithmetic) for Schwarz blocks whose half volume is a
+// multiple of 32: the thread layout and hop code of k_sap_sweep (four
+// threads per site, one runtime direction each, partial sums combined by
+// warp shuffles), with
+//  * the block's links, A_ee and A_oo^-1 staged into shared memory by bulk
+//    asynchronous copies (cp.async.bulk + mbarrier) that land while the
+//    residual is computed from global memory;
 //  * each thread's block-internal neighbour indices held in registers;
 //  * a programmatic-dependent-launch prologue: barrier set-up and the staging
 //    copies (links and clover are read-only during a solve) are issued before
 //    griddepcontrol.wait, so they overlap the previous sweep's tail.
+// Storage S: FP32 (16-byte units), or BF16 / FP16 (half.cuh: 8-byte units of
+// the same four values, spinors divided by their site norms).
 // ---------------------------------------------------------------------------
 namespace stg {
 
 using f2 = cpx<float>;
 
-// own 3 rows of a staged chiral block ([9][Vh] float4, site h) times v6
-__device__ __forceinline__ void rows3(const float4* Ablk, int Vh, int h, int half, const f2 v6[6], f2 y[3]) {
+// storage traits: unit type of the staged arrays and global loads / stores
+template <class S>
+struct IO;
+template <>
+struct IO<float> {
+  using T = float4;
+  __device__ __forceinline__ static void unpack(const T& t, float* v) {
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  // complex component k of the spinor at site d
+  __device__ __forceinline__ static f2 comp(const float* f, const float*, int d, int Vb, int k) {
+    return ld_comp(f, comp_off<float>(d, Vb, k));
+  }
+  __device__ __forceinline__ static void spinor(const float* f, const float*, int d, int Vb, Spinor<float>& s) {
+    load_spinor_cg<float>(f, d, Vb, s);
+  }
+  __device__ __forceinline__ static void link(const float* g, int d, int Vb, int mu, Link<float>& U) {
+    load_link<float>(g, d, Vb, mu, U);
+  }
+  // 36 values of chirality block cb of site d of a clover field
+  __device__ __forceinline__ static void block36(const float* c, int d, int Vb, int cb, float* P) {
+    load_units<float, CLOVER_NR>(c, d, Vb, cb * 9, 9, P);
+  }
+  // write this thread's 3 components (k0 = 3 sub) of site d
+  __device__ __forceinline__ static void store3(float* f, float*, int d, int Vb, int sub, const f2 v[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st_comp(f, comp_off<float>(d, Vb, 3 * sub + i), v[i]);
+  }
+};
+
+template <class S>
+struct IOH {
+  using T = uint2;
+  __device__ __forceinline__ static void unpack(const T& t, float* v) { unpack4<S>(t, v); }
+  // word of complex component k: unit k / 2, position k % 2 in the unit
+  __device__ __forceinline__ static size_t word(int d, int Vb, int k) {
+    const int B = d / Vb, q = d - B * Vb;
+    return ((size_t)B * 6 + k / 2) * Vb * 2 + (size_t)q * 2 + (k & 1);
+  }
+  __device__ __forceinline__ static f2 comp(const S* f, const float* nrm, int d, int Vb, int k) {
+    const uint32_t w = __ldcg(reinterpret_cast<const unsigned int*>(f) + word(d, Vb, k));
+    const float2 v = H2<S>::unpack(w);
+    const float m = __ldcg(nrm + d);
+    return mk(v.x * m, v.y * m);
+  }
+  __device__ __forceinline__ static void spinor(const S* f, const float* nrm, int d, int Vb, Spinor<float>& s) {
+    load_spinor_h_cg<S>(f, nrm, d, Vb, s);
+  }
+  __device__ __forceinline__ static void link(const S* g, int d, int Vb, int mu, Link<float>& U) {
+    load_link_h<S>(g, d, Vb, mu, U);
+  }
+  __device__ __forceinline__ static void block36(const S* c, int d, int Vb, int cb, float* P) {
+    const size_t b = Layout<float, CLOVER_NR>::base(d, Vb) + (size_t)(cb * 9) * Vb;
+#pragma unroll
+    for (int u = 0; u < 9; ++u) ld4<S>(c, b + (size_t)u * Vb, P + 4 * u);
+  }
+  // the site norm is the largest magnitude over the four threads of the
+  // site (adjacent lanes, combined by shuffles); thread 0 of the site
+  // writes it.  Every lane of the warp must call this.
+  __device__ __forceinline__ static void store3(S* f, float* nrm, int d, int Vb, int sub, const f2 v[3]) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) m = fmaxf(m, fmaxf(fabsf(v[i].re), fabsf(v[i].im)));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    unsigned int* w = reinterpret_cast<unsigned int*>(f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) w[word(d, Vb, 3 * sub + i)] = H2<S>::pack(v[i].re * inv, v[i].im * inv);
+    if (sub == 0) nrm[d] = m;
+  }
+};
+template <>
+struct IO<__half> : IOH<__half> {};
+template <>
+struct IO<__nv_bfloat16> : IOH<__nv_bfloat16> {};
+
+// own 3 rows of a staged chiral block ([9][Vh] units, site h) times v6
+template <class S>
+__device__ __forceinline__ void rows3(const typename IO<S>::T* Ablk, int Vh, int h, int half, const f2 v6[6],
+                                      f2 y[3]) {
   float P[36];
 #pragma unroll
-  for (int u = 0; u < 9; ++u) {
-    float4 t = Ablk[u * Vh + h];
-    P[4 * u] = t.x; P[4 * u + 1] = t.y; P[4 * u + 2] = t.z; P[4 * u + 3] = t.w;
-  }
+  for (int u = 0; u < 9; ++u) IO<S>::unpack(Ablk[u * Vh + h], P + 4 * u);
   f2 y6[6];
   herm6<float>(P, v6, y6);
 #pragma unroll
   for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
 }
 
+// link mu of local site q from the staged block links (rows of Vb + LPAD units)
+template <class S>
+__device__ __forceinline__ void slink(const typename IO<S>::T* sl, int Vbp, int q, int mu, Link<float>& U) {
+  float v[LINK_NR];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) IO<S>::unpack(sl[(mu * 3 + u) * Vbp + q], v + 4 * u);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) U.m[k / 3][k % 3] = mk(v[2 * k], v[2 * k + 1]);
+  complete_link(U);
+}
+
 // hop_block with the neighbour indices already known (-1: outside the block)
-__device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, const f2* buf, int Vbp, int Vh, int q,
-                                            int sub, f2 out[3]) {
+template <class S>
+__device__ __forceinline__ void hop_block_q(int qf, int qb, const typename IO<S>::T* sl, const f2* buf, int Vbp,
+                                            int Vh, int q, int sub, f2 out[3]) {
   Spinor<float> acc;
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
@@ -498,7 +592,7 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, co
     smem_spinor<float>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
     project_rt<float>(nb, dr, -1.f, hh);
     Link<float> U;
-    smem_link<float>(sl, Vbp, q, sub, U);
+    slink<S>(sl, Vbp, q, sub, U);
     su3_mul(U, hh, y);
     accumulate_rt<float>(acc, y, dr, -1.f, 1.f);
   }
@@ -506,9 +600,42 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, co
     smem_spinor<float>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
     project_rt<float>(nb, dr, 1.f, hh);
     Link<float> U;
-    smem_link<float>(sl, Vbp, qb, sub, U);
+    slink<S>(sl, Vbp, qb, sub, U);
     su3_mul_dag(U, hh, y);
     accumulate_rt<float>(acc, y, dr, 1.f, 1.f);
+  }
+  reduce_scatter<float>(acc, sub, out);
+}
+
+// own 3 components of the full (global) hopping sum at device site d
+template <class S>
+__device__ __forceinline__ void hop_global_s(const Geom& g, const S* x, const float* xn, const S* gauge, int d,
+                                             int sub, f2 out[3]) {
+  Spinor<float> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc.c[k] = mk(0.f, 0.f);
+  const Dir<float> dr = make_dir<float>(sub);
+  f2 hh[2][3], y[2][3];
+  Spinor<float> nb;
+  {
+    const uint32_t e = __ldg(g.nbr + (size_t)(2 * sub) * g.V + d);
+    const int n = (int)(e & ~NEG_BIT);
+    IO<S>::spinor(x, xn, n, g.Vb, nb);
+    project_rt<float>(nb, dr, -1.f, hh);
+    Link<float> U;
+    IO<S>::link(gauge, d, g.Vb, sub, U);
+    su3_mul(U, hh, y);
+    accumulate_rt<float>(acc, y, dr, -1.f, (e & NEG_BIT) ? -1.f : 1.f);
+  }
+  {
+    const uint32_t e = __ldg(g.nbr + (size_t)(2 * sub + 1) * g.V + d);
+    const int n = (int)(e & ~NEG_BIT);
+    IO<S>::spinor(x, xn, n, g.Vb, nb);
+    project_rt<float>(nb, dr, 1.f, hh);
+    Link<float> U;
+    IO<S>::link(gauge, n, g.Vb, sub, U);
+    su3_mul_dag(U, hh, y);
+    accumulate_rt<float>(acc, y, dr, 1.f, (e & NEG_BIT) ? -1.f : 1.f);
   }
   reduce_scatter<float>(acc, sub, out);
 }
@@ -516,25 +643,31 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const float4* sl, co
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// bn / xn: site norms of b and x (half storage only; ignored for FP32)
+template <class S>
 __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
-                                                 const float* __restrict__ b, float* __restrict__ x,
-                                                 const float* __restrict__ gauge, const float* __restrict__ clov,
-                                                 const float* __restrict__ clov_inv, int* status,
-                                                 long long wait_limit) {
-  using LYG = Layout<float, GAUGE_NR>;
+                                                 const S* __restrict__ b, const float* __restrict__ bn,
+                                                 S* __restrict__ x, float* __restrict__ xn,
+                                                 const S* __restrict__ gauge, const S* __restrict__ clov,
+                                                 const S* __restrict__ clov_inv, int* status, long long wait_limit) {
+  using T = typename IO<S>::T;
+  constexpr unsigned UB = sizeof(T);            // bytes per unit of four values
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
-  float4* sl = reinterpret_cast<float4*>(smem_raw);                    // [12][Vb + LPAD]
-  float4* Aee = sl + (size_t)LYG::NU * Vbp;                             // [2 cb][9][Vh]
-  float4* Aoi = Aee + 18 * Vh;                                          // [2 cb][9][Vh]
+  T* sl = reinterpret_cast<T*>(smem_raw);                               // [12][Vb + LPAD]
+  T* Aee = sl + (size_t)12 * Vbp;                                       // [2 cb][9][Vh]
+  T* Aoi = Aee + 18 * Vh;                                               // [2 cb][9][Vh]
   f2* E = reinterpret_cast<f2*>(Aoi + 18 * Vh);                         // [12][Vh]
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
   float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
 
   const int B = block_of_colour(g, colour, blockIdx.x);
   const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  const size_t noff = (size_t)blockIdx.y * g.V;
   b += off;
   x += off;
+  if (bn) bn += noff;       // site norms exist for half storage only
+  if (xn) xn += noff;
   const int t = threadIdx.x;
   const int h = t >> 2, sub = t & 3;
   const int cb = sub >> 1, half = sub & 1;
@@ -551,19 +684,19 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   }
   __syncthreads();
   {
-    const unsigned link_row = (unsigned)Vb * 16u, half_row = (unsigned)Vh * 16u;
-    if (t == 0) mbar_expect_tx(&mbar, LYG::NU * link_row + 36u * half_row);
+    const unsigned link_row = (unsigned)Vb * UB, half_row = (unsigned)Vh * UB;
+    if (t == 0) mbar_expect_tx(&mbar, 12u * link_row + 36u * half_row);
     __syncthreads();
-    if (t < LYG::NU) {
-      const float4* src = reinterpret_cast<const float4*>(gauge) + (size_t)B * LYG::NU * Vb;
+    if (t < 12) {
+      const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * 12 * Vb;
       bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
-    } else if (t < LYG::NU + 18) {
-      const int u = t - LYG::NU;
-      const float4* ca = reinterpret_cast<const float4*>(clov) + (size_t)B * 18 * Vb;
+    } else if (t < 12 + 18) {
+      const int u = t - 12;
+      const T* ca = reinterpret_cast<const T*>(clov) + (size_t)B * 18 * Vb;
       bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
-    } else if (t < LYG::NU + 36) {
-      const int u = t - LYG::NU - 18;
-      const float4* ci = reinterpret_cast<const float4*>(clov_inv) + (size_t)B * 18 * Vb;
+    } else if (t < 12 + 36) {
+      const int u = t - 12 - 18;
+      const T* ci = reinterpret_cast<const T*>(clov_inv) + (size_t)B * 18 * Vb;
       bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
     }
   }
@@ -577,13 +710,20 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     const int d = par ? dO : de;
     f2 r[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) r[i] = ld_comp(b, comp_off<float>(d, Vb, 3 * sub + i));
+    for (int i = 0; i < 3; ++i) r[i] = IO<S>::comp(b, bn, d, Vb, 3 * sub + i);
     if (!x_is_zero) {
       f2 hop[3], x6[6], ax[3];
-      hop_global<float>(g, x, gauge, d, sub, hop);
+      hop_global_s<S>(g, x, xn, gauge, d, sub, hop);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) x6[i] = ld_comp(x, comp_off<float>(d, Vb, 6 * cb + i));
-      clover_rows<float>(clov, d, Vb, sub, x6, ax);
+      for (int i = 0; i < 6; ++i) x6[i] = IO<S>::comp(x, xn, d, Vb, 6 * cb + i);
+      {
+        float P[36];
+        IO<S>::block36(clov, d, Vb, cb, P);
+        f2 y6[6];
+        herm6<float>(P, x6, y6);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ax[i] = half ? y6[3 + i] : y6[i];
+      }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         r[i].re -= ax[i].re - 0.5f * hop[i].re;
@@ -606,8 +746,8 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       return;
     }
   }
-  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3(Aoi + cb * 9 * Vh, Vh, h, half, v6, y); };
-  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3(Aee + cb * 9 * Vh, Vh, h, half, v6, y); };
+  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aoi + cb * 9 * Vh, Vh, h, half, v6, y); };
+  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aee + cb * 9 * Vh, Vh, h, half, v6, y); };
   // u_o = A_oo^-1 r_o
   {
     f2 v6[6], u[3];
@@ -621,7 +761,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 res[3], xe[3];
   {
     f2 tt[3];
-    hop_block_q(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
+    hop_block_q<S>(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       res[i] = mk(fmaf(0.5f, tt[i].re, re[i].re), fmaf(0.5f, tt[i].im, re[i].im));
@@ -634,7 +774,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     __syncthreads();
     {  // odd: w = A_oo^-1 (-1/2 hop(res))
       f2 tt[3], v6[6], w[3];
-      hop_block_q(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
+      hop_block_q<S>(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) tt[i] = -0.5f * tt[i];
       chiral6<float>(tt, sub, v6);
@@ -649,7 +789,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       f2 tt[3], v6[6];
       chiral6<float>(res, sub, v6);
       aee_rows(v6, p);
-      hop_block_q(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
+      hop_block_q<S>(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         p[i] = mk(fmaf(0.5f, tt[i].re, p[i].re), fmaf(0.5f, tt[i].im, p[i].im));
@@ -678,23 +818,24 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 eo[3];
   {
     f2 tt[3], v6[6];
-    hop_block_q(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
+    hop_block_q<S>(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) tt[i] = mk(fmaf(0.5f, tt[i].re, ro[i].re), fmaf(0.5f, tt[i].im, ro[i].im));
     chiral6<float>(tt, sub, v6);
     ainv_rows(v6, eo);
   }
+  f2 ve[3], vo[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const size_t oe = comp_off<float>(de, Vb, 3 * sub + i), oo = comp_off<float>(dO, Vb, 3 * sub + i);
-    f2 ve = xe[i], vo = eo[i];
+    ve[i] = xe[i];
+    vo[i] = eo[i];
     if (!x_is_zero) {
-      ve = ve + ld_comp(x, oe);
-      vo = vo + ld_comp(x, oo);
+      ve[i] = ve[i] + IO<S>::comp(x, xn, de, Vb, 3 * sub + i);
+      vo[i] = vo[i] + IO<S>::comp(x, xn, dO, Vb, 3 * sub + i);
     }
-    st_comp(x, oe, ve);
-    st_comp(x, oo, vo);
   }
+  IO<S>::store3(x, xn, de, Vb, sub, ve);
+  IO<S>::store3(x, xn, dO, Vb, sub, vo);
 }
 
 }  // namespace stg
@@ -709,29 +850,42 @@ size_t sap_smem_bytes(const Geom& g, int real_size) {
   return units * 16 + bufs + 100 * sizeof(double);
 }
 
-static size_t sap_stg_smem(const Geom& g) {
+static size_t sap_stg_smem(const Geom& g, int unit_bytes) {
   const int Vh = g.Vb / 2;
-  size_t bytes = (size_t)12 * (g.Vb + LPAD) * 16;               // links
-  bytes += (size_t)2 * 18 * Vh * 16;                            // A_ee, A_oo^-1
-  bytes += (size_t)24 * Vh * 8;                                 // E, O
+  size_t bytes = (size_t)12 * (g.Vb + LPAD) * unit_bytes;      // links
+  bytes += (size_t)2 * 18 * Vh * unit_bytes;                   // A_ee, A_oo^-1
+  bytes += (size_t)24 * Vh * 8;                                // E, O
   bytes += 100 * sizeof(double);
   return bytes;
 }
 
-static bool sap_stg_ok(const Geom& g) {
+static bool sap_stg_ok(const Geom& g, int unit_bytes) {
   const int Vh = g.Vb / 2;
-  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g) <= 226 * 1024;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g, unit_bytes) <= 226 * 1024;
 }
 
-static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const float* b, float* x,
-                              const float* gauge, const float* clover, const float* clover_inv, int nrhs,
+bool sap_half_ok(const Geom& g) { return sap_stg_ok(g, 8); }
+
+template <class S>
+static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const S* b, const float* bn,
+                              S* x, float* xn, const S* gauge, const S* clover, const S* clover_inv, int nrhs,
                               int* status, long long wait_limit, cudaStream_t st) {
-  static size_t cfg = 0;
-  const size_t need = sap_stg_smem(g);
-  if (cfg < need) {
-    cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-    if (e != cudaSuccess) return e;
-    cfg = need;
+  constexpr int UB = sizeof(typename stg::IO<S>::T);
+  const size_t need = sap_stg_smem(g, UB);
+  {
+    // the attribute is per device and per instance; set it on every launch
+    // whose size exceeds what this device's instance was given
+    static std::mutex mu;
+    static size_t cfg[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cfg[dev] < need) {
+      cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      if (e != cudaSuccess) return e;
+      cfg[dev] = need;
+    }
   }
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(g.nb / 2, nrhs);
@@ -744,30 +898,51 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
   lc.attrs = at;
   lc.numAttrs = 1;
   const int zero = x_is_zero ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg, g, colour, mr_iters, zero, b, x, gauge, clover,
+  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg<S>, g, colour, mr_iters, zero, b, bn, x, xn, gauge, clover,
                                      clover_inv, status, wait_limit);
   ++g_launches;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+template <class S>
+cudaError_t sap_sweep_h(const Geom& g, int colour, int mr_iters, bool x_is_zero, const void* b, const float* bn,
+                        void* x, float* xn, const void* gauge, const void* clover, const void* clover_inv, int nrhs,
+                        int* status, long long wait_limit, cudaStream_t st) {
+  if (!sap_half_ok(g)) return cudaErrorInvalidValue;
+  return launch_stg<S>(g, colour, mr_iters, x_is_zero, static_cast<const S*>(b), bn, static_cast<S*>(x), xn,
+                       static_cast<const S*>(gauge), static_cast<const S*>(clover),
+                       static_cast<const S*>(clover_inv), nrhs, status, wait_limit, st);
+}
+template cudaError_t sap_sweep_h<__half>(const Geom&, int, int, bool, const void*, const float*, void*, float*,
+                                         const void*, const void*, const void*, int, int*, long long, cudaStream_t);
+template cudaError_t sap_sweep_h<__nv_bfloat16>(const Geom&, int, int, bool, const void*, const float*, void*,
+                                                float*, const void*, const void*, const void*, int, int*, long long,
+                                                cudaStream_t);
 
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
                       long long wait_limit, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
-    if (sap_stg_ok(g)) {
-      return launch_stg(g, colour, mr_iters, x_is_zero, b, x, gauge, clover, clover_inv, nrhs, status, wait_limit,
-                        st);
+    if (sap_stg_ok(g, 16)) {
+      return launch_stg<float>(g, colour, mr_iters, x_is_zero, b, nullptr, x, nullptr, gauge, clover, clover_inv,
+                               nrhs, status, wait_limit, st);
     }
   }
   int threads = sap_threads(g);
   size_t smem = sap_smem_bytes(g, sizeof(R));
-  static size_t configured[2] = {0, 0};
-  cudaError_t e;
-  if (configured[sizeof(R) == 8] < smem) {
-    e = cudaFuncSetAttribute(k_sap_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[sizeof(R) == 8] = smem;
+  {
+    static std::mutex mu;
+    static size_t configured[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (configured[dev][sizeof(R) == 8] < smem) {
+      cudaError_t e = cudaFuncSetAttribute(k_sap_sweep<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured[dev][sizeof(R) == 8] = smem;
+    }
   }
   dim3 grid(g.nb / 2, nrhs);
   k_sap_sweep<R><<<grid, threads, smem, st>>>(g, colour, mr_iters, x_is_zero ? 1 : 0, b, x, gauge,

@@ -38,10 +38,12 @@ def maxrel(a, b) -> float:
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def assert_close(a, b, tol, what=""):
-    """Norm-wise and element-wise relative errors both below tol."""
+def assert_close(a, b, tol, what="", etol=None):
+    """Norm-wise relative error below tol and element-wise relative error
+    below etol (default tol)."""
+    etol = tol if etol is None else etol
     r, m = rel(a, b), maxrel(a, b)
-    assert r < tol and m < tol, f"{what} norm-wise {r:.3e}, element-wise {m:.3e}, bound {tol:.1e}"
+    assert r < tol and m < etol, f"{what} norm-wise {r:.3e} (bound {tol:.1e}), element-wise {m:.3e} (bound {etol:.1e})"
     return r, m
 
 
