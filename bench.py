@@ -508,6 +508,9 @@ def large_batched():
         return {"error": repr(e)[:400]}
 
 
+LARGE_RUN = dict(precisions=("f32", "bf16", "fp16"), passes=2, oracle_check=True)
+
+
 def large_batched_child():
     """Setup + the 12 point sources as one batch on 32^3 x 64 in each inner
     precision (FP32, then BF16 and FP16 storage), twice each (the first pass
@@ -532,12 +535,14 @@ def large_batched_child():
            "rhs": "12 point sources, one batch", "unit": UNIT, "gauge_generation_s": round(gen_s, 1),
            "timing": "CUDA events, second of two passes"}
     sols = {}
-    for name, prec in (("f32", P.FP32), ("bf16", P.BF16), ("fp16", P.FP16)):
+    precs = {"f32": P.FP32, "bf16": P.BF16, "fp16": P.FP16}
+    for name in LARGE_RUN["precisions"]:
+        prec = precs[name]
         params = P.default_params(L=s["L"], sap_block=s["block"], n_v=s["n_v"], m0=s["m0"], csw=s["csw"],
                                   outer_restart=s["outer_restart"], precision=prec)
         h = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
         try:
-            for _ in range(2):
+            for _ in range(LARGE_RUN["passes"]):
                 torch.cuda.synchronize()
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 ev[0].record(stream)
@@ -559,6 +564,9 @@ def large_batched_child():
         finally:
             h.close()
             torch.cuda.empty_cache()
+    if not LARGE_RUN["oracle_check"]:
+        print(json.dumps(out))
+        return
     # every source's true residual once more with the CPU oracle's own D
     t_or = time.perf_counter()
     del U_dev
@@ -576,7 +584,7 @@ def large_batched_child():
         out[name]["all_converged"] = out[name]["all_converged"] and max(res) <= s["tol"]
     out["oracle_check_s"] = round(time.perf_counter() - t_or, 1)
     # the line's headline for this workload: the BF16-storage batch
-    out["value"] = out["bf16"]["value"]
+    out["value"] = out.get("bf16", out.get("f32", {})).get("value")
     print(json.dumps(out))
 
 
@@ -649,6 +657,27 @@ def stencils(P, torch, stream, pk, pk_kind):
             gbs = byts / (us * 1e-6) / 1e9
             out[name] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
                          "frac": round(gbs / pk["hbm_gbs"], 4), "n_v": s["n_v"]}
+        # a batch of 12 right-hand sides (tensor-core products): the test
+        # vectors once, 12 spinors, per fine site
+        nb_ = 12
+        xfb = xf.reshape((1,) + tuple(xf.shape)).repeat(nb_, 1, 1, 1).contiguous()
+        xcb = xc.reshape((1,) + tuple(xc.shape)).repeat(nb_, 1, 1).contiguous()
+        for name, fn, arg, key in (("restrict_f32_batch12", h.restrict, xfb, "restrict"),
+                                   ("prolong_f32_batch12", h.prolong, xcb, "prolong")):
+            for _ in range(3):
+                fn(arg, P.FP32)
+            h.reset_stats()
+            h.enable_kernel_timing(True)
+            for _ in range(s["reps"]):
+                fn(arg, P.FP32)
+            st = h.stats()
+            h.enable_kernel_timing(False)
+            us = 1e3 * st[key + "_ms"] / st[key + "_launches"]
+            byts = V * (12 * s["n_v"] + 12 * nb_) * 8
+            gbs = byts / (us * 1e-6) / 1e9
+            out[name] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
+                         "frac": round(gbs / pk["hbm_gbs"], 4), "n_v": s["n_v"], "rhs": nb_,
+                         "us_per_rhs": round(us / nb_, 2)}
     finally:
         h.close()
     return out
@@ -789,6 +818,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 32^3 x 64 batched workload")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--large-precisions", default=None,
+                    help="comma list of f32,bf16,fp16 for the 32^3 x 64 workload (default all three)")
+    ap.add_argument("--large-passes", type=int, default=None, help="passes of the 32^3 x 64 workload (default 2)")
+    ap.add_argument("--large-no-oracle", action="store_true", help="skip the oracle residual check (profiling)")
     ap.add_argument("--stencils-only", action="store_true",
                     help="time only the stencils (for profiler captures) and print their JSON")
     ap.add_argument("--stencil-lattice", default=None,
@@ -801,6 +834,12 @@ def main():
         if len(L) != 4 or any(v % 8 for v in L):
             raise SystemExit("--stencil-lattice wants four multiples of 8")
         STENCIL["L"] = L
+    if args.large_precisions:
+        LARGE_RUN["precisions"] = tuple(v for v in args.large_precisions.split(",") if v)
+    if args.large_passes:
+        LARGE_RUN["passes"] = args.large_passes
+    if args.large_no_oracle:
+        LARGE_RUN["oracle_check"] = False
     if args.large_only:
         large_batched_child()
         return

@@ -570,6 +570,10 @@ template <class R> const R* lam_of(ddamg_ctx* h);
 template <> const float* lam_of<float>(ddamg_ctx* h) { return h->lam32; }
 template <> const double* lam_of<double>(ddamg_ctx* h) { return h->lam64; }
 
+// batches of at least this many right-hand sides go through R and P as
+// tensor-core matrix products (one read of the test vectors per 16)
+constexpr int MRHS_MIN = 2;
+
 // R and P of the inner solver (FP16 test vectors when half_vectors is set)
 template <class R>
 cudaError_t restrict_inner(ddamg_ctx* h, const R* in, R* bc, int nf) {
@@ -577,6 +581,9 @@ cudaError_t restrict_inner(ddamg_ctx* h, const R* in, R* bc, int nf) {
     if constexpr (sizeof(R) == 4) {
       const int k = lam_half_kind(h);
       if (k >= 0) return restrict_op_h(h->g, k, h->lam16, h->p.n_v, in, bc, nf, h->st);
+      // a batch: complex products over the right-hand sides on the tensor cores
+      if (nf >= MRHS_MIN && mrhs_ok(h->g, h->p.n_v))
+        return restrict_mrhs(h->g, h->lam32, h->p.n_v, in, bc, nf, h->st);
     }
     return restrict_op<R>(h->g, lam_of<R>(h), h->p.n_v, in, bc, nf, h->st);
   });
@@ -587,6 +594,8 @@ cudaError_t prolong_inner(ddamg_ctx* h, const R* xc, R* out, int nf) {
     if constexpr (sizeof(R) == 4) {
       const int k = lam_half_kind(h);
       if (k >= 0) return prolong_op_h(h->g, k, h->lam16, h->p.n_v, xc, out, nf, false, h->st);
+      if (nf >= MRHS_MIN && mrhs_ok(h->g, h->p.n_v))
+        return prolong_mrhs(h->g, h->lam32, h->p.n_v, xc, out, nf, h->st);
     }
     return prolong_op<R>(h->g, lam_of<R>(h), h->p.n_v, xc, out, nf, false, h->st);
   });

@@ -201,6 +201,15 @@ cudaError_t round_vectors_half(int bf16, float* lam32, void* lam16, size_t n, cu
 template <class R>
 cudaError_t prolong_op(const Geom& g, const R* lam, int n, const R* xc, R* x, int nrhs,
                        bool accumulate, cudaStream_t st);
+// a batch of nrhs right-hand sides through R (Eq. 3) / P (Eq. 4) as complex
+// matrix products per aggregate on the tensor cores (TF32 split into
+// hi + lo parts: FP32 accuracy), each test vector read once per 16
+// right-hand sides; FP32 fields and test vectors, n_v <= 32
+bool mrhs_ok(const Geom& g, int n);
+cudaError_t restrict_mrhs(const Geom& g, const float* lam, int n, const float* b, float* bc, int nrhs,
+                          cudaStream_t st);
+cudaError_t prolong_mrhs(const Geom& g, const float* lam, int n, const float* xc, float* x, int nrhs,
+                         cudaStream_t st);
 // D_c [X][9][2n][2n] from the test vectors; every 2n x 2n block is stored
 // column-major on the device (entry (r, c) at c * 2n + r)
 template <class R>

@@ -661,9 +661,14 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
   float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
 
-  const int B = block_of_colour(g, colour, blockIdx.x);
-  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
-  const size_t noff = (size_t)blockIdx.y * g.V;
+  // CTA c handles right-hand side c % nrhs of block c / nrhs of the colour:
+  // the CTAs of one block run side by side, so the block's links and clover
+  // blocks come from DRAM once and from L2 for the other right-hand sides
+  const int nrhs = gridDim.x / (g.nb / 2);
+  const int rhs = blockIdx.x % nrhs;
+  const int B = block_of_colour(g, colour, blockIdx.x / nrhs);
+  const size_t off = (size_t)rhs * g.V * SPINOR_NR;
+  const size_t noff = (size_t)rhs * g.V;
   b += off;
   x += off;
   if (bn) bn += noff;       // site norms exist for half storage only
@@ -888,7 +893,7 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
     }
   }
   cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(g.nb / 2, nrhs);
+  lc.gridDim = dim3((unsigned)(g.nb / 2) * (unsigned)nrhs);
   lc.blockDim = dim3(2 * g.Vb);
   lc.dynamicSmemBytes = need;
   lc.stream = st;

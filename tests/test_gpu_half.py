@@ -5,11 +5,14 @@ Per-apply bound 2e-2 (norm-wise and element-wise): a stored value carries a
 relative rounding error of at most 2^-9 (BF16) or 2^-12 (FP16, spinors
 scaled by their site norm into [-1, 1]); one D apply combines rounded
 links, clover blocks and spinors in a few dozen FP32 terms per component,
-which keeps its error within a few times that.  Composite steps are bounded
-by the chain they contain: a block solve (about a dozen dependent applies on
-rounded operators) and a SAP application (eight sweeps, each also rounding x
-into storage) are held to 5e-2 in BF16 and 1e-2 in FP16.  Whole solves
-reach the FP64 true residual 1e-10 through the FP64 outer FGMRES.
+which keeps its error within a few times that (measured on a GB300: BF16
+2.4e-3 norm-wise, 4.1e-3 element-wise; FP16 3.0e-4 and 4.1e-4).  The
+composite steps stay within the same bound: a block solve (about a dozen
+dependent applies on the rounded operators) and a SAP application (eight
+sweeps, each also rounding x into storage) contract the rounding errors
+rather than adding them (measured: BF16 2.9e-3 / 3.9e-3, FP16 3.6e-4 /
+5.8e-4).  Whole solves reach the FP64 true residual 1e-10 through the FP64
+outer FGMRES.
 """
 from __future__ import annotations
 
@@ -25,8 +28,8 @@ pytestmark = pytest.mark.gpu
 
 TOL_HALF = 2e-2
 # composite steps: (BF16, FP16)
-TOL_BLOCK = {2: 5e-2, 3: 1e-2}
-TOL_SAP = {2: 5e-2, 3: 1e-2}
+TOL_BLOCK = {2: 2e-2, 3: 2e-2}
+TOL_SAP = {2: 2e-2, 3: 2e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
