@@ -754,13 +754,13 @@ ddamg_status half_operators(ddamg_ctx* h, int k) {
     TRY(dalloc(h, &h->AiH[k], V * 72 * 2));
   }
   if (k == 0) {
-    CK(to_half<__half>(h->g32, h->gH[k], V * 48, h->st));
-    CK(to_half<__half>(h->A32, h->AH[k], V * 72, h->st));
-    CK(to_half<__half>(h->Ai32, h->AiH[k], V * 72, h->st));
+    CK(to_half<__half>(h->g, h->g32, h->gH[k], 48, h->st));
+    CK(to_half<__half>(h->g, h->A32, h->AH[k], 72, h->st));
+    CK(to_half<__half>(h->g, h->Ai32, h->AiH[k], 72, h->st));
   } else {
-    CK(to_half<__nv_bfloat16>(h->g32, h->gH[k], V * 48, h->st));
-    CK(to_half<__nv_bfloat16>(h->A32, h->AH[k], V * 72, h->st));
-    CK(to_half<__nv_bfloat16>(h->Ai32, h->AiH[k], V * 72, h->st));
+    CK(to_half<__nv_bfloat16>(h->g, h->g32, h->gH[k], 48, h->st));
+    CK(to_half<__nv_bfloat16>(h->g, h->A32, h->AH[k], 72, h->st));
+    CK(to_half<__nv_bfloat16>(h->g, h->Ai32, h->AiH[k], 72, h->st));
   }
   h->h_gen[k] = h->op_gen;
   return DDAMG_OK;

@@ -105,9 +105,9 @@ cudaError_t spinor_to_half(const Geom& g, const float* src, void* dst, float* nr
 template <class S>
 cudaError_t spinor_from_half(const Geom& g, const void* src, const float* nrm, float* dst, int nf, bool accumulate,
                              cudaStream_t st);
-// n FP32 values of a block-major field (links, clover, test vectors) -> half
+// an FP32 field of nr reals per site (links 48, clover 72) -> the half layout
 template <class S>
-cudaError_t to_half(const float* src, void* dst, size_t n, cudaStream_t st);
+cudaError_t to_half(const Geom& g, const float* src, void* dst, int nr, cudaStream_t st);
 
 // ---- BLAS-1 on flat complex arrays (n complex numbers) -------------------------
 // partial sums per CTA land in `scratch` (>= reduce_scratch_len(k) doubles)

@@ -163,7 +163,7 @@ __device__ __forceinline__ void load_lam(const R* lam, int d, int Vb, Spinor<R>&
 }
 template <class S>
 __device__ __forceinline__ void load_lam_h(const S* lam, int d, int Vb, Spinor<float>& s) {
-  load_site_h<S, SPINOR_NR>(lam, d, Vb, reinterpret_cast<float*>(s.c));
+  load_site_h4<S, SPINOR_NR>(lam, d, Vb, reinterpret_cast<float*>(s.c));
 }
 __device__ __forceinline__ void load_lam(const __half* lam, int d, int Vb, Spinor<float>& s) {
   load_lam_h<__half>(lam, d, Vb, s);

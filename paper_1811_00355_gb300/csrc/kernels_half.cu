@@ -3,8 +3,9 @@
 //
 // D x = A x - 1/2 sum_mu [(1-g_mu) U_mu(x) x(x+mu) + (1+g_mu) U_mu(x-mu)^H x(x-mu)]
 // (paper Sec. 1 and 3) with links, the two packed clover blocks and the
-// spinors read from half fields: per site 48 + 4 bytes of input spinor, 96
-// of links (two rows of four links), 144 of clover, 48 + 4 of output.
+// spinors read from half fields (16-byte units of eight values): per site
+// 48 + 4 bytes of input spinor, 96 of links (two rows of four links), 144 of
+// clover, 48 + 4 of output.
 #include "half.cuh"
 #include "kernels.h"
 
@@ -117,17 +118,20 @@ __global__ void k_spinor_from_half(Geom g, const S* __restrict__ src, const floa
   store_spinor<float>(dst + off, d, g.Vb, s);
 }
 
-// an FP32 array in the block-major layout -> the same array in half units
-// (four values per unit in both, so the order is element for element)
+// an FP32 field of nr reals per site (FP32 layout, 16-byte units of four)
+// -> the half layout (16-byte units of eight): half unit j of a site holds
+// FP32 units 2 j and 2 j + 1
 template <class S>
-__global__ void k_to_half(const float* __restrict__ src, S* __restrict__ dst, size_t n4) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; i < n4; i += stride) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + i);
-    const float w[4] = {v.x, v.y, v.z, v.w};
-    st4<S>(dst, i, w);
-  }
+__global__ void k_to_half(Geom g, const float* __restrict__ src, S* __restrict__ dst, int nu8) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)g.V * nu8) return;
+  const int d = (int)(i % g.V), j = (int)(i / g.V);
+  const int B = d / g.Vb, q = d - B * g.Vb;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  const size_t b4 = (size_t)B * (2 * nu8) * g.Vb + q;
+  const float4 a = __ldg(s4 + b4 + (size_t)(2 * j) * g.Vb), c = __ldg(s4 + b4 + (size_t)(2 * j + 1) * g.Vb);
+  const float w[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+  st8<S>(dst, ((size_t)B * nu8 + j) * g.Vb + q, w);
 }
 
 }  // namespace
@@ -170,12 +174,11 @@ cudaError_t spinor_from_half(const Geom& g, const void* src, const float* nrm, f
 }
 
 template <class S>
-cudaError_t to_half(const float* src, void* dst, size_t n, cudaStream_t st) {
-  const size_t n4 = n / 4;
-  unsigned nb = nblk(n4, 256);
-  if (nb > 4096) nb = 4096;
-  if (!nb) return cudaSuccess;
-  k_to_half<S><<<nb, 256, 0, st>>>(src, static_cast<S*>(dst), n4);
+cudaError_t to_half(const Geom& g, const float* src, void* dst, int nr, cudaStream_t st) {
+  const int nu8 = nr / 8;
+  const size_t n = (size_t)g.V * nu8;
+  if (!n) return cudaSuccess;
+  k_to_half<S><<<nblk(n, 256), 256, 0, st>>>(g, src, static_cast<S*>(dst), nu8);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -186,7 +189,7 @@ cudaError_t to_half(const float* src, void* dst, size_t n, cudaStream_t st) {
   template cudaError_t spinor_to_half<S>(const Geom&, const float*, void*, float*, int, cudaStream_t);         \
   template cudaError_t spinor_from_half<S>(const Geom&, const void*, const float*, float*, int, bool,           \
                                            cudaStream_t);                                                      \
-  template cudaError_t to_half<S>(const float*, void*, size_t, cudaStream_t);
+  template cudaError_t to_half<S>(const Geom&, const float*, void*, int, cudaStream_t);
 
 INST_H(__half)
 INST_H(__nv_bfloat16)

@@ -44,16 +44,23 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-// d += a b with both operands split (small terms first)
-__device__ __forceinline__ void mma3(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
-  uint32_t ah[4], al[4], bh[2], bl[2];
+// an operand fragment split into TF32 parts
+template <int N>
+struct Split {
+  uint32_t hi[N], lo[N];
+};
+template <int N>
+__device__ __forceinline__ Split<N> split_frag(const float (&v)[N]) {
+  Split<N> s;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) split(a[e], ah[e], al[e]);
-#pragma unroll
-  for (int e = 0; e < 2; ++e) split(b[e], bh[e], bl[e]);
-  mma_tf32(d, al, bh);
-  mma_tf32(d, ah, bl);
-  mma_tf32(d, ah, bh);
+  for (int e = 0; e < N; ++e) split(v[e], s.hi[e], s.lo[e]);
+  return s;
+}
+// d += a b from split operands (small terms first)
+__device__ __forceinline__ void mma3(float (&d)[4], const Split<4>& a, const Split<2>& b) {
+  mma_tf32(d, a.lo, b.hi);
+  mma_tf32(d, a.hi, b.lo);
+  mma_tf32(d, a.hi, b.hi);
 }
 
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
@@ -129,20 +136,34 @@ __global__ void __launch_bounds__(MT_THREADS) k_restrict_mma(Geom g, const float
       __syncthreads();
       const float* A = As[cur];
       const float* B = Bs[cur];
+      // the chunk's products go to fresh accumulators that are then added
+      // to the running sums with ordinary FP32 additions: the tensor cores'
+      // accumulation never runs over more than one chunk
+      float part[2][4][4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) part[a][c2][e] = 0.f;
       for (int ks = warp; ks < ksteps; ks += MT_THREADS / 32) {
         const int k0 = 8 * ks;
-        float bf[4][2];
+        Split<2> bs[4];
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
           const int col = nt * 8 + gq;
+          const bool raw = col < N, live = col < 2 * N;
+          const int r = raw ? col : (live ? col - N : 0);
+          float bv[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int k = k0 + tq + 4 * h;
-            float v = 0.f;
-            if (col < N) v = B[col * RSTR + k];
-            else if (col < 2 * N) v = (k & 1) ? -B[(col - N) * RSTR + k - 1] : B[(col - N) * RSTR + k + 1];
-            bf[nt][h] = v;
+            const float v1 = B[r * RSTR + k], v2 = B[r * RSTR + (k ^ 1)];
+            // b~ = (im, -re): at a real slot the imaginary part, at an imaginary slot minus the real part
+            const float rot = (k & 1) ? -v2 : v2;
+            bv[h] = live ? (raw ? v1 : rot) : 0.f;
           }
+          bs[nt] = split_frag<2>(bv);
         }
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
@@ -153,11 +174,18 @@ __global__ void __launch_bounds__(MT_THREADS) k_restrict_mma(Geom g, const float
           af[1] = r_hi < n ? A[r_hi * RSTR + k0 + tq] : 0.f;
           af[2] = r_lo < n ? A[r_lo * RSTR + k0 + tq + 4] : 0.f;
           af[3] = r_hi < n ? A[r_hi * RSTR + k0 + tq + 4] : 0.f;
+          const Split<4> as = split_frag<4>(af);
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt)
-            if (nt < NT) mma3(acc[mt][nt], af, bf[nt]);
+            if (nt < NT) mma3(part[mt][nt], as, bs[nt]);
         }
       }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[a][c2][e] += part[a][c2][e];
       __syncthreads();     // the buffer is refilled two chunks later
     }
     // sum the warps' partial products (the staging buffers are free now)
@@ -243,16 +271,18 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
           for (int e = 0; e < 4; ++e) {
             const int m = (e & 1) ? m_hi : m_lo;
             const int j = k0 + tq + ((e & 2) ? 4 : 0);
-            float v = 0.f;
-            if (j < n) v = Lm[j * PSTR + m];
-            else if (j < 2 * n) v = (m & 1) ? Lm[(j - n) * PSTR + m - 1] : -Lm[(j - n) * PSTR + m + 1];
-            af[e] = v;
+            // lam~ = (-im, re): at a real row minus the imaginary part, at an imaginary row the real part
+            const bool raw = j < n, live = j < 2 * n;
+            const int jj = raw ? j : (live ? j - n : 0);
+            const float v1 = Lm[jj * PSTR + m], v2 = Lm[jj * PSTR + (m ^ 1)];
+            af[e] = live ? (raw ? v1 : ((m & 1) ? v2 : -v2)) : 0.f;
           }
+          const Split<4> as = split_frag<4>(af);
 #pragma unroll
           for (int nt = 0; nt < 2; ++nt) {
             if (nt >= NT) break;
             const float bf[2] = {Cs[(k0 + tq) * 16 + nt * 8 + gq], Cs[(k0 + tq + 4) * 16 + nt * 8 + gq]};
-            mma3(acc[nt], af, bf);
+            mma3(acc[nt], as, split_frag<2>(bf));
           }
         }
 #pragma unroll

@@ -483,8 +483,24 @@ struct IO;
 template <>
 struct IO<float> {
   using T = float4;
+  static constexpr int LINK_U = 12;   // 16-byte units per site: links
+  static constexpr int CLOV_U = 18;   // clover blocks
   __device__ __forceinline__ static void unpack(const T& t, float* v) {
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  // 36 values of chiral block cb from a staged clover array ([units][Vh], site h)
+  __device__ __forceinline__ static void block_smem(const T* A, int Vh, int h, int cb, float* P) {
+#pragma unroll
+    for (int u = 0; u < 9; ++u) unpack(A[(9 * cb + u) * Vh + h], P + 4 * u);
+  }
+  // link mu of local site q from the staged links (rows of Vbp units)
+  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+    float v[LINK_NR];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) unpack(sl[(mu * 3 + u) * Vbp + q], v + 4 * u);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U.m[k / 3][k % 3] = mk(v[2 * k], v[2 * k + 1]);
+    complete_link(U);
   }
   // complex component k of the spinor at site d
   __device__ __forceinline__ static f2 comp(const float* f, const float*, int d, int Vb, int k) {
@@ -509,12 +525,28 @@ struct IO<float> {
 
 template <class S>
 struct IOH {
-  using T = uint2;
-  __device__ __forceinline__ static void unpack(const T& t, float* v) { unpack4<S>(t, v); }
-  // word of complex component k: unit k / 2, position k % 2 in the unit
+  using T = uint4;
+  static constexpr int LINK_U = HGAUGE_NU;
+  static constexpr int CLOV_U = HCLOV_NU;
+  __device__ __forceinline__ static void unpack(const T& t, float* v) { unpack8<S>(t, v); }
+  // chiral block cb: units 4 cb .. 4 cb + 4, offset 4 cb
+  __device__ __forceinline__ static void block_smem(const T* A, int Vh, int h, int cb, float* P) {
+    float v[40];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) unpack(A[(4 * cb + u) * Vh + h], v + 8 * u);
+#pragma unroll
+    for (int k = 0; k < 36; ++k) P[k] = cb ? v[4 + k] : v[k];
+  }
+  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+    float v[16];
+    const int u0 = link_unit(mu);
+    unpack(sl[u0 * Vbp + q], v);
+    unpack(sl[(u0 + 1) * Vbp + q], v + 8);
+    link_from16(v, mu, U);
+  }
+  // 32-bit word of complex component k: unit k / 4, position k % 4
   __device__ __forceinline__ static size_t word(int d, int Vb, int k) {
-    const int B = d / Vb, q = d - B * Vb;
-    return ((size_t)B * 6 + k / 2) * Vb * 2 + (size_t)q * 2 + (k & 1);
+    return hunit<HSPIN_NU>(d, Vb, k >> 2) * 4 + (k & 3);
   }
   __device__ __forceinline__ static f2 comp(const S* f, const float* nrm, int d, int Vb, int k) {
     const uint32_t w = __ldcg(reinterpret_cast<const unsigned int*>(f) + word(d, Vb, k));
@@ -529,9 +561,7 @@ struct IOH {
     load_link_h<S>(g, d, Vb, mu, U);
   }
   __device__ __forceinline__ static void block36(const S* c, int d, int Vb, int cb, float* P) {
-    const size_t b = Layout<float, CLOVER_NR>::base(d, Vb) + (size_t)(cb * 9) * Vb;
-#pragma unroll
-    for (int u = 0; u < 9; ++u) ld4<S>(c, b + (size_t)u * Vb, P + 4 * u);
+    load_block36_h<S>(c, d, Vb, cb, P);
   }
   // the site norm is the largest magnitude over the four threads of the
   // site (adjacent lanes, combined by shuffles); thread 0 of the site
@@ -554,28 +584,22 @@ struct IO<__half> : IOH<__half> {};
 template <>
 struct IO<__nv_bfloat16> : IOH<__nv_bfloat16> {};
 
-// own 3 rows of a staged chiral block ([9][Vh] units, site h) times v6
+// own 3 rows of a staged chiral block (site h) times v6
 template <class S>
-__device__ __forceinline__ void rows3(const typename IO<S>::T* Ablk, int Vh, int h, int half, const f2 v6[6],
+__device__ __forceinline__ void rows3(const typename IO<S>::T* A, int Vh, int h, int cb, int half, const f2 v6[6],
                                       f2 y[3]) {
   float P[36];
-#pragma unroll
-  for (int u = 0; u < 9; ++u) IO<S>::unpack(Ablk[u * Vh + h], P + 4 * u);
+  IO<S>::block_smem(A, Vh, h, cb, P);
   f2 y6[6];
   herm6<float>(P, v6, y6);
 #pragma unroll
   for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
 }
 
-// link mu of local site q from the staged block links (rows of Vb + LPAD units)
+// link mu of local site q from the staged block links
 template <class S>
 __device__ __forceinline__ void slink(const typename IO<S>::T* sl, int Vbp, int q, int mu, Link<float>& U) {
-  float v[LINK_NR];
-#pragma unroll
-  for (int u = 0; u < 3; ++u) IO<S>::unpack(sl[(mu * 3 + u) * Vbp + q], v + 4 * u);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) U.m[k / 3][k % 3] = mk(v[2 * k], v[2 * k + 1]);
-  complete_link(U);
+  IO<S>::link_smem(sl, Vbp, q, mu, U);
 }
 
 // hop_block with the neighbour indices already known (-1: outside the block)
@@ -651,13 +675,14 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
                                                  const S* __restrict__ gauge, const S* __restrict__ clov,
                                                  const S* __restrict__ clov_inv, int* status, long long wait_limit) {
   using T = typename IO<S>::T;
-  constexpr unsigned UB = sizeof(T);            // bytes per unit of four values
+  constexpr unsigned UB = sizeof(T);            // bytes per unit
+  constexpr int LU = IO<S>::LINK_U, CU = IO<S>::CLOV_U;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
-  T* sl = reinterpret_cast<T*>(smem_raw);                               // [12][Vb + LPAD]
-  T* Aee = sl + (size_t)12 * Vbp;                                       // [2 cb][9][Vh]
-  T* Aoi = Aee + 18 * Vh;                                               // [2 cb][9][Vh]
-  f2* E = reinterpret_cast<f2*>(Aoi + 18 * Vh);                         // [12][Vh]
+  T* sl = reinterpret_cast<T*>(smem_raw);                               // [LU][Vb + LPAD]
+  T* Aee = sl + (size_t)LU * Vbp;                                       // [CU][Vh]
+  T* Aoi = Aee + CU * Vh;                                               // [CU][Vh]
+  f2* E = reinterpret_cast<f2*>(Aoi + CU * Vh);                         // [12][Vh]
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
   float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
 
@@ -690,18 +715,18 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   __syncthreads();
   {
     const unsigned link_row = (unsigned)Vb * UB, half_row = (unsigned)Vh * UB;
-    if (t == 0) mbar_expect_tx(&mbar, 12u * link_row + 36u * half_row);
+    if (t == 0) mbar_expect_tx(&mbar, (unsigned)LU * link_row + 2u * CU * half_row);
     __syncthreads();
-    if (t < 12) {
-      const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * 12 * Vb;
+    if (t < LU) {
+      const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * LU * Vb;
       bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
-    } else if (t < 12 + 18) {
-      const int u = t - 12;
-      const T* ca = reinterpret_cast<const T*>(clov) + (size_t)B * 18 * Vb;
+    } else if (t < LU + CU) {
+      const int u = t - LU;
+      const T* ca = reinterpret_cast<const T*>(clov) + (size_t)B * CU * Vb;
       bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
-    } else if (t < 12 + 36) {
-      const int u = t - 12 - 18;
-      const T* ci = reinterpret_cast<const T*>(clov_inv) + (size_t)B * 18 * Vb;
+    } else if (t < LU + 2 * CU) {
+      const int u = t - LU - CU;
+      const T* ci = reinterpret_cast<const T*>(clov_inv) + (size_t)B * CU * Vb;
       bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
     }
   }
@@ -751,8 +776,8 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       return;
     }
   }
-  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aoi + cb * 9 * Vh, Vh, h, half, v6, y); };
-  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aee + cb * 9 * Vh, Vh, h, half, v6, y); };
+  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aoi, Vh, h, cb, half, v6, y); };
+  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aee, Vh, h, cb, half, v6, y); };
   // u_o = A_oo^-1 r_o
   {
     f2 v6[6], u[3];
@@ -855,28 +880,30 @@ size_t sap_smem_bytes(const Geom& g, int real_size) {
   return units * 16 + bufs + 100 * sizeof(double);
 }
 
-static size_t sap_stg_smem(const Geom& g, int unit_bytes) {
+// shared memory of the staged kernel: link rows (LU units per site, padded),
+// the even half of A and the odd half of A^-1 (CU units per site each), the
+// even and odd work vectors and the reduction slots; 16-byte units
+static size_t sap_stg_smem(const Geom& g, int LU, int CU) {
   const int Vh = g.Vb / 2;
-  size_t bytes = (size_t)12 * (g.Vb + LPAD) * unit_bytes;      // links
-  bytes += (size_t)2 * 18 * Vh * unit_bytes;                   // A_ee, A_oo^-1
-  bytes += (size_t)24 * Vh * 8;                                // E, O
+  size_t bytes = (size_t)LU * (g.Vb + LPAD) * 16;
+  bytes += (size_t)2 * CU * Vh * 16;
+  bytes += (size_t)24 * Vh * 8;
   bytes += 100 * sizeof(double);
   return bytes;
 }
 
-static bool sap_stg_ok(const Geom& g, int unit_bytes) {
+static bool sap_stg_ok(const Geom& g, int LU, int CU) {
   const int Vh = g.Vb / 2;
-  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g, unit_bytes) <= 226 * 1024;
+  return Vh % 32 == 0 && 4 * Vh <= 512 && sap_stg_smem(g, LU, CU) <= 226 * 1024;
 }
 
-bool sap_half_ok(const Geom& g) { return sap_stg_ok(g, 8); }
+bool sap_half_ok(const Geom& g) { return sap_stg_ok(g, HGAUGE_NU, HCLOV_NU); }
 
 template <class S>
 static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const S* b, const float* bn,
                               S* x, float* xn, const S* gauge, const S* clover, const S* clover_inv, int nrhs,
                               int* status, long long wait_limit, cudaStream_t st) {
-  constexpr int UB = sizeof(typename stg::IO<S>::T);
-  const size_t need = sap_stg_smem(g, UB);
+  const size_t need = sap_stg_smem(g, stg::IO<S>::LINK_U, stg::IO<S>::CLOV_U);
   {
     // the attribute is per device and per instance; set it on every launch
     // whose size exceeds what this device's instance was given
@@ -929,7 +956,7 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
                       long long wait_limit, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
-    if (sap_stg_ok(g, 16)) {
+    if (sap_stg_ok(g, 12, 18)) {
       return launch_stg<float>(g, colour, mr_iters, x_is_zero, b, nullptr, x, nullptr, gauge, clover, clover_inv,
                                nrhs, status, wait_limit, st);
     }
