@@ -620,6 +620,23 @@ def stencils(P, torch, stream, pk, pk_kind):
             gbs = byts / (us * 1e-6) / 1e9
             out[name] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
                          "frac": round(gbs / pk["hbm_gbs"], 4)}
+        # one SAP application (4 cycles of the two colours from a zero start,
+        # single right-hand side): per sweep the sites of one colour read b,
+        # x (and their neighbours' x, from L2), links, A, A^-1 and write x
+        for name, prec, rs, extra in (("sap_sweep_f32", P.FP32, 4, 0), ("sap_sweep_bf16", P.BF16, 2, 12)):
+            for _ in range(2):
+                h.sap(x, prec)
+            h.reset_stats()
+            h.enable_kernel_timing(True)
+            for _ in range(3):
+                h.sap(x, prec)
+            st = h.stats()
+            h.enable_kernel_timing(False)
+            us = 1e3 * st["sap_ms"] / st["sap_launches"]
+            byts = (V // 2) * ((24 + 24 + 24 + 48 + 72 + 72) * rs + extra)
+            gbs = byts / (us * 1e-6) / 1e9
+            out[name] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
+                         "frac": round(gbs / pk["hbm_gbs"], 4), "sweeps_timed": st["sap_launches"]}
         del x
         h.run_setup()                      # device-drawn test vectors, SAP, orthonormalise, D_c
         n2 = 2 * s["n_v"]

@@ -199,131 +199,6 @@ struct CGA {
   long long spin_limit;   // polls of a barrier wait before it gives up
 };
 
-// ---------------------------------------------------------------------------
-// Tensor-core form of the multi-right-hand-side block product (FP32, at
-// least four right-hand sides): out = sum_d M_d sv_d is one real matrix
-// product of the 2n2 x 2K real form of [M_d0 .. M_d1-1] (K = ND n2 complex
-// columns; complex entry m becomes the 2 x 2 block [[re, -im], [im, re]])
-// with the 2K x NR real form of the staged vectors, on mma.sync m16n8k8
-// with TF32 operands split into hi + lo parts (FP32 accuracy).  Warps take
-// (row tile, column tile, slice of the inner dimension) jobs; the slices'
-// partial sums meet in the mvp buffer and are added in a fixed order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t cg_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void cg_mma(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <int NR, bool SM>
-__device__ __forceinline__ void mrhs_matvec_tc(const cpx<float>* __restrict__ M, const cpx<float>* sv, int d0, int d1,
-                                               int n2, cpx<float>* mvp, cpx<float>* out, int out_stride,
-                                               bool m_from_d0) {
-  float* part = reinterpret_cast<float*>(mvp);
-  const int ND = d1 - d0;
-  const int rows = 2 * n2;                   // real output rows
-  const int MT = (rows + 15) / 16;
-  constexpr int NT = (NR + 7) / 8;
-  const int RP = MT * 16, CP = NT * 8;       // padded partial-sum tile
-  const int kreal = 2 * ND * n2;             // real inner dimension
-  const int KST = (kreal + 7) / 8;           // steps of 8
-  const int tiles = MT * NT;
-  const int nwarp = blockDim.x >> 5;
-  const int cap = (mvp_groups(NR) * NR * n2 * 2) / (RP * CP);   // slices the buffer holds
-  int KS = nwarp / tiles;
-  if (KS > cap) KS = cap;
-  if (KS > KST) KS = KST;
-  if (KS < 1) KS = 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-  const int mb = m_from_d0 ? 0 : d0;          // block index of direction d0 in M
-  for (int job = warp; job < tiles * KS; job += nwarp) {
-    const int tile = job % tiles, ks = job / tiles;
-    const int mt = tile % MT, nt = tile / MT;
-    const int s_lo = (KST * ks) / KS, s_hi = (KST * (ks + 1)) / KS;
-    const int row_lo = mt * 16 + gq, row_hi = row_lo + 8;
-    const int pr = gq & 1;                   // output row: real (0) or imaginary (1) part
-    const int col = nt * 8 + gq;             // right-hand side of this lane's B values
-    const bool col_ok = col < NR;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int st = s_lo; st < s_hi; ++st) {
-      // the step's 4 complex columns start at kc0; column kc0 + j lies in
-      // direction block dl (+1 where it passes the block's end)
-      const int kc0 = 4 * st;
-      const int dl0 = kc0 / n2, c0 = kc0 - dl0 * n2;
-      float av[4], bv[2];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int row = (e & 1) ? row_hi : row_lo;
-        const int jj = (tq >> 1) + ((e & 2) ? 2 : 0);        // complex column within the step
-        const int pc = tq & 1;                                 // real / imaginary input part
-        int c = c0 + jj, dl = dl0;
-        if (c >= n2) { c -= n2; ++dl; }
-        float v = 0.f;
-        if (row < rows && dl < ND) {
-          const size_t idx = ((size_t)(mb + dl) * n2 + c) * n2 + (row >> 1);
-          cpx<float> m;
-          if constexpr (SM) m = M[idx];
-          else {
-            const float2 t = __ldg(reinterpret_cast<const float2*>(M) + idx);
-            m = mk(t.x, t.y);
-          }
-          v = (pr == pc) ? m.re : (pr == 0 ? -m.im : m.im);
-        }
-        av[e] = v;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int jj = (tq >> 1) + 2 * h;
-        int c = c0 + jj, dl = dl0;
-        if (c >= n2) { c -= n2; ++dl; }
-        float v = 0.f;
-        if (col_ok && dl < ND) {
-          const cpx<float> x = sv[((size_t)col * 9 + d0 + dl) * n2 + c];
-          v = (tq & 1) ? x.im : x.re;
-        }
-        bv[h] = v;
-      }
-      uint32_t ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        ah[e] = cg_tf32(av[e]);
-        al[e] = cg_tf32(av[e] - __uint_as_float(ah[e]));
-      }
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        bh[e] = cg_tf32(bv[e]);
-        bl[e] = cg_tf32(bv[e] - __uint_as_float(bh[e]));
-      }
-      cg_mma(acc, al, bh);
-      cg_mma(acc, ah, bl);
-      cg_mma(acc, ah, bh);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = (e >= 2) ? row_hi : row_lo;
-      const int cc = nt * 8 + 2 * tq + (e & 1);
-      part[((size_t)ks * RP + row) * CP + cc] = acc[e];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < NR * n2; idx += blockDim.x) {
-    const int r = idx / n2, row = idx - r * n2;
-    float re = 0.f, im = 0.f;
-    for (int ks = 0; ks < KS; ++ks) {
-      re += part[((size_t)ks * RP + 2 * row) * CP + r];
-      im += part[((size_t)ks * RP + 2 * row + 1) * CP + r];
-    }
-    out[(size_t)r * out_stride + row] = mk(re, im);
-  }
-  __syncthreads();
-}
-
 // Multi-right-hand-side block product on one coarse site, whole CTA:
 //   out[r][row] = sum_{d in [d0, d1)} sum_c M_d[row][c] sv[r][d][c]
 // Blocks are column-major, so a thread streams RPU rows down the columns
@@ -338,10 +213,6 @@ template <class R, int NR, bool SM = false>
 __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const cpx<R>* sv, int d0, int d1,
                                             int n2, cpx<R>* mvp, cpx<R>* out, int out_stride,
                                             bool m_from_d0 = false) {
-  if constexpr (sizeof(R) == 4 && NR >= 4) {
-    mrhs_matvec_tc<NR, SM>(M, sv, d0, d1, n2, mvp, out, out_stride, m_from_d0);
-    return;
-  }
   using T = typename U16<R>::T;
   constexpr int RPU = 16 / (2 * sizeof(R));
   const int NP = n2 / RPU;

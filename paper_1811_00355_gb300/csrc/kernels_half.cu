@@ -47,8 +47,10 @@ __device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x
 }
 
 // one thread per site; right-hand side blockIdx.y (fields V sites apart)
+// at most 64 registers: eight CTAs per SM keep more loads in flight (the
+// kernel waits on memory latency, not on arithmetic)
 template <class S, int MODE>
-__global__ void __launch_bounds__(TPB) k_dslash_h(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
+__global__ void __launch_bounds__(TPB, 8) k_dslash_h(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
                                                   const S* __restrict__ b, const float* __restrict__ bn,
                                                   S* __restrict__ y, float* __restrict__ yn,
                                                   const S* __restrict__ gauge, const S* __restrict__ clover) {

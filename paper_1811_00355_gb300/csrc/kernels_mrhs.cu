@@ -28,6 +28,8 @@ constexpr int MT_THREADS = 256;   // 8 warps
 constexpr int MAXRQ = 64;         // sites per staged chunk
 constexpr int RSTR = 4 * MAXRQ + 4;   // row stride (floats) of the restriction's staged rows
 constexpr int PSTR = 4 * MAXRQ + 8;   // of the prolongation's
+constexpr int OSTR = 4 * MAXRQ + 4;   // row stride of the prolongation's output tile
+constexpr int CSTR = 24;              // row stride of its staged coarse coefficients
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -227,8 +229,8 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
   const size_t fstride = (size_t)g.V * SPINOR_NR;
   const int KG = ((2 * n + 7) / 8) * 8;        // inner dimension, padded to whole steps
   float* Ls[2] = {msh, msh + (size_t)n * PSTR};
-  float* Cs = msh + (size_t)2 * n * PSTR;       // [KG][16]
-  float* Os = Cs + (size_t)KG * 16;             // [16][4 rq] (output tile)
+  float* Cs = msh + (size_t)2 * n * PSTR;       // [KG][CSTR] (16 columns used)
+  float* Os = Cs + (size_t)KG * CSTR;           // [16][OSTR] (output tile)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   const int NT = (N + 7) / 8;
   const int nchunk = 3 * (g.Vb / rq);
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
         const cpx<float> c = xc[((size_t)(r0 + r) * g.nb + X) * 2 * n + s * n + (j < n ? j : j - n)];
         v = j < n ? c.re : c.im;
       }
-      Cs[idx] = v;
+      Cs[j * CSTR + r] = v;
     }
     stage_rows(Ls[0], PSTR, lam, fstride, n, chunk_off(X, g.Vb, s, 0, rq), rq);
     cp_commit();
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
 #pragma unroll
           for (int nt = 0; nt < 2; ++nt) {
             if (nt >= NT) break;
-            const float bf[2] = {Cs[(k0 + tq) * 16 + nt * 8 + gq], Cs[(k0 + tq + 4) * 16 + nt * 8 + gq]};
+            const float bf[2] = {Cs[(k0 + tq) * CSTR + nt * 8 + gq], Cs[(k0 + tq + 4) * CSTR + nt * 8 + gq]};
             mma3(acc[nt], as, split_frag<2>(bf));
           }
         }
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
           for (int e = 0; e < 4; ++e) {
             const int m = (e >= 2) ? m_hi : m_lo;
             const int r = nt * 8 + 2 * tq + (e & 1);
-            Os[r * (4 * rq) + m] = acc[nt][e];
+            Os[r * OSTR + m] = acc[nt][e];
           }
         }
       }
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_prolong_mma(Geom g, const float*
       const size_t off = chunk_off(X, g.Vb, s, c, rq);
       for (int idx = threadIdx.x; idx < N * rq; idx += MT_THREADS) {
         const int r = idx / rq, v = idx - r * rq;
-        const float4 o = *reinterpret_cast<const float4*>(Os + r * (4 * rq) + 4 * v);
+        const float4 o = *reinterpret_cast<const float4*>(Os + r * OSTR + 4 * v);
         *reinterpret_cast<float4*>(xb + (size_t)r * fstride + off + 4 * v) = o;
       }
       __syncthreads();
@@ -329,7 +331,8 @@ size_t restrict_mma_smem(int n, int N) {
 size_t prolong_mma_smem(const Geom& g, int n) {
   const int rq = chunk_sites(g.Vb);
   const int KG = ((2 * n + 7) / 8) * 8;
-  return ((size_t)2 * n * PSTR + (size_t)KG * 16 + (size_t)16 * 4 * rq) * sizeof(float);
+  (void)rq;
+  return ((size_t)2 * n * PSTR + (size_t)KG * CSTR + (size_t)16 * OSTR) * sizeof(float);
 }
 
 cudaError_t restrict_mrhs(const Geom& g, const float* lam, int n, const float* b, float* bc, int nrhs,

@@ -669,7 +669,7 @@ __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontr
 
 // bn / xn: site norms of b and x (half storage only; ignored for FP32)
 template <class S>
-__global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
+__global__ void __launch_bounds__(512, (sizeof(S) == 2 ? 2 : 1)) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
                                                  const S* __restrict__ b, const float* __restrict__ bn,
                                                  S* __restrict__ x, float* __restrict__ xn,
                                                  const S* __restrict__ gauge, const S* __restrict__ clov,
