@@ -225,6 +225,35 @@ DDAMG_API ddamg_status ddamg_solve_batched(ddamg_handle h, int nrhs, const doubl
                                  double *x, int on_device, double tol,
                                  ddamg_solve_info *info);
 
+/* ---- the batch as a resumable run (continuous batching) ------------------
+ * The lockstep batch of ddamg_solve_batched, advanced one FGMRES restart
+ * cycle at a time, with right-hand sides entering and leaving between
+ * cycles: a serving loop refills the slots of finished solves with waiting
+ * requests instead of waiting for the whole batch.  Not in the paper.  Each
+ * admitted right-hand side has its own tolerance and its own FGMRES (the
+ * arithmetic of ddamg_solve_batched); a free slot holds zero fields, which
+ * the batched kernels carry along.  Host or device buffers (on_device). */
+
+/* Start a batch of `slots` free slots (1..64) on a handle with a setup;
+ * replaces any batch in progress. */
+DDAMG_API ddamg_status ddamg_batch_begin(ddamg_handle h, int slots);
+/* Put one right-hand side (a spinor field) into a free slot, from a zero
+ * start, to be solved to ||b - D x|| <= tol ||b||. */
+DDAMG_API ddamg_status ddamg_batch_admit(ddamg_handle h, int slot, const double *rhs, int on_device,
+                                         double tol);
+/* One restart cycle of every running slot (Arnoldi steps in lockstep until
+ * each slot's cycle ended, x += Z y, FP64 true residuals); *running
+ * (nullable) receives the slots still running afterwards. */
+DDAMG_API ddamg_status ddamg_batch_cycle(ddamg_handle h, int *running);
+/* State of a slot: 0 free, 1 running, 2 finished (converged or capped). */
+DDAMG_API ddamg_status ddamg_batch_slot(ddamg_handle h, int slot, int *state);
+/* Copy a finished slot's solution to x (one spinor field) and its record to
+ * info (nullable; coarse_iters counts the batch since ddamg_batch_begin) and
+ * free the slot.  DDAMG_ENOCONV if it stopped at max_outer_iter (x holds
+ * the best solution). */
+DDAMG_API ddamg_status ddamg_batch_take(ddamg_handle h, int slot, double *x, int on_device,
+                                        ddamg_solve_info *info);
+
 /* ---- single steps of the method, for checking and benchmarking ---------- */
 
 /* out = D in (Wilson-clover operator above) in the given precision. */
@@ -294,6 +323,29 @@ typedef struct {
   size_t scratch_bytes;  /* global scratch the launch touches                */
 } ddamg_coarse_plan;
 DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan *out);
+
+/* Measured choices of kernel variants (the library's autotuner): the first
+ * time a kernel with variants runs for a problem (lattice, blocks,
+ * precision, right-hand sides) outside a stream capture, each variant is
+ * timed with CUDA events on the handle's stream and the fastest is used
+ * from then on, process-wide.  Record i of ddamg_tuning_count(): kernel,
+ * problem, the variants' mean times in microseconds and the choice.
+ * Variants so far: the Wilson-clover D with one thread per site (0) or four
+ * threads per site, one hop direction each (1), in FP32 and in BF16/FP16
+ * storage. */
+typedef struct {
+  char kernel[32];
+  char problem[96];
+  int variants;
+  int best;
+  float us[4];
+} ddamg_tuning;
+DDAMG_API int ddamg_tuning_count(void);
+DDAMG_API ddamg_status ddamg_get_tuning(int i, ddamg_tuning *out);
+/* Use `variant` of the named kernel ("D fp32", "D bf16", "D fp16") for every
+ * problem instead of the measured choice (variant < 0: measure again);
+ * process-wide, for reproducible runs and for checking each variant. */
+DDAMG_API ddamg_status ddamg_pin_variant(const char *kernel, int variant);
 
 /* Polls of the device-side bounded waits before they give up and the call
  * returns DDAMG_ETIMEOUT: the SAP kernel's wait for its staged block and the
@@ -385,32 +437,43 @@ DDAMG_API void ddamg_destroy(ddamg_handle h);
 /* ---- serving: continuous batching over resident gauge configurations ----
  * Not in the paper.  A server owns several gauge configurations ("configs"),
  * each with its own handle, setup and coarse operator kept resident in
- * device memory, and one worker thread that runs the solves.  Requests
- * (a config, nrhs right-hand sides, a tolerance) are submitted without
- * blocking and queue up; whenever the worker is free it takes the config of
- * the oldest waiting request and every waiting request of that config, in
- * arrival order, up to max_batch right-hand sides, and solves them as one
- * lockstep batch (ddamg_solve_batched, tolerance the smallest of the batch),
- * so requests that arrive while others run join the next batch.  A config
- * is set up on its first use; admission is by device-memory footprint: if
- * setting up a config would exceed hbm_budget, idle configs are released
- * (least recently used first) and set up again on their next request; a
- * config that cannot fit even alone fails its requests with DDAMG_ENOMEM.
+ * device memory, and worker threads that run the solves.  Requests (a
+ * config, nrhs right-hand sides, a tolerance) are submitted without blocking
+ * and queue up.  A free worker takes the config of the oldest waiting
+ * request that no other worker serves and runs that config's resumable
+ * lockstep batch (ddamg_batch_*, max_batch slots): before every FGMRES
+ * restart cycle it admits waiting requests of the config into free slots (in
+ * arrival order, a request entering when all its right-hand sides fit),
+ * and after it takes out every request whose right-hand sides have all
+ * finished, each to its own tolerance.  It serves the config until no
+ * request of it is running or waiting.  Workers serve different configs at
+ * the same time, each config on its own CUDA stream, so their kernels
+ * overlap on the device (the library orders the cooperative coarse-solver
+ * launches of different streams one after the other).  A config is set up on
+ * its first use; admission is by device-memory footprint: if setting up a
+ * config would exceed hbm_budget, idle configs (served by no worker) are
+ * released (least recently used first) and set up again on their next
+ * request; a config that cannot fit fails its requests with DDAMG_ENOMEM.
  * Host buffers only; rhs and x of a request belong to the caller and must
  * stay valid until ddamg_server_wait returns for it. */
 typedef struct ddamg_server *ddamg_server_handle;
 
 typedef struct {
-  ddamg_status status;    /* of the batch that solved this request           */
-  int batch_rhs;          /* right-hand sides in that batch                   */
-  int batch_requests;     /* requests in that batch                           */
-  int setup_run;          /* 1 if the batch had to set the config up first    */
-  double queue_seconds;   /* submit -> start of its batch                     */
+  ddamg_status status;    /* of this request's solves                         */
+  int batch_rhs;          /* most slots in use during a cycle it took part in */
+  int batch_requests;     /* most requests running together with it           */
+  int setup_run;          /* 1 if the config had to be set up for it          */
+  double queue_seconds;   /* submit -> admission into the batch               */
   double latency_seconds; /* submit -> results copied back                    */
 } ddamg_request_info;
 
-/* hbm_budget in bytes (0 = none), 1 <= max_batch <= 64; cuda_stream as in
- * ddamg_create (NULL = a stream the server creates). */
+/* hbm_budget in bytes (0 = none), 1 <= max_batch <= 64 slots per config,
+ * `workers` (1..16) configs served at the same time; cuda_stream: NULL = a
+ * stream of its own for every config, else all configs on that stream
+ * (then their kernels do not overlap). */
+DDAMG_API ddamg_status ddamg_server_create2(size_t hbm_budget, int max_batch, int workers, void *cuda_stream,
+                                            ddamg_server_handle *out);
+/* ddamg_server_create2 with two workers. */
 DDAMG_API ddamg_status ddamg_server_create(size_t hbm_budget, int max_batch, void *cuda_stream,
                                  ddamg_server_handle *out);
 /* Register a gauge configuration (host FP64 links, layout of ddamg_create,

@@ -6,7 +6,7 @@ package loads nothing; :func:`load` (or creating a :class:`DDAMG`) loads the
 library and fails loudly if it has not been built.
 """
 from ._ddamg import (BF16, FP16, FP32, FP64, DDAMG, DDAMGError, Params, RequestInfo, Server, SolveInfo,
-                     Stats, default_params, load)
+                     Stats, default_params, load, pin_variant, tuning)
 
 __all__ = ["BF16", "FP16", "FP32", "FP64", "DDAMG", "DDAMGError", "Params", "RequestInfo", "Server", "SolveInfo",
-           "Stats", "default_params", "load"]
+           "Stats", "default_params", "load", "pin_variant", "tuning"]

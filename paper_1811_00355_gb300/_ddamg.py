@@ -90,6 +90,16 @@ class CoarsePlan(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("kernel", C.c_char * 32), ("problem", C.c_char * 96), ("variants", C.c_int), ("best", C.c_int),
+                ("us", C.c_float * 4)]
+
+    def as_dict(self):
+        n = self.variants
+        return {"kernel": self.kernel.decode(), "problem": self.problem.decode(), "best": self.best,
+                "us": [round(float(v), 2) for v in self.us[:n]]}
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -122,8 +132,16 @@ SIGNATURES = {
     "ddamg_coarse_solve_noalloc": (_I, [_H, _I, _P, _P, _D, _P]),
     "ddamg_apply_M": (_I, [_H, _I, _I, _P, _P, _I]),
     "ddamg_set_coarse_op": (_I, [_H, _P, _I]),
+    "ddamg_batch_begin": (_I, [_H, _I]),
+    "ddamg_batch_admit": (_I, [_H, _I, _P, _I, _D]),
+    "ddamg_batch_cycle": (_I, [_H, C.POINTER(_I)]),
+    "ddamg_batch_slot": (_I, [_H, _I, C.POINTER(_I)]),
+    "ddamg_batch_take": (_I, [_H, _I, _P, _I, C.POINTER(SolveInfo)]),
     "ddamg_get_coarse_plan": (_I, [_H, _I, C.POINTER(CoarsePlan)]),
     "ddamg_set_wait_limit": (_I, [_H, C.c_int64]),
+    "ddamg_tuning_count": (_I, []),
+    "ddamg_get_tuning": (_I, [_I, C.POINTER(Tuning)]),
+    "ddamg_pin_variant": (_I, [C.c_char_p, _I]),
     "ddamg_get_index_maps": (_I, [_H, _P, _P, _P, _P, _P]),
     "ddamg_get_stats": (_I, [_H, C.POINTER(Stats)]),
     "ddamg_reset_stats": (_I, [_H]),
@@ -132,6 +150,7 @@ SIGNATURES = {
     "ddamg_get_history": (_I, [_H, _I, _P, _P, C.POINTER(_I)]),
     "ddamg_last_error": (C.c_char_p, [_H]),
     "ddamg_server_create": (_I, [C.c_size_t, _I, _P, C.POINTER(_H)]),
+    "ddamg_server_create2": (_I, [C.c_size_t, _I, _I, _P, C.POINTER(_H)]),
     "ddamg_server_add_config": (_I, [_H, C.POINTER(Params), _P, C.POINTER(_I)]),
     "ddamg_server_submit": (_I, [_H, _I, _I, _P, _P, _D, _P, C.POINTER(C.c_uint64)]),
     "ddamg_server_wait": (_I, [_H, C.c_uint64, C.POINTER(RequestInfo)]),
@@ -158,6 +177,22 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def tuning():
+    """The autotuner's measured choices so far (kernel, problem, times, choice)."""
+    lib = load()
+    out = []
+    for i in range(lib.ddamg_tuning_count()):
+        t = Tuning()
+        if lib.ddamg_get_tuning(i, C.byref(t)) == 0:
+            out.append(t.as_dict())
+    return out
+
+
+def pin_variant(kernel: str, variant: int) -> None:
+    """Fix the variant of a kernel with measured variants (variant < 0: measure)."""
+    load().ddamg_pin_variant(kernel.encode(), int(variant))
 
 
 def default_params(**kw) -> Params:
@@ -298,6 +333,35 @@ class DDAMG:
         if not (allow_noconv and st == 4):
             self._check(st)
         return x, [i.as_dict() for i in info]
+
+    # -- the batch as a resumable run ---------------------------------------------------
+    def batch_begin(self, slots):
+        self._check(self.lib.ddamg_batch_begin(self.h, slots))
+
+    def batch_admit(self, slot, rhs, tol=1e-10):
+        p, dev = _ptr(rhs)
+        self._check(self.lib.ddamg_batch_admit(self.h, slot, p, dev, tol))
+
+    def batch_cycle(self):
+        """One restart cycle; returns the number of slots still running."""
+        n = _I()
+        self._check(self.lib.ddamg_batch_cycle(self.h, C.byref(n)))
+        return n.value
+
+    def batch_slot(self, slot):
+        """0 free, 1 running, 2 finished."""
+        st = _I()
+        self._check(self.lib.ddamg_batch_slot(self.h, slot, C.byref(st)))
+        return st.value
+
+    def batch_take(self, slot, out=None, allow_noconv=False):
+        x = np.empty((self.V, 4, 3), np.complex128) if out is None else out
+        info = SolveInfo()
+        p, dev = _ptr(x)
+        st = self.lib.ddamg_batch_take(self.h, slot, p, dev, C.byref(info))
+        if not (allow_noconv and st == 4):
+            self._check(st)
+        return x, info.as_dict()
 
     # -- single steps ----------------------------------------------------------------
     def _fine_op(self, fn, x, *args):
@@ -476,13 +540,15 @@ class DDAMG:
 
 class Server:
     """Continuous-batching request loop over resident gauge configurations
-    (ddamg_server_*): submit returns at once, wait blocks for one request."""
+    (ddamg_server_*): submit returns at once, wait blocks for one request;
+    `workers` configurations are served at the same time, each on its own
+    stream unless `stream` is given."""
 
-    def __init__(self, hbm_budget=0, max_batch=12, stream=None):
+    def __init__(self, hbm_budget=0, max_batch=12, stream=None, workers=2):
         self.lib = load()
         h = _H()
         st = C.c_void_p(stream) if stream else None
-        status = self.lib.ddamg_server_create(hbm_budget, max_batch, st, C.byref(h))
+        status = self.lib.ddamg_server_create2(hbm_budget, max_batch, workers, st, C.byref(h))
         if status != 0:
             raise DDAMGError(status, self.lib.ddamg_status_string(status).decode())
         self.h = h

@@ -39,6 +39,15 @@ struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
 };
 
+// host state of a resumable lockstep batch (one entry per slot)
+struct BatchRun {
+  int nb = 0;
+  std::vector<double> bnorm, beta, tol;
+  std::vector<int> live, done, iters, restarts, calls;
+  std::vector<std::chrono::steady_clock::time_point> t0;
+  int cit0 = 0;
+};
+
 // polls before a device-side wait gives up (each poll about an L2 round
 // trip): about a second for a staged SAP block and for a grid barrier
 constexpr long long WAIT_SAP_DEFAULT = 1ll << 22;
@@ -129,6 +138,7 @@ struct ddamg_ctx {
   void *bin = nullptr, *bout = nullptr;   // inner-precision staging
   double* bsmall = nullptr;      // coefficients and norms of the batch
   double* h_bpinned = nullptr;
+  BatchRun brun;                 // the lockstep batch in progress
   double *fx = nullptr, *fb = nullptr, *fr = nullptr, *fw = nullptr;
   void* fin = nullptr;           // inner-precision in/out for M
   void* fout = nullptr;
@@ -611,11 +621,98 @@ cudaError_t by_half(int k, F&& f) {
   return f((__nv_bfloat16*)nullptr);
 }
 
+// ---- measured choice among kernel variants (autotuner) ----------------------------
+// For a kernel and a problem (lattice, precision, right-hand sides) every
+// variant runs once to warm up and then three times between CUDA events on
+// the handle's stream; the fastest is kept for the process and used from
+// then on, also inside captured graphs.  Inside a stream capture nothing can
+// be timed: an undecided choice takes variant 0 there.  The variants compute
+// the same result, so running them on the caller's data is harmless.
+struct TuneEntry {
+  std::string kernel, key;
+  int best = 0;
+  std::vector<float> us;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+std::vector<std::pair<std::string, int>> g_pins;   // kernels whose variant the caller fixed
+
+template <class F>
+ddamg_status tuned(ddamg_ctx* h, const std::string& kernel, const std::string& key, int nvar, F&& run,
+                   int* choice) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& p : g_pins)
+      if (p.first == kernel) {
+        *choice = p.second < nvar ? p.second : 0;
+        return DDAMG_OK;
+      }
+    for (const auto& e : g_tune)
+      if (e.kernel == kernel && e.key == key) {
+        *choice = e.best;
+        return DDAMG_OK;
+      }
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(h->st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {
+    *choice = 0;
+    return DDAMG_OK;
+  }
+  TuneEntry e;
+  e.kernel = kernel;
+  e.key = key;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 0.f;
+  for (int v = 0; v < nvar; ++v) {
+    CK(run(v));
+    CK(cudaEventRecord(a, h->st));
+    for (int k = 0; k < 3; ++k) CK(run(v));
+    CK(cudaEventRecord(b, h->st));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    e.us.push_back(1e3f * ms / 3.f);
+    if (v == 0 || e.us.back() < best) {
+      best = e.us.back();
+      e.best = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *choice = e.best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.push_back(e);
+  return DDAMG_OK;
+}
+
+std::string lattice_key(const ddamg_ctx* h, const char* prec, int nf) {
+  char buf[96];
+  snprintf(buf, sizeof buf, "%dx%dx%dx%d/%dx%dx%dx%d %s nrhs %d", h->g.L[0], h->g.L[1], h->g.L[2], h->g.L[3],
+           h->g.b[0], h->g.b[1], h->g.b[2], h->g.b[3], prec, nf);
+  return buf;
+}
+
 // ---- operators on device fields ---------------------------------------------------
 template <class R>
 ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
   addf(h, (double)nf * h->g.V * (mode == DSLASH_RES ? F_RES : mode == DSLASH_CLOVER ? F_CLOV : F_D));
+  int v = 0;
+  if constexpr (sizeof(R) == 4) {
+    // y = D x in FP32: one thread per site (0) or four (1), measured
+    if (mode == DSLASH_D && h->g.V % 8 == 0) {
+      auto run = [&](int var) -> cudaError_t {
+        if (var == 1) return dslash4<float>(h->g, x, nullptr, y, nullptr, h->g32, h->A32, nf, h->st);
+        return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
+      };
+      TRY(tuned(h, "D fp32", lattice_key(h, "fp32", nf), 2, run, &v));
+    }
+  }
   CK(timed(h, 0, [&] {
+    if constexpr (sizeof(R) == 4)
+      if (v == 1) return dslash4<float>(h->g, x, nullptr, y, nullptr, h->g32, h->A32, nf, h->st);
     return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
   }));
   return DDAMG_OK;
@@ -933,6 +1030,9 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
   }
   if (inner32(h)) coarse_gmres_exact_bytes<float>(h->g, h->p.n_v, h->p.coarse_restart, 1);
   else coarse_gmres_exact_bytes<double>(h->g, h->p.n_v, h->p.coarse_restart, 1);
+  // the D of the captured iterations (FP32 inner precision) is chosen now:
+  // nothing can be timed inside a capture
+  if (refine_mode(h)) TRY(op_dslash<float>(h, DSLASH_D, (const float*)h->fin, nullptr, (float*)h->fout, 1));
   return DDAMG_OK;
 }
 
@@ -1282,8 +1382,80 @@ ddamg_status alloc_batch(ddamg_ctx* h, int nb) {
   return DDAMG_OK;
 }
 
+// The lockstep batch as a resumable run: slots are admitted (a right-hand
+// side with its own tolerance), advanced one restart cycle at a time, and
+// taken out when finished, so that a serving loop can refill finished slots
+// between cycles.  Slots without a right-hand side hold zero fields and are
+// carried along by the batched kernels.
+ddamg_status batch_begin(ddamg_ctx* h, int nb) {
+  TRY(alloc_batch(h, nb));
+  TRY(need_tmp(h, nb, 6));
+  BatchRun& B = h->brun;
+  B.nb = nb;
+  B.bnorm.assign(nb, 0.0);
+  B.beta.assign(nb, 0.0);
+  B.tol.assign(nb, 0.0);
+  B.live.assign(nb, 0);
+  B.done.assign(nb, 1);
+  B.iters.assign(nb, 0);
+  B.restarts.assign(nb, 0);
+  B.calls.assign(nb, 0);
+  B.t0.assign(nb, std::chrono::steady_clock::now());
+  B.cit0 = 0;
+  const size_t bytes = (size_t)nb * h->V24 * sizeof(double);
+  CK(cudaMemsetAsync(h->bb, 0, bytes, h->st));
+  CK(cudaMemsetAsync(h->bx, 0, bytes, h->st));
+  CK(cudaMemsetAsync(h->br, 0, bytes, h->st));
+  const int m = h->p.outer_restart;
+  double* norms = h->bsmall + (size_t)nb * (4 * (m + 2) + 2 + 2 * (m + 1));
+  CK(cudaMemsetAsync(norms, 0, 2 * nb * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+// right-hand side b (host or device, one spinor field) into a free slot
+ddamg_status batch_admit(ddamg_ctx* h, int slot, const double* b, int on_device, double tol) {
+  BatchRun& B = h->brun;
+  const size_t N = h->V24, NC = N / 2;
+  double* bs = h->bb + (size_t)slot * N;
+  TRY(import_fields<double>(h, b, on_device, 1, bs));
+  CK(cudaMemsetAsync(h->bx + (size_t)slot * N, 0, N * sizeof(double), h->st));
+  CK(cudaMemcpyAsync(h->br + (size_t)slot * N, bs, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  const int m = h->p.outer_restart;
+  const int nb = B.nb;
+  double* norms = h->bsmall + (size_t)nb * (4 * (m + 2) + 2 + 2 * (m + 1));
+  CK(norm2<double>(bs, NC, h->red, norms + 2 * slot, h->st));
+  double nn[2];
+  CK(cudaMemcpyAsync(nn, norms + 2 * slot, sizeof nn, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const double bn = std::sqrt(nn[0]);
+  if (!std::isfinite(bn)) {
+    CK(cudaMemsetAsync(bs, 0, N * sizeof(double), h->st));
+    CK(cudaMemsetAsync(h->br + (size_t)slot * N, 0, N * sizeof(double), h->st));
+    CK(cudaMemsetAsync(norms + 2 * slot, 0, 2 * sizeof(double), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return fail(h, DDAMG_ENUMERIC, "right-hand side of slot %d: norm is not finite", slot);
+  }
+  B.bnorm[slot] = bn;
+  B.beta[slot] = bn;
+  B.tol[slot] = tol;
+  B.live[slot] = 1;
+  B.done[slot] = bn == 0.0;
+  B.iters[slot] = 0;
+  B.restarts[slot] = 0;
+  B.calls[slot] = 0;
+  B.t0[slot] = std::chrono::steady_clock::now();
+  return DDAMG_OK;
+}
+
+// one restart cycle of every live slot that has not finished: Arnoldi steps
+// in lockstep until each slot's cycle has ended (its recurrence residual
+// reached its target, or m steps), then x += Z y and the FP64 true residual
 template <class R>
-ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* info) {
+ddamg_status batch_cycle(ddamg_ctx* h) {
+  BatchRun& B = h->brun;
+  const int nb = B.nb;
   const int m = h->p.outer_restart;
   const size_t N = h->V24, NC = N / 2;
   const bool refine = refine_mode(h);
@@ -1306,195 +1478,193 @@ ddamg_status fgmres_batched(ddamg_ctx* h, int nb, double tol, ddamg_solve_info* 
   double* coef = nn + 2 * nb;
   double* norms = coef + (size_t)nb * 2 * (m + 1);
   double* hp = h->h_bpinned;
+  std::vector<double> cstop(nb), cs((size_t)nb * m);
+  std::vector<cd> Hc((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m), y(m);
+  std::vector<int> kdone(nb, 0), open(nb, 0);
+  auto& done = B.done;
+  auto& iters = B.iters;
+  auto& beta = B.beta;
+  auto& bnorm = B.bnorm;
 
-  CK(cudaMemsetAsync(h->bx, 0, nb * N * sizeof(double), h->st));
-  CK(cudaMemsetAsync(h->d_iters_acc, 0, sizeof(int), h->st));
-  CK(norm2_batched<double>(h->bb, NC, nb, NC, h->red, norms, h->st));
+  // V_0 = r / beta for every right-hand side (norms holds beta^2)
+  CK(scale_by_inv_norm_batched<double>(h->br, Vk(0), norms, N, nb, h->st));
+  for (int r = 0; r < nb; ++r) {
+    std::fill(g.begin() + (size_t)r * (m + 1), g.begin() + (size_t)(r + 1) * (m + 1), cd(0));
+    g[(size_t)r * (m + 1)] = beta[r];
+    kdone[r] = 0;
+    open[r] = B.live[r] && !done[r];
+    cstop[r] = std::max(B.tol[r] * bnorm[r], refine ? h->p.outer_refine * beta[r] : 0.0);
+  }
+  for (int k = 0; k < m; ++k) {
+    // z_k = M v_k and w = D z_k for the whole batch
+    if (refine) {
+      float* zk = Z32 + (size_t)k * blk;
+      TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+      TRY(op_M<float>(h, (float*)h->bin, zk, nb));
+      TRY(op_dslash<float>(h, DSLASH_D, zk, nullptr, (float*)h->bout, nb));
+      TRY(from_inner<float>(h, (float*)h->bout, h->bw, nb));
+    } else {
+      double* zk = Z64 + (size_t)k * blk;
+      if constexpr (sizeof(R) == 8) {
+        TRY(op_M<double>(h, Vk(k), zk, nb));
+      } else {
+        TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+        TRY(op_M<float>(h, (float*)h->bin, (float*)h->bout, nb));
+        TRY(from_inner<float>(h, (float*)h->bout, zk, nb));
+      }
+      TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
+    }
+    for (int r = 0; r < nb; ++r)
+      if (open[r]) ++B.calls[r];
+    // classical Gram-Schmidt per right-hand side (two passes; in the
+    // refinement mode one, plus a second when the first cancelled most of
+    // some w -- as in fgmres), ||w||, v_{k+1}
+    const int kk = k + 1;
+    const int kd1 = refine ? kk + 1 : kk;     // first-pass dots (+ ||w||^2 in the refinement mode)
+    const double* keep = vlist[k + 1];
+    if (refine) vlist[k + 1] = h->bw;
+    CK(multi_dot_batched<double>(vlist.data(), kd1, h->bw, NC, nb, NC, h->red, c1, h->st));
+    vlist[k + 1] = keep;
+    bool second = !refine;
+    if (refine) {
+      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kd1, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+      CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      const double* hn2 = hp + (size_t)nb * 4 * (m + 2);
+      for (int r = 0; r < nb; ++r)
+        if (open[r] && hn2[2 * r] < REORTH_RATIO * hp[2 * (r * kd1 + kk)]) second = true;
+      if (second) ++h->reorth;
+    } else {
+      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr,
+                                    h->st));
+    }
+    if (second) {
+      CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
+      CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
+    }
+    addf(h, nb * ((second ? 2.0 : 1.0) * flops_gs_pass(h, kk) + 2.0 * flops_gs_pass(h, 1)));
+    CK(scale_by_inv_norm_batched<double>(h->bw, Vk(k + 1), nn, N, nb, h->st));
+    if (second) {
+      CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
+    const double* h1 = hp;
+    const double* h2 = hp + (size_t)nb * 2 * (m + 2);
+    const double* hn2 = h2 + (size_t)nb * 2 * (m + 2);
+    bool any_open = false;
+    for (int r = 0; r < nb; ++r) {
+      if (!open[r]) continue;
+      std::vector<cd> col(k + 2);
+      for (int j = 0; j <= k; ++j) {
+        col[j] = cd(h1[2 * (r * kd1 + j)], h1[2 * (r * kd1 + j) + 1]);
+        if (second) col[j] += cd(h2[2 * (r * kk + j)], h2[2 * (r * kk + j) + 1]);
+      }
+      const double hn = std::sqrt(hn2[2 * r]);
+      if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the basis norm", r);
+      col[k + 1] = hn;
+      double* csr = cs.data() + (size_t)r * m;
+      cd* snr = sn.data() + (size_t)r * m;
+      cd* gr = g.data() + (size_t)r * (m + 1);
+      for (int j = 0; j < k; ++j) {
+        cd t = csr[j] * col[j] + snr[j] * col[j + 1];
+        col[j + 1] = -std::conj(snr[j]) * col[j] + csr[j] * col[j + 1];
+        col[j] = t;
+      }
+      double a1 = std::abs(col[k]), a2 = std::abs(col[k + 1]);
+      if (a2 == 0.0) { csr[k] = 1.0; snr[k] = 0.0; }
+      else if (a1 == 0.0) { csr[k] = 0.0; snr[k] = std::conj(col[k + 1]) / a2; col[k] = a2; }
+      else {
+        double rho = std::hypot(a1, a2);
+        cd ph = col[k] / a1;
+        csr[k] = a1 / rho;
+        snr[k] = ph * std::conj(col[k + 1]) / rho;
+        col[k] = ph * rho;
+      }
+      for (int j = 0; j <= k; ++j) Hc[((size_t)r * (m + 1) + j) * m + k] = col[j];
+      gr[k + 1] = -std::conj(snr[k]) * gr[k];
+      gr[k] = csr[k] * gr[k];
+      ++iters[r];
+      kdone[r] = k + 1;
+      if (std::abs(gr[k + 1]) <= cstop[r] || iters[r] >= h->p.max_outer_iter || hn == 0.0) open[r] = 0;
+      any_open |= open[r] != 0;
+    }
+    if (!any_open) break;
+  }
+  // x_r += Z_r y_r (zero coefficients beyond each right-hand side's kdone)
+  int kmax = 0;
+  std::vector<double> cf((size_t)nb * 2 * (m + 1), 0.0);
+  for (int r = 0; r < nb; ++r) {
+    if (done[r] || !B.live[r] || kdone[r] == 0) continue;
+    const int kd = kdone[r];
+    kmax = std::max(kmax, kd);
+    const cd* gr = g.data() + (size_t)r * (m + 1);
+    for (int i = kd - 1; i >= 0; --i) {
+      cd acc = gr[i];
+      for (int j = i + 1; j < kd; ++j) acc -= Hc[((size_t)r * (m + 1) + i) * m + j] * y[j];
+      y[i] = acc / Hc[((size_t)r * (m + 1) + i) * m + i];
+    }
+    for (int j = 0; j < kd; ++j) {
+      cf[(size_t)r * 2 * (m + 1) + 2 * j] = y[j].real();
+      cf[(size_t)r * 2 * (m + 1) + 2 * j + 1] = y[j].imag();
+    }
+  }
+  if (kmax > 0) {
+    addf(h, nb * ((double)h->g.V * 12.0 * kmax * 8.0 + flops_gs_pass(h, 1)));
+    CK(cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if (refine)
+      CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, nb, h->st));
+    else
+      CK(multi_axpy_batched<double>(zlist.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, NC, nb, NC, nullptr, nullptr,
+                                    h->st));
+  }
+  // FP64 true residuals
+  TRY(op_dslash<double>(h, DSLASH_RES, h->bx, h->bb, h->br, nb));
+  CK(norm2_batched<double>(h->br, NC, nb, NC, h->red, norms, h->st));
   CK(cudaMemcpyAsync(hp, norms, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  std::vector<double> bnorm(nb), beta(nb), cstop(nb), cs((size_t)nb * m);
-  std::vector<cd> Hc((size_t)nb * (m + 1) * m), g((size_t)nb * (m + 1)), sn((size_t)nb * m), y(m);
-  std::vector<int> done(nb, 0), iters(nb, 0), restarts(nb, 0), kdone(nb, 0), open(nb, 0);
   for (int r = 0; r < nb; ++r) {
-    bnorm[r] = std::sqrt(hp[2 * r]);
-    if (!std::isfinite(bnorm[r])) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: norm is not finite", r);
-    beta[r] = bnorm[r];
-    done[r] = bnorm[r] == 0.0;
+    if (done[r] || !B.live[r]) continue;
+    beta[r] = std::sqrt(hp[2 * r]);
+    ++B.restarts[r];
+    if (!std::isfinite(beta[r])) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the residual", r);
+    if (beta[r] <= B.tol[r] * bnorm[r] || iters[r] >= h->p.max_outer_iter) done[r] = 1;
   }
-  CK(cudaMemcpyAsync(h->br, h->bb, nb * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-  CK(cudaMemcpyAsync(norms, hp, 2 * nb * sizeof(double), cudaMemcpyHostToDevice, h->st));
-  int calls = 0, total = 0;
-  auto all_done = [&] {
-    for (int r = 0; r < nb; ++r)
-      if (!done[r]) return false;
-    return true;
-  };
-  while (!all_done() && total < h->p.max_outer_iter) {
-    // V_0 = r / beta for every right-hand side (norms holds beta^2)
-    CK(scale_by_inv_norm_batched<double>(h->br, Vk(0), norms, N, nb, h->st));
-    for (int r = 0; r < nb; ++r) {
-      std::fill(g.begin() + (size_t)r * (m + 1), g.begin() + (size_t)(r + 1) * (m + 1), cd(0));
-      g[(size_t)r * (m + 1)] = beta[r];
-      kdone[r] = 0;
-      open[r] = !done[r];
-      cstop[r] = std::max(tol * bnorm[r], refine ? h->p.outer_refine * beta[r] : 0.0);
-    }
-    int k = 0;
-    for (; k < m; ++k) {
-      // z_k = M v_k and w = D z_k for the whole batch
-      if (refine) {
-        float* zk = Z32 + (size_t)k * blk;
-        TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
-        TRY(op_M<float>(h, (float*)h->bin, zk, nb));
-        TRY(op_dslash<float>(h, DSLASH_D, zk, nullptr, (float*)h->bout, nb));
-        TRY(from_inner<float>(h, (float*)h->bout, h->bw, nb));
-      } else {
-        double* zk = Z64 + (size_t)k * blk;
-        if constexpr (sizeof(R) == 8) {
-          TRY(op_M<double>(h, Vk(k), zk, nb));
-        } else {
-          TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
-          TRY(op_M<float>(h, (float*)h->bin, (float*)h->bout, nb));
-          TRY(from_inner<float>(h, (float*)h->bout, zk, nb));
-        }
-        TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
-      }
-      ++calls;
-      // classical Gram-Schmidt per right-hand side (two passes; in the
-      // refinement mode one, plus a second when the first cancelled most of
-      // some w -- as in fgmres), ||w||, v_{k+1}
-      const int kk = k + 1;
-      const int kd1 = refine ? kk + 1 : kk;     // first-pass dots (+ ||w||^2 in the refinement mode)
-      const double* keep = vlist[k + 1];
-      if (refine) vlist[k + 1] = h->bw;
-      CK(multi_dot_batched<double>(vlist.data(), kd1, h->bw, NC, nb, NC, h->red, c1, h->st));
-      vlist[k + 1] = keep;
-      bool second = !refine;
-      if (refine) {
-        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kd1, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
-        CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        const double* hn2 = hp + (size_t)nb * 4 * (m + 2);
-        for (int r = 0; r < nb; ++r)
-          if (open[r] && hn2[2 * r] < REORTH_RATIO * hp[2 * (r * kd1 + kk)]) second = true;
-        if (second) ++h->reorth;
-      } else {
-        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr,
-                                      h->st));
-      }
-      if (second) {
-        CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
-        CK(multi_axpy_batched<double>(vlist.data(), kk, c2, 2 * kk, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
-      }
-      addf(h, nb * ((second ? 2.0 : 1.0) * flops_gs_pass(h, kk) + 2.0 * flops_gs_pass(h, 1)));
-      CK(scale_by_inv_norm_batched<double>(h->bw, Vk(k + 1), nn, N, nb, h->st));
-      if (second) {
-        CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                           h->st));
-        CK(cudaStreamSynchronize(h->st));
-      }
-      const double* h1 = hp;
-      const double* h2 = hp + (size_t)nb * 2 * (m + 2);
-      const double* hn2 = h2 + (size_t)nb * 2 * (m + 2);
-      bool any_open = false;
-      for (int r = 0; r < nb; ++r) {
-        if (!open[r]) continue;
-        std::vector<cd> col(k + 2);
-        for (int j = 0; j <= k; ++j) {
-          col[j] = cd(h1[2 * (r * kd1 + j)], h1[2 * (r * kd1 + j) + 1]);
-          if (second) col[j] += cd(h2[2 * (r * kk + j)], h2[2 * (r * kk + j) + 1]);
-        }
-        const double hn = std::sqrt(hn2[2 * r]);
-        if (!std::isfinite(hn)) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the basis norm", r);
-        col[k + 1] = hn;
-        double* csr = cs.data() + (size_t)r * m;
-        cd* snr = sn.data() + (size_t)r * m;
-        cd* gr = g.data() + (size_t)r * (m + 1);
-        for (int j = 0; j < k; ++j) {
-          cd t = csr[j] * col[j] + snr[j] * col[j + 1];
-          col[j + 1] = -std::conj(snr[j]) * col[j] + csr[j] * col[j + 1];
-          col[j] = t;
-        }
-        double a1 = std::abs(col[k]), a2 = std::abs(col[k + 1]);
-        if (a2 == 0.0) { csr[k] = 1.0; snr[k] = 0.0; }
-        else if (a1 == 0.0) { csr[k] = 0.0; snr[k] = std::conj(col[k + 1]) / a2; col[k] = a2; }
-        else {
-          double rho = std::hypot(a1, a2);
-          cd ph = col[k] / a1;
-          csr[k] = a1 / rho;
-          snr[k] = ph * std::conj(col[k + 1]) / rho;
-          col[k] = ph * rho;
-        }
-        for (int j = 0; j <= k; ++j) Hc[((size_t)r * (m + 1) + j) * m + k] = col[j];
-        gr[k + 1] = -std::conj(snr[k]) * gr[k];
-        gr[k] = csr[k] * gr[k];
-        ++iters[r];
-        kdone[r] = k + 1;
-        if (std::abs(gr[k + 1]) <= cstop[r] || iters[r] >= h->p.max_outer_iter || hn == 0.0) open[r] = 0;
-        any_open |= open[r] != 0;
-      }
-      ++total;
-      if (!any_open || total >= h->p.max_outer_iter) break;
-    }
-    // x_r += Z_r y_r (zero coefficients beyond each right-hand side's kdone)
-    int kmax = 0;
-    std::vector<double> cf((size_t)nb * 2 * (m + 1), 0.0);
-    for (int r = 0; r < nb; ++r) {
-      if (done[r] || kdone[r] == 0) continue;
-      const int kd = kdone[r];
-      kmax = std::max(kmax, kd);
-      const cd* gr = g.data() + (size_t)r * (m + 1);
-      for (int i = kd - 1; i >= 0; --i) {
-        cd acc = gr[i];
-        for (int j = i + 1; j < kd; ++j) acc -= Hc[((size_t)r * (m + 1) + i) * m + j] * y[j];
-        y[i] = acc / Hc[((size_t)r * (m + 1) + i) * m + i];
-      }
-      for (int j = 0; j < kd; ++j) {
-        cf[(size_t)r * 2 * (m + 1) + 2 * j] = y[j].real();
-        cf[(size_t)r * 2 * (m + 1) + 2 * j + 1] = y[j].imag();
-      }
-    }
-    if (kmax > 0) {
-      addf(h, nb * ((double)h->g.V * 12.0 * kmax * 8.0 + flops_gs_pass(h, 1)));
-      CK(cudaMemcpyAsync(coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
-      if (refine)
-        CK(multi_axpy_f32_into_f64(h->g, zlist32.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, nb, h->st));
-      else
-        CK(multi_axpy_batched<double>(zlist.data(), kmax, coef, 2 * (m + 1), 1.0, h->bx, NC, nb, NC, nullptr,
-                                      nullptr, h->st));
-    }
-    // FP64 true residuals
-    TRY(op_dslash<double>(h, DSLASH_RES, h->bx, h->bb, h->br, nb));
-    CK(norm2_batched<double>(h->br, NC, nb, NC, h->red, norms, h->st));
-    CK(cudaMemcpyAsync(hp, norms, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    for (int r = 0; r < nb; ++r) {
-      if (done[r]) continue;
-      beta[r] = std::sqrt(hp[2 * r]);
-      ++restarts[r];
-      if (!std::isfinite(beta[r])) return fail(h, DDAMG_ENUMERIC, "right-hand side %d: NaN or Inf in the residual", r);
-      if (beta[r] <= tol * bnorm[r] || iters[r] >= h->p.max_outer_iter) done[r] = 1;
-    }
-  }
-  TRY(check_status(h));
+  return check_status(h);
+}
+
+// finished slot -> x (host or device) and its record; the slot is freed
+ddamg_status batch_take(ddamg_ctx* h, int slot, double* x, int on_device, ddamg_solve_info* info) {
+  BatchRun& B = h->brun;
+  const size_t N = h->V24;
+  TRY(export_fields<double>(h, h->bx + (size_t)slot * N, 1, x, on_device));
   int cit = 0;
   CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
-  addf(h, cit * flops_coarse_iter(h));
-  bool all_conv = true;
-  for (int r = 0; r < nb; ++r) {
-    const bool conv = bnorm[r] == 0.0 || beta[r] <= tol * bnorm[r];
-    all_conv &= conv;
-    if (info) {
-      info[r].outer_iters = iters[r];
-      info[r].restarts = restarts[r];
-      info[r].coarse_iters = cit;
-      info[r].precond_calls = calls;
-      info[r].true_residual = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
-      info[r].converged = conv ? 1 : 0;
-    }
+  const double bn = B.bnorm[slot], be = B.beta[slot];
+  const bool conv = bn == 0.0 || be <= B.tol[slot] * bn;
+  if (info) {
+    info->outer_iters = B.iters[slot];
+    info->restarts = B.restarts[slot];
+    info->coarse_iters = cit;
+    info->precond_calls = B.calls[slot];
+    info->true_residual = bn > 0 ? be / bn : 0.0;
+    info->converged = conv ? 1 : 0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - B.t0[slot]).count();
   }
-  if (!all_conv) return fail(h, DDAMG_ENOCONV, "FGMRES reached max_outer_iter for part of the batch");
-  return DDAMG_OK;
+  const int m = h->p.outer_restart;
+  double* norms = h->bsmall + (size_t)B.nb * (4 * (m + 2) + 2 + 2 * (m + 1));
+  CK(cudaMemsetAsync(h->bb + (size_t)slot * N, 0, N * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->bx + (size_t)slot * N, 0, N * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->br + (size_t)slot * N, 0, N * sizeof(double), h->st));
+  CK(cudaMemsetAsync(norms + 2 * slot, 0, 2 * sizeof(double), h->st));
+  CK(cudaStreamSynchronize(h->st));
+  B.live[slot] = 0;
+  B.done[slot] = 1;
+  return conv ? DDAMG_OK : DDAMG_ENOCONV;
+}
+
+ddamg_status batch_cycle_any(ddamg_ctx* h) {
+  return h->p.precision == DDAMG_FP64 ? batch_cycle<double>(h) : batch_cycle<float>(h);
 }
 
 bool is_prec_ok(ddamg_ctx* h, int prec) {
@@ -1808,16 +1978,82 @@ ddamg_status ddamg_solve_batched(ddamg_handle h, int nrhs, const double* rhs, do
   if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "run the setup first");
   if (nrhs == 0) return DDAMG_OK;
   auto t0 = std::chrono::steady_clock::now();
-  TRY(alloc_batch(h, nrhs));
-  TRY(need_tmp(h, nrhs, 6));
-  TRY(import_fields<double>(h, rhs, on_device, nrhs, h->bb));
-  ddamg_status s = h->p.precision == DDAMG_FP64 ? fgmres_batched<double>(h, nrhs, tol, info)
-                                                : fgmres_batched<float>(h, nrhs, tol, info);
-  if (s != DDAMG_OK && s != DDAMG_ENOCONV) return s;
-  TRY(export_fields<double>(h, h->bx, nrhs, x, on_device));
+  TRY(batch_begin(h, nrhs));
+  const size_t N = h->V24;
+  for (int r = 0; r < nrhs; ++r) TRY(batch_admit(h, r, rhs + (size_t)r * N, on_device, tol));
+  BatchRun& B = h->brun;
+  for (;;) {
+    bool running = false;
+    for (int r = 0; r < nrhs; ++r) running |= B.live[r] && !B.done[r];
+    if (!running) break;
+    TRY(batch_cycle_any(h));
+  }
+  int cit = 0;
+  CK(cudaMemcpy(&cit, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost));
+  addf(h, cit * flops_coarse_iter(h));
+  int calls = 0;
+  for (int r = 0; r < nrhs; ++r) calls = std::max(calls, B.calls[r]);
+  ddamg_status s = DDAMG_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    ddamg_solve_info one{};
+    const ddamg_status sr = batch_take(h, r, x + (size_t)r * N, on_device, &one);
+    if (sr != DDAMG_OK && sr != DDAMG_ENOCONV) return sr;
+    if (sr == DDAMG_ENOCONV) s = sr;
+    one.precond_calls = calls;
+    if (info) info[r] = one;
+  }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info)
     for (int r = 0; r < nrhs; ++r) info[r].seconds = secs;
+  if (s == DDAMG_ENOCONV) return fail(h, DDAMG_ENOCONV, "FGMRES reached max_outer_iter for part of the batch");
+  return s;
+}
+
+ddamg_status ddamg_batch_begin(ddamg_handle h, int slots) {
+  if (!h) return DDAMG_EINVAL;
+  if (slots < 1 || slots > MAX_BATCH) return fail(h, DDAMG_EINVAL, "slots must be in [1, %d]", MAX_BATCH);
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "run the setup first");
+  return batch_begin(h, slots);
+}
+
+ddamg_status ddamg_batch_admit(ddamg_handle h, int slot, const double* rhs, int on_device, double tol) {
+  if (!h) return DDAMG_EINVAL;
+  BatchRun& B = h->brun;
+  if (slot < 0 || slot >= B.nb || !rhs || !(tol > 0.0)) return fail(h, DDAMG_EINVAL, "bad slot, buffer or tolerance");
+  if (B.live[slot]) return fail(h, DDAMG_ESTATE, "slot %d holds a right-hand side", slot);
+  return batch_admit(h, slot, rhs, on_device, tol);
+}
+
+ddamg_status ddamg_batch_cycle(ddamg_handle h, int* running) {
+  if (!h) return DDAMG_EINVAL;
+  BatchRun& B = h->brun;
+  if (B.nb == 0) return fail(h, DDAMG_ESTATE, "no batch begun");
+  bool any = false;
+  for (int r = 0; r < B.nb; ++r) any |= B.live[r] && !B.done[r];
+  if (any) TRY(batch_cycle_any(h));
+  if (running) {
+    int n = 0;
+    for (int r = 0; r < B.nb; ++r) n += B.live[r] && !B.done[r];
+    *running = n;
+  }
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_batch_slot(ddamg_handle h, int slot, int* state) {
+  if (!h || !state) return DDAMG_EINVAL;
+  BatchRun& B = h->brun;
+  if (slot < 0 || slot >= B.nb) return fail(h, DDAMG_EINVAL, "bad slot");
+  *state = !B.live[slot] ? 0 : B.done[slot] ? 2 : 1;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_batch_take(ddamg_handle h, int slot, double* x, int on_device, ddamg_solve_info* info) {
+  if (!h || !x) return DDAMG_EINVAL;
+  BatchRun& B = h->brun;
+  if (slot < 0 || slot >= B.nb) return fail(h, DDAMG_EINVAL, "bad slot");
+  if (!B.live[slot] || !B.done[slot]) return fail(h, DDAMG_ESTATE, "slot %d has no finished solve", slot);
+  const ddamg_status s = batch_take(h, slot, x, on_device, info);
+  if (s == DDAMG_ENOCONV) return fail(h, DDAMG_ENOCONV, "slot %d reached max_outer_iter", slot);
   return s;
 }
 
@@ -1835,13 +2071,24 @@ ddamg_status ddamg_apply_D(ddamg_handle h, int prec, int nrhs, const double* in,
     addf(h, (double)nrhs * h->g.V * F_D);
     CK(by_half(k, [&](auto* tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      cudaError_t e = spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
-      if (e != cudaSuccess) return e;
-      e = timed(h, 0, [&] {
-        return dslash_h<S>(h->g, DSLASH_D, h->hb, h->hbn, nullptr, nullptr, h->hx, h->hxn, h->gH[k], h->AH[k], nrhs,
-                           h->st);
+      return spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
+    }));
+    // one thread per site (0) or four (1), measured
+    auto run = [&](int var) -> cudaError_t {
+      return by_half(k, [&](auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        if (var == 1 && h->g.V % 8 == 0)
+          return dslash4<S>(h->g, h->hb, h->hbn, h->hx, h->hxn, h->gH[k], h->AH[k], nrhs, h->st);
+        return dslash_h<S>(h->g, DSLASH_D, h->hb, h->hbn, nullptr, nullptr, h->hx, h->hxn, h->gH[k], h->AH[k],
+                           nrhs, h->st);
       });
-      if (e != cudaSuccess) return e;
+    };
+    int v = 0;
+    TRY(tuned(h, k ? "D bf16" : "D fp16", lattice_key(h, k ? "bf16" : "fp16", nrhs), h->g.V % 8 == 0 ? 2 : 1, run,
+              &v));
+    CK(timed(h, 0, [&] { return run(v); }));
+    CK(by_half(k, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
       return spinor_from_half<S>(h->g, h->hx, h->hxn, t1, nrhs, false, h->st);
     }));
     return export_fields<float>(h, t1, nrhs, out, on_device);
@@ -2034,6 +2281,37 @@ ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan* 
   out->shared_bytes = c.smem_bytes;
   out->scratch_bytes = c.work_bytes;
   return DDAMG_OK;
+}
+
+ddamg_status ddamg_get_tuning(int i, ddamg_tuning* out) {
+  if (!out) return DDAMG_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (i < 0 || i >= (int)g_tune.size()) return DDAMG_EINVAL;
+  const TuneEntry& e = g_tune[i];
+  std::memset(out, 0, sizeof *out);
+  snprintf(out->kernel, sizeof out->kernel, "%s", e.kernel.c_str());
+  snprintf(out->problem, sizeof out->problem, "%s", e.key.c_str());
+  out->variants = (int)e.us.size();
+  out->best = e.best;
+  for (int v = 0; v < out->variants && v < 4; ++v) out->us[v] = e.us[v];
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_pin_variant(const char* kernel, int variant) {
+  if (!kernel) return DDAMG_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto it = g_pins.begin(); it != g_pins.end(); ++it)
+    if (it->first == kernel) {
+      g_pins.erase(it);
+      break;
+    }
+  if (variant >= 0) g_pins.emplace_back(kernel, variant);
+  return DDAMG_OK;
+}
+
+int ddamg_tuning_count(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
 }
 
 ddamg_status ddamg_set_wait_limit(ddamg_handle h, int64_t polls) {

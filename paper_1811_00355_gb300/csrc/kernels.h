@@ -99,6 +99,11 @@ cudaError_t dslash(const Geom& g, int mode, const R* x, const R* b, R* y, const 
 template <class S>
 cudaError_t dslash_h(const Geom& g, int mode, const void* x, const float* xn, const void* b, const float* bn,
                      void* y, float* yn, const void* gauge, const void* clover, int nrhs, cudaStream_t st);
+// y = D x with four threads per site (one hop direction each), storage S =
+// float (FP32 layout, xn / yn unused) or a half type (with site norms)
+template <class S>
+cudaError_t dslash4(const Geom& g, const void* x, const float* xn, void* y, float* yn, const void* gauge,
+                    const void* clover, int nrhs, cudaStream_t st);
 // nf FP32 spinor fields -> half fields with site norms, and back (dst = or +=)
 template <class S>
 cudaError_t spinor_to_half(const Geom& g, const float* src, void* dst, float* nrm, int nf, cudaStream_t st);

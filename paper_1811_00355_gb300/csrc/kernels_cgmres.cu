@@ -815,6 +815,10 @@ std::mutex g_cfg_mu;
 
 constexpr int MAXDEV = 64;
 
+// completion of the last cooperative coarse-GMRES launch per device
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_done[MAXDEV] = {};
+
 inline int nr_slot(int NR) { return NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4; }
 
 // caller holds g_cfg_mu
@@ -995,6 +999,28 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   }
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
+  // Cooperative launches from different streams (several batches served at
+  // once) must not overlap: each sizes its grid for the whole GPU and spins
+  // on a grid barrier, so two of them sharing the SMs could wait on each
+  // other's blocks.  Outside stream capture every launch waits for the
+  // previous one of the process on this device.
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return e;
+  const bool order = cap == cudaStreamCaptureStatusNone && dev >= 0 && dev < MAXDEV;
+  std::unique_lock<std::mutex> order_lock(g_coop_mu, std::defer_lock);
+  if (order) {
+    order_lock.lock();
+    if (!g_coop_done[dev]) {
+      e = cudaEventCreateWithFlags(&g_coop_done[dev], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    } else {
+      e = cudaStreamWaitEvent(st, g_coop_done[dev], 0);
+      if (e != cudaSuccess) return e;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ch.G);
   cfg.blockDim = dim3(TPB);
@@ -1007,6 +1033,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   cfg.numAttrs = 1;
   e = cudaLaunchKernelExC(&cfg, fn, args);
   ++g_launches;
+  if (e == cudaSuccess && order) e = cudaEventRecord(g_coop_done[dev], st);
   return e;
 }
 

@@ -669,7 +669,7 @@ __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontr
 
 // bn / xn: site norms of b and x (half storage only; ignored for FP32)
 template <class S>
-__global__ void __launch_bounds__(512, (sizeof(S) == 2 ? 2 : 1)) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
+__global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
                                                  const S* __restrict__ b, const float* __restrict__ bn,
                                                  S* __restrict__ x, float* __restrict__ xn,
                                                  const S* __restrict__ gauge, const S* __restrict__ clov,
@@ -868,6 +868,48 @@ __global__ void __launch_bounds__(512, (sizeof(S) == 2 ? 2 : 1)) k_sap_stg(Geom 
   IO<S>::store3(x, xn, dO, Vb, sub, vo);
 }
 
+// ---------------------------------------------------------------------------
+// Wilson-clover D on the whole lattice with four threads per site (the
+// thread layout of the SAP kernel): thread sub applies the two hops of
+// direction mu = sub and the three rows of its chiral clover block that it
+// owns; the hop sums are combined by warp shuffles.  A quarter of the
+// loads per thread and four times the threads of the one-thread-per-site
+// kernel keep more memory requests in flight.
+//   y = A x - 1/2 hop(x)                       (DSLASH_D)
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void __launch_bounds__(256) k_dslash4(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
+                                                 S* __restrict__ y, float* __restrict__ yn,
+                                                 const S* __restrict__ gauge, const S* __restrict__ clov) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)4 * g.V) return;        // whole warps (4 V is a multiple of 32)
+  const int d = (int)(t >> 2), sub = (int)(t & 3);
+  const int cb = sub >> 1, half = sub & 1;
+  const size_t off = (size_t)blockIdx.y * g.V * SPINOR_NR;
+  const size_t noff = (size_t)blockIdx.y * g.V;
+  x += off;
+  y += off;
+  if (xn) xn += noff;        // site norms exist for half storage only
+  if (yn) yn += noff;
+  f2 hop[3];
+  hop_global_s<S>(g, x, xn, gauge, d, sub, hop);
+  f2 x6[6], ax[3];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) x6[i] = IO<S>::comp(x, xn, d, g.Vb, 6 * cb + i);
+  {
+    float P[36];
+    IO<S>::block36(clov, d, g.Vb, cb, P);
+    f2 y6[6];
+    herm6<float>(P, x6, y6);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ax[i] = half ? y6[3 + i] : y6[i];
+  }
+  f2 out[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] = mk(fmaf(-0.5f, hop[i].re, ax[i].re), fmaf(-0.5f, hop[i].im, ax[i].im));
+  IO<S>::store3(y, yn, d, g.Vb, sub, out);
+}
+
 }  // namespace stg
 
 }  // namespace
@@ -950,6 +992,24 @@ template cudaError_t sap_sweep_h<__half>(const Geom&, int, int, bool, const void
 template cudaError_t sap_sweep_h<__nv_bfloat16>(const Geom&, int, int, bool, const void*, const float*, void*,
                                                 float*, const void*, const void*, const void*, int, int*, long long,
                                                 cudaStream_t);
+
+template <class S>
+cudaError_t dslash4(const Geom& g, const void* x, const float* xn, void* y, float* yn, const void* gauge,
+                    const void* clover, int nrhs, cudaStream_t st) {
+  if (g.V % 8) return cudaErrorInvalidValue;
+  const size_t threads = (size_t)4 * g.V;
+  stg::k_dslash4<S><<<dim3((unsigned)((threads + 255) / 256), nrhs), 256, 0, st>>>(
+      g, static_cast<const S*>(x), xn, static_cast<S*>(y), yn, static_cast<const S*>(gauge),
+      static_cast<const S*>(clover));
+  ++g_launches;
+  return cudaGetLastError();
+}
+template cudaError_t dslash4<float>(const Geom&, const void*, const float*, void*, float*, const void*, const void*,
+                                    int, cudaStream_t);
+template cudaError_t dslash4<__half>(const Geom&, const void*, const float*, void*, float*, const void*, const void*,
+                                     int, cudaStream_t);
+template cudaError_t dslash4<__nv_bfloat16>(const Geom&, const void*, const float*, void*, float*, const void*,
+                                            const void*, int, cudaStream_t);
 
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,

@@ -1,8 +1,12 @@
 // Serving loop of the library (declared in include/ddamg.h): propagator
-// requests over several resident gauge configurations, solved by one worker
-// thread in lockstep batches (continuous batching), with admission of
-// configurations by device-memory footprint.  Host code only; every solve
-// goes through ddamg_setup / ddamg_solve_batched of the same library.
+// requests over several resident gauge configurations with continuous
+// batching.  A worker thread serves one configuration at a time through the
+// resumable lockstep batch (ddamg_batch_*): between FGMRES restart cycles it
+// takes finished solves out and admits waiting requests of that
+// configuration into the freed slots.  Several workers serve different
+// configurations at once, each on its own CUDA stream, so their kernels
+// overlap on the device.  Configurations are admitted by device-memory
+// footprint.  Host code only; every solve goes through the library's ABI.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,6 +36,9 @@ struct Request {
   Clock::time_point t_submit, t_start;
   ddamg_request_info rinfo{};
   bool done = false;
+  std::vector<int> slots;        // batch slots of its right-hand sides
+  int taken = 0;                 // right-hand sides finished
+  ddamg_status status = DDAMG_OK;
 };
 
 struct Config {
@@ -41,6 +48,8 @@ struct Config {
   ddamg_handle h = nullptr;      // resident handle, nullptr when released
   size_t bytes = 0;              // device bytes last measured (0: never set up)
   uint64_t last_use = 0;
+  bool busy = false;             // a worker is serving it
+  cudaStream_t st = nullptr;     // its stream (created with its handle)
 };
 
 // Estimate of a configuration's device memory before its first setup (it
@@ -67,20 +76,17 @@ size_t estimate_bytes(const ddamg_params& p, int max_batch) {
 struct ddamg_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_idle;   // a configuration stopped being served
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, Request*> reqs;
   std::deque<Config> cfgs;       // stable references while configs are added
-  std::thread worker;
+  std::vector<std::thread> workers;
   bool stop = false;
   size_t budget = 0;
   int max_batch = 12;
   int device = 0;
-  cudaStream_t st = nullptr;
-  bool own_stream = false;
+  cudaStream_t st = nullptr;     // the caller's stream (nullptr: one stream per config)
   uint64_t next_id = 1, tick = 0;
-  double* stage_rhs = nullptr;   // pinned staging of a batch
-  double* stage_x = nullptr;
-  size_t stage_reals = 0;
 };
 
 namespace {
@@ -129,11 +135,20 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   for (;;) {
     Config* lru = nullptr;
     {
-      std::lock_guard<std::mutex> lk(s->mu);
+      std::unique_lock<std::mutex> lk(s->mu);
       used = resident_bytes(s);
       if (!s->budget || used + need <= s->budget) break;
-      for (auto& o : s->cfgs)
-        if (o.h && &o != &c && (!lru || o.last_use < lru->last_use)) lru = &o;
+      bool other_busy = false;
+      for (auto& o : s->cfgs) {
+        if (o.h && &o != &c && !o.busy && (!lru || o.last_use < lru->last_use)) lru = &o;
+        other_busy |= o.h && &o != &c && o.busy;
+      }
+      if (!lru && other_busy) {
+        // the memory belongs to configurations being served: wait until one
+        // of them is idle (and may be released), then look again
+        s->cv_idle.wait(lk);
+        continue;
+      }
     }
     if (!lru) break;                 // nothing left to release: try, the handle's budget decides
     release(s, *lru);
@@ -141,8 +156,17 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   if (s->budget && used >= s->budget) return DDAMG_ENOMEM;
   ddamg_params p = c.p;
   p.hbm_budget = s->budget ? s->budget - used : 0;
+  if (!c.st) {
+    if (s->st) {
+      c.st = s->st;
+    } else if (cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c.st = nullptr;
+      return DDAMG_ECUDA;
+    }
+  }
   ddamg_handle h = nullptr;
-  ddamg_status st = ddamg_setup(&p, c.gauge.data(), 0, s->st, &h);
+  ddamg_status st = ddamg_setup(&p, c.gauge.data(), 0, c.st, &h);
   if (st != DDAMG_OK) {
     if (h) ddamg_destroy(h);
     return st;
@@ -156,100 +180,138 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   return DDAMG_OK;
 }
 
-bool grow_stage(ddamg_server* s, size_t reals) {
-  if (s->stage_reals >= reals) return true;
-  if (s->stage_rhs) cudaFreeHost(s->stage_rhs);
-  if (s->stage_x) cudaFreeHost(s->stage_x);
-  s->stage_rhs = s->stage_x = nullptr;
-  s->stage_reals = 0;
-  if (cudaHostAlloc(&s->stage_rhs, reals * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc(&s->stage_x, reals * sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  s->stage_reals = reals;
-  return true;
+void finish(ddamg_server* s, Request* r, Clock::time_point t) {
+  // caller holds s->mu
+  r->rinfo.status = r->status;
+  r->rinfo.queue_seconds = std::chrono::duration<double>(r->t_start - r->t_submit).count();
+  r->rinfo.latency_seconds = std::chrono::duration<double>(t - r->t_submit).count();
+  r->done = true;
+  s->cv_done.notify_all();
 }
 
-// one batch: the config of the oldest request and every waiting request of
-// that config, in arrival order, up to max_batch right-hand sides
-void run_batch(ddamg_server* s, std::vector<Request*>& batch) {
-  const int ci = batch[0]->cfg;
-  int tot = 0;
-  double tol = batch[0]->tol;
-  for (Request* r : batch) {
-    tot += r->nrhs;
-    tol = std::min(tol, r->tol);
-  }
+// Serve configuration ci until it has neither running nor waiting requests:
+// admit waiting requests (arrival order) into free slots, run a restart
+// cycle, take out the requests whose right-hand sides have all finished.
+void serve(ddamg_server* s, int ci) {
   int setup_run = 0;
   ddamg_status st = ensure_resident(s, ci, &setup_run);
-  Config* cp;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    cp = &s->cfgs[ci];
-  }
-  Config& c = *cp;
-  std::vector<ddamg_solve_info> info(tot);
-  if (st == DDAMG_OK && !grow_stage(s, (size_t)tot * c.field_reals)) st = DDAMG_ENOMEM;
-  if (st == DDAMG_OK) {
-    size_t off = 0;
-    for (Request* r : batch) {
-      std::memcpy(s->stage_rhs + off, r->rhs, (size_t)r->nrhs * c.field_reals * sizeof(double));
-      off += (size_t)r->nrhs * c.field_reals;
-    }
-    st = ddamg_solve_batched(c.h, tot, s->stage_rhs, s->stage_x, 0, tol, info.data());
-    measure(s, c);
-    if (st == DDAMG_OK || st == DDAMG_ENOCONV) {
-      off = 0;
-      int k = 0;
-      for (Request* r : batch) {
-        std::memcpy(r->x, s->stage_x + off, (size_t)r->nrhs * c.field_reals * sizeof(double));
-        off += (size_t)r->nrhs * c.field_reals;
-        if (r->info) std::memcpy(r->info, info.data() + k, (size_t)r->nrhs * sizeof(ddamg_solve_info));
-        k += r->nrhs;
+  Config& c = s->cfgs[ci];
+  const int S = s->max_batch;
+  std::vector<Request*> slot_req(S, nullptr);
+  std::vector<Request*> active;
+  if (st == DDAMG_OK) st = ddamg_batch_begin(c.h, S);
+  for (;;) {
+    // admission (requests that fit into the free slots)
+    std::vector<Request*> fresh;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      int free_slots = 0;
+      for (int k = 0; k < S; ++k) free_slots += slot_req[k] == nullptr;
+      for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Request* r = *it;
+        if (r->cfg == ci && (st != DDAMG_OK || r->nrhs <= free_slots)) {
+          if (st == DDAMG_OK) free_slots -= r->nrhs;
+          fresh.push_back(r);
+          it = s->queue.erase(it);
+        } else {
+          ++it;
+        }
       }
-    } else {
-      release(s, c);     // a handle that failed mid-solve is set up afresh next time
     }
+    const auto now = Clock::now();
+    for (Request* r : fresh) {
+      r->t_start = now;
+      r->rinfo.setup_run = setup_run;
+      if (st != DDAMG_OK) {          // the configuration could not be set up
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->status = st;
+        finish(s, r, now);
+        continue;
+      }
+      for (int j = 0, k = 0; j < r->nrhs; ++j) {
+        while (slot_req[k]) ++k;
+        slot_req[k] = r;
+        r->slots.push_back(k);
+        const ddamg_status a = ddamg_batch_admit(c.h, k, r->rhs + (size_t)j * c.field_reals, 0, r->tol);
+        if (a != DDAMG_OK && r->status == DDAMG_OK) r->status = a;
+      }
+      active.push_back(r);
+    }
+    setup_run = 0;
+    if (active.empty()) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      bool more = false;
+      for (Request* r : s->queue) more |= r->cfg == ci;
+      if (!more) break;
+      continue;
+    }
+    int running = 0;
+    for (Request* r : active) r->rinfo.batch_requests = std::max(r->rinfo.batch_requests, (int)active.size());
+    int in_use = 0;
+    for (int k = 0; k < S; ++k) in_use += slot_req[k] != nullptr;
+    for (Request* r : active) r->rinfo.batch_rhs = std::max(r->rinfo.batch_rhs, in_use);
+    const ddamg_status cy = ddamg_batch_cycle(c.h, &running);
+    // take out finished right-hand sides; complete requests
+    std::vector<Request*> still;
+    for (Request* r : active) {
+      bool all = true;
+      for (size_t j = 0; j < r->slots.size(); ++j) {
+        const int k = r->slots[j];
+        if (k < 0) continue;
+        int state = 0;
+        if (cy == DDAMG_OK) ddamg_batch_slot(c.h, k, &state);
+        if (cy != DDAMG_OK || state == 2) {
+          ddamg_solve_info inf{};
+          ddamg_status t = cy;
+          if (cy == DDAMG_OK) t = ddamg_batch_take(c.h, k, r->x + j * c.field_reals, 0, &inf);
+          if (r->info) r->info[j] = inf;
+          if (t != DDAMG_OK && r->status == DDAMG_OK) r->status = t;
+          slot_req[k] = nullptr;
+          r->slots[j] = -1;
+        } else {
+          all = false;
+        }
+      }
+      if (all) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        finish(s, r, Clock::now());
+      } else {
+        still.push_back(r);
+      }
+    }
+    active.swap(still);
+    if (cy != DDAMG_OK) {
+      release(s, c);                 // a handle that failed mid-solve is set up afresh next time
+      st = cy;
+    }
+    measure(s, c);
   }
-  const auto t_done = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);
-  for (Request* r : batch) {
-    r->rinfo.status = st;
-    r->rinfo.batch_rhs = tot;
-    r->rinfo.batch_requests = (int)batch.size();
-    r->rinfo.setup_run = setup_run;
-    r->rinfo.queue_seconds = std::chrono::duration<double>(r->t_start - r->t_submit).count();
-    r->rinfo.latency_seconds = std::chrono::duration<double>(t_done - r->t_submit).count();
-    r->done = true;
-  }
-  s->cv_done.notify_all();
+  c.busy = false;
+  s->cv_idle.notify_all();
 }
 
 void worker_loop(ddamg_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-    if (s->queue.empty()) break;          // stop requested and nothing left
-    const int ci = s->queue.front()->cfg;
-    std::vector<Request*> batch;
-    int tot = 0;
-    for (auto it = s->queue.begin(); it != s->queue.end();) {
-      Request* r = *it;
-      if (r->cfg == ci && tot + r->nrhs <= s->max_batch) {
-        tot += r->nrhs;
-        batch.push_back(r);
-        it = s->queue.erase(it);
-      } else {
-        ++it;
-      }
-    }
-    const auto t0 = Clock::now();
-    for (Request* r : batch) r->t_start = t0;
+    // the configuration of the oldest waiting request that no other worker serves
+    int ci = -1;
+    s->cv_work.wait(lk, [&] {
+      ci = -1;
+      for (Request* r : s->queue)
+        if (!s->cfgs[r->cfg].busy) {
+          ci = r->cfg;
+          break;
+        }
+      return ci >= 0 || (s->stop && s->queue.empty());
+    });
+    if (ci < 0) break;                 // stop requested and nothing left
+    s->cfgs[ci].busy = true;
     lk.unlock();
-    run_batch(s, batch);
+    serve(s, ci);
     lk.lock();
+    s->cv_work.notify_all();         // another configuration may now be free to serve
   }
 }
 
@@ -259,9 +321,14 @@ extern "C" {
 
 DDAMG_API ddamg_status ddamg_server_create(size_t hbm_budget, int max_batch, void* cuda_stream,
                                            ddamg_server_handle* out) {
+  return ddamg_server_create2(hbm_budget, max_batch, 2, cuda_stream, out);
+}
+
+DDAMG_API ddamg_status ddamg_server_create2(size_t hbm_budget, int max_batch, int workers, void* cuda_stream,
+                                            ddamg_server_handle* out) {
   if (!out) return DDAMG_EINVAL;
   *out = nullptr;
-  if (max_batch < 1 || max_batch > 64) return DDAMG_EINVAL;
+  if (max_batch < 1 || max_batch > 64 || workers < 1 || workers > 16) return DDAMG_EINVAL;
   auto* s = new ddamg_server();
   s->budget = hbm_budget;
   s->max_batch = max_batch;
@@ -270,17 +337,8 @@ DDAMG_API ddamg_status ddamg_server_create(size_t hbm_budget, int max_batch, voi
     delete s;
     return DDAMG_ECUDA;
   }
-  if (cuda_stream) {
-    s->st = (cudaStream_t)cuda_stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      delete s;
-      return DDAMG_ECUDA;
-    }
-    s->own_stream = true;
-  }
-  s->worker = std::thread(worker_loop, s);
+  s->st = (cudaStream_t)cuda_stream;   // nullptr: every configuration gets a stream of its own
+  for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_loop, s);
   *out = s;
   return DDAMG_OK;
 }
@@ -319,7 +377,7 @@ DDAMG_API ddamg_status ddamg_server_submit(ddamg_server_handle s, int config_id,
   s->reqs[r->id] = r;
   s->queue.push_back(r);
   *request_id = r->id;
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   return DDAMG_OK;
 }
 
@@ -351,12 +409,13 @@ DDAMG_API void ddamg_server_destroy(ddamg_server_handle s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
-  for (auto& c : s->cfgs) release(s, c);
+  for (auto& w : s->workers)
+    if (w.joinable()) w.join();
+  for (auto& c : s->cfgs) {
+    release(s, c);
+    if (c.st && c.st != s->st) cudaStreamDestroy(c.st);
+  }
   for (auto& kv : s->reqs) delete kv.second;
-  if (s->stage_rhs) cudaFreeHost(s->stage_rhs);
-  if (s->stage_x) cudaFreeHost(s->stage_x);
-  if (s->own_stream) cudaStreamDestroy(s->st);
   delete s;
 }
 

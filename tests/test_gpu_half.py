@@ -41,8 +41,12 @@ def _lib():
 
 @pytest.mark.parametrize("cfg", [SMALL, MID, FULL])
 @pytest.mark.parametrize("prec", [2, 3])
-def test_half_storage_D(cfg, prec):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_half_storage_D(cfg, prec, variant):
+    import paper_1811_00355_gb300 as P
     L, b, eps, m0, csw, n_v, seed = cfg
+    name = "D bf16" if prec == 2 else "D fp16"
+    P.pin_variant(name, variant)
     s = make(cfg, 1)
     try:
         op = oracle_op(L, eps, seed, m0, csw)
@@ -59,6 +63,7 @@ def test_half_storage_D(cfg, prec):
         assert_close(yz[0], rz[0], TOL_HALF, "tiny point source")
     finally:
         s.close()
+        P.pin_variant(name, -1)
 
 
 @pytest.mark.parametrize("prec", [2, 3])

@@ -65,6 +65,27 @@ def test_wilson_clover_D(cfg, prec):
         assert_close(y[k], ref[k], tol)
 
 
+@pytest.mark.parametrize("cfg", [SMALL, MID, FULL])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_D_variants_fp32(cfg, variant):
+    """Both measured variants of the FP32 D (one thread per site, four threads
+    per site) match the oracle; the autotuner records its choice."""
+    P = _P()
+    L, b, eps, m0, csw, n_v, seed = cfg
+    P.pin_variant("D fp32", variant)
+    try:
+        s = make(cfg, 1)
+        op = oracle_op(L, eps, seed, m0, csw)
+        x = syn.gaussian_spinors(2, L, 47)
+        y = s.apply_D(x, precision=1)
+        ref = op.apply(t(x)).numpy()
+        for k in range(2):
+            assert_close(y[k], ref[k], TOL32)
+        s.close()
+    finally:
+        P.pin_variant("D fp32", -1)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_clover_and_inverse_apply(prec):
     L, b, eps, m0, csw, n_v, seed = MID
