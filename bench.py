@@ -413,9 +413,11 @@ def variants(P, torch, stream, U_dev, b_dev, steps, flush):
 # [-0.4, -0.2], csw in [1.0, 1.5] with a fixed seed), Poisson arrivals, 1-12
 # Gaussian or point-source right-hand sides per request at tol 1e-8 or
 # 1e-10, two configurations served at a time, device memory admitted up to
-# 250 GB (the two large configurations together fit, all four do not).
-SERVING = dict(lattices=((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)), requests=32,
-               rate_hz=2.0, seed=2024, max_batch=12, restart=16, workers=2, budget=250 * 2 ** 30)
+# 250 GB (the two large configurations together fit, all four do not).  The
+# arrival rate keeps the offered load (about 3 right-hand sides per second,
+# a quarter of them on 32^3 x 64) below what the largest lattice can serve.
+SERVING = dict(lattices=((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)), requests=24,
+               rate_hz=0.5, seed=2024, max_batch=12, restart=16, workers=2, budget=250 * 2 ** 30)
 
 
 def serving(P, torch, stream):

@@ -696,20 +696,24 @@ std::string lattice_key(const ddamg_ctx* h, const char* prec, int nf) {
 }
 
 // ---- operators on device fields ---------------------------------------------------
+// variant of the FP32 y = D x for nf fields: one thread per site (0) or
+// four (1), measured on x and y the first time
+ddamg_status dslash32_variant(ddamg_ctx* h, const float* x, float* y, int nf, int* v) {
+  *v = 0;
+  if (h->g.V % 8) return DDAMG_OK;
+  auto run = [&](int var) -> cudaError_t {
+    if (var == 1) return dslash4<float>(h->g, x, nullptr, y, nullptr, h->g32, h->A32, nf, h->st);
+    return dslash<float>(h->g, DSLASH_D, x, nullptr, y, h->g32, h->A32, nf, h->st);
+  };
+  return tuned(h, "D fp32", lattice_key(h, "fp32", nf), 2, run, v);
+}
+
 template <class R>
 ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int nf) {
   addf(h, (double)nf * h->g.V * (mode == DSLASH_RES ? F_RES : mode == DSLASH_CLOVER ? F_CLOV : F_D));
   int v = 0;
-  if constexpr (sizeof(R) == 4) {
-    // y = D x in FP32: one thread per site (0) or four (1), measured
-    if (mode == DSLASH_D && h->g.V % 8 == 0) {
-      auto run = [&](int var) -> cudaError_t {
-        if (var == 1) return dslash4<float>(h->g, x, nullptr, y, nullptr, h->g32, h->A32, nf, h->st);
-        return dslash<R>(h->g, mode, x, b, y, gauge_of<R>(h), clov_of<R>(h, false), nf, h->st);
-      };
-      TRY(tuned(h, "D fp32", lattice_key(h, "fp32", nf), 2, run, &v));
-    }
-  }
+  if constexpr (sizeof(R) == 4)
+    if (mode == DSLASH_D) TRY(dslash32_variant(h, x, y, nf, &v));
   CK(timed(h, 0, [&] {
     if constexpr (sizeof(R) == 4)
       if (v == 1) return dslash4<float>(h->g, x, nullptr, y, nullptr, h->g32, h->A32, nf, h->st);
@@ -1032,7 +1036,10 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
   else coarse_gmres_exact_bytes<double>(h->g, h->p.n_v, h->p.coarse_restart, 1);
   // the D of the captured iterations (FP32 inner precision) is chosen now:
   // nothing can be timed inside a capture
-  if (refine_mode(h)) TRY(op_dslash<float>(h, DSLASH_D, (const float*)h->fin, nullptr, (float*)h->fout, 1));
+  if (refine_mode(h)) {
+    int v = 0;
+    TRY(dslash32_variant(h, (const float*)h->fin, (float*)h->fout, 1, &v));
+  }
   return DDAMG_OK;
 }
 
