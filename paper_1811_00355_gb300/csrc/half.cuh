@@ -123,6 +123,13 @@ __device__ __forceinline__ void load_spinor_h(const S* f, const float* nrm, int 
 #pragma unroll
   for (int k = 0; k < SPINOR_NR; ++k) v[k] *= m;
 }
+// the stored values of site d's spinor, not yet multiplied by the site norm
+template <class S>
+__device__ __forceinline__ void load_spinor_h_raw(const S* f, int d, int Vb, Spinor<float>& s) {
+  float* v = reinterpret_cast<float*>(s.c);
+#pragma unroll
+  for (int u = 0; u < HSPIN_NU; ++u) ld8<S>(f, hunit<HSPIN_NU>(d, Vb, u), v + 8 * u);
+}
 // the same for data written by an earlier kernel of the same sequence
 template <class S>
 __device__ __forceinline__ void load_spinor_h_cg(const S* f, const float* nrm, int d, int Vb, Spinor<float>& s) {

@@ -215,23 +215,33 @@ __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const 
                                             bool m_from_d0 = false) {
   using T = typename U16<R>::T;
   constexpr int RPU = 16 / (2 * sizeof(R));
+  // wide lockstep groups split their right-hand sides over RS units, so
+  // that more threads share a site's work and each one's chain of
+  // multiply-adds per column is shorter (the block entries are then read by
+  // RS threads, the later ones from L1); the slices write disjoint rows of
+  // the partial sums
+  constexpr int RS = NR >= 8 ? 2 : 1;
+  constexpr int NRS = NR / RS;
+  static_assert(NR % RS == 0, "right-hand-side slices must divide the lockstep width");
   const int NP = n2 / RPU;
   const int ND = d1 - d0;
   // column chunks: enough units for every thread, at most mvp_groups(NR) groups
-  int CC = (int)blockDim.x / (ND * NP);
+  int CC = (int)blockDim.x / (ND * NP * RS);
   if (CC * ND > mvp_groups(NR)) CC = mvp_groups(NR) / ND;
   if (CC < 1) CC = 1;
   if (CC > n2) CC = n2;
   const int CW = (n2 + CC - 1) / CC;
-  const int units = ND * CC * NP;
+  const int units = ND * CC * NP * RS;
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int grp = u / NP, j = u - grp * NP;
+    const int rs = u % RS, uu = u / RS;
+    const int grp = uu / NP, j = uu - grp * NP;
     const int dd = grp / CC, cc = grp - dd * CC, d = d0 + dd;
     const int c0 = cc * CW, c1 = min(n2, c0 + CW);
     const T* col = reinterpret_cast<const T*>(M + (size_t)(m_from_d0 ? d - d0 : d) * n2 * n2) + j;
-    cpx<R> acc[NR][RPU];
+    const cpx<R>* svr = sv + (size_t)rs * NRS * 9 * n2;
+    cpx<R> acc[NRS][RPU];
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
+    for (int r = 0; r < NRS; ++r)
 #pragma unroll
       for (int q = 0; q < RPU; ++q) acc[r][q] = mk(R(0), R(0));
 #pragma unroll 8
@@ -243,16 +253,17 @@ __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const 
       if constexpr (RPU == 2) { e0 = mk((R)mm.x, (R)mm.y); e1 = mk((R)mm.z, (R)mm.w); }
       else { e0 = mk((R)mm.x, (R)mm.y); e1 = e0; }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        cpx<R> v = sv[(r * 9 + d) * n2 + c];
+      for (int r = 0; r < NRS; ++r) {
+        cpx<R> v = svr[(r * 9 + d) * n2 + c];
         fma(acc[r][0], e0, v);
         if constexpr (RPU == 2) fma(acc[r][1], e1, v);
       }
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
+    for (int r = 0; r < NRS; ++r)
 #pragma unroll
-      for (int q = 0; q < RPU; ++q) mvp[((size_t)grp * NR + r) * n2 + RPU * j + q] = acc[r][q];
+      for (int q = 0; q < RPU; ++q)
+        mvp[((size_t)grp * NR + rs * NRS + r) * n2 + RPU * j + q] = acc[r][q];
   }
   __syncthreads();
   const int ngrp = ND * CC;

@@ -17,6 +17,9 @@ constexpr int TPB = 128;
 
 inline unsigned nblk(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
 
+// The hop is linear in the neighbour spinor, so its site norm m rides on the
+// boundary sign: the stored values are projected and multiplied as they are
+// and the result is accumulated with the factor +-m.
 template <int MU, class S>
 __device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x, const float* __restrict__ xn,
                                           const S* __restrict__ gauge, int d, Spinor<float>& acc) {
@@ -25,8 +28,9 @@ __device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x
   {  // forward: (1 - g_mu) U_mu(x) x(x+mu)
     const uint32_t e = __ldg(g.nbr + (size_t)(2 * MU) * g.V + d);
     const int n = (int)(e & ~NEG_BIT);
-    const float sc = (e & NEG_BIT) ? -1.f : 1.f;
-    load_spinor_h<S>(x, xn, n, g.Vb, nb);
+    const float m = __ldg(xn + n);
+    const float sc = (e & NEG_BIT) ? -m : m;
+    load_spinor_h_raw<S>(x, n, g.Vb, nb);
     project<MU, -1>(nb, h);
     Link<float> U;
     load_link_h<S>(gauge, d, g.Vb, MU, U);
@@ -36,8 +40,9 @@ __device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x
   {  // backward: (1 + g_mu) U_mu(x-mu)^H x(x-mu)
     const uint32_t e = __ldg(g.nbr + (size_t)(2 * MU + 1) * g.V + d);
     const int n = (int)(e & ~NEG_BIT);
-    const float sc = (e & NEG_BIT) ? -1.f : 1.f;
-    load_spinor_h<S>(x, xn, n, g.Vb, nb);
+    const float m = __ldg(xn + n);
+    const float sc = (e & NEG_BIT) ? -m : m;
+    load_spinor_h_raw<S>(x, n, g.Vb, nb);
     project<MU, +1>(nb, h);
     Link<float> U;
     load_link_h<S>(gauge, n, g.Vb, MU, U);
@@ -47,10 +52,10 @@ __device__ __forceinline__ void hop_dir_h(const Geom& g, const S* __restrict__ x
 }
 
 // one thread per site; right-hand side blockIdx.y (fields V sites apart)
-// at most 64 registers: eight CTAs per SM keep more loads in flight (the
-// kernel waits on memory latency, not on arithmetic)
+// at most 80 registers: six CTAs per SM keep more loads in flight than the
+// unbounded 96, and unlike 64 (eight CTAs) leave almost nothing to spill
 template <class S, int MODE>
-__global__ void __launch_bounds__(TPB, 8) k_dslash_h(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
+__global__ void __launch_bounds__(TPB, 6) k_dslash_h(Geom g, const S* __restrict__ x, const float* __restrict__ xn,
                                                   const S* __restrict__ b, const float* __restrict__ bn,
                                                   S* __restrict__ y, float* __restrict__ yn,
                                                   const S* __restrict__ gauge, const S* __restrict__ clover) {
@@ -63,10 +68,13 @@ __global__ void __launch_bounds__(TPB, 8) k_dslash_h(Geom g, const S* __restrict
   y += off;
   yn += noff;
   Spinor<float> out;
-  {
+  {  // A x on the stored values, then the site norm
     Spinor<float> xs;
-    load_spinor_h<S>(x, xn, d, g.Vb, xs);
+    load_spinor_h_raw<S>(x, d, g.Vb, xs);
     clover_mul_h<S>(clover, d, g.Vb, xs, out);
+    const float m = __ldg(xn + d);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out.c[k] = m * out.c[k];
   }
   if (MODE != DSLASH_CLOVER) {
     Spinor<float> acc;
