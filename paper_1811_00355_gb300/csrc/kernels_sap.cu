@@ -138,44 +138,65 @@ __device__ __forceinline__ void clover_rows(const R* __restrict__ clov, int d, i
 // non-zero per row, B[r][pi(r)] = c_r with pi the identity (z, t) or the
 // swap (x, y) and c_r in {+-1, +-i}.  Writing the projector this way keeps
 // the four threads of a site (four directions) in one instruction stream.
+// A factor c in {+-1, +-i} is held as (rot, a): c = a when rot is false and
+// c = -i a when it is true, so c t = rot ? (a t.im, -a t.re) : (a t.re, a t.im)
+// costs two selects and no multiplications.
 template <class R>
 struct Dir {
-  bool swp;
-  cpx<R> c0, c1;
+  bool swp;          // pi swaps the spin pairs
+  bool rot0, rot1;   // c_0, c_1 imaginary
+  R a0, a1;
 };
 template <class R>
 __device__ __forceinline__ Dir<R> make_dir(int mu) {
   Dir<R> d;
   d.swp = mu < 2;
-  if (mu == 0) { d.c0 = mk(R(0), R(-1)); d.c1 = mk(R(0), R(-1)); }
-  else if (mu == 1) { d.c0 = mk(R(-1), R(0)); d.c1 = mk(R(1), R(0)); }
-  else if (mu == 2) { d.c0 = mk(R(0), R(-1)); d.c1 = mk(R(0), R(1)); }
-  else { d.c0 = mk(R(1), R(0)); d.c1 = mk(R(1), R(0)); }
+  d.rot0 = d.rot1 = (mu == 0 || mu == 2);
+  d.a0 = (mu == 1) ? R(-1) : R(1);      // c_0: -i, -1, -i, 1
+  d.a1 = (mu == 2) ? R(-1) : R(1);      // c_1: -i,  1,  i, 1
   return d;
+}
+// acc += s c t for c = (rot, a) and a real scale s (sa = s a)
+template <class R>
+__device__ __forceinline__ void add_ct(cpx<R>& acc, bool rot, R sa, cpx<R> t) {
+  const R u = rot ? t.im : t.re, v = rot ? t.re : t.im;
+  const R sb = rot ? -sa : sa;
+  acc.re += sa * u;
+  acc.im += sb * v;
 }
 // h_r = s_r + sigma c_r s_{2 + pi(r)}
 template <class R>
 __device__ __forceinline__ void project_rt(const Spinor<R>& p, const Dir<R>& dr, R sigma, cpx<R> h[2][3]) {
+  const R s0 = sigma * dr.a0, s1 = sigma * dr.a1;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     cpx<R> s2 = p.c[6 + a], s3 = p.c[9 + a];
     cpx<R> t0 = dr.swp ? s3 : s2, t1 = dr.swp ? s2 : s3;
-    h[0][a] = p.c[a] + sigma * (dr.c0 * t0);
-    h[1][a] = p.c[3 + a] + sigma * (dr.c1 * t1);
+    h[0][a] = p.c[a];
+    h[1][a] = p.c[3 + a];
+    add_ct(h[0][a], dr.rot0, s0, t0);
+    add_ct(h[1][a], dr.rot1, s1, t1);
   }
 }
-// acc += sc [y; sigma B^H y],  (B^H y)_r = conj(c_pi(r)) y_pi(r)
+// acc += sc [y; sigma B^H y],  (B^H y)_r = conj(c_pi(r)) y_pi(r); the
+// conjugate of (rot, a) is (rot, -a) when rot is true
 template <class R>
 __device__ __forceinline__ void accumulate_rt(Spinor<R>& acc, const cpx<R> y[2][3], const Dir<R>& dr,
                                               R sigma, R sc) {
-  cpx<R> k2 = conj(dr.swp ? dr.c1 : dr.c0), k3 = conj(dr.swp ? dr.c0 : dr.c1);
+  const bool r2 = dr.swp ? dr.rot1 : dr.rot0, r3 = dr.swp ? dr.rot0 : dr.rot1;
+  R a2 = dr.swp ? dr.a1 : dr.a0, a3 = dr.swp ? dr.a0 : dr.a1;
+  if (r2) a2 = -a2;
+  if (r3) a3 = -a3;
+  const R s2 = sigma * sc * a2, s3 = sigma * sc * a3;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    cpx<R> y0 = sc * y[0][a], y1 = sc * y[1][a];
-    acc.c[a] = acc.c[a] + y0;
-    acc.c[3 + a] = acc.c[3 + a] + y1;
-    acc.c[6 + a] = acc.c[6 + a] + sigma * (k2 * (dr.swp ? y1 : y0));
-    acc.c[9 + a] = acc.c[9 + a] + sigma * (k3 * (dr.swp ? y0 : y1));
+    const cpx<R> y0 = y[0][a], y1 = y[1][a];
+    acc.c[a].re += sc * y0.re;
+    acc.c[a].im += sc * y0.im;
+    acc.c[3 + a].re += sc * y1.re;
+    acc.c[3 + a].im += sc * y1.im;
+    add_ct(acc.c[6 + a], r2, s2, dr.swp ? y1 : y0);
+    add_ct(acc.c[9 + a], r3, s3, dr.swp ? y0 : y1);
   }
 }
 
@@ -584,6 +605,25 @@ struct IO<__half> : IOH<__half> {};
 template <>
 struct IO<__nv_bfloat16> : IOH<__nv_bfloat16> {};
 
+// block sum of three per-thread partials with one barrier: every warp
+// leaves its three warp sums in sh[3 w ..], and after the barrier every warp
+// adds all of them up itself, in the same fixed order, so every thread holds
+// the same bits.  Two calls must be separated by another barrier of the CTA
+// (all reads of one call are done before the next call writes).
+__device__ __forceinline__ void block_sum3_1(float ra, float rb, float rc, float& a, float& b, float& c,
+                                             float* sh) {
+  ra = warp_sum_r<float>(ra);
+  rb = warp_sum_r<float>(rb);
+  rc = warp_sum_r<float>(rc);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (l == 0) { sh[3 * w] = ra; sh[3 * w + 1] = rb; sh[3 * w + 2] = rc; }
+  __syncthreads();
+  const float x = l < nw ? sh[3 * l] : 0.f, y = l < nw ? sh[3 * l + 1] : 0.f, z = l < nw ? sh[3 * l + 2] : 0.f;
+  a = warp_sum_r<float>(x);
+  b = warp_sum_r<float>(y);
+  c = warp_sum_r<float>(z);
+}
+
 // own 3 rows of a staged chiral block (site h) times v6
 template <class S>
 __device__ __forceinline__ void rows3(const typename IO<S>::T* A, int Vh, int h, int cb, int half, const f2 v6[6],
@@ -801,6 +841,13 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   for (int it = 0; it < mr_iters; ++it) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) E[(3 * sub + i) * Vh + h] = res[i];
+    // A_ee res needs only this site's res: formed while the barrier waits
+    f2 p[3];
+    {
+      f2 v6[6];
+      chiral6<float>(res, sub, v6);
+      aee_rows(v6, p);
+    }
     __syncthreads();
     {  // odd: w = A_oo^-1 (-1/2 hop(res))
       f2 tt[3], v6[6], w[3];
@@ -814,11 +861,8 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     }
     __syncthreads();
     float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
-    f2 p[3];
     {  // even: p = A_ee res + 1/2 hop(w)
-      f2 tt[3], v6[6];
-      chiral6<float>(res, sub, v6);
-      aee_rows(v6, p);
+      f2 tt[3];
       hop_block_q<S>(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -829,7 +873,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       }
     }
     float dre, dim, pp;
-    block_sum3<float>(pr_re, pr_im, pp_r, dre, dim, pp, red);
+    block_sum3_1(pr_re, pr_im, pp_r, dre, dim, pp, red);
     if (pp > 0.f) {
       const f2 a = mk(dre / pp, dim / pp);
 #pragma unroll
