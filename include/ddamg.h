@@ -492,6 +492,10 @@ DDAMG_API ddamg_status ddamg_server_wait(ddamg_server_handle s, uint64_t request
                                ddamg_request_info *rinfo);
 /* Device memory currently held by the server's resident configs. */
 DDAMG_API ddamg_status ddamg_server_device_bytes(ddamg_server_handle s, size_t *bytes);
+/* Message of the most recent failed library call made while serving (empty
+ * when none failed).  The string belongs to the calling thread and stays
+ * valid until its next call of this function. */
+DDAMG_API const char *ddamg_server_last_error(ddamg_server_handle s);
 /* Finish the queued requests, stop the worker, release everything. */
 DDAMG_API void ddamg_server_destroy(ddamg_server_handle s);
 

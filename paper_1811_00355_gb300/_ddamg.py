@@ -155,6 +155,7 @@ SIGNATURES = {
     "ddamg_server_submit": (_I, [_H, _I, _I, _P, _P, _D, _P, C.POINTER(C.c_uint64)]),
     "ddamg_server_wait": (_I, [_H, C.c_uint64, C.POINTER(RequestInfo)]),
     "ddamg_server_device_bytes": (_I, [_H, C.POINTER(C.c_size_t)]),
+    "ddamg_server_last_error": (C.c_char_p, [_H]),
     "ddamg_server_destroy": (None, [_H]),
     "ddamg_destroy": (None, [_H]),
 }
@@ -557,7 +558,8 @@ class Server:
 
     def _check(self, status):
         if status != 0:
-            raise DDAMGError(status, self.lib.ddamg_status_string(status).decode())
+            msg = self.lib.ddamg_server_last_error(self.h) if self.h else b""
+            raise DDAMGError(status, (msg or self.lib.ddamg_status_string(status)).decode())
 
     def add_config(self, params: Params, gauge) -> int:
         gauge = np.ascontiguousarray(gauge, dtype=np.complex128)

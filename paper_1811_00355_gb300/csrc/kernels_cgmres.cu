@@ -33,6 +33,10 @@ constexpr int TPB = 512;
 // partial-sum groups of mrhs_matvec (the plan's mvp buffer): more column
 // chunks for few right-hand sides, fewer where the buffer grows with NR
 __host__ __device__ constexpr int mvp_groups(int NR) { return NR >= 8 ? 9 : 18; }
+// row stride (complex entries) of the staged vectors sv[r][d][.]: one more
+// than n2, so that rows of different directions and right-hand sides read
+// at the same column fall on different shared-memory banks
+__host__ __device__ constexpr int sv_stride(int n2) { return n2 + 1; }
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
 constexpr int NRMAX = 12;
@@ -110,6 +114,20 @@ __device__ bool grid_barrier(unsigned* bar, int* status, long long limit) {
   return grid_wait(bar, status, limit);
 }
 
+// L2 prefetch of `bytes` bytes at p (16-byte aligned, a multiple of 16) by
+// the calling warp, in bulk prefetches of at most 32 KB per lane: the block
+// operators of the next coarse site travel from HBM while this site's block
+// product runs
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  constexpr size_t PIECE = 32768;
+  for (size_t off = (size_t)(threadIdx.x & 31) * PIECE; off < bytes; off += 32 * PIECE) {
+    const size_t n = bytes - off < PIECE ? bytes - off : PIECE;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char*>(p) + off),
+                 "r"((unsigned)n)
+                 : "memory");
+  }
+}
+
 // shared-memory plan, identical on host and device
 struct Plan {
   size_t V, x, rl, w, sv, mvp, tmp;                                    // cpx offsets (bytes)
@@ -144,7 +162,7 @@ __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, 
     p.w = putg((size_t)NR * L * c);
     lb = g;
   }
-  p.sv = put((size_t)NR * 9 * n2 * c);
+  p.sv = put((size_t)NR * 9 * sv_stride(n2) * c);
   p.mvp = put((size_t)mvp_groups(NR) * NR * n2 * c);
   p.tmp = put((size_t)NR * n2 * c);
   p.hc = put((size_t)NR * 2 * (m + 1) * 8);
@@ -201,6 +219,7 @@ struct CGA {
 
 // Multi-right-hand-side block product on one coarse site, whole CTA:
 //   out[r][row] = sum_{d in [d0, d1)} sum_c M_d[row][c] sv[r][d][c]
+// (sv rows sv_stride(n2) entries apart)
 // Blocks are column-major, so a thread streams RPU rows down the columns
 // (16-byte loads, neighbouring threads on neighbouring rows) and applies each
 // loaded entry to all NR vectors.  The column range is split into CC chunks
@@ -238,7 +257,8 @@ __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const 
     const int dd = grp / CC, cc = grp - dd * CC, d = d0 + dd;
     const int c0 = cc * CW, c1 = min(n2, c0 + CW);
     const T* col = reinterpret_cast<const T*>(M + (size_t)(m_from_d0 ? d - d0 : d) * n2 * n2) + j;
-    const cpx<R>* svr = sv + (size_t)rs * NRS * 9 * n2;
+    const int svs = sv_stride(n2);
+    const cpx<R>* svr = sv + (size_t)rs * NRS * 9 * svs;
     cpx<R> acc[NRS][RPU];
 #pragma unroll
     for (int r = 0; r < NRS; ++r)
@@ -254,7 +274,7 @@ __device__ __forceinline__ void mrhs_matvec(const cpx<R>* __restrict__ M, const 
       else { e0 = mk((R)mm.x, (R)mm.y); e1 = e0; }
 #pragma unroll
       for (int r = 0; r < NRS; ++r) {
-        cpx<R> v = svr[(r * 9 + d) * n2 + c];
+        cpx<R> v = svr[(r * 9 + d) * svs + c];
         fma(acc[r][0], e0, v);
         if constexpr (RPU == 2) fma(acc[r][1], e1, v);
       }
@@ -331,6 +351,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tx = threadIdx.x;
   const int TRI = m * (m + 1) / 2;
+  const int svs = sv_stride(n2);
 
   auto Vk = [&](int k, int r) { return V + ((size_t)k * NR + r) * L; };
 
@@ -340,14 +361,25 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
       cpx<R> v = mk(R(0), R(0));
       if (d > 0) v = (R)scl[r] * ldc(src + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
-      sv[idx] = v;
+      sv[(r * 9 + d) * svs + c] = v;
     }
     __syncthreads();
   };
   // odd phase: to[r][ko] = sum_{d>=1} (A_oo^-1 Dc[X][d]) src[r][nbr]
+  // block operators streamed from global memory (not resident): warp 0
+  // prefetches the next site's into L2 while the CTA works on this one
+  const size_t od_bytes = (size_t)8 * n2 * n2 * sizeof(cpx<R>), ev_bytes = (size_t)9 * n2 * n2 * sizeof(cpx<R>);
+  auto prefetch_odd = [&](int ko) {
+    if (ko < hi && tx < 32) prefetch_l2(a.AD + (size_t)ko * 8 * n2 * n2, od_bytes);
+  };
+  auto prefetch_even = [&](int ke) {
+    if (!a.resident && ke < hi && tx < 32) prefetch_l2(a.Dc + (size_t)a.g.ceven[ke] * 9 * n2 * n2, ev_bytes);
+  };
   auto phase_odd = [&](const cpx<R>* src) {
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
+      prefetch_odd(ko + 1);
+      if (ko + 1 == hi) prefetch_even(lo);
       stage_odd(X, src);
       mrhs_matvec<R, NR>(a.AD + (size_t)ko * 8 * n2 * n2, sv, 1, 9, n2, mvp, a.to + (size_t)ko * n2, (int)vstr,
                          true);
@@ -357,12 +389,14 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   auto phase_even = [&](const cpx<R>* vself, bool self, cpx<R>* out, const cpx<R>* bsrc) {
     for (int ke = lo; ke < hi; ++ke) {
       const int X = a.g.ceven[ke], kk = ke - lo;
+      prefetch_even(ke + 1);
+      if (ke + 1 == hi) prefetch_odd(lo);
       for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
         const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
         cpx<R> v;
         if (d == 0) v = self ? vself[(size_t)r * L + kk * n2 + c] : mk(R(0), R(0));
         else v = -ldc(a.to + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
-        sv[idx] = v;
+        sv[(r * 9 + d) * svs + c] = v;
       }
       __syncthreads();
       if (a.resident)
@@ -493,7 +527,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       const int X = a.g.codd[ko];
       for (int idx = tx; idx < NR * n2; idx += TPB) {
         const int r = idx / n2, c = idx - r * n2;
-        sv[(r * 9) * n2 + c] = r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0));
+        sv[(r * 9) * svs + c] = r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0));
       }
       __syncthreads();
       mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, a.to + (size_t)ko * n2, (int)vstr);
@@ -774,7 +808,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, 1, 9, n2, mvp, tmp, n2);
       for (int idx = tx; idx < NR * n2; idx += TPB) {
         const int r = idx / n2, c = idx - r * n2;
-        sv[(r * 9) * n2 + c] = tmp[idx] + (r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0)));
+        sv[(r * 9) * svs + c] = tmp[idx] + (r < nr ? bb[(size_t)r * a.g.nb * n2 + (size_t)X * n2 + c] : mk(R(0), R(0)));
       }
       __syncthreads();
       mrhs_matvec<R, NR>(a.Ainv + (size_t)X * n2 * n2, sv, 0, 1, n2, mvp, tmp, n2);
@@ -837,8 +871,11 @@ template <class R>
 cudaError_t smem_attr_locked(int dev, int NR, size_t bytes) {
   static size_t current[MAXDEV][5] = {};
   if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  // the limit only grows: a thread that sized its launch for a plan and
+  // released the lock must not find the limit lowered by another thread's
+  // smaller plan when it launches
   size_t& c = current[dev][nr_slot(NR)];
-  if (c == bytes) return cudaSuccess;
+  if (c >= bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel_for<R>(NR), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) c = bytes;
   return e;

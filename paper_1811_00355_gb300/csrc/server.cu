@@ -15,6 +15,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -87,9 +88,17 @@ struct ddamg_server {
   int device = 0;
   cudaStream_t st = nullptr;     // the caller's stream (nullptr: one stream per config)
   uint64_t next_id = 1, tick = 0;
+  std::string last_error;        // message of the most recent failed library call
 };
 
 namespace {
+
+// keep the message of a failed call on handle h (under the server's lock)
+void note_error(ddamg_server* s, ddamg_handle h, ddamg_status st) {
+  if (st == DDAMG_OK) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->last_error = ddamg_last_error(h);
+}
 
 // Configs are added by callers (under the lock) while the worker uses them:
 // the worker changes a config's handle and byte count, and scans the list,
@@ -233,6 +242,7 @@ void serve(ddamg_server* s, int ci) {
         slot_req[k] = r;
         r->slots.push_back(k);
         const ddamg_status a = ddamg_batch_admit(c.h, k, r->rhs + (size_t)j * c.field_reals, 0, r->tol);
+        note_error(s, c.h, a);
         if (a != DDAMG_OK && r->status == DDAMG_OK) r->status = a;
       }
       active.push_back(r);
@@ -251,6 +261,7 @@ void serve(ddamg_server* s, int ci) {
     for (int k = 0; k < S; ++k) in_use += slot_req[k] != nullptr;
     for (Request* r : active) r->rinfo.batch_rhs = std::max(r->rinfo.batch_rhs, in_use);
     const ddamg_status cy = ddamg_batch_cycle(c.h, &running);
+    note_error(s, c.h, cy);
     // take out finished right-hand sides; complete requests
     std::vector<Request*> still;
     for (Request* r : active) {
@@ -263,7 +274,10 @@ void serve(ddamg_server* s, int ci) {
         if (cy != DDAMG_OK || state == 2) {
           ddamg_solve_info inf{};
           ddamg_status t = cy;
-          if (cy == DDAMG_OK) t = ddamg_batch_take(c.h, k, r->x + j * c.field_reals, 0, &inf);
+          if (cy == DDAMG_OK) {
+            t = ddamg_batch_take(c.h, k, r->x + j * c.field_reals, 0, &inf);
+            if (t != DDAMG_ENOCONV) note_error(s, c.h, t);
+          }
           if (r->info) r->info[j] = inf;
           if (t != DDAMG_OK && r->status == DDAMG_OK) r->status = t;
           slot_req[k] = nullptr;
@@ -400,6 +414,14 @@ DDAMG_API ddamg_status ddamg_server_device_bytes(ddamg_server_handle s, size_t* 
   std::lock_guard<std::mutex> lk(s->mu);
   *bytes = resident_bytes(s);
   return DDAMG_OK;
+}
+
+DDAMG_API const char* ddamg_server_last_error(ddamg_server_handle s) {
+  static thread_local std::string copy;
+  if (!s) return "";
+  std::lock_guard<std::mutex> lk(s->mu);
+  copy = s->last_error;
+  return copy.c_str();
 }
 
 DDAMG_API void ddamg_server_destroy(ddamg_server_handle s) {
