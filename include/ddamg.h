@@ -319,6 +319,9 @@ typedef struct {
                             0: in global scratch                             */
   int resident_blocks;   /* 1: the even site's nine D_c blocks stay in shared
                             memory for the launch                            */
+  int block_ring;        /* 1: the blocks are streamed from global memory
+                            through a ring of shared-memory slots filled by
+                            bulk asynchronous copies ahead of their use      */
   size_t shared_bytes;   /* dynamic shared memory per CTA                    */
   size_t scratch_bytes;  /* global scratch the launch touches                */
 } ddamg_coarse_plan;

@@ -82,7 +82,7 @@ class RequestInfo(C.Structure):
 class CoarsePlan(C.Structure):
     _fields_ = [
         ("rhs_per_pass", C.c_int), ("ctas", C.c_int), ("sites_per_cta", C.c_int),
-        ("krylov_in_shared", C.c_int), ("resident_blocks", C.c_int),
+        ("krylov_in_shared", C.c_int), ("resident_blocks", C.c_int), ("block_ring", C.c_int),
         ("shared_bytes", C.c_size_t), ("scratch_bytes", C.c_size_t),
     ]
 

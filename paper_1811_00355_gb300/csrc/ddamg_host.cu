@@ -2285,6 +2285,7 @@ ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan* 
   out->sites_per_cta = c.per;
   out->krylov_in_shared = c.local_in_smem;
   out->resident_blocks = c.resident;
+  out->block_ring = c.ring;
   out->shared_bytes = c.smem_bytes;
   out->scratch_bytes = c.work_bytes;
   return DDAMG_OK;

@@ -267,7 +267,7 @@ struct CoarseSolveArgs {
 // blocks resident in shared memory; dynamic shared memory per CTA and the
 // bytes of `work` the launch touches
 struct CoarsePlan {
-  int NR, G, per, local_in_smem, resident;
+  int NR, G, per, local_in_smem, resident, ring;
   size_t smem_bytes, work_bytes;
 };
 template <class R>

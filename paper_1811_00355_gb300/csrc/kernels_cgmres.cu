@@ -40,6 +40,11 @@ __host__ __device__ constexpr int sv_stride(int n2) { return n2 + 1; }
 constexpr int NW = TPB / 32;
 constexpr int MAXM = 64;
 constexpr int NRMAX = 12;
+// block ring: slots of one 2n x 2n block each through which the block
+// operators of plans that do not keep them resident are streamed (FP32,
+// blocks of at least RING_MIN_N2 rows, where the loads are worth hiding)
+constexpr int RING = 4;
+constexpr int RING_MIN_N2 = 32;
 
 __device__ __forceinline__ cpx<float> ldc(const cpx<float>* p) {
   float2 t = __ldcg(reinterpret_cast<const float2*>(p));
@@ -134,6 +139,7 @@ struct Plan {
   size_t hc, h2, Rf, cs, sn, gv, yv, beta, bnorm, hn, scale;           // double offsets
   size_t act, kd, tot, conv;                                            // int offsets
   size_t Mres;         // resident D_c blocks of the CTA's even site (0: none)
+  size_t ring;         // block ring, RING blocks (0: none)
   size_t bytes;        // total shared memory
   size_t local_bytes;  // V + x + rl + w (moved to global when too large)
 };
@@ -141,7 +147,7 @@ struct Plan {
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) / 16 * 16; }
 
 __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, bool local_in_smem,
-                                          bool resident = false) {
+                                          bool resident = false, bool ring = false) {
   Plan p;
   const size_t c = 2 * (size_t)rs;
   size_t o = 0;
@@ -181,6 +187,7 @@ __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, 
   p.tot = put((size_t)NR * 4);
   p.conv = put((size_t)NR * 4);
   p.Mres = resident ? put((size_t)9 * n2 * n2 * c) : 0;
+  p.ring = ring ? put((size_t)RING * n2 * n2 * c) : 0;
   p.bytes = o;
   p.local_bytes = lb;
   return p;
@@ -204,6 +211,7 @@ struct CGA {
   int per;
   int local_in_smem;
   int resident;      // the CTA keeps its even site's D_c blocks in shared memory
+  int ring;          // block operators streamed through the shared-memory ring
   cpx<R>* wg;        // [NR][NE][n2]
   cpx<R>* to;        // [NR][NE][n2]
   cpx<R>* xg;        // [NR][NE][n2]
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   using A = R;
   const int n2 = a.n2, m = a.m, NE = a.NE;
   const int L = a.per * n2;
-  const Plan P = make_plan(NR, L, n2, m, sizeof(R), a.local_in_smem != 0, a.resident != 0);
+  const Plan P = make_plan(NR, L, n2, m, sizeof(R), a.local_in_smem != 0, a.resident != 0, a.ring != 0);
   cpx<R>* Mres = reinterpret_cast<cpx<R>*>(sm + P.Mres);   // [9][n2][n2] when resident
   unsigned char* lbase = a.local_in_smem ? sm : a.lglob + (size_t)blockIdx.x * a.lstride;
   cpx<R>* V = reinterpret_cast<cpx<R>*>(lbase + P.V);     // [m+1][NR][L]
@@ -375,7 +383,121 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   auto prefetch_even = [&](int ke) {
     if (!a.resident && ke < hi && tx < 32) prefetch_l2(a.Dc + (size_t)a.g.ceven[ke] * 9 * n2 * n2, ev_bytes);
   };
-  auto phase_odd = [&](const cpx<R>* src) {
+  // ---- block ring ------------------------------------------------------------
+  // The blocks a phase multiplies (nd per site, for the CTA's sites in
+  // order) are copied into RING shared-memory slots by bulk asynchronous
+  // copies that thread 0 issues up to RING - 1 blocks ahead of the CTA's
+  // use; slot s completes its copies on ring_full[s].  All threads wait for
+  // block b's copy (bounded), then meet at a barrier: past it every thread
+  // is done with block b - 1, so its slot may take block b + RING - 1.
+  __shared__ __align__(8) uint64_t ring_full[RING];
+  unsigned ring_used = 0;      // blocks consumed (the same in every thread)
+  unsigned ring_issued = 0;    // blocks whose copy was issued (thread 0)
+  if (a.ring && tx == 0) {
+    for (int q = 0; q < RING; ++q) mbar_init(&ring_full[q], 1);
+    mbar_fence_init();
+  }
+  // phase products out[si][r][row] = sum_t M_{b(si, t)}[row][c] sv[r][d0 + t][c]
+  // for the CTA's sites si < nsites: blk(i) is the address of the phase's
+  // block i (site i / nd, direction d0 + i % nd), stage(si) fills sv for
+  // site si (ending with a barrier), emit(si, r, row, value) stores a
+  // result.  False when a copy did not land in time (status DDAMG_ETIMEOUT
+  // set, the copies in flight waited for).
+  auto ring_phase = [&](int nsites, int nd, int d0, auto&& blk, auto&& stage, auto&& emit) -> bool {
+    if constexpr (sizeof(R) != 4) {
+      return false;        // FP32 only (the host never plans a ring otherwise)
+    } else {
+      using T = typename U16<R>::T;
+      constexpr int RPU = 2;                       // complex rows per 16-byte unit
+      constexpr int RS = NR >= 8 ? 2 : 1, NRS = NR / RS;
+      const unsigned nn = (unsigned)(n2 * n2);
+      const unsigned bytes = nn * (unsigned)sizeof(cpx<R>);
+      cpx<R>* ringbuf = reinterpret_cast<cpx<R>*>(sm + P.ring);
+      const unsigned base = ring_used, end = base + (unsigned)(nsites * nd);
+      auto issue = [&](unsigned i) {
+        const unsigned q = i % RING;
+        mbar_expect_tx(&ring_full[q], bytes);
+        bulk_g2s(ringbuf + (size_t)q * nn, blk(i - base), bytes, &ring_full[q]);
+      };
+      if (tx == 0)
+        for (; ring_issued < end && ring_issued < base + RING; ++ring_issued) issue(ring_issued);
+      // this thread's unit: row pair j, right-hand-side slice rs, column chunk cc
+      const int NP = n2 / RPU;
+      int CC = TPB / (NP * RS);
+      if (CC > mvp_groups(NR)) CC = mvp_groups(NR);
+      if (CC > n2) CC = n2;
+      if (CC < 1) CC = 1;
+      const int CW = (n2 + CC - 1) / CC;
+      const int units = NP * RS * CC;
+      const int j = tx % NP, rest = tx / NP, rs = rest % RS, cc = rest / RS;
+      const int c0 = cc * CW, c1 = min(n2, c0 + CW);
+      const cpx<R>* svr = sv + (size_t)rs * NRS * 9 * svs;
+      for (int si = 0; si < nsites; ++si) {
+        // a site's nd blocks are contiguous: the next site's go to L2 now
+        if (si + 1 < nsites && tx < 32) prefetch_l2(blk((unsigned)((si + 1) * nd)), (size_t)nd * bytes);
+        stage(si);
+        cpx<R> acc[NRS][RPU];
+#pragma unroll
+        for (int r = 0; r < NRS; ++r)
+#pragma unroll
+          for (int q = 0; q < RPU; ++q) acc[r][q] = mk(R(0), R(0));
+        for (int t = 0; t < nd; ++t) {
+          const unsigned b = base + (unsigned)(si * nd + t);
+          const bool ok = mbar_wait_bounded(&ring_full[b % RING], (b / RING) & 1u, a.spin_limit);
+          if (__syncthreads_or(!ok)) {
+            if (tx == 0) {
+              atomicExch(a.status, 6);
+              for (unsigned i = b; i < ring_issued; ++i)
+                mbar_wait_bounded(&ring_full[i % RING], (i / RING) & 1u, MBAR_POLL_LIMIT);
+            }
+            return false;
+          }
+          if (tx == 0)
+            for (; ring_issued < end && ring_issued < b + RING; ++ring_issued) issue(ring_issued);
+          if (tx < units) {
+            const T* col = reinterpret_cast<const T*>(ringbuf + (size_t)(b % RING) * nn) + j;
+            const int d = d0 + t;
+#pragma unroll 4
+            for (int c = c0; c < c1; ++c) {
+              const T mm = col[(size_t)c * NP];
+              const cpx<R> e0 = mk(mm.x, mm.y), e1 = mk(mm.z, mm.w);
+#pragma unroll
+              for (int r = 0; r < NRS; ++r) {
+                const cpx<R> v = svr[(r * 9 + d) * svs + c];
+                fma(acc[r][0], e0, v);
+                fma(acc[r][1], e1, v);
+              }
+            }
+          }
+        }
+        if (tx < units)
+#pragma unroll
+          for (int r = 0; r < NRS; ++r)
+#pragma unroll
+            for (int q = 0; q < RPU; ++q) mvp[((size_t)cc * NR + rs * NRS + r) * n2 + RPU * j + q] = acc[r][q];
+        __syncthreads();
+        for (int idx = tx; idx < NR * n2; idx += TPB) {
+          const int r = idx / n2, row = idx - r * n2;
+          cpx<R> sum = mk(R(0), R(0));
+          for (int gq = 0; gq < CC; ++gq) sum = sum + mvp[((size_t)gq * NR + r) * n2 + row];
+          emit(si, r, row, sum);
+        }
+        __syncthreads();
+      }
+      ring_used = end;
+      return true;
+    }
+  };
+
+  // odd phase: to[r][ko] = sum_{d>=1} (A_oo^-1 Dc[X][d]) src[r][nbr]
+  auto phase_odd = [&](const cpx<R>* src) -> bool {
+    if (a.ring) {
+      prefetch_even(lo);
+      return ring_phase(
+          hi - lo, 8, 1, [&](unsigned i) { return a.AD + ((size_t)lo * 8 + i) * n2 * n2; },
+          [&](int si) { stage_odd(a.g.codd[lo + si], src); },
+          [&](int si, int r, int row, cpx<R> v) { a.to[r * vstr + (size_t)(lo + si) * n2 + row] = v; });
+    }
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
       prefetch_odd(ko + 1);
@@ -384,21 +506,41 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       mrhs_matvec<R, NR>(a.AD + (size_t)ko * 8 * n2 * n2, sv, 1, 9, n2, mvp, a.to + (size_t)ko * n2, (int)vstr,
                          true);
     }
+    return true;
+  };
+  // stage the vectors of even site ke: its own (self) and the odd neighbours' to
+  auto stage_even = [&](int ke, const cpx<R>* vself, bool self) {
+    const int X = a.g.ceven[ke], kk = ke - lo;
+    for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
+      const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
+      cpx<R> v;
+      if (d == 0) v = self ? vself[(size_t)r * L + kk * n2 + c] : mk(R(0), R(0));
+      else v = -ldc(a.to + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
+      sv[(r * 9 + d) * svs + c] = v;
+    }
+    __syncthreads();
   };
   // even phase: out[r][kk] = (self ? A_ee v : 0) - sum_{d>=1} Dc[X][d] to[r][nbr] (+ bsrc)
-  auto phase_even = [&](const cpx<R>* vself, bool self, cpx<R>* out, const cpx<R>* bsrc) {
+  auto phase_even = [&](const cpx<R>* vself, bool self, cpx<R>* out, const cpx<R>* bsrc) -> bool {
+    if (a.ring) {
+      prefetch_odd(lo);
+      const int nd = self ? 9 : 8, d0 = self ? 0 : 1;
+      return ring_phase(
+          hi - lo, nd, d0,
+          [&](unsigned i) {
+            return a.Dc + ((size_t)a.g.ceven[lo + (int)(i / (unsigned)nd)] * 9 + d0 + (int)(i % (unsigned)nd)) * n2 * n2;
+          },
+          [&](int si) { stage_even(lo + si, vself, self); },
+          [&](int si, int r, int row, cpx<R> v) {
+            if (bsrc) v = v + bsrc[(size_t)r * a.g.nb * n2 + (size_t)a.g.ceven[lo + si] * n2 + row];
+            out[(size_t)r * L + si * n2 + row] = v;
+          });
+    }
     for (int ke = lo; ke < hi; ++ke) {
       const int X = a.g.ceven[ke], kk = ke - lo;
       prefetch_even(ke + 1);
       if (ke + 1 == hi) prefetch_odd(lo);
-      for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
-        const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
-        cpx<R> v;
-        if (d == 0) v = self ? vself[(size_t)r * L + kk * n2 + c] : mk(R(0), R(0));
-        else v = -ldc(a.to + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
-        sv[(r * 9 + d) * svs + c] = v;
-      }
-      __syncthreads();
+      stage_even(ke, vself, self);
       if (a.resident)
         mrhs_matvec<R, NR, true>(Mres, sv, self ? 0 : 1, 9, n2, mvp, out + kk * n2, L);
       else
@@ -411,6 +553,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         __syncthreads();
       }
     }
+    return true;
   };
   // partial dots (r, j < kcount) of V_j[r] with wl[r]; slot = j * NR + r
   auto partial = [&](int kcount, bool norm) {
@@ -534,7 +677,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
     }
     if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
     // rhs_e = b_e - D_eo to ; x_e = 0 ; w = rhs_e
-    phase_even(nullptr, false, rl, bb);
+    if (!phase_even(nullptr, false, rl, bb)) return;
     for (int idx = tx; idx < NR * L; idx += TPB) {
       const int r = idx / L, e = idx - r * L;
       cpx<R> v = (r < nr && e < Lo) ? rl[idx] : mk(R(0), R(0));
@@ -582,9 +725,9 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       for (int k = 0; k < m; ++k) {
         // w = S V_k: odd phase from the neighbours' unnormalised w (scale 1/h)
-        phase_odd(a.wg);
+        if (!phase_odd(a.wg)) return;
         if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
-        phase_even(V + (size_t)k * NR * L, true, wl, nullptr);
+        if (!phase_even(V + (size_t)k * NR * L, true, wl, nullptr)) return;
         // Givens rotation of right-hand side r's new Hessenberg column (one
         // thread), new residual estimate, scale 1/h of V_{k+1}, convergence
         auto givens = [&](int r) {
@@ -777,9 +920,9 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       if (tx < NR) scl[tx] = A(1);
       if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
       // true residual w = rhs_e - S x_e
-      phase_odd(a.xg);
+      if (!phase_odd(a.xg)) return;
       if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
-      phase_even(xl, true, wl, nullptr);
+      if (!phase_even(xl, true, wl, nullptr)) return;
       for (int idx = tx; idx < NR * Lo; idx += TPB) {
         const int r = idx / Lo, e = idx - r * Lo;
         wl[(size_t)r * L + e] = rl[(size_t)r * L + e] - wl[(size_t)r * L + e];
@@ -849,6 +992,7 @@ struct Choice {
   bool local;
   Plan plan;
   bool resident;
+  bool ring;
 };
 
 // Host state of the launch configurations: the dynamic shared-memory limit
@@ -931,7 +1075,17 @@ Choice choose_uncached(int dev, const Geom& g, int n2, int m, int nrhs) {
           if (pr.bytes <= SMEM_RESIDENT_MAX && smem_attr_locked<R>(dev, NR, pr.bytes) == cudaSuccess &&
               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, pr.bytes) == cudaSuccess &&
               occ >= 1 && G <= occ * sms)
-            return Choice{NR, G, per, true, pr, true};
+            return Choice{NR, G, per, true, pr, true, false};
+          cudaGetLastError();
+        }
+        if (sizeof(R) == 4 && n2 >= RING_MIN_N2 && n2 <= 256) {
+          // the block operators streamed through a ring when it fits
+          Plan pg = make_plan(NR, per * n2, n2, m, sizeof(R), local, false, true);
+          int og = 0;
+          if (pg.bytes <= SMEM_RESIDENT_MAX && smem_attr_locked<R>(dev, NR, pg.bytes) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&og, fn, TPB, pg.bytes) == cudaSuccess &&
+              og >= 1 && G <= og * sms)
+            return Choice{NR, G, per, local, pg, false, true};
           cudaGetLastError();
         }
         Plan p = make_plan(NR, per * n2, n2, m, sizeof(R), local);
@@ -939,7 +1093,7 @@ Choice choose_uncached(int dev, const Geom& g, int n2, int m, int nrhs) {
         if (smem_attr_locked<R>(dev, NR, p.bytes) != cudaSuccess) break;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TPB, p.bytes);
         if (occ < 1) break;
-        if (G <= occ * sms) return Choice{NR, G, per, local, p, false};
+        if (G <= occ * sms) return Choice{NR, G, per, local, p, false, false};
       }
     }
   }
@@ -959,6 +1113,7 @@ CoarsePlan coarse_gmres_plan(const Geom& g, int n, int restart, int nrhs) {
   out.per = ch.per;
   out.local_in_smem = ch.local ? 1 : 0;
   out.resident = ch.resident ? 1 : 0;
+  out.ring = ch.ring ? 1 : 0;
   out.smem_bytes = ch.plan.bytes;
   // the layout of coarse_gmres() below
   const size_t NE = g.nb / 2, n2 = 2 * n;
@@ -1000,7 +1155,8 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   if (ch.NR == 0) return cudaErrorInvalidConfiguration;
   // a caller that sized `work` for a plan must get exactly that plan
   if (sized && (sized->NR != ch.NR || sized->G != ch.G || sized->per != ch.per ||
-                sized->local_in_smem != (ch.local ? 1 : 0) || sized->resident != (ch.resident ? 1 : 0)))
+                sized->local_in_smem != (ch.local ? 1 : 0) || sized->resident != (ch.resident ? 1 : 0) ||
+                sized->ring != (ch.ring ? 1 : 0)))
     return cudaErrorInvalidValue;
   CGA<R> a;
   a.g = g;
@@ -1019,6 +1175,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.per = ch.per;
   a.local_in_smem = ch.local ? 1 : 0;
   a.resident = ch.resident ? 1 : 0;
+  a.ring = ch.ring ? 1 : 0;
   const size_t NE = a.NE;
   const size_t vec = (size_t)NRMAX * NE * n2;
   unsigned char* w8 = reinterpret_cast<unsigned char*>(work);

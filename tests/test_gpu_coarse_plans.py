@@ -2,7 +2,8 @@
 library chooses, against the oracle's coarse solver on the same operator.
 
 The plan (right-hand sides in lockstep, sites per CTA, Krylov slices in
-shared or global memory, resident D_c blocks) depends on the size of the
+shared or global memory, resident D_c blocks, blocks streamed through the
+shared-memory ring) depends on the size of the
 coarse lattice, n_v, the restart length and the batch.  The workloads of the
 solver reach all of them: a few dozen coarse sites keep one even site per CTA
 with its blocks resident, a 4^3 x 8 coarse lattice needs two sites per CTA, an
@@ -52,6 +53,11 @@ CASES = [
     ((16, 16, 16, 32), (2, 2, 2, 2), 4, 0, 1, 8, dict(rhs_per_pass=1, krylov_in_shared=1)),
     ((16, 16, 16, 32), (2, 2, 2, 2), 8, 1, 2, 30, dict(rhs_per_pass=2)),
     ((16, 16, 16, 32), (2, 2, 2, 2), 4, 1, 12, 30, dict(rhs_per_pass=12, krylov_in_shared=0)),
+    # n_v 16: 32 x 32 blocks, streamed through the shared-memory block ring
+    ((8, 8, 8, 16), (2, 2, 2, 2), 16, 1, 1, 30, dict(rhs_per_pass=1, block_ring=1, krylov_in_shared=1)),
+    ((8, 8, 8, 16), (2, 2, 2, 2), 16, 1, 4, 30, dict(rhs_per_pass=4, block_ring=1, sites_per_cta=2)),
+    ((8, 8, 8, 16), (2, 2, 2, 2), 16, 1, 8, 30, dict(rhs_per_pass=8, block_ring=1, krylov_in_shared=0)),
+    ((8, 8, 8, 16), (2, 2, 2, 2), 16, 1, 12, 30, dict(rhs_per_pass=12, block_ring=1)),
 ]
 
 
@@ -114,6 +120,7 @@ def test_plans_cover_every_kind():
     global-scratch configurations, and every lockstep width."""
     seen = set()
     widths = set()
+    rings = set()
     for L, b, n_v, prec, nrhs, restart, _ in CASES:
         s = _handle(L, b, n_v, prec, restart, 300)
         try:
@@ -123,7 +130,9 @@ def test_plans_cover_every_kind():
         seen.add(("resident" if p["resident_blocks"] else "per1" if p["sites_per_cta"] == 1 else "per>1",
                   "smem" if p["krylov_in_shared"] else "global"))
         widths.add(p["rhs_per_pass"])
+        rings.add((p["block_ring"], p["krylov_in_shared"]))
     assert ("resident", "smem") in seen and ("per>1", "smem") in seen
+    assert (1, 1) in rings and (1, 0) in rings and (0, 0) in rings
     assert any(k[1] == "global" for k in seen)
     assert widths == {1, 2, 4, 8, 12}
 
