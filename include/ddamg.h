@@ -335,7 +335,9 @@ DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coa
  * problem, the variants' mean times in microseconds and the choice.
  * Variants so far: the Wilson-clover D with one thread per site (0) or four
  * threads per site, one hop direction each (1), in FP32 and in BF16/FP16
- * storage. */
+ * storage; the coarse GMRES's block products for eight right-hand sides in
+ * lockstep with the blocks streamed through shared memory, on the CUDA
+ * cores (0) or the tensor cores (1, 3xTF32) ("coarse product"). */
 typedef struct {
   char kernel[32];
   char problem[96];

@@ -781,6 +781,22 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   a.restart = h->p.coarse_restart;
   a.max_iter = h->p.coarse_max_iter;
   a.wait_limit = h->wait_grid;
+  if (sizeof(R) == 4) {
+    // eight right-hand sides through the block ring: the block products on
+    // the CUDA cores (0) or the tensor cores (1), the faster one measured on
+    // this call's data the first time (iteration counters left alone)
+    const CoarsePlan pl = coarse_gmres_plan<R>(h->g, h->p.n_v, h->p.coarse_restart, nf);
+    if (pl.ring && pl.NR == 8) {
+      auto run = [&](int var) -> cudaError_t {
+        CoarseSolveArgs t = a;
+        t.tc = var;
+        return coarse_gmres<R>(h->g, t, bc, xc, nf, h->cwork, nullptr, nullptr, h->d_status, h->st);
+      };
+      char key[96];
+      snprintf(key, sizeof key, "coarse %d sites n_v %d fp32 nrhs %d", h->g.nb, h->p.n_v, nf);
+      TRY(tuned(h, "coarse product", key, 2, run, &a.tc));
+    }
+  }
   addf(h, nf * flops_coarse_fixed(h));   // iterations are added when their counts are read
   CK(timed(h, 2, [&] {
     return coarse_gmres<R>(h->g, a, bc, xc, nf, h->cwork, iters_dev, h->d_iters_acc, h->d_status, h->st);

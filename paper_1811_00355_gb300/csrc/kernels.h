@@ -259,6 +259,7 @@ struct CoarseSolveArgs {
   int restart;      // <= 64
   int max_iter;
   long long wait_limit;   // polls of a grid-barrier wait before it gives up (DDAMG_ETIMEOUT)
+  int tc = 0;             // eight right-hand sides through the block ring: products on the tensor cores
 };
 // launch configuration of the coarse GMRES for nrhs right-hand sides (all
 // zero if none exists): NR right-hand sides in lockstep per launch pass, G

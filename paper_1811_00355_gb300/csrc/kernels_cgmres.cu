@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mma_tf32.cuh"
 
 namespace ddamg {
 
@@ -138,6 +139,7 @@ struct Plan {
   size_t V, x, rl, w, sv, mvp, tmp;                                    // cpx offsets (bytes)
   size_t hc, h2, Rf, cs, sn, gv, yv, beta, bnorm, hn, scale;           // double offsets
   size_t act, kd, tot, conv;                                            // int offsets
+  size_t nbo;          // [2][per][8] neighbour offsets of the CTA's odd and even sites
   size_t Mres;         // resident D_c blocks of the CTA's even site (0: none)
   size_t ring;         // block ring, RING blocks (0: none)
   size_t bytes;        // total shared memory
@@ -186,6 +188,7 @@ __host__ __device__ inline Plan make_plan(int NR, int L, int n2, int m, int rs, 
   p.kd = put((size_t)NR * 4);
   p.tot = put((size_t)NR * 4);
   p.conv = put((size_t)NR * 4);
+  p.nbo = put((size_t)2 * (L / n2) * 8 * 4);
   p.Mres = resident ? put((size_t)9 * n2 * n2 * c) : 0;
   p.ring = ring ? put((size_t)RING * n2 * n2 * c) : 0;
   p.bytes = o;
@@ -212,6 +215,7 @@ struct CGA {
   int local_in_smem;
   int resident;      // the CTA keeps its even site's D_c blocks in shared memory
   int ring;          // block operators streamed through the shared-memory ring
+  int tc;            // ring products of eight right-hand sides on the tensor cores
   cpx<R>* wg;        // [NR][NE][n2]
   cpx<R>* to;        // [NR][NE][n2]
   cpx<R>* xg;        // [NR][NE][n2]
@@ -360,16 +364,32 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   const int tx = threadIdx.x;
   const int TRI = m * (m + 1) / 2;
   const int svs = sv_stride(n2);
+  // offsets (in the [NE][n2] vectors) of the eight neighbours of the CTA's
+  // odd sites (nbo[kk][d - 1]) and even sites (nbo[per + kk][d - 1]), looked
+  // up once per launch instead of two dependent loads per staging
+  int* nbo = reinterpret_cast<int*>(sm + P.nbo);
+  for (int i = tx; i < 2 * nown * 8; i += TPB) {
+    const int par = i / (nown * 8), rem = i - par * nown * 8, kk = rem / 8, d = 1 + rem % 8;
+    const int X = par ? a.g.ceven[lo + kk] : a.g.codd[lo + kk];
+    nbo[(par * a.per + kk) * 8 + d - 1] = a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2;
+  }
 
   auto Vk = [&](int k, int r) { return V + ((size_t)k * NR + r) * L; };
 
   // stage neighbours of odd site X from global vectors src[r] (scaled), d >= 1
-  auto stage_odd = [&](int X, const cpx<R>* src) {
-    for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
-      const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
-      cpx<R> v = mk(R(0), R(0));
-      if (d > 0) v = (R)scl[r] * ldc(src + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
-      sv[(r * 9 + d) * svs + c] = v;
+  // (one warp per row (r, d) of sv: the neighbour's position is looked up
+  // once per row, and the lanes run along the row)
+  auto stage_odd = [&](int kk, const cpx<R>* src) {
+    for (int row = wid; row < NR * 9; row += NW) {
+      const int r = row / 9, d = row - 9 * r;
+      cpx<R>* dst = sv + (size_t)row * svs;
+      if (d == 0) {
+        for (int c = lane; c < n2; c += 32) dst[c] = mk(R(0), R(0));
+        continue;
+      }
+      const cpx<R>* s = src + r * vstr + nbo[kk * 8 + d - 1];
+      const R f = (R)scl[r];
+      for (int c = lane; c < n2; c += 32) dst[c] = f * ldc(s + c);
     }
     __syncthreads();
   };
@@ -432,6 +452,26 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       const int j = tx % NP, rest = tx / NP, rs = rest % RS, cc = rest / RS;
       const int c0 = cc * CW, c1 = min(n2, c0 + CW);
       const cpx<R>* svr = sv + (size_t)rs * NRS * 9 * svs;
+      // Eight right-hand sides on the tensor cores (3xTF32, FP32 accuracy):
+      // per site C' (16 x n2) = A' (16 x 2K) B (2K x n2), with A' rows
+      // m = r + 8 p the real (p = 0) and imaginary (p = 1) rows of the
+      // staged vectors and B the raw blocks.  In a k-step of four complex
+      // columns c0 .. c0 + 3, lane t's k = t and k = t + 4 stand for the real
+      // and imaginary parts of column c0 + t, so for v = sv[r][d][c0 + t]
+      //   A'[r][t] = v.re, A'[r][t + 4] = -v.im, A'[r + 8][t] = v.im, A'[r + 8][t + 4] = v.re
+      // and (b0, b1) = M_d[n0 + g][c0 + t] (one 8-byte load).  Warp (kg, ng)
+      // takes k-steps 2 kg, 2 kg + 1 of every block and n-tiles
+      // ng TPW .. ng TPW + TPW - 1; each block's products go to fresh
+      // accumulators added in FP32, the k-groups' partials meet in mvp.
+      constexpr int TPWMAX = 4;
+      const int NT = n2 / 8, KG = n2 / 8;      // n-tiles; k-groups of two k-steps (n2 / 4 k-steps a block)
+      const int NGR = min(NT, NW / (KG > 0 ? KG : 1));
+      const int TPW = NGR > 0 ? (NT + NGR - 1) / NGR : 0;
+      const bool tc = a.tc && NR == 8 && n2 % 8 == 0 && NGR >= 1 && TPW <= TPWMAX;
+      const int gq = lane >> 2, tq = lane & 3;
+      const int kg = wid % (KG > 0 ? KG : 1), ng = wid / (KG > 0 ? KG : 1);
+      const bool mw = tc && ng < NGR;
+      float* mvpf = reinterpret_cast<float*>(mvp);
       for (int si = 0; si < nsites; ++si) {
         // a site's nd blocks are contiguous: the next site's go to L2 now
         if (si + 1 < nsites && tx < 32) prefetch_l2(blk((unsigned)((si + 1) * nd)), (size_t)nd * bytes);
@@ -441,6 +481,11 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
         for (int r = 0; r < NRS; ++r)
 #pragma unroll
           for (int q = 0; q < RPU; ++q) acc[r][q] = mk(R(0), R(0));
+        float tacc[TPWMAX][4];
+#pragma unroll
+        for (int i = 0; i < TPWMAX; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) tacc[i][e] = 0.f;
         for (int t = 0; t < nd; ++t) {
           const unsigned b = base + (unsigned)(si * nd + t);
           const bool ok = mbar_wait_bounded(&ring_full[b % RING], (b / RING) & 1u, a.spin_limit);
@@ -454,7 +499,37 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
           }
           if (tx == 0)
             for (; ring_issued < end && ring_issued < b + RING; ++ring_issued) issue(ring_issued);
-          if (tx < units) {
+          if (tc) {
+            if (mw) {
+              const float* slot = reinterpret_cast<const float*>(ringbuf + (size_t)(b % RING) * nn);
+              const int d = d0 + t;
+              float part[TPWMAX][4];
+#pragma unroll
+              for (int i = 0; i < TPWMAX; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) part[i][e] = 0.f;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int c = 4 * (2 * kg + h) + tq;
+                const cpx<R> v = sv[(size_t)(gq * 9 + d) * svs + c];
+                const float af[4] = {v.re, v.im, -v.im, v.re};
+                const Split<4> as = split_frag<4>(af);
+#pragma unroll
+                for (int i = 0; i < TPWMAX; ++i) {
+                  const int nt = ng * TPW + i;
+                  if (i < TPW && nt < NT) {
+                    const float2 mv = *reinterpret_cast<const float2*>(slot + ((size_t)c * n2 + nt * 8 + gq) * 2);
+                    const float bv[2] = {mv.x, mv.y};
+                    mma3(part[i], as, split_frag<2>(bv));
+                  }
+                }
+              }
+#pragma unroll
+              for (int i = 0; i < TPWMAX; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) tacc[i][e] += part[i][e];
+            }
+          } else if (tx < units) {
             const T* col = reinterpret_cast<const T*>(ringbuf + (size_t)(b % RING) * nn) + j;
             const int d = d0 + t;
 #pragma unroll 4
@@ -470,17 +545,39 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
             }
           }
         }
-        if (tx < units)
+        if (tc) {
+          if (mw)
 #pragma unroll
-          for (int r = 0; r < NRS; ++r)
+            for (int i = 0; i < TPWMAX; ++i) {
+              const int nt = ng * TPW + i;
+              if (i < TPW && nt < NT)
 #pragma unroll
-            for (int q = 0; q < RPU; ++q) mvp[((size_t)cc * NR + rs * NRS + r) * n2 + RPU * j + q] = acc[r][q];
-        __syncthreads();
-        for (int idx = tx; idx < NR * n2; idx += TPB) {
-          const int r = idx / n2, row = idx - r * n2;
-          cpx<R> sum = mk(R(0), R(0));
-          for (int gq = 0; gq < CC; ++gq) sum = sum + mvp[((size_t)gq * NR + r) * n2 + row];
-          emit(si, r, row, sum);
+                for (int e = 0; e < 4; ++e)
+                  mvpf[((size_t)kg * 16 + gq + (e >= 2 ? 8 : 0)) * n2 + nt * 8 + 2 * tq + (e & 1)] = tacc[i][e];
+            }
+          __syncthreads();
+          for (int idx = tx; idx < NR * n2; idx += TPB) {
+            const int r = idx / n2, row = idx - r * n2;
+            float re = 0.f, im = 0.f;
+            for (int q = 0; q < KG; ++q) {
+              re += mvpf[((size_t)q * 16 + r) * n2 + row];
+              im += mvpf[((size_t)q * 16 + 8 + r) * n2 + row];
+            }
+            emit(si, r, row, mk(re, im));
+          }
+        } else {
+          if (tx < units)
+#pragma unroll
+            for (int r = 0; r < NRS; ++r)
+#pragma unroll
+              for (int q = 0; q < RPU; ++q) mvp[((size_t)cc * NR + rs * NRS + r) * n2 + RPU * j + q] = acc[r][q];
+          __syncthreads();
+          for (int idx = tx; idx < NR * n2; idx += TPB) {
+            const int r = idx / n2, row = idx - r * n2;
+            cpx<R> sum = mk(R(0), R(0));
+            for (int q = 0; q < CC; ++q) sum = sum + mvp[((size_t)q * NR + r) * n2 + row];
+            emit(si, r, row, sum);
+          }
         }
         __syncthreads();
       }
@@ -495,14 +592,14 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
       prefetch_even(lo);
       return ring_phase(
           hi - lo, 8, 1, [&](unsigned i) { return a.AD + ((size_t)lo * 8 + i) * n2 * n2; },
-          [&](int si) { stage_odd(a.g.codd[lo + si], src); },
+          [&](int si) { stage_odd(si, src); },
           [&](int si, int r, int row, cpx<R> v) { a.to[r * vstr + (size_t)(lo + si) * n2 + row] = v; });
     }
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
       prefetch_odd(ko + 1);
       if (ko + 1 == hi) prefetch_even(lo);
-      stage_odd(X, src);
+      stage_odd(ko - lo, src);
       mrhs_matvec<R, NR>(a.AD + (size_t)ko * 8 * n2 * n2, sv, 1, 9, n2, mvp, a.to + (size_t)ko * n2, (int)vstr,
                          true);
     }
@@ -510,13 +607,19 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
   };
   // stage the vectors of even site ke: its own (self) and the odd neighbours' to
   auto stage_even = [&](int ke, const cpx<R>* vself, bool self) {
-    const int X = a.g.ceven[ke], kk = ke - lo;
-    for (int idx = tx; idx < NR * 9 * n2; idx += TPB) {
-      const int r = idx / (9 * n2), rem = idx - r * 9 * n2, d = rem / n2, c = rem - d * n2;
-      cpx<R> v;
-      if (d == 0) v = self ? vself[(size_t)r * L + kk * n2 + c] : mk(R(0), R(0));
-      else v = -ldc(a.to + r * vstr + (size_t)a.g.cpos[a.g.cnbr[d * a.g.nb + X]] * n2 + c);
-      sv[(r * 9 + d) * svs + c] = v;
+    const int kk = ke - lo;
+    for (int row = wid; row < NR * 9; row += NW) {
+      const int r = row / 9, d = row - 9 * r;
+      cpx<R>* dst = sv + (size_t)row * svs;
+      if (d == 0 && self) {
+        const cpx<R>* s = vself + (size_t)r * L + kk * n2;
+        for (int c = lane; c < n2; c += 32) dst[c] = s[c];
+      } else if (d == 0) {
+        for (int c = lane; c < n2; c += 32) dst[c] = mk(R(0), R(0));
+      } else {
+        const cpx<R>* s = a.to + r * vstr + nbo[(a.per + kk) * 8 + d - 1];
+        for (int c = lane; c < n2; c += 32) dst[c] = -ldc(s + c);
+      }
     }
     __syncthreads();
   };
@@ -947,7 +1050,7 @@ __global__ void __launch_bounds__(TPB) k_cgmres(CGA<R> a) {
     if (!grid_barrier(a.bar, a.status, a.spin_limit)) return;
     for (int ko = lo; ko < hi; ++ko) {
       const int X = a.g.codd[ko];
-      stage_odd(X, a.xg);
+      stage_odd(ko - lo, a.xg);
       mrhs_matvec<R, NR>(a.Dc + (size_t)X * 9 * n2 * n2, sv, 1, 9, n2, mvp, tmp, n2);
       for (int idx = tx; idx < NR * n2; idx += TPB) {
         const int r = idx / n2, c = idx - r * n2;
@@ -1176,6 +1279,7 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   a.local_in_smem = ch.local ? 1 : 0;
   a.resident = ch.resident ? 1 : 0;
   a.ring = ch.ring ? 1 : 0;
+  a.tc = ca.tc;
   const size_t NE = a.NE;
   const size_t vec = (size_t)NRMAX * NE * n2;
   unsigned char* w8 = reinterpret_cast<unsigned char*>(work);

@@ -166,3 +166,33 @@ def test_bounded_waits_time_out_and_the_handle_recovers():
         assert its[0] > 0 and np.all(np.isfinite(x))
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ring_block_products_on_cuda_and_tensor_cores(variant):
+    """Eight right-hand sides through the block ring: the block products on
+    the CUDA cores (0) and on the tensor cores (1, 3xTF32) both return the
+    oracle's Krylov iterate after a fixed number of iterations."""
+    import paper_1811_00355_gb300 as P
+    L, b, n_v, nrhs = (8, 8, 8, 16), (2, 2, 2, 2), 16, 8
+    cL = tuple(L[mu] // b[mu] for mu in range(4))
+    geom = Geometry(cL)
+    n2 = 2 * n_v
+    Dc = syn.coarse_stencil(geom.V, n2, 7, DIAG, HOP)
+    cop = CoarseOperator(torch.from_numpy(Dc), geom)
+    gen = np.random.default_rng(95)
+    bc = gen.standard_normal((nrhs, geom.V, n2)) + 1j * gen.standard_normal((nrhs, geom.V, n2))
+    P.pin_variant("coarse product", variant)
+    s = _handle(L, b, n_v, P.FP32, 30, FIXED_ITERS)
+    try:
+        s.set_coarse_op(Dc)
+        plan = s.coarse_plan(nrhs)
+        assert plan["block_ring"] == 1 and plan["rhs_per_pass"] == 8, plan
+        x, its = s.coarse_solve(bc, 1e-30, P.FP32)
+        assert np.all(its == FIXED_ITERS), its
+        for r in range(nrhs):
+            xr, _ = cop.solve(torch.from_numpy(bc[r]), 1e-30, 30, FIXED_ITERS)
+            assert_close(x[r], xr.numpy(), TOL_FIXED32, f"variant {variant} rhs {r}")
+    finally:
+        s.close()
+        P.pin_variant("coarse product", -1)
