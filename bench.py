@@ -53,6 +53,14 @@ STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.
 # the GPU: about 2100 iterations predicted there, no mass reaches 5000)
 LARGE = dict(L=(32, 32, 32, 64), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.125, csw=1.5, n_v=24,
              outer_restart=10, tol=1e-10)
+# the 48^3 x 96 light-mass workload: eps 0.15, csw 1.6, m0 = m_c + 0.02 with
+# m_c read from an 8^4 proxy (seed 5) and corrected for the proxy's
+# antiperiodic lowest mode, n_v 32, FP16 storage with FP32 arithmetic and
+# FP64 refinement, the 12 point sources in lockstep batches of three (outer
+# restart 6), the setup's temporaries and FP64 test vectors released
+# before the solves
+HUGE = dict(L=(48, 48, 48, 96), block=(4, 4, 4, 4), eps=0.15, seed=5, m0=-0.034, csw=1.6, n_v=32,
+            outer_restart=6, batch=3, tol=1e-10)
 # compulsory bytes per site of one fine D apply: in and out spinor (24 reals
 # each), four two-row links (12 reals each), packed clover A (72 reals)
 D_REALS_PER_SITE = 24 + 24 + 4 * 12 + 72
@@ -342,6 +350,14 @@ def run_ours(args):
         torch.cuda.empty_cache()
         large = large_batched()
 
+    huge = None
+    if rank == 0 and world == 1 and not args.no_huge:
+        solver.close()                 # (idempotent) the child needs nearly all of the device memory
+        del flush
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        huge = huge_batched()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -367,6 +383,7 @@ def run_ours(args):
             "serving": srv,
             "stencils": sten,
             "batched_32x32x32x64": large,
+            "light_mass_48x48x48x96": huge,
             "autotune": P.tuning(),
         }
         print(json.dumps(line))
@@ -644,6 +661,97 @@ def large_batched_child():
     print(json.dumps(out))
 
 
+def huge_batched():
+    """The 48^3 x 96 light-mass workload in a child process; returns its
+    JSON object, or {"error": ...}."""
+    import subprocess
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--huge-only"], cwd=ROOT,
+                           capture_output=True, text=True, timeout=2400)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"error": "exit %d: %s" % (r.returncode, (r.stderr or r.stdout)[-400:])}
+        return json.loads(lines[-1])
+    except Exception as e:                      # noqa: BLE001 - reported in the JSON line
+        return {"error": repr(e)[:400]}
+
+
+def huge_batched_child():
+    """Setup + the 12 point sources (lockstep batches of three) on 48^3 x 96
+    at the light mass, FP16 storage, one pass timed with CUDA events (host
+    buffers: each batch's right-hand sides and solutions cross PCIe/NVLink-C2C
+    inside its timed region).  The library reports every solution's FP64
+    true residual; the first source of every batch is checked once more
+    with the CPU oracle's D.  Prints one JSON object."""
+    import torch
+    import paper_1811_00355_gb300 as P
+    import synthetic as syn
+    s = HUGE
+    if not torch.cuda.is_available():
+        raise SystemExit("no CUDA device")
+    t0 = time.perf_counter()
+    U = syn.gauge_field_sliced(s["L"], s["eps"], s["seed"], workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    b = syn.point_sources(s["L"])
+    torch.cuda.set_device(0)
+    P.load()
+    stream = torch.cuda.current_stream()
+    params = P.default_params(L=s["L"], sap_block=s["block"], n_v=s["n_v"], m0=s["m0"], csw=s["csw"],
+                              outer_restart=s["outer_restart"], precision=P.FP16)
+    out = {"lattice": "48x48x48x96", "m0": s["m0"], "csw": s["csw"], "eps": s["eps"], "n_v": s["n_v"],
+           "rhs": "12 point sources, lockstep batches of %d" % s["batch"], "unit": UNIT, "dtype": "fp16+f64",
+           "gauge_generation_s": round(gen_s, 1),
+           "timing": "CUDA events, one pass; solves include the host<->device copies of their fields"}
+    h = P.DDAMG(params, U, stream=stream.cuda_stream)
+    xs = np.empty_like(b)
+    infos = []
+    try:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        h.run_setup()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        setup_s = ev[0].elapsed_time(ev[1]) / 1e3
+        setup_GB = h.stats()["device_bytes"] / 1e9
+        h.trim()
+        solve_s = 0.0
+        for k0 in range(0, 12, s["batch"]):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            x, info = h.solve_batched(np.ascontiguousarray(b[k0:k0 + s["batch"]]), s["tol"])
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            solve_s += ev[0].elapsed_time(ev[1]) / 1e3
+            xs[k0:k0 + s["batch"]] = x
+            infos.extend(info)
+        out.update({"value": round(12 / (setup_s + solve_s), 4), "setup_s": round(setup_s, 2),
+                    "solve_s": round(solve_s, 2),
+                    "outer_iters_per_rhs": statistics.mean(i["outer_iters"] for i in infos),
+                    "coarse_iters_per_precond": round(sum(i["coarse_iters"] for i in infos)
+                                                      / max(1, sum(i["precond_calls"] for i in infos)), 1),
+                    "max_true_residual": max(i["true_residual"] for i in infos),
+                    "all_converged": all(i["converged"] and i["true_residual"] <= s["tol"] for i in infos),
+                    "device_GB_setup": round(setup_GB, 1),
+                    "device_GB_solve": round(h.stats()["device_bytes"] / 1e9, 1)})
+    finally:
+        h.close()
+    t_or = time.perf_counter()
+    from oracle.dirac import WilsonClover
+    op = WilsonClover(torch.from_numpy(U), s["L"], s["m0"], s["csw"])
+    del U
+    res = []
+    checked = list(range(0, 12, s["batch"]))       # the first source of every batch
+    for k in checked:
+        r = torch.from_numpy(b[k]) - op.apply(torch.from_numpy(xs[k]))
+        res.append(float(torch.linalg.vector_norm(r) / np.linalg.norm(b[k])))
+    out["max_true_residual_oracle_D"] = max(res)
+    out["oracle_D_sources"] = checked
+    out["all_converged"] = out["all_converged"] and max(res) <= s["tol"]
+    out["oracle_check_s"] = round(time.perf_counter() - t_or, 1)
+    print(json.dumps(out))
+
+
 def stencils(P, torch, stream, pk, pk_kind):
     """Achieved HBM bandwidth of the fine D (FP32, FP64) and of the coarse
     9-point stencil (FP32) on a lattice far larger than L2, from the
@@ -891,6 +999,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 32^3 x 64 batched workload")
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-huge", action="store_true", help="skip the 48^3 x 96 light-mass workload")
+    ap.add_argument("--huge-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--large-precisions", default=None,
                     help="comma list of f32,bf16,fp16 for the 32^3 x 64 workload (default all three)")
     ap.add_argument("--large-passes", type=int, default=None, help="passes of the 32^3 x 64 workload (default 2)")
@@ -915,6 +1025,9 @@ def main():
         LARGE_RUN["oracle_check"] = False
     if args.large_only:
         large_batched_child()
+        return
+    if args.huge_only:
+        huge_batched_child()
         return
     if args.stencils_only:
         import torch

@@ -297,6 +297,16 @@ DDAMG_API ddamg_status ddamg_orthonormalize(ddamg_handle h);
  * precision, and invert its self blocks for the even-odd coarse solve. */
 DDAMG_API ddamg_status ddamg_build_coarse(ddamg_handle h);
 
+/* Release device memory the solves do not need once the setup is done: the
+ * temporaries sized for the setup's batch of test vectors and the
+ * host-exchange staging buffer (both reallocated when needed), and, for an
+ * inner precision other than FP64, the FP64 copy of the test vectors (the
+ * inner-precision copy that R, P and the D_c of Eq. 2 use is kept).
+ * Afterwards calls that read the FP64 test vectors (ddamg_get_test_vectors,
+ * ddamg_orthonormalize, FP64 R and P) return DDAMG_ESTATE; ddamg_run_setup
+ * and ddamg_set_test_vectors allocate them again. */
+DDAMG_API ddamg_status ddamg_trim(ddamg_handle h);
+
 /* Export D_c in the coarse-op layout (host buffer, NX*9*(2n)^2 complex). */
 DDAMG_API ddamg_status ddamg_get_coarse_op(ddamg_handle h, double *out);
 

@@ -138,6 +138,7 @@ SIGNATURES = {
     "ddamg_batch_slot": (_I, [_H, _I, C.POINTER(_I)]),
     "ddamg_batch_take": (_I, [_H, _I, _P, _I, C.POINTER(SolveInfo)]),
     "ddamg_get_coarse_plan": (_I, [_H, _I, C.POINTER(CoarsePlan)]),
+    "ddamg_trim": (_I, [_H]),
     "ddamg_set_wait_limit": (_I, [_H, C.c_int64]),
     "ddamg_tuning_count": (_I, []),
     "ddamg_get_tuning": (_I, [_I, C.POINTER(Tuning)]),
@@ -436,6 +437,11 @@ class DDAMG:
         invert its self blocks."""
         p, dev = _ptr(dc)
         self._check(self.lib.ddamg_set_coarse_op(self.h, p, dev))
+
+    def trim(self):
+        """Release the setup's temporaries and, for an inner precision other
+        than FP64, the FP64 copy of the test vectors (ddamg_trim)."""
+        self._check(self.lib.ddamg_trim(self.h))
 
     def coarse_plan(self, nrhs=1):
         """Launch configuration of the coarse GMRES for nrhs right-hand sides."""

@@ -90,6 +90,7 @@ struct ddamg_ctx {
   double* lam64 = nullptr;
   float* lam32 = nullptr;
   bool have_vectors = false;
+  bool lam64_gone = false;       // FP64 test vectors released by ddamg_trim (lam32 holds them)
   bool have_coarse = false;
   void* Dc = nullptr;
   void* Ainv = nullptr;
@@ -434,6 +435,9 @@ ddamg_status build_tables(ddamg_ctx* h) {
 // lexicographic FP64 staging for nf fields
 ddamg_status need_lexbuf(ddamg_ctx* h, size_t nf) {
   if (h->lexbuf_fields >= nf) return DDAMG_OK;
+  dfree(h, h->lexbuf, h->lexbuf_fields * h->V24 * sizeof(double));   // (cudaFree waits for its users)
+  h->lexbuf = nullptr;
+  h->lexbuf_fields = 0;
   void* p;
   TRY(dalloc(h, &p, nf * h->V24 * sizeof(double)));
   h->lexbuf = (double*)p;
@@ -444,7 +448,9 @@ ddamg_status need_lexbuf(ddamg_ctx* h, size_t nf) {
 ddamg_status need_tmp(ddamg_ctx* h, size_t nf, int k) {
   if (h->tmp_fields >= nf && (int)h->tmp.size() >= k) return DDAMG_OK;
   size_t want = nf > h->tmp_fields ? nf : h->tmp_fields;
+  for (void* p : h->tmp) dfree(h, p, h->tmp_fields * h->V24 * sizeof(double));
   h->tmp.clear();
+  h->tmp_fields = 0;
   ++h->gen;   // captured graphs refer to the old temporaries
   for (int i = 0; i < (k > 6 ? k : 6); ++i) {
     void* p;
@@ -848,10 +854,24 @@ ddamg_status alloc_coarse(ddamg_ctx* h) {
   return DDAMG_OK;
 }
 
+// FP64 test vectors for a call that reads them (released by ddamg_trim)
+ddamg_status need_lam64(ddamg_ctx* h) {
+  if (!h->lam64_gone) return DDAMG_OK;
+  return fail(h, DDAMG_ESTATE, "the FP64 test vectors were released by ddamg_trim");
+}
+// FP64 test vectors for a call that writes all of them
+ddamg_status revive_lam64(ddamg_ctx* h) {
+  if (!h->lam64_gone) return DDAMG_OK;
+  TRY(dalloc_t(h, &h->lam64, (size_t)h->p.n_v * h->V24));
+  h->lam64_gone = false;
+  return DDAMG_OK;
+}
+
 ddamg_status sync_lam32(ddamg_ctx* h) {
   if (inner32(h)) {
     if (!h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
-    CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    // after ddamg_trim the FP32 copy is the only one (and current)
+    if (!h->lam64_gone) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
     const int k = lam_half_kind(h);
     if (k >= 0) {
       if (!h->lam16) TRY(dalloc(h, &h->lam16, (size_t)h->p.n_v * h->V24 * 2));
@@ -975,7 +995,31 @@ ddamg_status coarse_iters_since(ddamg_ctx* h, int* its) {
 template <class R>
 ddamg_status setup_impl(ddamg_ctx* h) {
   const int n = h->p.n_v;
-  TRY(need_tmp(h, n, 6));
+  // the vectors go through the smoother and M in chunks whose temporaries
+  // (six FP64-sized fields each) fit in the device memory left once the
+  // setup's other arrays (inner-precision test vectors, the coarse operator,
+  // half-storage operators) are in place
+  if (inner32(h) && !h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)n * h->V24));
+  if (lam_half_kind(h) >= 0 && !h->lam16) TRY(dalloc(h, &h->lam16, (size_t)n * h->V24 * 2));
+  TRY(alloc_coarse(h));
+  if (half_kind(h->p.precision) >= 0 && sap_half_ok(h->g)) TRY(half_operators(h, half_kind(h->p.precision)));
+  int ch = n;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+      cudaGetLastError();
+      const size_t per = 6 * h->V24 * sizeof(double) + 2 * h->V24 * 2 + 2 * h->g.V * sizeof(float);
+      size_t avail = fr + h->tmp_fields * 6 * h->V24 * sizeof(double);
+      if (h->p.hbm_budget) {
+        const size_t left = h->p.hbm_budget > h->bytes ? h->p.hbm_budget - h->bytes : 0;
+        avail = std::min(avail, left + h->tmp_fields * 6 * h->V24 * sizeof(double));
+      }
+      avail = avail / 10 * 8;            // headroom for the coarse scratch and the library's own
+      const size_t fit = avail / per;
+      ch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, fit));
+    }
+  }
+  TRY(need_tmp(h, ch, 6));
   int its = 0;
   TRY(coarse_iters_since(h, &its));
   h->fphase = 0;
@@ -983,17 +1027,25 @@ ddamg_status setup_impl(ddamg_ctx* h) {
   R* a = (R*)h->tmp[4];
   R* b = (R*)h->tmp[5];
   // lambda_i <- SAP(lambda_i)
-  TRY(to_inner<R>(h, h->lam64, a, n));
-  TRY(op_sap<R>(h, a, b, n));
-  TRY(from_inner<R>(h, b, h->lam64, n));
+  for (int c0 = 0; c0 < n; c0 += ch) {
+    const int cn = std::min(ch, n - c0);
+    double* lv = h->lam64 + (size_t)c0 * h->V24;
+    TRY(to_inner<R>(h, lv, a, cn));
+    TRY(op_sap<R>(h, a, b, cn));
+    TRY(from_inner<R>(h, b, lv, cn));
+  }
   for (int it = 0; it < h->p.setup_iters; ++it) {
     addf(h, flops_ortho(h));
     CK(orthonormalise(h->g, h->lam64, n, h->st));
     TRY(build_coarse_op(h));
     // lambda_i <- M lambda_i
-    TRY(to_inner<R>(h, h->lam64, a, n));
-    TRY(op_M<R>(h, a, b, n));
-    TRY(from_inner<R>(h, b, h->lam64, n));
+    for (int c0 = 0; c0 < n; c0 += ch) {
+      const int cn = std::min(ch, n - c0);
+      double* lv = h->lam64 + (size_t)c0 * h->V24;
+      TRY(to_inner<R>(h, lv, a, cn));
+      TRY(op_M<R>(h, a, b, cn));
+      TRY(from_inner<R>(h, b, lv, cn));
+    }
     TRY(check_status(h));
   }
   addf(h, flops_ortho(h));
@@ -1931,6 +1983,7 @@ ddamg_status ddamg_run_setup(ddamg_handle h, const double* init, int on_device) 
   // the clover term and its inverse are part of the setup (rebuilt from the
   // resident links, so a repeated setup redoes all of its work)
   TRY(rebuild_clover(h, h->p.m0, h->p.csw));
+  TRY(revive_lam64(h));
   if (init) {
     TRY(import_fields<double>(h, init, on_device, n, h->lam64));
   } else {
@@ -2202,6 +2255,7 @@ ddamg_status ddamg_sap(ddamg_handle h, int prec, int nrhs, const double* in, dou
 
 ddamg_status ddamg_set_test_vectors(ddamg_handle h, const double* vecs, int on_device) {
   if (!h || !vecs) return DDAMG_EINVAL;
+  TRY(revive_lam64(h));
   TRY(import_fields<double>(h, vecs, on_device, h->p.n_v, h->lam64));
   CK(cudaStreamSynchronize(h->st));
   h->have_vectors = true;
@@ -2212,16 +2266,36 @@ ddamg_status ddamg_set_test_vectors(ddamg_handle h, const double* vecs, int on_d
 ddamg_status ddamg_get_test_vectors(ddamg_handle h, double* vecs) {
   if (!h || !vecs) return DDAMG_EINVAL;
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  TRY(need_lam64(h));
   return export_fields<double>(h, h->lam64, h->p.n_v, vecs, 0);
 }
 
 ddamg_status ddamg_orthonormalize(ddamg_handle h) {
   if (!h) return DDAMG_EINVAL;
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
+  TRY(need_lam64(h));
   CK(orthonormalise(h->g, h->lam64, h->p.n_v, h->st));
   TRY(sync_lam32(h));
   CK(cudaStreamSynchronize(h->st));
   h->have_coarse = false;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_trim(ddamg_handle h) {
+  if (!h) return DDAMG_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  if (inner32(h) && h->have_vectors && h->lam32 && !h->lam64_gone) {
+    dfree(h, h->lam64, (size_t)h->p.n_v * h->V24 * sizeof(double));
+    h->lam64 = nullptr;
+    h->lam64_gone = true;
+  }
+  for (void* q : h->tmp) dfree(h, q, h->tmp_fields * h->V24 * sizeof(double));
+  h->tmp.clear();
+  h->tmp_fields = 0;
+  dfree(h, h->lexbuf, h->lexbuf_fields * h->V24 * sizeof(double));
+  h->lexbuf = nullptr;
+  h->lexbuf_fields = 0;
+  ++h->gen;                        // captured graphs referred to the temporaries
   return DDAMG_OK;
 }
 
@@ -2355,8 +2429,9 @@ ddamg_status ddamg_restrict(ddamg_handle h, int prec, int nrhs, const double* in
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
   return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
     using R = std::remove_pointer_t<decltype(tag)>;
+    if (sizeof(R) == 8 || !h->lam32) TRY(need_lam64(h));
     if (sizeof(R) == 4 && !h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
-    if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    if (sizeof(R) == 4 && !h->lam64_gone) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
     TRY(need_tmp(h, nrhs, 6));
     TRY(import_fields<R>(h, in, on_device, nrhs, (R*)h->tmp[0]));
     CK(restrict_inner<R>(h, (R*)h->tmp[0], (R*)h->tmp[1], nrhs));
@@ -2369,8 +2444,9 @@ ddamg_status ddamg_prolong(ddamg_handle h, int prec, int nrhs, const double* in,
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
   return dispatch(h, prec, [&](auto* tag) -> ddamg_status {
     using R = std::remove_pointer_t<decltype(tag)>;
+    if (sizeof(R) == 8 || !h->lam32) TRY(need_lam64(h));
     if (sizeof(R) == 4 && !h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
-    if (sizeof(R) == 4) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+    if (sizeof(R) == 4 && !h->lam64_gone) CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
     TRY(need_tmp(h, nrhs, 6));
     TRY(coarse_in<R>(h, in, on_device, (size_t)nrhs * h->g.nb * h->n2, (R*)h->tmp[0]));
     CK(prolong_inner<R>(h, (R*)h->tmp[0], (R*)h->tmp[1], nrhs));

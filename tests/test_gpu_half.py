@@ -132,3 +132,37 @@ def test_half_storage_solves_reach_tolerance(prec):
               f"batched {[i['outer_iters'] for i in ib]}")
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_trim_releases_setup_memory_and_keeps_the_solver(prec):
+    """After ddamg_trim (the FP64 test vectors and the setup's temporaries
+    released) the solves give the same solutions, a mass update still
+    rebuilds D_c from the kept inner-precision vectors, calls that read the
+    FP64 test vectors report DDAMG_ESTATE, and a new setup allocates them
+    again."""
+    import paper_1811_00355_gb300 as P
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, prec)
+    try:
+        s.run_setup()
+        rhs = np.ascontiguousarray(syn.point_sources(L)[:2])
+        x0, _ = s.solve(rhs, 1e-10)
+        s.trim()
+        x1, info = s.solve(rhs, 1e-10)
+        for k in range(rhs.shape[0]):
+            assert info[k]["converged"] == 1
+            assert_close(x1[k], x0[k], 1e-12)
+        with pytest.raises(P.DDAMGError) as e:
+            s.get_test_vectors()
+        assert e.value.status == 7
+        op = oracle_op(L, eps, seed, m0 + 0.05, csw)
+        s.update_mass(m0 + 0.05, csw)
+        x2, info = s.solve(rhs, 1e-10)
+        for k in range(rhs.shape[0]):
+            assert rel(op.apply(t(x2[k])).numpy(), rhs[k]) <= 1e-10 and info[k]["converged"] == 1
+        s.update_mass(m0, csw)
+        s.run_setup()
+        assert s.get_test_vectors().shape[0] == n_v
+    finally:
+        s.close()
