@@ -307,6 +307,13 @@ DDAMG_API ddamg_status ddamg_build_coarse(ddamg_handle h);
  * and ddamg_set_test_vectors allocate them again. */
 DDAMG_API ddamg_status ddamg_trim(ddamg_handle h);
 
+/* Outer FGMRES iterations (single and batched) through CUDA graphs captured
+ * on first reuse (on: the default) or launched kernel by kernel (off).  A
+ * graph capture on one host thread cannot overlap a synchronising call such
+ * as cudaFree on another, so a program that drives several handles from
+ * several host threads (the serving loop below does) turns graphs off. */
+DDAMG_API ddamg_status ddamg_set_graphs(ddamg_handle h, int on);
+
 /* Export D_c in the coarse-op layout (host buffer, NX*9*(2n)^2 complex). */
 DDAMG_API ddamg_status ddamg_get_coarse_op(ddamg_handle h, double *out);
 

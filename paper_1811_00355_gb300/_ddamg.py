@@ -139,6 +139,7 @@ SIGNATURES = {
     "ddamg_batch_take": (_I, [_H, _I, _P, _I, C.POINTER(SolveInfo)]),
     "ddamg_get_coarse_plan": (_I, [_H, _I, C.POINTER(CoarsePlan)]),
     "ddamg_trim": (_I, [_H]),
+    "ddamg_set_graphs": (_I, [_H, _I]),
     "ddamg_set_wait_limit": (_I, [_H, C.c_int64]),
     "ddamg_tuning_count": (_I, []),
     "ddamg_get_tuning": (_I, [_I, C.POINTER(Tuning)]),
@@ -442,6 +443,10 @@ class DDAMG:
         """Release the setup's temporaries and, for an inner precision other
         than FP64, the FP64 copy of the test vectors (ddamg_trim)."""
         self._check(self.lib.ddamg_trim(self.h))
+
+    def set_graphs(self, on=True):
+        """Outer iterations through CUDA graphs (default) or kernel by kernel."""
+        self._check(self.lib.ddamg_set_graphs(self.h, int(bool(on))))
 
     def coarse_plan(self, nrhs=1):
         """Launch configuration of the coarse GMRES for nrhs right-hand sides."""

@@ -169,8 +169,12 @@ struct ddamg_ctx {
     uint64_t n_cls[NCLS] = {};
     int gen = -1;
     bool timing = false;
+    int nb = 0;                         // batch width (batched iterations)
+    int uses = 0;                       // eager runs since the last capture
   };
   std::vector<IterGraph> graphs;
+  std::vector<IterGraph> bgraphs;       // batched outer iterations, per Krylov index
+  bool graphs_on = true;                // outer iterations through CUDA graphs (ddamg_set_graphs)
   int gen = 0;                          // bumped whenever buffers move
   std::vector<GraphTimer>* capture_timers = nullptr;
   double* h_pinned = nullptr;           // device-to-host landing buffer
@@ -1191,6 +1195,7 @@ constexpr double REORTH_RATIO = 1e-2;
 template <class R>
 ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlist, double* vk, double* zk,
                            double* vk1) {
+  if (!h->graphs_on) return enqueue_iteration<R>(h, k, vlist, vk, zk, vk1);
   auto& G = h->graphs[k];
   if (!G.exec || G.gen != h->gen || G.timing != h->timing) {
     if (G.exec) {
@@ -1240,7 +1245,66 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
     G.gen = h->gen;
     G.timing = h->timing;
   }
-  CK(cudaGraphLaunch(G.exec, h->st));
+  CK(launch_graph_ordered(G.exec, h->st));
+  g_launches += G.launches;
+  addf(h, G.flops);
+  for (int c = 0; c < NCLS; ++c) h->n_cls[c] += G.n_cls[c];
+  return DDAMG_OK;
+}
+
+// Run the work `enqueue` puts on the handle's stream through graph G: eagerly
+// the first time (allocations and autotuning happen there), captured the
+// second time and replayed from then on; captured anew when buffers moved or
+// the batch width changed.  With kernel timing on every run is eager.
+template <class F>
+ddamg_status graph_run(ddamg_ctx* h, ddamg_ctx::IterGraph& G, int nb, F&& enqueue) {
+  if (h->timing || !h->graphs_on) return enqueue();
+  if (G.exec && (G.gen != h->gen || G.nb != nb)) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.uses = 0;
+  }
+  if (!G.exec) {
+    if (G.nb != nb) {
+      G.nb = nb;
+      G.uses = 0;
+    }
+    if (G.uses++ == 0) return enqueue();
+    if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    const uint64_t l0 = LaunchCount::mine();
+    const double f0 = h->flops[h->fphase];
+    uint64_t c0[NCLS];
+    for (int c = 0; c < NCLS; ++c) c0[c] = h->n_cls[c];
+    cudaStream_t user = h->st;
+    h->st = h->cap_st;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      h->st = user;
+      CK(e);
+    }
+    ddamg_status s = enqueue();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->st, &graph);
+    h->st = user;
+    G.launches = LaunchCount::mine() - l0;
+    G.flops = h->flops[h->fphase] - f0;
+    h->flops[h->fphase] = f0;
+    for (int c = 0; c < NCLS; ++c) {
+      G.n_cls[c] = h->n_cls[c] - c0[c];
+      h->n_cls[c] = c0[c];
+    }
+    g_launches.remove_mine(G.launches);
+    if (s != DDAMG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    G.gen = h->gen;
+  }
+  CK(launch_graph_ordered(G.exec, h->st));
   g_launches += G.launches;
   addf(h, G.flops);
   for (int c = 0; c < NCLS; ++c) h->n_cls[c] += G.n_cls[c];
@@ -1429,6 +1493,7 @@ ddamg_status alloc_batch(ddamg_ctx* h, int nb) {
     dfree(h, h->bmem, h->bbytes);
     h->bmem = nullptr;
     h->bcap = 0;
+    ++h->gen;                      // captured batched iterations referred to the old buffers
   }
   const int m = h->p.outer_restart;
   const size_t F = h->V24 * sizeof(double);            // one FP64 field
@@ -1570,48 +1635,60 @@ ddamg_status batch_cycle(ddamg_ctx* h) {
     open[r] = B.live[r] && !done[r];
     cstop[r] = std::max(B.tol[r] * bnorm[r], refine ? h->p.outer_refine * beta[r] : 0.0);
   }
+  if ((int)h->bgraphs.size() < m) h->bgraphs.resize(m);
   for (int k = 0; k < m; ++k) {
-    // z_k = M v_k and w = D z_k for the whole batch
-    if (refine) {
-      float* zk = Z32 + (size_t)k * blk;
-      TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
-      TRY(op_M<float>(h, (float*)h->bin, zk, nb));
-      TRY(op_dslash<float>(h, DSLASH_D, zk, nullptr, (float*)h->bout, nb));
-      TRY(from_inner<float>(h, (float*)h->bout, h->bw, nb));
-    } else {
-      double* zk = Z64 + (size_t)k * blk;
-      if constexpr (sizeof(R) == 8) {
-        TRY(op_M<double>(h, Vk(k), zk, nb));
-      } else {
-        TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
-        TRY(op_M<float>(h, (float*)h->bin, (float*)h->bout, nb));
-        TRY(from_inner<float>(h, (float*)h->bout, zk, nb));
-      }
-      TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
-    }
-    for (int r = 0; r < nb; ++r)
-      if (open[r]) ++B.calls[r];
-    // classical Gram-Schmidt per right-hand side (two passes; in the
-    // refinement mode one, plus a second when the first cancelled most of
-    // some w -- as in fgmres), ||w||, v_{k+1}
     const int kk = k + 1;
     const int kd1 = refine ? kk + 1 : kk;     // first-pass dots (+ ||w||^2 in the refinement mode)
-    const double* keep = vlist[k + 1];
-    if (refine) vlist[k + 1] = h->bw;
-    CK(multi_dot_batched<double>(vlist.data(), kd1, h->bw, NC, nb, NC, h->red, c1, h->st));
-    vlist[k + 1] = keep;
+    // z_k = M v_k and w = D z_k for the whole batch, then the first
+    // Gram-Schmidt pass (classical, per right-hand side; in the refinement
+    // mode with ||w||^2, the update and the coefficients' copy to the host):
+    // one CUDA graph per Krylov index and batch width
+    auto front = [&]() -> ddamg_status {
+      if (refine) {
+        float* zk = Z32 + (size_t)k * blk;
+        TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+        TRY(op_M<float>(h, (float*)h->bin, zk, nb));
+        TRY(op_dslash<float>(h, DSLASH_D, zk, nullptr, (float*)h->bout, nb));
+        TRY(from_inner<float>(h, (float*)h->bout, h->bw, nb));
+      } else {
+        double* zk = Z64 + (size_t)k * blk;
+        if constexpr (sizeof(R) == 8) {
+          TRY(op_M<double>(h, Vk(k), zk, nb));
+        } else {
+          TRY(to_inner<float>(h, Vk(k), (float*)h->bin, nb));
+          TRY(op_M<float>(h, (float*)h->bin, (float*)h->bout, nb));
+          TRY(from_inner<float>(h, (float*)h->bout, zk, nb));
+        }
+        TRY(op_dslash<double>(h, DSLASH_D, zk, nullptr, h->bw, nb));
+      }
+      const double* keep = vlist[k + 1];
+      if (refine) vlist[k + 1] = h->bw;
+      CK(multi_dot_batched<double>(vlist.data(), kd1, h->bw, NC, nb, NC, h->red, c1, h->st));
+      vlist[k + 1] = keep;
+      if (refine) {
+        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kd1, -1.0, h->bw, NC, nb, NC, h->red, nn,
+                                      h->st));
+        CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->st));
+      } else {
+        CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr,
+                                      h->st));
+      }
+      return DDAMG_OK;
+    };
+    TRY(graph_run(h, h->bgraphs[k], nb, front));
+    for (int r = 0; r < nb; ++r)
+      if (open[r]) ++B.calls[r];
+    // second pass where needed (always without the refinement mode; in it
+    // when the first pass cancelled most of some w -- as in fgmres), ||w||,
+    // v_{k+1}
     bool second = !refine;
     if (refine) {
-      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kd1, -1.0, h->bw, NC, nb, NC, h->red, nn, h->st));
-      CK(cudaMemcpyAsync(hp, c1, (size_t)nb * (4 * (m + 2) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
       CK(cudaStreamSynchronize(h->st));
       const double* hn2 = hp + (size_t)nb * 4 * (m + 2);
       for (int r = 0; r < nb; ++r)
         if (open[r] && hn2[2 * r] < REORTH_RATIO * hp[2 * (r * kd1 + kk)]) second = true;
       if (second) ++h->reorth;
-    } else {
-      CK(multi_axpy_batched<double>(vlist.data(), kk, c1, 2 * kk, -1.0, h->bw, NC, nb, NC, nullptr, nullptr,
-                                    h->st));
     }
     if (second) {
       CK(multi_dot_batched<double>(vlist.data(), kk, h->bw, NC, nb, NC, h->red, c2, h->st));
@@ -2281,6 +2358,12 @@ ddamg_status ddamg_orthonormalize(ddamg_handle h) {
   return DDAMG_OK;
 }
 
+ddamg_status ddamg_set_graphs(ddamg_handle h, int on) {
+  if (!h) return DDAMG_EINVAL;
+  h->graphs_on = on != 0;
+  return DDAMG_OK;
+}
+
 ddamg_status ddamg_trim(ddamg_handle h) {
   if (!h) return DDAMG_EINVAL;
   CK(cudaStreamSynchronize(h->st));
@@ -2612,6 +2695,8 @@ void ddamg_destroy(ddamg_handle h) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
+  for (auto& gph : h->bgraphs)
+    if (gph.exec) cudaGraphExecDestroy(gph.exec);
   for (auto& gph : h->graphs) {
     if (gph.exec) cudaGraphExecDestroy(gph.exec);
     for (auto& gt : gph.timers) {

@@ -267,6 +267,9 @@ struct CoarseSolveArgs {
 // in shared memory (local_in_smem) or in global scratch, the even site's D_c
 // blocks resident in shared memory; dynamic shared memory per CTA and the
 // bytes of `work` the launch touches
+// launch a captured graph holding a cooperative coarse-GMRES kernel in the
+// process-wide order of cooperative launches on the current device
+cudaError_t launch_graph_ordered(cudaGraphExec_t g, cudaStream_t st);
 struct CoarsePlan {
   int NR, G, per, local_in_smem, resident, ring;
   size_t smem_bytes, work_bytes;

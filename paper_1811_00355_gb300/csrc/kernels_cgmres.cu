@@ -1346,6 +1346,26 @@ cudaError_t coarse_gmres(const Geom& g, const CoarseSolveArgs& ca, const R* b, R
   return e;
 }
 
+// A captured graph that holds a cooperative coarse-GMRES launch joins the
+// order of the cooperative launches made outside graphs: it waits for the
+// previous one of the process on this device, and the next one waits for it
+cudaError_t launch_graph_ordered(cudaGraphExec_t g, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_done[dev]) {
+    e = cudaEventCreateWithFlags(&g_coop_done[dev], cudaEventDisableTiming);
+  } else {
+    e = cudaStreamWaitEvent(st, g_coop_done[dev], 0);
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphLaunch(g, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g_coop_done[dev], st);
+  return e;
+}
+
 template cudaError_t coarse_gmres<float>(const Geom&, const CoarseSolveArgs&, const float*, float*, int, void*,
                                          int*, int*, int*, cudaStream_t, const CoarsePlan*);
 template cudaError_t coarse_gmres<double>(const Geom&, const CoarseSolveArgs&, const double*, double*, int,

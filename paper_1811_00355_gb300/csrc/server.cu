@@ -177,9 +177,14 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   ddamg_handle h = nullptr;
   ddamg_status st = ddamg_setup(&p, c.gauge.data(), 0, c.st, &h);
   if (st != DDAMG_OK) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->last_error = ddamg_last_error(h);
+    }
     if (h) ddamg_destroy(h);
     return st;
   }
+  ddamg_set_graphs(h, 0);          // the workers' threads share the device (no captures)
   {
     std::lock_guard<std::mutex> lk(s->mu);
     c.h = h;
