@@ -861,6 +861,60 @@ def stencils(P, torch, stream, pk, pk_kind):
                          "us_per_rhs": round(us / nb_, 2)}
     finally:
         h.close()
+    out["coarse_gmres_8x8x8x16"] = coarse_solver_timing(P, torch, stream, pk)
+    return out
+
+
+# the coarse lattice of the 32^3 x 64 workload (8^3 x 16 aggregates, n_v 24),
+# reached from a 16^3 x 32 fine lattice with 2^4 aggregates and the seeded
+# synthetic 9-point stencil as D_c (no fine setup needed)
+COARSE = dict(L=(16, 16, 16, 32), block=(2, 2, 2, 2), n_v=24, iters=20, reps=5, nrhs=(1, 8, 12))
+
+
+def coarse_solver_timing(P, torch, stream, pk=None):
+    """The coarse even-odd GMRES on 8^3 x 16 coarse sites, n_v 24, FP32, for
+    1, 8 and 12 right-hand sides: a fixed number of iterations, timed with
+    CUDA events over repeated solves; per iteration it touches the nine D_c
+    blocks of every even site and the eight A_oo^-1 D_c blocks of every odd
+    site (1.28 GB)."""
+    import synthetic as syn
+    c = COARSE
+    L = c["L"]
+    p = P.default_params(L=L, sap_block=c["block"], n_v=c["n_v"], precision=P.FP32, coarse_restart=30,
+                         coarse_max_iter=c["iters"])
+    h = P.DDAMG(p, syn.unit_gauge(L), stream=stream.cuda_stream)
+    n2 = 2 * c["n_v"]
+    NX = h.NX
+    out = {"coarse_sites": NX, "n_v": c["n_v"], "operator": "synthetic 9-point stencil, diag 1.0, hop 0.21",
+           "timing": "CUDA events over %d solves of %d iterations" % (c["reps"], c["iters"])}
+    try:
+        h.set_coarse_op(syn.coarse_stencil(NX, n2, 5, 1.0, 0.21))
+        per_iter = (NX // 2) * (9 + 8) * n2 * n2 * 8
+        for nrhs in c["nrhs"]:
+            gen = np.random.default_rng(1)
+            bc = torch.from_numpy(gen.standard_normal((nrhs, NX, n2)) + 1j * gen.standard_normal((nrhs, NX, n2)))
+            bc = bc.cuda()
+            for _ in range(2):
+                h.coarse_solve(bc, 1e-30, P.FP32)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(c["reps"]):
+                x, its = h.coarse_solve(bc, 1e-30, P.FP32)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / c["reps"]
+            it = int(its.max())
+            plan = h.coarse_plan(nrhs)
+            passes = -(-nrhs // plan["rhs_per_pass"])
+            ent = {"us_per_iter": round(us / it, 1), "plan": plan, "passes": passes}
+            if pk:
+                gbs = per_iter * passes / (us / it * 1e-6) / 1e9
+                ent.update({"operator_GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)})
+            out["nrhs_%d" % nrhs] = ent
+    finally:
+        h.close()
     return out
 
 
@@ -1007,6 +1061,8 @@ def main():
     ap.add_argument("--large-no-oracle", action="store_true", help="skip the oracle residual check (profiling)")
     ap.add_argument("--stencils-only", action="store_true",
                     help="time only the stencils (for profiler captures) and print their JSON")
+    ap.add_argument("--coarse-only", action="store_true",
+                    help="time only the coarse GMRES on 8^3 x 16 coarse sites (for profiler captures)")
     ap.add_argument("--stencil-lattice", default=None,
                     help="X,Y,Z,T of the stencil lattice (multiples of 8; default 32,32,32,64)")
     args = ap.parse_args()
@@ -1028,6 +1084,15 @@ def main():
         return
     if args.huge_only:
         huge_batched_child()
+        return
+    if args.coarse_only:
+        import torch
+        import paper_1811_00355_gb300 as P
+        torch.cuda.set_device(0)
+        P.load()
+        print(json.dumps({"coarse_gmres_8x8x8x16": coarse_solver_timing(P, torch, torch.cuda.current_stream(),
+                                                                         peaks()[0]),
+                          "autotune": P.tuning()}))
         return
     if args.stencils_only:
         import torch

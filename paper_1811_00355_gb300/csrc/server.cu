@@ -162,7 +162,11 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
     if (!lru) break;                 // nothing left to release: try, the handle's budget decides
     release(s, *lru);
   }
-  if (s->budget && used >= s->budget) return DDAMG_ENOMEM;
+  if (s->budget && used >= s->budget) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->last_error = "device memory budget held by configurations being served";
+    return DDAMG_ENOMEM;
+  }
   ddamg_params p = c.p;
   p.hbm_budget = s->budget ? s->budget - used : 0;
   if (!c.st) {
@@ -213,7 +217,12 @@ void serve(ddamg_server* s, int ci) {
   const int S = s->max_batch;
   std::vector<Request*> slot_req(S, nullptr);
   std::vector<Request*> active;
-  if (st == DDAMG_OK) st = ddamg_batch_begin(c.h, S);
+  if (st == DDAMG_OK) {
+    st = ddamg_batch_begin(c.h, S);
+    note_error(s, c.h, st);
+    // the footprint that later admissions count includes the batch buffers
+    if (st == DDAMG_OK) measure(s, c);
+  }
   for (;;) {
     // admission (requests that fit into the free slots)
     std::vector<Request*> fresh;
