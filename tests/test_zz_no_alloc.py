@@ -49,10 +49,13 @@ def test_noalloc_coarse_solve_matches_coarse_solve(prec):
             got, its = s.coarse_solve_noalloc(dev_in, 5e-2)
             torch.cuda.synchronize()
             free_after = torch.cuda.mem_get_info()[0]
+            # the primary check: the handle allocated nothing
             assert s.stats()["device_bytes"] == held
-            # the first call on a device may load the fixed 16 MiB array (module
-            # loading is lazy); no call allocates beyond that
-            slack = (1 << 21) + ((16 << 20) if call == 0 else 0)
+            # a loose secondary bound on the device-wide free memory (other
+            # processes on the GPU could move it): the first call on a device
+            # may load the fixed 16 MiB array (module loading is lazy), and
+            # no call allocates anything near a spinor field's size beyond that
+            slack = (16 << 20) + ((16 << 20) if call == 0 else 0)
             assert free_after >= free_before - slack
             assert np.array_equal(its, its_ref), call
             assert_close(got.cpu().numpy(), ref, tol, call)
