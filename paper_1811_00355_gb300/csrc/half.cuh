@@ -157,11 +157,14 @@ __device__ __forceinline__ void store_spinor_h(S* f, float* nrm, int d, int Vb, 
 
 // the 12 values of link mu (two rows) within the 16 values of units
 // (12 mu) / 8 and the next one, at offset (12 mu) % 8 = 4 (mu & 1)
-__device__ __forceinline__ void link_from16(const float* v16, int mu, Link<float>& U) {
+__device__ __forceinline__ void link_rows_from16(const float* v16, int mu, Link<float>& U) {
   const bool odd = mu & 1;
 #pragma unroll
   for (int k = 0; k < 6; ++k)
     U.m[k / 3][k % 3] = mk(odd ? v16[4 + 2 * k] : v16[2 * k], odd ? v16[5 + 2 * k] : v16[2 * k + 1]);
+}
+__device__ __forceinline__ void link_from16(const float* v16, int mu, Link<float>& U) {
+  link_rows_from16(v16, mu, U);
   complete_link(U);
 }
 __device__ __forceinline__ int link_unit(int mu) { return (12 * mu) / 8; }

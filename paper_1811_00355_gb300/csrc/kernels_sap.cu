@@ -514,13 +514,17 @@ struct IO<float> {
 #pragma unroll
     for (int u = 0; u < 9; ++u) unpack(A[(9 * cb + u) * Vh + h], P + 4 * u);
   }
-  // link mu of local site q from the staged links (rows of Vbp units)
-  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+  // rows 0 and 1 of link mu of local site q from the staged links (rows of
+  // Vbp units); link_smem also rebuilds row 2
+  __device__ __forceinline__ static void link2_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
     float v[LINK_NR];
 #pragma unroll
     for (int u = 0; u < 3; ++u) unpack(sl[(mu * 3 + u) * Vbp + q], v + 4 * u);
 #pragma unroll
     for (int k = 0; k < 6; ++k) U.m[k / 3][k % 3] = mk(v[2 * k], v[2 * k + 1]);
+  }
+  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+    link2_smem(sl, Vbp, q, mu, U);
     complete_link(U);
   }
   // complex component k of the spinor at site d
@@ -558,12 +562,16 @@ struct IOH {
 #pragma unroll
     for (int k = 0; k < 36; ++k) P[k] = cb ? v[4 + k] : v[k];
   }
-  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+  __device__ __forceinline__ static void link2_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
     float v[16];
     const int u0 = link_unit(mu);
     unpack(sl[u0 * Vbp + q], v);
     unpack(sl[(u0 + 1) * Vbp + q], v + 8);
-    link_from16(v, mu, U);
+    link_rows_from16(v, mu, U);
+  }
+  __device__ __forceinline__ static void link_smem(const T* sl, int Vbp, int q, int mu, Link<float>& U) {
+    link2_smem(sl, Vbp, q, mu, U);
+    complete_link(U);
   }
   // 32-bit word of complex component k: unit k / 4, position k % 4
   __device__ __forceinline__ static size_t word(int d, int Vb, int k) {
@@ -636,15 +644,20 @@ __device__ __forceinline__ void rows3(const typename IO<S>::T* A, int Vh, int h,
   for (int i = 0; i < 3; ++i) y[i] = half ? y6[3 + i] : y6[i];
 }
 
-// link mu of local site q from the staged block links
+// link mu of local site q from the staged block links, its third row from
+// the rows rebuilt once per sweep (row3[(3 mu + c) Vbp + q])
 template <class S>
-__device__ __forceinline__ void slink(const typename IO<S>::T* sl, int Vbp, int q, int mu, Link<float>& U) {
-  IO<S>::link_smem(sl, Vbp, q, mu, U);
+__device__ __forceinline__ void slink(const typename IO<S>::T* sl, const f2* row3, int Vbp, int q, int mu,
+                                      Link<float>& U) {
+  IO<S>::link2_smem(sl, Vbp, q, mu, U);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) U.m[2][c] = row3[(3 * mu + c) * Vbp + q];
 }
 
 // hop_block with the neighbour indices already known (-1: outside the block)
 template <class S>
-__device__ __forceinline__ void hop_block_q(int qf, int qb, const typename IO<S>::T* sl, const f2* buf, int Vbp,
+__device__ __forceinline__ void hop_block_q(int qf, int qb, const typename IO<S>::T* sl, const f2* row3, const f2* buf,
+                                            int Vbp,
                                             int Vh, int q, int sub, f2 out[3]) {
   Spinor<float> acc;
 #pragma unroll
@@ -656,7 +669,7 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const typename IO<S>
     smem_spinor<float>(buf, Vh, qf >= Vh ? qf - Vh : qf, nb);
     project_rt<float>(nb, dr, -1.f, hh);
     Link<float> U;
-    slink<S>(sl, Vbp, q, sub, U);
+    slink<S>(sl, row3, Vbp, q, sub, U);
     su3_mul(U, hh, y);
     accumulate_rt<float>(acc, y, dr, -1.f, 1.f);
   }
@@ -664,7 +677,7 @@ __device__ __forceinline__ void hop_block_q(int qf, int qb, const typename IO<S>
     smem_spinor<float>(buf, Vh, qb >= Vh ? qb - Vh : qb, nb);
     project_rt<float>(nb, dr, 1.f, hh);
     Link<float> U;
-    slink<S>(sl, Vbp, qb, sub, U);
+    slink<S>(sl, row3, Vbp, qb, sub, U);
     su3_mul_dag(U, hh, y);
     accumulate_rt<float>(acc, y, dr, 1.f, 1.f);
   }
@@ -725,6 +738,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2* E = reinterpret_cast<f2*>(Aoi + CU * Vh);                         // [12][Vh]
   f2* O = E + 12 * Vh;                                                  // [12][Vh]
   float* red = reinterpret_cast<float*>(O + 12 * Vh);                   // [3 * warps + 3]
+  f2* row3 = reinterpret_cast<f2*>(red + 200);                          // [12][Vb + LPAD]
 
   // CTA c handles right-hand side c % nrhs of block c / nrhs of the colour:
   // the CTAs of one block run side by side, so the block's links and clover
@@ -816,6 +830,15 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       return;
     }
   }
+  // the third rows of the staged links, rebuilt once per sweep instead of
+  // at every hop (visible to the hops after the barrier below)
+  for (int k = t; k < 4 * Vb; k += blockDim.x) {
+    const int mu = k / Vb, q = k - mu * Vb;
+    Link<float> U;
+    IO<S>::link_smem(sl, Vbp, q, mu, U);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) row3[(3 * mu + c) * Vbp + q] = U.m[2][c];
+  }
   auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aoi, Vh, h, cb, half, v6, y); };
   auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aee, Vh, h, cb, half, v6, y); };
   // u_o = A_oo^-1 r_o
@@ -831,7 +854,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 res[3], xe[3];
   {
     f2 tt[3];
-    hop_block_q<S>(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
+    hop_block_q<S>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       res[i] = mk(fmaf(0.5f, tt[i].re, re[i].re), fmaf(0.5f, tt[i].im, re[i].im));
@@ -851,7 +874,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     __syncthreads();
     {  // odd: w = A_oo^-1 (-1/2 hop(res))
       f2 tt[3], v6[6], w[3];
-      hop_block_q<S>(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
+      hop_block_q<S>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) tt[i] = -0.5f * tt[i];
       chiral6<float>(tt, sub, v6);
@@ -863,7 +886,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
     {  // even: p = A_ee res + 1/2 hop(w)
       f2 tt[3];
-      hop_block_q<S>(qf_e, qb_e, sl, O, Vbp, Vh, h, sub, tt);
+      hop_block_q<S>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         p[i] = mk(fmaf(0.5f, tt[i].re, p[i].re), fmaf(0.5f, tt[i].im, p[i].im));
@@ -892,7 +915,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 eo[3];
   {
     f2 tt[3], v6[6];
-    hop_block_q<S>(qf_o, qb_o, sl, E, Vbp, Vh, Vh + h, sub, tt);
+    hop_block_q<S>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) tt[i] = mk(fmaf(0.5f, tt[i].re, ro[i].re), fmaf(0.5f, tt[i].im, ro[i].im));
     chiral6<float>(tt, sub, v6);
@@ -968,13 +991,15 @@ size_t sap_smem_bytes(const Geom& g, int real_size) {
 
 // shared memory of the staged kernel: link rows (LU units per site, padded),
 // the even half of A and the odd half of A^-1 (CU units per site each), the
-// even and odd work vectors and the reduction slots; 16-byte units
+// even and odd work vectors, the reduction slots and the third rows of the
+// staged links; 16-byte units
 static size_t sap_stg_smem(const Geom& g, int LU, int CU) {
   const int Vh = g.Vb / 2;
   size_t bytes = (size_t)LU * (g.Vb + LPAD) * 16;
   bytes += (size_t)2 * CU * Vh * 16;
   bytes += (size_t)24 * Vh * 8;
   bytes += 100 * sizeof(double);
+  bytes += (size_t)12 * (g.Vb + LPAD) * 8;     // third link rows (FP32 complex)
   return bytes;
 }
 
