@@ -354,7 +354,9 @@ DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coa
  * threads per site, one hop direction each (1), in FP32 and in BF16/FP16
  * storage; the coarse GMRES's block products for eight right-hand sides in
  * lockstep with the blocks streamed through shared memory, on the CUDA
- * cores (0) or the tensor cores (1, 3xTF32) ("coarse product"). */
+ * cores (0) or the tensor cores (1, 3xTF32) ("coarse product"); the FP32
+ * Schwarz sweep with the block's links and clover blocks staged in shared
+ * memory (0) or read from global memory (1) ("SAP fp32"). */
 typedef struct {
   char kernel[32];
   char problem[96];

@@ -733,6 +733,27 @@ ddamg_status op_dslash(ddamg_ctx* h, int mode, const R* x, const R* b, R* y, int
 }
 
 // SAP from zero: x = S b
+// FP32 Schwarz sweeps with blocks the staged kernel takes: staged (0) or
+// general kernel (1), measured on the caller's fields the first time for a
+// problem (the smoother starts from x = 0, so a trial run leaves nothing
+// behind in x that the real run keeps)
+ddamg_status sap32_staged(ddamg_ctx* h, const float* b, float* x, int nf, bool* staged) {
+  *staged = true;
+  if (!sap_staged_ok(h->g)) return DDAMG_OK;
+  auto trial = [&](int var) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(x, 0, nf * h->V24 * sizeof(float), h->st);
+    for (int cyc = 0; cyc < h->p.n_sap && e == cudaSuccess; ++cyc)
+      for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = sap_sweep<float>(h->g, c, h->p.mr_iters, cyc == 0 && c == 0, b, x, h->g32, h->A32, h->Ai32, nf,
+                             h->d_status, h->wait_sap, h->st, var == 0);
+    return e;
+  };
+  int v = 0;
+  TRY(tuned(h, "SAP fp32", lattice_key(h, "fp32", nf), 2, trial, &v));
+  *staged = v == 0;
+  return DDAMG_OK;
+}
+
 template <class R>
 ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
   if (kind == -2) kind = half_kind(h->p.precision);
@@ -767,6 +788,8 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
       return DDAMG_OK;
     }
   }
+  bool staged = true;
+  if constexpr (sizeof(R) == 4) TRY(sap32_staged(h, b, x, nf, &staged));
   CK(cudaMemsetAsync(x, 0, nf * h->V24 * sizeof(R), h->st));
   for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
     for (int c = 0; c < 2; ++c) {
@@ -774,7 +797,7 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
       addf(h, nf * flops_sap_sweep(h, zero));
       CK(timed(h, 1, [&] {
         return sap_sweep<R>(h->g, c, h->p.mr_iters, zero, b, x, gauge_of<R>(h), clov_of<R>(h, false),
-                            clov_of<R>(h, true), nf, h->d_status, h->wait_sap, h->st);
+                            clov_of<R>(h, true), nf, h->d_status, h->wait_sap, h->st, staged);
       }));
     }
   return DDAMG_OK;
@@ -1111,6 +1134,11 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
   if (refine_mode(h)) {
     int v = 0;
     TRY(dslash32_variant(h, (const float*)h->fin, (float*)h->fout, 1, &v));
+  }
+  // and the FP32 smoother's kernel (the FP32 fields as scratch)
+  if (inner32(h) && half_kind(h->p.precision) < 0) {
+    bool staged = true;
+    TRY(sap32_staged(h, (const float*)h->fin, (float*)h->fout, 1, &staged));
   }
   return DDAMG_OK;
 }

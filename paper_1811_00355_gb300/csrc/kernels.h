@@ -173,10 +173,14 @@ cudaError_t index_maps(const Geom& g, int* parity, int* block, int* colour, cuda
 //   x += e (x is overwritten with e if x_is_zero)
 // *status receives DDAMG_ETIMEOUT (6) if a bounded wait for staged data gives
 // up after wait_limit polls (the CTA then leaves x untouched)
+// (staged: the FP32 kernel with the block's links and clover blocks staged
+// in shared memory where the block shape allows it, else the general one)
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b,
                       R* x, const R* gauge, const R* clover, const R* clover_inv, int nrhs,
-                      int* status, long long wait_limit, cudaStream_t st);
+                      int* status, long long wait_limit, cudaStream_t st, bool staged = true);
+// the staged FP32 kernel applies to the block shape of g
+bool sap_staged_ok(const Geom& g);
 size_t sap_smem_bytes(const Geom& g, int real_size);
 // one colour of a Schwarz sweep with half storage (FP32 arithmetic): links,
 // clover blocks A and A^-1 and the spinors b, x (with their site norms) in

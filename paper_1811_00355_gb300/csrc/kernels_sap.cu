@@ -1009,6 +1009,7 @@ static bool sap_stg_ok(const Geom& g, int LU, int CU) {
 }
 
 bool sap_half_ok(const Geom& g) { return sap_stg_ok(g, HGAUGE_NU, HCLOV_NU); }
+bool sap_staged_ok(const Geom& g) { return sap_stg_ok(g, 12, 18); }
 
 template <class S>
 static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const S* b, const float* bn,
@@ -1083,9 +1084,9 @@ template cudaError_t dslash4<__nv_bfloat16>(const Geom&, const void*, const floa
 template <class R>
 cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, const R* b, R* x,
                       const R* gauge, const R* clover, const R* clover_inv, int nrhs, int* status,
-                      long long wait_limit, cudaStream_t st) {
+                      long long wait_limit, cudaStream_t st, bool staged) {
   if constexpr (sizeof(R) == 4) {
-    if (sap_stg_ok(g, 12, 18)) {
+    if (staged && sap_stg_ok(g, 12, 18)) {
       return launch_stg<float>(g, colour, mr_iters, x_is_zero, b, nullptr, x, nullptr, gauge, clover, clover_inv,
                                nrhs, status, wait_limit, st);
     }
@@ -1113,9 +1114,9 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
 }
 
 template cudaError_t sap_sweep<float>(const Geom&, int, int, bool, const float*, float*, const float*,
-                                      const float*, const float*, int, int*, long long, cudaStream_t);
+                                      const float*, const float*, int, int*, long long, cudaStream_t, bool);
 template cudaError_t sap_sweep<double>(const Geom&, int, int, bool, const double*, double*,
                                        const double*, const double*, const double*, int, int*, long long,
-                                       cudaStream_t);
+                                       cudaStream_t, bool);
 
 }  // namespace ddamg

@@ -127,6 +127,24 @@ def test_sap(cfg, prec):
     assert_close(got[0], ref, tol)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sap_variants_fp32(variant):
+    """Both measured variants of the FP32 Schwarz sweep on 4^4 blocks (links
+    and clover blocks staged in shared memory, or read from global memory)
+    match the oracle's SAP."""
+    P = _P()
+    P.pin_variant("SAP fp32", variant)
+    try:
+        s = make(MID, 1)
+        r = syn.gaussian_spinors(1, MID[0], 48)
+        got = s.sap(r, 1)
+        ref = smoother(MID).apply(t(r[0]), 4, 4).numpy()
+        assert_close(got[0], ref, 2e-5)
+        s.close()
+    finally:
+        P.pin_variant("SAP fp32", -1)
+
+
 @pytest.mark.parametrize("cfg", [SMALL, MID])
 def test_orthonormalise(cfg):
     L, b, eps, m0, csw, n_v, seed = cfg
