@@ -787,8 +787,10 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   // b and x may still be written by the previous kernel of the stream
   grid_dependency_wait();
 
-  // residual r = b - D x on the own components of both sites
-  f2 re[3], ro[3];
+  // residual r = b - D x on the own components of both sites: the hops and
+  // the odd site's clover product from global memory while the block is
+  // staged, the even site's clover product from the staged A_ee after it
+  f2 re[3], ro[3], xe6[6];
 #pragma unroll
   for (int par = 0; par < 2; ++par) {
     const int d = par ? dO : de;
@@ -796,22 +798,25 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
 #pragma unroll
     for (int i = 0; i < 3; ++i) r[i] = IO<S>::comp(b, bn, d, Vb, 3 * sub + i);
     if (!x_is_zero) {
-      f2 hop[3], x6[6], ax[3];
+      f2 hop[3], x6[6];
       hop_global_s<S>(g, x, xn, gauge, d, sub, hop);
 #pragma unroll
       for (int i = 0; i < 6; ++i) x6[i] = IO<S>::comp(x, xn, d, Vb, 6 * cb + i);
-      {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        r[i].re += 0.5f * hop[i].re;
+        r[i].im += 0.5f * hop[i].im;
+      }
+      if (par) {
         float P[36];
         IO<S>::block36(clov, d, Vb, cb, P);
         f2 y6[6];
         herm6<float>(P, x6, y6);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) ax[i] = half ? y6[3 + i] : y6[i];
-      }
+        for (int i = 0; i < 3; ++i) r[i] = r[i] - (half ? y6[3 + i] : y6[i]);
+      } else {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        r[i].re -= ax[i].re - 0.5f * hop[i].re;
-        r[i].im -= ax[i].im - 0.5f * hop[i].im;
+        for (int i = 0; i < 6; ++i) xe6[i] = x6[i];
       }
     }
 #pragma unroll
@@ -829,6 +834,12 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       mbar_wait_bounded(&mbar, 0, MBAR_POLL_LIMIT);
       return;
     }
+  }
+  if (!x_is_zero) {     // r_e -= A_ee x_e, A_ee staged
+    f2 ax[3];
+    rows3<S>(Aee, Vh, h, cb, half, xe6, ax);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) re[i] = re[i] - ax[i];
   }
   // the third rows of the staged links, rebuilt once per sweep instead of
   // at every hop (visible to the hops after the barrier below)
