@@ -41,8 +41,9 @@ SAP_BYTES_PER_SITE = 4 * (24 + 24 + 24 + 48 + 72 + 72)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) per launch of each timed kernel class on this
 # workload, from an ncu capture of the kernel as it is now (a single-RHS
-# sweep, a single-RHS coarse solve); None where the kernel changed since
-TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": 18_965_760 + 0, "coarse_gmres": 42_868_736 + 9_984}
+# coarse solve); None where no capture of a single-RHS launch of the kernel
+# as it is now exists
+TRAFFIC_BYTES_PER_LAUNCH = {"sap_sweep": None, "coarse_gmres": 42_921_472 + 40_448}
 # stencil bandwidth lattice: 32^3 x 64 (the lattice of the batched workload),
 # far larger than L2, links tiled from an 8^4 field of the same generator
 STENCIL = dict(L=(32, 32, 32, 64), tile=(8, 8, 8, 8), block=(4, 4, 4, 4), eps=0.2, seed=3, m0=-0.3, csw=1.5,
