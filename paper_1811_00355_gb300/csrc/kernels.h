@@ -271,6 +271,11 @@ struct CoarseSolveArgs {
 // in shared memory (local_in_smem) or in global scratch, the even site's D_c
 // blocks resident in shared memory; dynamic shared memory per CTA and the
 // bytes of `work` the launch touches
+// Raise kernel fn's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit only grows (per device and kernel, under a lock):
+// a launch sized by one host thread stays valid whatever a smaller launch of
+// another thread sets in between.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 // launch a captured graph holding a cooperative coarse-GMRES kernel in the
 // process-wide order of cooperative launches on the current device
 cudaError_t launch_graph_ordered(cudaGraphExec_t g, cudaStream_t st);

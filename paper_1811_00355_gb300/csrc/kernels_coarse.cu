@@ -723,7 +723,7 @@ cudaError_t assemble_coarse(const Geom& g, const R* lam, int n, const R* gauge, 
   if (4 * n * n > 16 * threads) return cudaErrorInvalidValue;
   int ch = assemble_chunk(n, sizeof(R));
   size_t smem = (size_t)ch * 12 * 3 * n * 2 * sizeof(R) + ch * sizeof(int) + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_assemble<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_assemble<R>, smem);
   if (e != cudaSuccess) return e;
   k_assemble<R><<<g.nb, threads, smem, st>>>(g, lam, n, gauge, clover, reinterpret_cast<cpx<R>*>(Dc), ch);
   ++g_launches;
@@ -734,7 +734,7 @@ template <class R>
 cudaError_t invert_self_blocks(const Geom& g, const R* Dc, int n, R* Ainv, int* singular, cudaStream_t st) {
   int n2 = 2 * n;
   size_t smem = (size_t)n2 * 2 * n2 * sizeof(cpx<double>);
-  cudaError_t e = cudaFuncSetAttribute(k_invert_self<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_invert_self<R>, smem);
   if (e != cudaSuccess) return e;
   k_invert_self<R><<<g.nb, 256, smem, st>>>(g, reinterpret_cast<const cpx<R>*>(Dc), n2,
                                             reinterpret_cast<cpx<R>*>(Ainv), singular);
@@ -746,7 +746,7 @@ template <class R>
 cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R* AD, cudaStream_t st) {
   const int n2 = 2 * n;
   const size_t smem = (size_t)2 * n2 * n2 * sizeof(cpx<R>);
-  cudaError_t e = cudaFuncSetAttribute(k_premultiply_odd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_premultiply_odd<R>, smem);
   if (e != cudaSuccess) return e;
   k_premultiply_odd<R><<<dim3(g.nb / 2, 8), 256, smem, st>>>(g, reinterpret_cast<const cpx<R>*>(Dc),
                                                            reinterpret_cast<const cpx<R>*>(Ainv), n2,
@@ -765,7 +765,7 @@ cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, in
   while (S > 1 && S * NP > 1024) S /= 2;
   const size_t smem = (size_t)S * (9 * n2 + 1) * sizeof(cpx<R>);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k_coarse_apply<R>, smem);
     if (e != cudaSuccess) return e;
   }
   k_coarse_apply<R><<<dim3((g.nb + S - 1) / S, nrhs), S * NP, smem, st>>>(

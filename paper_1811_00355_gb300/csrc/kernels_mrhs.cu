@@ -305,7 +305,7 @@ cudaError_t restrict_mrhs(const Geom& g, const float* lam, int n, const float* b
   if (!mrhs_ok(g, n) || nrhs < 1) return cudaErrorInvalidValue;
   const int N = nrhs < 16 ? nrhs : 16;
   const size_t smem = restrict_mma_smem(n, N);
-  cudaError_t e = cudaFuncSetAttribute(k_restrict_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_restrict_mma, smem);
   if (e != cudaSuccess) return e;
   k_restrict_mma<<<dim3(g.nb, (nrhs + 15) / 16), MT_THREADS, smem, st>>>(g, lam, n, b, nrhs, chunk_sites(g.Vb),
                                                                         reinterpret_cast<cpx<float>*>(bc));
@@ -317,7 +317,7 @@ cudaError_t prolong_mrhs(const Geom& g, const float* lam, int n, const float* xc
                          cudaStream_t st) {
   if (!mrhs_ok(g, n) || nrhs < 1) return cudaErrorInvalidValue;
   const size_t smem = prolong_mma_smem(g, n);
-  cudaError_t e = cudaFuncSetAttribute(k_prolong_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_prolong_mma, smem);
   if (e != cudaSuccess) return e;
   k_prolong_mma<<<dim3(g.nb, (nrhs + 15) / 16), MT_THREADS, smem, st>>>(
       g, lam, n, reinterpret_cast<const cpx<float>*>(xc), nrhs, chunk_sites(g.Vb), x);
