@@ -476,7 +476,7 @@ def variants(P, torch, stream, U_dev, b_dev, steps, flush):
 # arrival rate keeps the offered load (about 3 right-hand sides per second,
 # a quarter of them on 32^3 x 64) below what the largest lattice can serve.
 SERVING = dict(lattices=((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)), requests=24,
-               rate_hz=0.5, seed=2024, max_batch=12, restart=16, workers=2, budget=250 * 2 ** 30)
+               rate_hz=0.5, seed=2024, max_batch=12, restart=16, workers=4, budget=250 * 2 ** 30)
 
 
 def serving(P, torch, stream):
@@ -553,8 +553,9 @@ def serving(P, torch, stream):
                              requests=len(per_cfg.get(c["id"], [])))
                         for c in cfgs],
             "note": ("latency = submit to results in host memory; continuous batching (requests join a running "
-                     "batch between restart cycles), two configurations served at a time on their own streams; "
-                     "setups done before the stream, idle configurations released by the memory budget")}
+                     "batch between restart cycles), up to %d configurations served at a time on their own "
+                     "streams; setups done before the stream, idle configurations released by the memory budget"
+                     % sv["workers"])}
 
 
 def _tiled(a, small, L):
