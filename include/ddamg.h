@@ -76,9 +76,9 @@ typedef enum {
   DDAMG_ESTATE = 7    /* call needs state the handle does not have yet       */
 } ddamg_status;
 
-/* Arithmetic of the smoother, coarse grid and projections.  The outer
- * FGMRES, its residual r = b - D x and the test-vector orthonormalisation
- * are always FP64.  DDAMG_BF16 and DDAMG_FP16 compute in FP32 like
+/* Arithmetic of the smoother, coarse grid, projections and test-vector
+ * orthonormalisation.  The outer FGMRES and its residual r = b - D x are
+ * always FP64.  DDAMG_BF16 and DDAMG_FP16 compute in FP32 like
  * DDAMG_FP32 but store in that half type: the smoother's links, clover
  * blocks (A and A^-1) and spinor fields (each spinor divided by its site
  * norm, the largest magnitude of its 24 reals, kept in FP32), and the test
@@ -289,8 +289,10 @@ DDAMG_API ddamg_status ddamg_set_test_vectors(ddamg_handle h, const double *vecs
 DDAMG_API ddamg_status ddamg_get_test_vectors(ddamg_handle h, double *vecs);
 
 /* Orthonormalise the test vectors inside every aggregate X and chirality s
- * (classical Gram-Schmidt applied twice, i = 1..n, FP64), so that the
- * projections of Eq. 1 satisfy P^H P = 1. */
+ * (classical Gram-Schmidt applied twice, i = 1..n), so that the
+ * projections of Eq. 1 satisfy P^H P = 1: in FP64, or in FP32 for a handle
+ * whose inner solver is FP32 (its R and P use the vectors in FP32; the FP64
+ * copy takes the FP32 result).  The setup orthonormalises the same way. */
 DDAMG_API ddamg_status ddamg_orthonormalize(ddamg_handle h);
 
 /* Assemble D_c (Eq. 2) from the current test vectors in the inner
@@ -356,7 +358,9 @@ DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coa
  * lockstep with the blocks streamed through shared memory, on the CUDA
  * cores (0) or the tensor cores (1, 3xTF32) ("coarse product"); the FP32
  * Schwarz sweep with the block's links and clover blocks staged in shared
- * memory (0) or read from global memory (1) ("SAP fp32"). */
+ * memory (0) or read from global memory (1) ("SAP fp32"); the half-storage
+ * Schwarz sweep with the staged block operators widened to FP32 in shared
+ * memory (0) or kept in the half type (1) ("SAP bf16", "SAP fp16"). */
 typedef struct {
   char kernel[32];
   char problem[96];
@@ -366,7 +370,8 @@ typedef struct {
 } ddamg_tuning;
 DDAMG_API int ddamg_tuning_count(void);
 DDAMG_API ddamg_status ddamg_get_tuning(int i, ddamg_tuning *out);
-/* Use `variant` of the named kernel ("D fp32", "D bf16", "D fp16") for every
+/* Use `variant` of the named kernel ("D fp32", "D bf16", "D fp16", "coarse
+ * product", "SAP fp32", "SAP bf16", "SAP fp16") for every
  * problem instead of the measured choice (variant < 0: measure again);
  * process-wide, for reproducible runs and for checking each variant. */
 DDAMG_API ddamg_status ddamg_pin_variant(const char *kernel, int variant);

@@ -754,6 +754,32 @@ ddamg_status sap32_staged(ddamg_ctx* h, const float* b, float* x, int nf, bool* 
   return DDAMG_OK;
 }
 
+// half-storage Schwarz sweeps: the staged block operators widened to FP32
+// in shared memory (0) or kept in the half type (1), measured the first time
+// for a problem on the half right-hand sides already in hb (the smoother
+// starts from x = 0; the caller clears x afterwards)
+ddamg_status sap_half_widen(ddamg_ctx* h, int kind, int nf, bool* widen) {
+  *widen = true;
+  if (!sap_staged_ok(h->g)) return DDAMG_OK;
+  auto trial = [&](int var) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(h->hx, 0, nf * h->V24 * 2, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->hxn, 0, nf * h->g.V * sizeof(float), h->st);
+    for (int cyc = 0; cyc < h->p.n_sap && e == cudaSuccess; ++cyc)
+      for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = by_half(kind, [&](auto* tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          return sap_sweep_h<S>(h->g, c, h->p.mr_iters, cyc == 0 && c == 0, h->hb, h->hbn, h->hx, h->hxn,
+                                h->gH[kind], h->AH[kind], h->AiH[kind], nf, h->d_status, h->wait_sap, h->st,
+                                var == 0);
+        });
+    return e;
+  };
+  int v = 0;
+  TRY(tuned(h, kind ? "SAP bf16" : "SAP fp16", lattice_key(h, kind ? "bf16" : "fp16", nf), 2, trial, &v));
+  *widen = v == 0;
+  return DDAMG_OK;
+}
+
 template <class R>
 ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
   if (kind == -2) kind = half_kind(h->p.precision);
@@ -763,12 +789,14 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
     if (kind >= 0 && sap_half_ok(h->g)) {
       TRY(half_operators(h, kind));
       TRY(need_half_fields(h, nf));
-      CK(cudaMemsetAsync(h->hx, 0, nf * h->V24 * 2, h->st));
-      CK(cudaMemsetAsync(h->hxn, 0, nf * h->g.V * sizeof(float), h->st));
       CK(by_half(kind, [&](auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         return spinor_to_half<S>(h->g, b, h->hb, h->hbn, nf, h->st);
       }));
+      bool widen = true;
+      TRY(sap_half_widen(h, kind, nf, &widen));
+      CK(cudaMemsetAsync(h->hx, 0, nf * h->V24 * 2, h->st));
+      CK(cudaMemsetAsync(h->hxn, 0, nf * h->g.V * sizeof(float), h->st));
       for (int cyc = 0; cyc < h->p.n_sap; ++cyc)
         for (int c = 0; c < 2; ++c) {
           const bool zero = cyc == 0 && c == 0;
@@ -777,7 +805,7 @@ ddamg_status op_sap(ddamg_ctx* h, const R* b, R* x, int nf, int kind = -2) {
             return by_half(kind, [&](auto* tag) {
               using S = std::remove_pointer_t<decltype(tag)>;
               return sap_sweep_h<S>(h->g, c, h->p.mr_iters, zero, h->hb, h->hbn, h->hx, h->hxn, h->gH[kind],
-                                    h->AH[kind], h->AiH[kind], nf, h->d_status, h->wait_sap, h->st);
+                                    h->AH[kind], h->AiH[kind], nf, h->d_status, h->wait_sap, h->st, widen);
             });
           }));
         }
@@ -1019,6 +1047,21 @@ ddamg_status coarse_iters_since(ddamg_ctx* h, int* its) {
   return DDAMG_OK;
 }
 
+// the test vectors orthonormalised per (aggregate, chirality) in the inner
+// precision: FP64 in place, or (FP32 inner solver, whose R and P use them in
+// FP32) on the FP32 copy, which the FP64 copy then takes
+ddamg_status ortho_inner(ddamg_ctx* h) {
+  if (!inner32(h)) {
+    CK(orthonormalise(h->g, h->lam64, h->p.n_v, h->st));
+    return DDAMG_OK;
+  }
+  if (!h->lam32) TRY(dalloc_t(h, &h->lam32, (size_t)h->p.n_v * h->V24));
+  CK(convert_spinor<float, double>(h->g, h->lam64, h->lam32, h->p.n_v, h->st));
+  CK(orthonormalise(h->g, h->lam32, h->p.n_v, h->st));
+  CK(convert_spinor<double, float>(h->g, h->lam32, h->lam64, h->p.n_v, h->st));
+  return DDAMG_OK;
+}
+
 template <class R>
 ddamg_status setup_impl(ddamg_ctx* h) {
   const int n = h->p.n_v;
@@ -1063,7 +1106,7 @@ ddamg_status setup_impl(ddamg_ctx* h) {
   }
   for (int it = 0; it < h->p.setup_iters; ++it) {
     addf(h, flops_ortho(h));
-    CK(orthonormalise(h->g, h->lam64, n, h->st));
+    TRY(ortho_inner(h));
     TRY(build_coarse_op(h));
     // lambda_i <- M lambda_i
     for (int c0 = 0; c0 < n; c0 += ch) {
@@ -1076,7 +1119,7 @@ ddamg_status setup_impl(ddamg_ctx* h) {
     TRY(check_status(h));
   }
   addf(h, flops_ortho(h));
-  CK(orthonormalise(h->g, h->lam64, n, h->st));
+  TRY(ortho_inner(h));
   TRY(build_coarse_op(h));
   TRY(coarse_iters_since(h, &its));
   addf(h, its * flops_coarse_iter(h));
@@ -1135,10 +1178,19 @@ ddamg_status prepare_capture(ddamg_ctx* h) {
     int v = 0;
     TRY(dslash32_variant(h, (const float*)h->fin, (float*)h->fout, 1, &v));
   }
-  // and the FP32 smoother's kernel (the FP32 fields as scratch)
-  if (inner32(h) && half_kind(h->p.precision) < 0) {
+  // and the smoother's kernel (the FP32 fields as scratch)
+  if (inner32(h) && k < 0) {
     bool staged = true;
     TRY(sap32_staged(h, (const float*)h->fin, (float*)h->fout, 1, &staged));
+  }
+  if (k >= 0 && sap_half_ok(h->g)) {
+    CK(cudaMemsetAsync(h->fin, 0, h->V24 * sizeof(float), h->st));
+    CK(by_half(k, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      return spinor_to_half<S>(h->g, (const float*)h->fin, h->hb, h->hbn, 1, h->st);
+    }));
+    bool widen = true;
+    TRY(sap_half_widen(h, k, 1, &widen));
   }
   return DDAMG_OK;
 }
@@ -2316,15 +2368,19 @@ ddamg_status ddamg_block_solve(ddamg_handle h, int prec, int colour, int nrhs, c
     TRY(need_half_fields(h, nrhs));
     float* t0 = (float*)h->tmp[0];
     TRY(import_fields<float>(h, in, on_device, nrhs, t0));
+    CK(by_half(k, [&](auto* tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      return spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
+    }));
+    bool widen = true;
+    TRY(sap_half_widen(h, k, nrhs, &widen));
     CK(cudaMemsetAsync(h->hx, 0, nrhs * h->V24 * 2, h->st));
     CK(cudaMemsetAsync(h->hxn, 0, nrhs * h->g.V * sizeof(float), h->st));
     ++h->n_cls[1];
     CK(by_half(k, [&](auto* tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      cudaError_t e = spinor_to_half<S>(h->g, t0, h->hb, h->hbn, nrhs, h->st);
-      if (e != cudaSuccess) return e;
-      e = sap_sweep_h<S>(h->g, colour, h->p.mr_iters, true, h->hb, h->hbn, h->hx, h->hxn, h->gH[k], h->AH[k],
-                         h->AiH[k], nrhs, h->d_status, h->wait_sap, h->st);
+      cudaError_t e = sap_sweep_h<S>(h->g, colour, h->p.mr_iters, true, h->hb, h->hbn, h->hx, h->hxn, h->gH[k],
+                                     h->AH[k], h->AiH[k], nrhs, h->d_status, h->wait_sap, h->st, widen);
       if (e != cudaSuccess) return e;
       return spinor_from_half<S>(h->g, h->hx, h->hxn, t0, nrhs, false, h->st);
     }));
@@ -2379,7 +2435,7 @@ ddamg_status ddamg_orthonormalize(ddamg_handle h) {
   if (!h) return DDAMG_EINVAL;
   if (!h->have_vectors) return fail(h, DDAMG_ESTATE, "no test vectors");
   TRY(need_lam64(h));
-  CK(orthonormalise(h->g, h->lam64, h->p.n_v, h->st));
+  TRY(ortho_inner(h));
   TRY(sync_lam32(h));
   CK(cudaStreamSynchronize(h->st));
   h->have_coarse = false;

@@ -184,16 +184,20 @@ bool sap_staged_ok(const Geom& g);
 size_t sap_smem_bytes(const Geom& g, int real_size);
 // one colour of a Schwarz sweep with half storage (FP32 arithmetic): links,
 // clover blocks A and A^-1 and the spinors b, x (with their site norms) in
-// the half type S; needs blocks whose half volume is a multiple of 32
+// the half type S; needs blocks whose half volume is a multiple of 32.
+// widen: the staged block operators are widened to FP32 in shared memory
+// (where the FP32 staging fits the block), else kept in the half type
 template <class S>
 cudaError_t sap_sweep_h(const Geom& g, int colour, int mr_iters, bool x_is_zero, const void* b, const float* bn,
                         void* x, float* xn, const void* gauge, const void* clover, const void* clover_inv, int nrhs,
-                        int* status, long long wait_limit, cudaStream_t st);
+                        int* status, long long wait_limit, cudaStream_t st, bool widen = true);
 bool sap_half_ok(const Geom& g);
 
 // ---- coarse grid ----------------------------------------------------------------
-// classical Gram-Schmidt twice per (aggregate, chirality) on n FP64 fields
+// classical Gram-Schmidt twice per (aggregate, chirality) on n FP64 or FP32
+// fields
 cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st);
+cudaError_t orthonormalise(const Geom& g, float* lam, int n, cudaStream_t st);
 // b_c = R b  (coarse layout [rhs][X][2n] complex)
 template <class R>
 cudaError_t restrict_op(const Geom& g, const R* lam, int n, const R* b, R* bc, int nrhs,

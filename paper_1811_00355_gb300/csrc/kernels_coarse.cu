@@ -21,12 +21,6 @@ namespace {
 
 inline unsigned nblk(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <class R>
 __device__ __forceinline__ R warp_sum_t(R v) {
 #pragma unroll
@@ -34,25 +28,27 @@ __device__ __forceinline__ R warp_sum_t(R v) {
   return v;
 }
 
-// sum of (a, b) over the CTA, broadcast to every thread; sh >= 2 * warps doubles
-__device__ __forceinline__ void block_sum2_all(double& a, double& b, double* sh) {
-  a = warp_sum(a);
-  b = warp_sum(b);
+// sum of (a, b) over the CTA, broadcast to every thread; sh >= 2 * warps values
+template <class R>
+__device__ __forceinline__ void block_sum2_all(R& a, R& b, R* sh) {
+  a = warp_sum_t<R>(a);
+  b = warp_sum_t<R>(b);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
   __syncthreads();
-  a = 0.0; b = 0.0;
+  a = R(0); b = R(0);
   for (int i = 0; i < nw; ++i) { a += sh[2 * i]; b += sh[2 * i + 1]; }
   __syncthreads();
 }
 
-// sum of (a, b) over a warp with five FP64 additions per lane instead of ten:
+// sum of (a, b) over a warp with five additions per lane instead of ten:
 // the halves trade one value each first.  Lane 0 returns the sum of a, lane
 // 16 the sum of b.
-__device__ __forceinline__ double warp_sum_pair(double a, double b) {
+template <class R>
+__device__ __forceinline__ R warp_sum_pair(R a, R b) {
   const bool up = (threadIdx.x & 16) != 0;
-  double keep = up ? b : a;
+  R keep = up ? b : a;
   keep += __shfl_xor_sync(0xffffffffu, up ? a : b, 16);
 #pragma unroll
   for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
@@ -60,94 +56,137 @@ __device__ __forceinline__ double warp_sum_pair(double a, double b) {
 }
 
 // ---------------------------------------------------------------------------
-// orthonormalisation: CTA per (aggregate, chirality), ORTHO_SITES sites per
-// thread.
-// Classical Gram-Schmidt, two passes, FP64: for vector i every thread forms
-// its partial products with all earlier vectors j < i at once, and the CTA
-// reduces the i coefficients together (one barrier per pass, not per j).
-// Several sites per thread cut the share of FP64 additions spent in the
-// cross-thread sums, FP64 being GB300's scarce arithmetic.
+// orthonormalisation: CTA per (aggregate, chirality), SITES sites per thread.
+// Classical Gram-Schmidt, two passes, in FP64 or FP32: for vector i every
+// thread forms its partial products with all earlier vectors j < i at once,
+// and the CTA reduces the i coefficients together (one barrier per pass, not
+// per j).  In FP64 several sites per thread cut the share of additions spent
+// in the cross-thread sums, FP64 being GB300's scarce arithmetic; in FP32 one
+// site per thread keeps more loads in flight.
 // ---------------------------------------------------------------------------
-constexpr int ORTHO_SITES = 4;
-
-__global__ void k_orthonormalise(Geom g, double* __restrict__ lam, int n) {
-  extern __shared__ double osh[];          // red [warps][n][2], coef [n][2]
-  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  double* red = osh;
-  double* coef = osh + (size_t)2 * nw * n;
-  const int X = blockIdx.x, s = blockIdx.y;
-  const size_t fstride = (size_t)g.V * SPINOR_NR;
-  using LY = Layout<double, SPINOR_NR>;
-  bool own[ORTHO_SITES];
-  size_t base[ORTHO_SITES];
+// the six complex components 6 s .. 6 s + 5 (chirality s) of the site whose
+// unit 0 is at b: one component per FP64 unit, two per FP32 unit
+template <class R>
+struct Chiral6;
+template <>
+struct Chiral6<double> {
+  __device__ __forceinline__ static void load(const double* f, size_t b, int Vb, int s, cpx<double>* v) {
+    const double2* p = reinterpret_cast<const double2*>(f) + b + (size_t)6 * s * Vb;
 #pragma unroll
-  for (int e = 0; e < ORTHO_SITES; ++e) {
+    for (int u = 0; u < 6; ++u) {
+      const double2 a = p[(size_t)u * Vb];
+      v[u] = mk(a.x, a.y);
+    }
+  }
+  __device__ __forceinline__ static void store(double* f, size_t b, int Vb, int s, const cpx<double>* v) {
+    double2* p = reinterpret_cast<double2*>(f) + b + (size_t)6 * s * Vb;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) p[(size_t)u * Vb] = make_double2(v[u].re, v[u].im);
+  }
+};
+template <>
+struct Chiral6<float> {
+  __device__ __forceinline__ static void load(const float* f, size_t b, int Vb, int s, cpx<float>* v) {
+    const float4* p = reinterpret_cast<const float4*>(f) + b + (size_t)3 * s * Vb;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const float4 a = p[(size_t)u * Vb];
+      v[2 * u] = mk(a.x, a.y);
+      v[2 * u + 1] = mk(a.z, a.w);
+    }
+  }
+  __device__ __forceinline__ static void store(float* f, size_t b, int Vb, int s, const cpx<float>* v) {
+    float4* p = reinterpret_cast<float4*>(f) + b + (size_t)3 * s * Vb;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) p[(size_t)u * Vb] = make_float4(v[2 * u].re, v[2 * u].im, v[2 * u + 1].re, v[2 * u + 1].im);
+  }
+};
+
+template <class R, int SITES>
+__global__ void k_orthonormalise(Geom g, R* __restrict__ lam, int n) {
+  extern __shared__ __align__(16) unsigned char osh_raw[];   // red [warps][n][2], coef [n][2]
+  R* osh = reinterpret_cast<R*>(osh_raw);
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  R* red = osh;
+  R* coef = osh + (size_t)2 * nw * n;
+  const int X = blockIdx.x, s = blockIdx.y;
+  const size_t fstride = (size_t)g.V * SPINOR_NR / U16<R>::N;    // units per field
+  using LY = Layout<R, SPINOR_NR>;
+  using C6 = Chiral6<R>;
+  bool own[SITES];
+  size_t base[SITES];
+#pragma unroll
+  for (int e = 0; e < SITES; ++e) {
     const int q = threadIdx.x + e * blockDim.x;
     own[e] = q < g.Vb;
-    base[e] = LY::base(X * g.Vb + (own[e] ? q : 0), g.Vb) + (size_t)6 * s * g.Vb;
+    base[e] = LY::base(X * g.Vb + (own[e] ? q : 0), g.Vb);
   }
-  auto at = [&](int j, int e, int u) -> double2* {
-    return reinterpret_cast<double2*>(lam + j * fstride) + base[e] + (size_t)u * g.Vb;
-  };
   for (int i = 0; i < n; ++i) {
-    double2 v[ORTHO_SITES][6];
+    cpx<R> v[SITES][6];
 #pragma unroll
-    for (int e = 0; e < ORTHO_SITES; ++e)
+    for (int e = 0; e < SITES; ++e) {
+      if (own[e]) C6::load(lam, base[e] + i * fstride, g.Vb, s, v[e]);
+      else
 #pragma unroll
-      for (int u = 0; u < 6; ++u) v[e][u] = own[e] ? *at(i, e, u) : make_double2(0.0, 0.0);
+        for (int u = 0; u < 6; ++u) v[e][u] = mk(R(0), R(0));
+    }
     for (int pass = 0; pass < 2 && i > 0; ++pass) {
       for (int j = 0; j < i; ++j) {
-        double re = 0.0, im = 0.0;
+        R re = R(0), im = R(0);
 #pragma unroll
-        for (int e = 0; e < ORTHO_SITES; ++e) {
+        for (int e = 0; e < SITES; ++e) {
           if (own[e]) {
+            cpx<R> a[6];
+            C6::load(lam, base[e] + j * fstride, g.Vb, s, a);
 #pragma unroll
             for (int u = 0; u < 6; ++u) {
-              const double2 a = *at(j, e, u);
-              re = ::fma(a.x, v[e][u].x, ::fma(a.y, v[e][u].y, re));
-              im = ::fma(a.x, v[e][u].y, ::fma(-a.y, v[e][u].x, im));
+              re = ::fma(a[u].re, v[e][u].re, ::fma(a[u].im, v[e][u].im, re));
+              im = ::fma(a[u].re, v[e][u].im, ::fma(-a[u].im, v[e][u].re, im));
             }
           }
         }
-        const double r = warp_sum_pair(re, im);
+        const R r = warp_sum_pair<R>(re, im);
         if ((l & 15) == 0) red[(w * n + j) * 2 + (l >> 4)] = r;
       }
       __syncthreads();
       for (int j = threadIdx.x; j < i; j += blockDim.x) {
-        double re = 0.0, im = 0.0;
+        R re = R(0), im = R(0);
         for (int ww = 0; ww < nw; ++ww) { re += red[(ww * n + j) * 2]; im += red[(ww * n + j) * 2 + 1]; }
         coef[2 * j] = re;
         coef[2 * j + 1] = im;
       }
       __syncthreads();
       for (int j = 0; j < i; ++j) {
-        const double cr = coef[2 * j], ci = coef[2 * j + 1];
+        const R cr = coef[2 * j], ci = coef[2 * j + 1];
 #pragma unroll
-        for (int e = 0; e < ORTHO_SITES; ++e) {
+        for (int e = 0; e < SITES; ++e) {
           if (own[e]) {
+            cpx<R> a[6];
+            C6::load(lam, base[e] + j * fstride, g.Vb, s, a);
 #pragma unroll
             for (int u = 0; u < 6; ++u) {
-              const double2 a = *at(j, e, u);
-              v[e][u].x = ::fma(-cr, a.x, ::fma(ci, a.y, v[e][u].x));
-              v[e][u].y = ::fma(-cr, a.y, ::fma(-ci, a.x, v[e][u].y));
+              v[e][u].re = ::fma(-cr, a[u].re, ::fma(ci, a[u].im, v[e][u].re));
+              v[e][u].im = ::fma(-cr, a[u].im, ::fma(-ci, a[u].re, v[e][u].im));
             }
           }
         }
       }
       __syncthreads();
     }
-    double nn = 0.0, dummy = 0.0;
+    R nn = R(0), dummy = R(0);
 #pragma unroll
-    for (int e = 0; e < ORTHO_SITES; ++e)
+    for (int e = 0; e < SITES; ++e)
 #pragma unroll
-      for (int u = 0; u < 6; ++u) nn = ::fma(v[e][u].x, v[e][u].x, ::fma(v[e][u].y, v[e][u].y, nn));
-    block_sum2_all(nn, dummy, red);
-    const double f = 1.0 / sqrt(nn);
+      for (int u = 0; u < 6; ++u) nn = ::fma(v[e][u].re, v[e][u].re, ::fma(v[e][u].im, v[e][u].im, nn));
+    block_sum2_all<R>(nn, dummy, red);
+    const R f = R(1) / sqrt(nn);
 #pragma unroll
-    for (int e = 0; e < ORTHO_SITES; ++e)
-      if (own[e])
+    for (int e = 0; e < SITES; ++e)
+      if (own[e]) {
 #pragma unroll
-        for (int u = 0; u < 6; ++u) *at(i, e, u) = make_double2(v[e][u].x * f, v[e][u].y * f);
+        for (int u = 0; u < 6; ++u) v[e][u] = mk(v[e][u].re * f, v[e][u].im * f);
+        C6::store(lam, base[e] + i * fstride, g.Vb, s, v[e]);
+      }
     __syncthreads();
   }
 }
@@ -647,12 +686,21 @@ __global__ void k_conv_c(const RS* __restrict__ s, RD* __restrict__ d, size_t n)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st) {
-  int threads = (((g.Vb + ORTHO_SITES - 1) / ORTHO_SITES + 31) / 32) * 32;
-  size_t smem = ((size_t)2 * (threads / 32) * (n > 1 ? n : 1) + 2 * n) * sizeof(double);
-  k_orthonormalise<<<dim3(g.nb, 2), threads, smem, st>>>(g, lam, n);
+template <class R, int SITES>
+static cudaError_t ortho_launch(const Geom& g, R* lam, int n, cudaStream_t st) {
+  const int threads = (((g.Vb + SITES - 1) / SITES + 31) / 32) * 32;
+  if (threads > 1024) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)2 * (threads / 32) * (n > 1 ? n : 1) + 2 * n) * sizeof(R);
+  k_orthonormalise<R, SITES><<<dim3(g.nb, 2), threads, smem, st>>>(g, lam, n);
   ++g_launches;
   return cudaGetLastError();
+}
+cudaError_t orthonormalise(const Geom& g, double* lam, int n, cudaStream_t st) {
+  return ortho_launch<double, 4>(g, lam, n, st);
+}
+cudaError_t orthonormalise(const Geom& g, float* lam, int n, cudaStream_t st) {
+  if (g.Vb <= 1024) return ortho_launch<float, 1>(g, lam, n, st);
+  return ortho_launch<float, 4>(g, lam, n, st);
 }
 
 template <class R, class S>

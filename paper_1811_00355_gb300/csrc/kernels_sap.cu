@@ -15,6 +15,7 @@
 //   x  += e
 // with D_eo, D_oe the hops that stay inside the block (-1/2 (1 -+ g) U).
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "half.cuh"
@@ -720,16 +721,25 @@ __device__ __forceinline__ void hop_global_s(const Geom& g, const S* x, const fl
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// bn / xn: site norms of b and x (half storage only; ignored for FP32)
-template <class S>
+// bn / xn: site norms of b and x (half storage only; ignored for FP32).
+// SM is the type the staged block operators are kept in: the storage type S,
+// or FP32 for half storage (SM = float, S half): the half units are staged
+// into the upper half of each FP32 array and widened in place once per
+// sweep, so that the block solve's many reads of the staged links and
+// clover blocks need no unpacking.
+template <class S, class SM>
 __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iters, int x_is_zero,
                                                  const S* __restrict__ b, const float* __restrict__ bn,
                                                  S* __restrict__ x, float* __restrict__ xn,
                                                  const S* __restrict__ gauge, const S* __restrict__ clov,
                                                  const S* __restrict__ clov_inv, int* status, long long wait_limit) {
-  using T = typename IO<S>::T;
+  using T = typename IO<SM>::T;
+  constexpr bool WIDEN = !std::is_same<S, SM>::value;
+  static_assert(sizeof(T) == sizeof(typename IO<S>::T), "16-byte units in both types");
   constexpr unsigned UB = sizeof(T);            // bytes per unit
-  constexpr int LU = IO<S>::LINK_U, CU = IO<S>::CLOV_U;
+  constexpr int LU = IO<SM>::LINK_U, CU = IO<SM>::CLOV_U;     // staged units per site
+  constexpr int LG = IO<S>::LINK_U, CG = IO<S>::CLOV_U;       // units per site in global memory
+  static_assert(!WIDEN || (LU == 2 * LG && CU == 2 * CG), "a half unit widens into two FP32 units");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Vb = g.Vb, Vh = Vb / 2, Vbp = Vb + LPAD;
   T* sl = reinterpret_cast<T*>(smem_raw);                               // [LU][Vb + LPAD]
@@ -760,7 +770,9 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   const int qf_e = __ldg(g.bnbr + (2 * sub) * Vb + h), qb_e = __ldg(g.bnbr + (2 * sub + 1) * Vb + h);
   const int qf_o = __ldg(g.bnbr + (2 * sub) * Vb + Vh + h), qb_o = __ldg(g.bnbr + (2 * sub + 1) * Vb + Vh + h);
 
-  // stage the block's links (and A_ee, A_oo^-1) with bulk asynchronous copies
+  // stage the block's links (and A_ee, A_oo^-1) with bulk asynchronous
+  // copies: global unit row u lands in staged row u, or in row LU - LG + u
+  // (CU - CG + u) when it is widened afterwards
   __shared__ __align__(8) uint64_t mbar;
   if (t == 0) {
     mbar_init(&mbar, 1);
@@ -769,19 +781,19 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   __syncthreads();
   {
     const unsigned link_row = (unsigned)Vb * UB, half_row = (unsigned)Vh * UB;
-    if (t == 0) mbar_expect_tx(&mbar, (unsigned)LU * link_row + 2u * CU * half_row);
+    if (t == 0) mbar_expect_tx(&mbar, (unsigned)LG * link_row + 2u * CG * half_row);
     __syncthreads();
-    if (t < LU) {
-      const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * LU * Vb;
-      bulk_g2s(sl + (size_t)t * Vbp, src + (size_t)t * Vb, link_row, &mbar);
-    } else if (t < LU + CU) {
-      const int u = t - LU;
-      const T* ca = reinterpret_cast<const T*>(clov) + (size_t)B * CU * Vb;
-      bulk_g2s(Aee + (size_t)u * Vh, ca + (size_t)u * Vb, half_row, &mbar);
-    } else if (t < LU + 2 * CU) {
-      const int u = t - LU - CU;
-      const T* ci = reinterpret_cast<const T*>(clov_inv) + (size_t)B * CU * Vb;
-      bulk_g2s(Aoi + (size_t)u * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
+    if (t < LG) {
+      const T* src = reinterpret_cast<const T*>(gauge) + (size_t)B * LG * Vb;
+      bulk_g2s(sl + (size_t)(LU - LG + t) * Vbp, src + (size_t)t * Vb, link_row, &mbar);
+    } else if (t < LG + CG) {
+      const int u = t - LG;
+      const T* ca = reinterpret_cast<const T*>(clov) + (size_t)B * CG * Vb;
+      bulk_g2s(Aee + (size_t)(CU - CG + u) * Vh, ca + (size_t)u * Vb, half_row, &mbar);
+    } else if (t < LG + 2 * CG) {
+      const int u = t - LG - CG;
+      const T* ci = reinterpret_cast<const T*>(clov_inv) + (size_t)B * CG * Vb;
+      bulk_g2s(Aoi + (size_t)(CU - CG + u) * Vh, ci + (size_t)u * Vb + Vh, half_row, &mbar);
     }
   }
   // b and x may still be written by the previous kernel of the stream
@@ -835,9 +847,30 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
       return;
     }
   }
+  if constexpr (WIDEN) {
+    // half unit k of a site (staged row n + k of an array of 2 n rows) holds
+    // the values of FP32 units 2 k and 2 k + 1.  One thread widens one site
+    // of one array in increasing k: the rows 2 k, 2 k + 1 it writes are
+    // half rows n + k' with k' <= k, already read by the same thread, and
+    // no other thread touches the site's column.
+    for (int s = t; s < Vb + 2 * Vh; s += blockDim.x) {
+      T* a;
+      int n, stride, q;
+      if (s < Vb) { a = sl; n = LG; stride = Vbp; q = s; }
+      else if (s < Vb + Vh) { a = Aee; n = CG; stride = Vh; q = s - Vb; }
+      else { a = Aoi; n = CG; stride = Vh; q = s - Vb - Vh; }
+      for (int k = 0; k < n; ++k) {
+        float v[8];
+        unpack8<S>(*reinterpret_cast<const uint4*>(a + (size_t)(n + k) * stride + q), v);
+        a[(size_t)(2 * k) * stride + q] = make_float4(v[0], v[1], v[2], v[3]);
+        a[(size_t)(2 * k + 1) * stride + q] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
+    __syncthreads();
+  }
   if (!x_is_zero) {     // r_e -= A_ee x_e, A_ee staged
     f2 ax[3];
-    rows3<S>(Aee, Vh, h, cb, half, xe6, ax);
+    rows3<SM>(Aee, Vh, h, cb, half, xe6, ax);
 #pragma unroll
     for (int i = 0; i < 3; ++i) re[i] = re[i] - ax[i];
   }
@@ -846,12 +879,12 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   for (int k = t; k < 4 * Vb; k += blockDim.x) {
     const int mu = k / Vb, q = k - mu * Vb;
     Link<float> U;
-    IO<S>::link_smem(sl, Vbp, q, mu, U);
+    IO<SM>::link_smem(sl, Vbp, q, mu, U);
 #pragma unroll
     for (int c = 0; c < 3; ++c) row3[(3 * mu + c) * Vbp + q] = U.m[2][c];
   }
-  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aoi, Vh, h, cb, half, v6, y); };
-  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<S>(Aee, Vh, h, cb, half, v6, y); };
+  auto ainv_rows = [&](const f2 v6[6], f2 y[3]) { rows3<SM>(Aoi, Vh, h, cb, half, v6, y); };
+  auto aee_rows = [&](const f2 v6[6], f2 y[3]) { rows3<SM>(Aee, Vh, h, cb, half, v6, y); };
   // u_o = A_oo^-1 r_o
   {
     f2 v6[6], u[3];
@@ -865,7 +898,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 res[3], xe[3];
   {
     f2 tt[3];
-    hop_block_q<S>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
+    hop_block_q<SM>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       res[i] = mk(fmaf(0.5f, tt[i].re, re[i].re), fmaf(0.5f, tt[i].im, re[i].im));
@@ -885,7 +918,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     __syncthreads();
     {  // odd: w = A_oo^-1 (-1/2 hop(res))
       f2 tt[3], v6[6], w[3];
-      hop_block_q<S>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
+      hop_block_q<SM>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) tt[i] = -0.5f * tt[i];
       chiral6<float>(tt, sub, v6);
@@ -897,7 +930,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
     float pr_re = 0.f, pr_im = 0.f, pp_r = 0.f;
     {  // even: p = A_ee res + 1/2 hop(w)
       f2 tt[3];
-      hop_block_q<S>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
+      hop_block_q<SM>(qf_e, qb_e, sl, row3, O, Vbp, Vh, h, sub, tt);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         p[i] = mk(fmaf(0.5f, tt[i].re, p[i].re), fmaf(0.5f, tt[i].im, p[i].im));
@@ -926,7 +959,7 @@ __global__ void __launch_bounds__(512) k_sap_stg(Geom g, int colour, int mr_iter
   f2 eo[3];
   {
     f2 tt[3], v6[6];
-    hop_block_q<S>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
+    hop_block_q<SM>(qf_o, qb_o, sl, row3, E, Vbp, Vh, Vh + h, sub, tt);
 #pragma unroll
     for (int i = 0; i < 3; ++i) tt[i] = mk(fmaf(0.5f, tt[i].re, ro[i].re), fmaf(0.5f, tt[i].im, ro[i].im));
     chiral6<float>(tt, sub, v6);
@@ -1022,11 +1055,11 @@ static bool sap_stg_ok(const Geom& g, int LU, int CU) {
 bool sap_half_ok(const Geom& g) { return sap_stg_ok(g, HGAUGE_NU, HCLOV_NU); }
 bool sap_staged_ok(const Geom& g) { return sap_stg_ok(g, 12, 18); }
 
-template <class S>
+template <class S, class SM>
 static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is_zero, const S* b, const float* bn,
                               S* x, float* xn, const S* gauge, const S* clover, const S* clover_inv, int nrhs,
                               int* status, long long wait_limit, cudaStream_t st) {
-  const size_t need = sap_stg_smem(g, stg::IO<S>::LINK_U, stg::IO<S>::CLOV_U);
+  const size_t need = sap_stg_smem(g, stg::IO<SM>::LINK_U, stg::IO<SM>::CLOV_U);
   {
     // the attribute is per device and per instance; set it on every launch
     // whose size exceeds what this device's instance was given
@@ -1037,7 +1070,8 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (cfg[dev] < need) {
-      cudaError_t e = cudaFuncSetAttribute(stg::k_sap_stg<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+      cudaError_t e =
+          cudaFuncSetAttribute(stg::k_sap_stg<S, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
       if (e != cudaSuccess) return e;
       cfg[dev] = need;
     }
@@ -1053,8 +1087,8 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
   lc.attrs = at;
   lc.numAttrs = 1;
   const int zero = x_is_zero ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg<S>, g, colour, mr_iters, zero, b, bn, x, xn, gauge, clover,
-                                     clover_inv, status, wait_limit);
+  cudaError_t e = cudaLaunchKernelEx(&lc, stg::k_sap_stg<S, SM>, g, colour, mr_iters, zero, b, bn, x, xn, gauge,
+                                     clover, clover_inv, status, wait_limit);
   ++g_launches;
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1062,17 +1096,22 @@ static cudaError_t launch_stg(const Geom& g, int colour, int mr_iters, bool x_is
 template <class S>
 cudaError_t sap_sweep_h(const Geom& g, int colour, int mr_iters, bool x_is_zero, const void* b, const float* bn,
                         void* x, float* xn, const void* gauge, const void* clover, const void* clover_inv, int nrhs,
-                        int* status, long long wait_limit, cudaStream_t st) {
+                        int* status, long long wait_limit, cudaStream_t st, bool widen) {
   if (!sap_half_ok(g)) return cudaErrorInvalidValue;
-  return launch_stg<S>(g, colour, mr_iters, x_is_zero, static_cast<const S*>(b), bn, static_cast<S*>(x), xn,
-                       static_cast<const S*>(gauge), static_cast<const S*>(clover),
-                       static_cast<const S*>(clover_inv), nrhs, status, wait_limit, st);
+  if (widen && sap_staged_ok(g))
+    return launch_stg<S, float>(g, colour, mr_iters, x_is_zero, static_cast<const S*>(b), bn, static_cast<S*>(x), xn,
+                                static_cast<const S*>(gauge), static_cast<const S*>(clover),
+                                static_cast<const S*>(clover_inv), nrhs, status, wait_limit, st);
+  return launch_stg<S, S>(g, colour, mr_iters, x_is_zero, static_cast<const S*>(b), bn, static_cast<S*>(x), xn,
+                          static_cast<const S*>(gauge), static_cast<const S*>(clover),
+                          static_cast<const S*>(clover_inv), nrhs, status, wait_limit, st);
 }
 template cudaError_t sap_sweep_h<__half>(const Geom&, int, int, bool, const void*, const float*, void*, float*,
-                                         const void*, const void*, const void*, int, int*, long long, cudaStream_t);
+                                         const void*, const void*, const void*, int, int*, long long, cudaStream_t,
+                                         bool);
 template cudaError_t sap_sweep_h<__nv_bfloat16>(const Geom&, int, int, bool, const void*, const float*, void*,
                                                 float*, const void*, const void*, const void*, int, int*, long long,
-                                                cudaStream_t);
+                                                cudaStream_t, bool);
 
 template <class S>
 cudaError_t dslash4(const Geom& g, const void* x, const float* xn, void* y, float* yn, const void* gauge,
@@ -1098,8 +1137,8 @@ cudaError_t sap_sweep(const Geom& g, int colour, int mr_iters, bool x_is_zero, c
                       long long wait_limit, cudaStream_t st, bool staged) {
   if constexpr (sizeof(R) == 4) {
     if (staged && sap_stg_ok(g, 12, 18)) {
-      return launch_stg<float>(g, colour, mr_iters, x_is_zero, b, nullptr, x, nullptr, gauge, clover, clover_inv,
-                               nrhs, status, wait_limit, st);
+      return launch_stg<float, float>(g, colour, mr_iters, x_is_zero, b, nullptr, x, nullptr, gauge, clover,
+                                      clover_inv, nrhs, status, wait_limit, st);
     }
   }
   int threads = sap_threads(g);

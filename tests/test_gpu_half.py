@@ -67,8 +67,15 @@ def test_half_storage_D(cfg, prec, variant):
 
 
 @pytest.mark.parametrize("prec", [2, 3])
-def test_half_storage_block_solve_and_sap(prec):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_half_storage_block_solve_and_sap(prec, variant):
+    """Both forms of the half-storage Schwarz sweep: the staged block
+    operators widened to FP32 in shared memory (0) or kept in the half type
+    (1)."""
+    import paper_1811_00355_gb300 as P
     L = MID[0]
+    name = "SAP bf16" if prec == 2 else "SAP fp16"
+    P.pin_variant(name, variant)
     s = make(MID, prec)
     try:
         sm = smoother(MID)
@@ -83,9 +90,10 @@ def test_half_storage_block_solve_and_sap(prec):
         got = s.sap(r, prec)
         ref = sm.apply(t(r[0]), 4, 4).numpy()
         e = assert_close(got[0], ref, TOL_SAP[prec], "SAP")
-        print(f"half SAP prec {prec}: {e}")
+        print(f"half SAP prec {prec} variant {variant}: {e}")
     finally:
         s.close()
+        P.pin_variant(name, -1)
 
 
 @pytest.mark.parametrize("prec", [2, 3])

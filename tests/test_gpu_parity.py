@@ -145,16 +145,22 @@ def test_sap_variants_fp32(variant):
         P.pin_variant("SAP fp32", -1)
 
 
+# FP32 Gram-Schmidt: each coefficient is a sum of 6 |aggregate| products,
+# each vector update i of them; for well-conditioned (Gaussian) vectors the
+# result carries a few FP32 roundings, 1e-5 with room to spare
 @pytest.mark.parametrize("cfg", [SMALL, MID])
-def test_orthonormalise(cfg):
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-5)])
+def test_orthonormalise(cfg, prec, tol):
+    """FP64 handles orthonormalise in FP64, FP32 handles in FP32; both give
+    the oracle's vectors within their precision."""
     L, b, eps, m0, csw, n_v, seed = cfg
-    s = make(cfg, _P().FP64)
+    s = make(cfg, prec)
     lam = syn.gaussian_spinors(n_v, L, 44)
     s.set_test_vectors(lam)
     s.orthonormalize()
     op = oracle_op(L, eps, seed, m0, csw)
     ref = orthonormalise(t(lam), Aggregation(op.geom, b)).numpy()
-    assert_close(s.get_test_vectors(), ref, 1e-13)
+    assert_close(s.get_test_vectors(), ref, tol)
 
 
 @pytest.mark.parametrize("cfg", [SMALL, MID])
