@@ -395,15 +395,18 @@ def run_ours(args):
 def variants(P, torch, stream, U_dev, b_dev, steps, flush):
     """The same 12-RHS workload (setup + 12 point sources to 1e-10) in other
     forms: the 12 sources solved together in one lockstep batch (FP32 inner
-    solver), the plain single-RHS form with an FP64 inner solver, and the
-    single-RHS form with the test vectors of R and P stored in FP16."""
+    solver), the plain single-RHS form with an FP64 inner solver, the
+    single-RHS form with the test vectors of R and P stored in FP16, and the
+    single-RHS form with the test vectors orthonormalised in FP32."""
     w = WORKLOAD
     out = {}
     for name, prec, batched, n in (("batched_f32", P.FP32, True, steps), ("single_f64", P.FP64, False, 1),
-                                   ("single_f32_half_vectors", P.FP32, False, steps)):
+                                   ("single_f32_half_vectors", P.FP32, False, steps),
+                                   ("single_f32_ortho_fp32", P.FP32, False, steps)):
         params = workload_params(P)
         params.precision = prec
         params.half_vectors = 1 if name.endswith("half_vectors") else 0
+        params.ortho_fp32 = 1 if name.endswith("ortho_fp32") else 0
         s = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
         solve = s.solve_batched if batched else s.solve
         try:

@@ -76,9 +76,9 @@ typedef enum {
   DDAMG_ESTATE = 7    /* call needs state the handle does not have yet       */
 } ddamg_status;
 
-/* Arithmetic of the smoother, coarse grid, projections and test-vector
- * orthonormalisation.  The outer FGMRES and its residual r = b - D x are
- * always FP64.  DDAMG_BF16 and DDAMG_FP16 compute in FP32 like
+/* Arithmetic of the smoother, coarse grid and projections.  The outer
+ * FGMRES, its residual r = b - D x and the test-vector orthonormalisation
+ * are FP64 (the orthonormalisation FP32 on request, ortho_fp32).  DDAMG_BF16 and DDAMG_FP16 compute in FP32 like
  * DDAMG_FP32 but store in that half type: the smoother's links, clover
  * blocks (A and A^-1) and spinor fields (each spinor divided by its site
  * norm, the largest magnitude of its 24 reals, kept in FP32), and the test
@@ -119,6 +119,10 @@ typedef struct {
                           (FP32 arithmetic), and D_c is assembled from the
                           same rounded vectors; 0 = FP32 vectors (BF16 and
                           FP16 inner precisions always store them in half) */
+  int ortho_fp32;      /* inner precision FP32, BF16 or FP16 only: 1 = the
+                          test vectors are orthonormalised in FP32, the
+                          precision R and P use them in (the FP64 copy takes
+                          the FP32 result); 0 = in FP64 (default)            */
 } ddamg_params;
 
 typedef struct {
@@ -291,8 +295,7 @@ DDAMG_API ddamg_status ddamg_get_test_vectors(ddamg_handle h, double *vecs);
 /* Orthonormalise the test vectors inside every aggregate X and chirality s
  * (classical Gram-Schmidt applied twice, i = 1..n), so that the
  * projections of Eq. 1 satisfy P^H P = 1: in FP64, or in FP32 for a handle
- * whose inner solver is FP32 (its R and P use the vectors in FP32; the FP64
- * copy takes the FP32 result).  The setup orthonormalises the same way. */
+ * created with ortho_fp32.  The setup orthonormalises the same way. */
 DDAMG_API ddamg_status ddamg_orthonormalize(ddamg_handle h);
 
 /* Assemble D_c (Eq. 2) from the current test vectors in the inner

@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("precision", C.c_int), ("outer_restart", C.c_int), ("max_outer_iter", C.c_int),
         ("seed", C.c_uint64), ("hbm_budget", C.c_size_t), ("outer_refine", C.c_double),
         ("half_vectors", C.c_int),
+        ("ortho_fp32", C.c_int),
     ]
 
 

@@ -298,6 +298,8 @@ ddamg_status validate(const ddamg_params* p, std::string& why) {
   if (!(p->outer_refine >= 0.0 && p->outer_refine < 1.0)) return bad("outer_refine in [0, 1)");
   if (p->half_vectors != 0 && (p->half_vectors != 1 || p->precision != DDAMG_FP32))
     return bad("half_vectors is 0, or 1 with the FP32 inner precision");
+  if (p->ortho_fp32 != 0 && (p->ortho_fp32 != 1 || p->precision == DDAMG_FP64))
+    return bad("ortho_fp32 is 0, or 1 with an FP32-arithmetic inner precision");
   if (!std::isfinite(p->m0) || !std::isfinite(p->csw)) return bad("m0 and csw must be finite");
   return DDAMG_OK;
 }
@@ -1047,11 +1049,11 @@ ddamg_status coarse_iters_since(ddamg_ctx* h, int* its) {
   return DDAMG_OK;
 }
 
-// the test vectors orthonormalised per (aggregate, chirality) in the inner
-// precision: FP64 in place, or (FP32 inner solver, whose R and P use them in
-// FP32) on the FP32 copy, which the FP64 copy then takes
+// the test vectors orthonormalised per (aggregate, chirality): FP64 in
+// place, or (ortho_fp32, an FP32-arithmetic inner solver whose R and P use
+// them in FP32) on the FP32 copy, which the FP64 copy then takes
 ddamg_status ortho_inner(ddamg_ctx* h) {
-  if (!inner32(h)) {
+  if (!inner32(h) || !h->p.ortho_fp32) {
     CK(orthonormalise(h->g, h->lam64, h->p.n_v, h->st));
     return DDAMG_OK;
   }
@@ -2030,6 +2032,7 @@ void ddamg_default_params(ddamg_params* p) {
   p->hbm_budget = 0;
   p->outer_refine = 1e-5;
   p->half_vectors = 0;
+  p->ortho_fp32 = 0;
 }
 
 const char* ddamg_status_string(ddamg_status s) {

@@ -82,6 +82,8 @@ def _create(lib, **kw):
     (dict(L=(8, 8, 8, 8), sap_block=(2, 2, 2, 2), coarse_restart=65), "coarse_restart"),
     (dict(L=(8, 8, 8, 8), sap_block=(2, 2, 2, 2), precision=7), "precision"),
     (dict(L=(8, 8, 8, 8), sap_block=(2, 2, 2, 2), m0=float("nan")), "finite"),
+    (dict(L=(8, 8, 8, 8), sap_block=(2, 2, 2, 2), precision=0, ortho_fp32=1), "ortho_fp32"),
+    (dict(L=(8, 8, 8, 8), sap_block=(2, 2, 2, 2), precision=1, ortho_fp32=2), "ortho_fp32"),
 ])
 def test_invalid_parameters_rejected_before_device_work(lib, kw, words):
     st, msg = _create(lib, **kw)

@@ -149,12 +149,13 @@ def test_sap_variants_fp32(variant):
 # each vector update i of them; for well-conditioned (Gaussian) vectors the
 # result carries a few FP32 roundings, 1e-5 with room to spare
 @pytest.mark.parametrize("cfg", [SMALL, MID])
-@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-5)])
-def test_orthonormalise(cfg, prec, tol):
-    """FP64 handles orthonormalise in FP64, FP32 handles in FP32; both give
-    the oracle's vectors within their precision."""
+@pytest.mark.parametrize("prec,ortho32,tol", [(0, 0, 1e-13), (1, 0, 1e-13), (1, 1, 1e-5)])
+def test_orthonormalise(cfg, prec, ortho32, tol):
+    """FP64 orthonormalisation (the default, whatever the inner precision)
+    and the FP32 one of ortho_fp32 give the oracle's vectors within their
+    precision."""
     L, b, eps, m0, csw, n_v, seed = cfg
-    s = make(cfg, prec)
+    s = make(cfg, prec, ortho_fp32=ortho32)
     lam = syn.gaussian_spinors(n_v, L, 44)
     s.set_test_vectors(lam)
     s.orthonormalize()
