@@ -48,8 +48,10 @@ struct Config {
   size_t field_reals = 0;        // reals of one spinor field
   ddamg_handle h = nullptr;      // resident handle, nullptr when released
   size_t bytes = 0;              // device bytes last measured (0: never set up)
+  size_t reserved = 0;           // bytes counted for a setup or batch allocation in progress
   uint64_t last_use = 0;
   bool busy = false;             // a worker is serving it
+  bool waiting = false;          // its worker waits for device memory
   cudaStream_t st = nullptr;     // its stream (created with its handle)
 };
 
@@ -102,12 +104,20 @@ void note_error(ddamg_server* s, ddamg_handle h, ddamg_status st) {
 
 // Configs are added by callers (under the lock) while the worker uses them:
 // the worker changes a config's handle and byte count, and scans the list,
-// only under the lock; the long calls (setup, solve) run outside it.
+// only under the lock; the long calls (setup, solve) run outside it.  A
+// configuration being set up, or allocating its batch, counts with the bytes
+// reserved for it, so that no other worker admits itself into that memory
+// before the allocations are done and measured.
 size_t resident_bytes(ddamg_server* s) {
   size_t u = 0;
-  for (auto& c : s->cfgs)
-    if (c.h) u += c.bytes;
+  for (auto& c : s->cfgs) u += std::max(c.h ? c.bytes : 0, c.reserved);
   return u;
+}
+
+void unreserve(ddamg_server* s, Config& c) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  c.reserved = 0;
+  s->cv_idle.notify_all();
 }
 
 void release(ddamg_server* s, Config& c) {
@@ -146,7 +156,10 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       used = resident_bytes(s);
-      if (!s->budget || used + need <= s->budget) break;
+      if (!s->budget || used + need <= s->budget) {
+        c.reserved = need;
+        break;
+      }
       bool other_busy = false;
       for (auto& o : s->cfgs) {
         if (o.h && &o != &c && !o.busy && (!lru || o.last_use < lru->last_use)) lru = &o;
@@ -155,15 +168,22 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
       if (!lru && other_busy) {
         // the memory belongs to configurations being served: wait until one
         // of them is idle (and may be released), then look again
+        c.waiting = true;
         s->cv_idle.wait(lk);
+        c.waiting = false;
         continue;
       }
     }
-    if (!lru) break;                 // nothing left to release: try, the handle's budget decides
+    if (!lru) {                      // nothing left to release: try, the handle's budget decides
+      std::lock_guard<std::mutex> lk(s->mu);
+      c.reserved = need;
+      break;
+    }
     release(s, *lru);
   }
   if (s->budget && used >= s->budget) {
     std::lock_guard<std::mutex> lk(s->mu);
+    c.reserved = 0;
     s->last_error = "device memory budget held by configurations being served";
     return DDAMG_ENOMEM;
   }
@@ -175,6 +195,7 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
     } else if (cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       c.st = nullptr;
+      unreserve(s, c);
       return DDAMG_ECUDA;
     }
   }
@@ -186,6 +207,7 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
       s->last_error = ddamg_last_error(h);
     }
     if (h) ddamg_destroy(h);
+    unreserve(s, c);
     return st;
   }
   ddamg_set_graphs(h, 0);          // the workers' threads share the device (no captures)
@@ -196,6 +218,37 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   measure(s, c);
   *setup_run = 1;
   return DDAMG_OK;
+}
+
+// the batch buffers of config c.  Device memory can still run short of the
+// budget's arithmetic (other processes, the allocator's granularity): on
+// DDAMG_ENOMEM idle configurations are released, least recently used first,
+// and while other configurations are being served (and not waiting for
+// memory themselves) the worker waits for one of them to end and tries
+// again; with nothing left to wait for, the error stands.
+ddamg_status begin_batch(ddamg_server* s, Config& c, int S) {
+  for (;;) {
+    const ddamg_status st = ddamg_batch_begin(c.h, S);
+    if (st != DDAMG_ENOMEM) return st;
+    Config* lru = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      bool progress = false;
+      for (auto& o : s->cfgs) {
+        if (&o == &c) continue;
+        if (o.h && !o.busy && (!lru || o.last_use < lru->last_use)) lru = &o;
+        progress |= o.busy && !o.waiting;
+      }
+      if (!lru) {
+        if (!progress) return st;
+        c.waiting = true;
+        s->cv_idle.wait_for(lk, std::chrono::milliseconds(200));
+        c.waiting = false;
+        continue;
+      }
+    }
+    release(s, *lru);
+  }
 }
 
 void finish(ddamg_server* s, Request* r, Clock::time_point t) {
@@ -218,10 +271,11 @@ void serve(ddamg_server* s, int ci) {
   std::vector<Request*> slot_req(S, nullptr);
   std::vector<Request*> active;
   if (st == DDAMG_OK) {
-    st = ddamg_batch_begin(c.h, S);
+    st = begin_batch(s, c, S);
     note_error(s, c.h, st);
     // the footprint that later admissions count includes the batch buffers
     if (st == DDAMG_OK) measure(s, c);
+    unreserve(s, c);
   }
   for (;;) {
     // admission (requests that fit into the free slots)
