@@ -49,6 +49,7 @@ struct Config {
   ddamg_handle h = nullptr;      // resident handle, nullptr when released
   size_t bytes = 0;              // device bytes last measured (0: never set up)
   size_t reserved = 0;           // bytes counted for a setup or batch allocation in progress
+  size_t handle_budget = 0;      // the device-memory budget its handle was created with
   uint64_t last_use = 0;
   bool busy = false;             // a worker is serving it
   bool waiting = false;          // its worker waits for device memory
@@ -61,16 +62,25 @@ struct Config {
 // links and clover terms in both precisions, test vectors (FP64 + FP32),
 // the temporaries of the setup (6 x n_v fields), the coarse operator with its
 // inverses and premultiplied blocks, and the buffers of a full batch.
+// the buffers of a batch of `slots` right-hand sides (FGMRES basis V, the
+// preconditioned directions, six work fields per slot)
+size_t batch_bytes(const ddamg_params& p, int slots) {
+  const size_t V = (size_t)p.L[0] * p.L[1] * p.L[2] * p.L[3];
+  const size_t F = V * 24 * sizeof(double);               // one FP64 spinor field
+  const size_t m = (size_t)p.outer_restart;
+  return (size_t)slots * (m + 1 + m / 2 + 6) * F;
+}
+
 size_t estimate_bytes(const ddamg_params& p, int max_batch) {
   const size_t V = (size_t)p.L[0] * p.L[1] * p.L[2] * p.L[3];
   const size_t F = V * 24 * sizeof(double);               // one FP64 spinor field
-  const size_t n = (size_t)p.n_v, m = (size_t)p.outer_restart;
+  const size_t n = (size_t)p.n_v;
   const size_t nb = V / ((size_t)p.sap_block[0] * p.sap_block[1] * p.sap_block[2] * p.sap_block[3]);
   size_t b = V * (4 * 12 + 2 * 72) * 12;                  // links + A, A^-1 in FP64 and FP32
   b += n * F * 3 / 2;                                     // test vectors
   b += 6 * n * F;                                         // temporaries
   b += nb * (9 + 1 + 4) * (2 * n) * (2 * n) * 16;         // D_c, A^-1, A^-1 D_c (FP64 bound)
-  b += (size_t)max_batch * (m + 1 + m / 2 + 6) * F;       // batched FGMRES
+  b += batch_bytes(p, max_batch);                         // batched FGMRES
   return b + ((size_t)16 << 20);
 }
 
@@ -163,7 +173,7 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
       bool other_busy = false;
       for (auto& o : s->cfgs) {
         if (o.h && &o != &c && !o.busy && (!lru || o.last_use < lru->last_use)) lru = &o;
-        other_busy |= o.h && &o != &c && o.busy;
+        other_busy |= (o.h || o.reserved) && &o != &c && o.busy;    // served, or being set up
       }
       if (!lru && other_busy) {
         // the memory belongs to configurations being served: wait until one
@@ -189,6 +199,7 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
   }
   ddamg_params p = c.p;
   p.hbm_budget = s->budget ? s->budget - used : 0;
+  c.handle_budget = p.hbm_budget;
   if (!c.st) {
     if (s->st) {
       c.st = s->st;
@@ -225,11 +236,20 @@ ddamg_status ensure_resident(ddamg_server* s, int ci, int* setup_run) {
 // DDAMG_ENOMEM idle configurations are released, least recently used first,
 // and while other configurations are being served (and not waiting for
 // memory themselves) the worker waits for one of them to end and tries
-// again; with nothing left to wait for, the error stands.
+// again; with nothing left to wait for, or when the handle's own budget is
+// what the batch exceeds, the error stands (the caller then sets the
+// configuration up again).
 ddamg_status begin_batch(ddamg_server* s, Config& c, int S) {
   for (;;) {
     const ddamg_status st = ddamg_batch_begin(c.h, S);
     if (st != DDAMG_ENOMEM) return st;
+    {
+      // the handle's own budget is the limit: waiting for memory cannot help
+      ddamg_stats hs{};
+      if (c.handle_budget && ddamg_get_stats(c.h, &hs) == DDAMG_OK &&
+          hs.device_bytes + batch_bytes(c.p, S) > c.handle_budget)
+        return st;
+    }
     Config* lru = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -272,7 +292,21 @@ void serve(ddamg_server* s, int ci) {
   std::vector<Request*> active;
   if (st == DDAMG_OK) {
     st = begin_batch(s, c, S);
-    note_error(s, c.h, st);
+    if (st == DDAMG_ENOMEM) {
+      // the handle's own budget (what the server's budget left at its setup)
+      // is too small for the batch: set the configuration up once more,
+      // admitted with its full estimate, under what the budget leaves now
+      note_error(s, c.h, st);
+      release(s, c);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        c.bytes = 0;
+        c.reserved = 0;
+      }
+      st = ensure_resident(s, ci, &setup_run);
+      if (st == DDAMG_OK) st = begin_batch(s, c, S);
+    }
+    if (c.h) note_error(s, c.h, st);     // (a failed setup kept its own message)
     // the footprint that later admissions count includes the batch buffers
     if (st == DDAMG_OK) measure(s, c);
     unreserve(s, c);
