@@ -821,10 +821,13 @@ def stencils(P, torch, stream, pk, pk_kind):
         st = h.stats()
         h.enable_kernel_timing(False)
         us = 1e3 * st["coarse_apply_ms"] / st["coarse_apply_launches"]
-        byts = nx * (9 * n2 * n2 + 2 * n2) * 8
+        # compulsory bytes: the self and the four forward blocks (the backward
+        # blocks follow from them by G5-hermiticity) and the vectors in and out
+        byts = nx * (5 * n2 * n2 + 2 * n2) * 8
         gbs = byts / (us * 1e-6) / 1e9
         out["coarse_f32"] = {"us": round(us, 2), "bytes_per_launch": byts, "GB/s": round(gbs, 1),
-                             "frac": round(gbs / pk["hbm_gbs"], 4), "n_v": s["n_v"]}
+                             "frac": round(gbs / pk["hbm_gbs"], 4), "n_v": s["n_v"],
+                             "bytes": "self + 4 forward 2n x 2n blocks per coarse site, x and y"}
         # restriction (Eq. 3) and prolongation (Eq. 4), one right-hand side:
         # per fine site the n_v test vectors (12 complex each) and one spinor
         xf = torch.from_numpy(_tiled(syn.gaussian_spinors(1, s["tile"], s["seed"] + 3)[0], s["tile"], L)).cuda()

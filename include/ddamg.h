@@ -363,7 +363,10 @@ DDAMG_API ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coa
  * Schwarz sweep with the block's links and clover blocks staged in shared
  * memory (0) or read from global memory (1) ("SAP fp32"); the half-storage
  * Schwarz sweep with the staged block operators widened to FP32 in shared
- * memory (0) or kept in the half type (1) ("SAP bf16", "SAP fp16"). */
+ * memory (0) or kept in the half type (1) ("SAP bf16", "SAP fp16"); the
+ * coarse stencil of an assembled D_c (ddamg_apply_coarse) from all nine
+ * blocks (0) or from the self and forward blocks, the backward ones by
+ * G5-hermiticity (1) ("coarse stencil"). */
 typedef struct {
   char kernel[32];
   char problem[96];
@@ -374,7 +377,7 @@ typedef struct {
 DDAMG_API int ddamg_tuning_count(void);
 DDAMG_API ddamg_status ddamg_get_tuning(int i, ddamg_tuning *out);
 /* Use `variant` of the named kernel ("D fp32", "D bf16", "D fp16", "coarse
- * product", "SAP fp32", "SAP bf16", "SAP fp16") for every
+ * product", "SAP fp32", "SAP bf16", "SAP fp16", "coarse stencil") for every
  * problem instead of the measured choice (variant < 0: measure again);
  * process-wide, for reproducible runs and for checking each variant. */
 DDAMG_API ddamg_status ddamg_pin_variant(const char *kernel, int variant);

@@ -92,6 +92,7 @@ struct ddamg_ctx {
   bool have_vectors = false;
   bool lam64_gone = false;       // FP64 test vectors released by ddamg_trim (lam32 holds them)
   bool have_coarse = false;
+  bool dc_g5 = false;             // D_c assembled from D (G5-hermitian block by block), not given
   void* Dc = nullptr;
   void* Ainv = nullptr;
   void* AD = nullptr;             // A_oo^-1 D_c hop blocks of the odd coarse sites
@@ -1017,6 +1018,7 @@ ddamg_status build_coarse_op(ddamg_ctx* h) {
     return fail(h, DDAMG_ENUMERIC, "a coarse self block is singular");
   }
   h->have_coarse = true;
+  h->dc_g5 = true;
   return DDAMG_OK;
 }
 
@@ -2529,6 +2531,7 @@ ddamg_status ddamg_set_coarse_op(ddamg_handle h, const double* dc, int on_device
     return fail(h, DDAMG_ENUMERIC, "a coarse self block is singular");
   }
   h->have_coarse = true;
+  h->dc_g5 = false;                  // a given stencil need not be G5-hermitian
   return DDAMG_OK;
 }
 
@@ -2634,8 +2637,20 @@ ddamg_status ddamg_apply_coarse(ddamg_handle h, int prec, int nrhs, const double
     TRY(need_tmp(h, nrhs, 6));
     size_t nc = (size_t)nrhs * h->g.nb * h->n2;
     TRY(coarse_in<R>(h, in, on_device, nc, (R*)h->tmp[0]));
+    // an assembled D_c: all nine blocks (0) or the self and forward blocks
+    // with the backward ones from G5-hermiticity (1), measured
+    int v = 0;
+    if (h->dc_g5) {
+      char key[64];
+      snprintf(key, sizeof key, "coarse %d sites n_v %d %s nrhs %d", h->g.nb, h->p.n_v,
+               sizeof(R) == 4 ? "fp32" : "fp64", nrhs);
+      TRY(tuned(h, "coarse stencil", key, 2, [&](int var) {
+        return coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st,
+                               var == 1);
+      }, &v));
+    }
     CK(timed(h, 3, [&] {
-      return coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st);
+      return coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, (R*)h->tmp[0], (R*)h->tmp[1], nrhs, h->st, v == 1);
     }));
     return coarse_out<R>(h, (R*)h->tmp[1], nc, out, on_device);
   });

@@ -244,10 +244,12 @@ cudaError_t coarse_import(const double* src, int n, size_t nblocks, R* Dc, cudaS
 // nblocks column-major blocks -> row-major complex doubles (host layout)
 template <class R>
 cudaError_t coarse_export(const R* Dc, int n, size_t nblocks, double* out, cudaStream_t st);
-// y = D_c x (all sites)
+// y = D_c x (all sites); g5: from the self and forward blocks only, the
+// backward blocks taken as G5 (forward block of the neighbour)^H G5 (valid
+// for a D_c assembled from a gamma5-hermitian D)
 template <class R>
 cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs,
-                         cudaStream_t st);
+                         cudaStream_t st, bool g5 = false);
 // coarse host layout <-> device coarse layout (same order, conversion only)
 template <class R>
 cudaError_t coarse_from_f64(const double* src, R* dst, size_t ncomplex, cudaStream_t st);

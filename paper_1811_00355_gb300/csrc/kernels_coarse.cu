@@ -11,6 +11,8 @@
 // sites [X Vb, (X+1) Vb).
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "half.cuh"
 #include "kernels.h"
@@ -619,6 +621,92 @@ __global__ void k_coarse_apply(Geom g, const cpx<R>* __restrict__ Dc, int n2, in
   if constexpr (RPU == 2) out[1] = a1;
 }
 
+// The same stencil from five of the nine blocks.  D is gamma5-hermitian term
+// by term (the backward hop x+mu -> x is gamma5 T^H gamma5 of the forward hop
+// T: x -> x+mu), and P keeps chirality, so every backward block of D_c is
+// the conjugate of its neighbour's forward block:
+//   D_c(X, d = 2 + 2 mu) = G5 D_c(X - mu, d = 1 + 2 mu)^H G5,
+// G5 = diag(1_n, -1_n) on a coarse site.  A team reads the self block and the
+// four forward blocks of its site as above, and for the backward terms the
+// neighbour's forward block M: (G5 M^H G5 v)[r] = g_r sum_c conj(M(c, r)) g_c
+// v[c], where M(c, r), column r of the column-major M, is contiguous, so a
+// thread streams the columns of its own rows.  The signs g_c ride on the
+// staged neighbour vectors, g_r on the backward sum.  Valid for a D_c that
+// was assembled from a gamma5-hermitian D (not for an arbitrary stencil).
+template <class R>
+__global__ void k_coarse_apply_g5(Geom g, const cpx<R>* __restrict__ Dc, int n2, int S,
+                                  const cpx<R>* __restrict__ x, cpx<R>* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char csh[];
+  using T = typename U16<R>::T;
+  constexpr int RPU = 16 / (2 * sizeof(R));      // rows per 16-byte load
+  const int NP = n2 / RPU, n = n2 / 2;
+  const int NC = 9 * n2;
+  const int team = threadIdx.x / NP, j = threadIdx.x - team * NP;
+  const int X = blockIdx.x * S + team;
+  const bool live = team < S && X < g.nb;
+  cpx<R>* sv = reinterpret_cast<cpx<R>*>(csh) + team * (NC + 1);
+  const size_t roff = (size_t)blockIdx.y * g.nb * n2;
+  if (live) {
+    const cpx<R>* xr = x + roff;
+    for (int idx = j; idx < NC; idx += NP) {
+      const int d = idx / n2, c = idx - d * n2;
+      const cpx<R> v = xr[(size_t)g.cnbr[d * g.nb + X] * n2 + c];
+      sv[idx] = (d >= 2 && (d & 1) == 0 && c >= n) ? mk(-v.re, -v.im) : v;
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  // self and forward blocks (d = 0, 1, 3, 5, 7) of the site
+  cpx<R> a[RPU];
+#pragma unroll
+  for (int q = 0; q < RPU; ++q) a[q] = mk(R(0), R(0));
+  const T* site = reinterpret_cast<const T*>(Dc + (size_t)X * NC * n2) + j;
+  for (int t = 0; t < 5; ++t) {
+    const int d = t == 0 ? 0 : 2 * t - 1;
+    const T* col = site + (size_t)d * n2 * NP;
+    const cpx<R>* vs = sv + d * n2;
+#pragma unroll 8
+    for (int c = 0; c < n2; ++c) {
+      const T m = __ldg(col + (size_t)c * NP);
+      const cpx<R> vc = vs[c];
+      if constexpr (RPU == 2) {
+        fma(a[0], mk((R)m.x, (R)m.y), vc);
+        fma(a[1], mk((R)m.z, (R)m.w), vc);
+      } else {
+        fma(a[0], mk((R)m.x, (R)m.y), vc);
+      }
+    }
+  }
+  // backward blocks from the neighbours' forward blocks
+  cpx<R> b[RPU];
+#pragma unroll
+  for (int q = 0; q < RPU; ++q) b[q] = mk(R(0), R(0));
+  for (int mu = 0; mu < 4; ++mu) {
+    const int Y = g.cnbr[(2 + 2 * mu) * g.nb + X];
+    const cpx<R>* M = Dc + ((size_t)Y * 9 + 1 + 2 * mu) * n2 * n2;
+    const cpx<R>* vs = sv + (2 + 2 * mu) * n2;
+#pragma unroll
+    for (int q = 0; q < RPU; ++q) {
+      const T* colr = reinterpret_cast<const T*>(M + (size_t)(RPU * j + q) * n2);
+      cpx<R> s = mk(R(0), R(0));
+#pragma unroll 4
+      for (int u = 0; u < NP; ++u) {
+        const T m = __ldg(colr + u);
+        if constexpr (RPU == 2) {
+          fma(s, mk((R)m.x, (R)-m.y), vs[2 * u]);
+          fma(s, mk((R)m.z, (R)-m.w), vs[2 * u + 1]);
+        } else {
+          fma(s, mk((R)m.x, (R)-m.y), vs[u]);
+        }
+      }
+      b[q] = b[q] + s;
+    }
+  }
+  cpx<R>* out = y + roff + (size_t)X * n2 + RPU * j;
+#pragma unroll
+  for (int q = 0; q < RPU; ++q) out[q] = (RPU * j + q < n) ? a[q] + b[q] : a[q] - b[q];
+}
+
 // C = A B for one odd site X and direction d (column-major 2n x 2n blocks)
 template <class R>
 __global__ void k_premultiply_odd(Geom g, const cpx<R>* __restrict__ Dc, const cpx<R>* __restrict__ Ainv, int n2,
@@ -804,7 +892,8 @@ cudaError_t premultiply_odd(const Geom& g, const R* Dc, const R* Ainv, int n, R*
 }
 
 template <class R>
-cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs, cudaStream_t st) {
+cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, int nrhs, cudaStream_t st,
+                         bool g5) {
   const int n2 = 2 * n;
   const int NP = n2 / (16 / (2 * (int)sizeof(R)));
   // sites per CTA: the fewest that fill whole warps, at most 1024 threads
@@ -812,12 +901,27 @@ cudaError_t coarse_apply(const Geom& g, const R* Dc, int n, const R* x, R* y, in
   while (S > 1 && (S / 2) * NP % 32 == 0) S /= 2;
   while (S > 1 && S * NP > 1024) S /= 2;
   const size_t smem = (size_t)S * (9 * n2 + 1) * sizeof(cpx<R>);
+  const void* fn = g5 ? (const void*)k_coarse_apply_g5<R> : (const void*)k_coarse_apply<R>;
   if (smem > 48 * 1024) {
-    cudaError_t e = raise_smem_limit((const void*)k_coarse_apply<R>, smem);
+    cudaError_t e = raise_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
   }
-  k_coarse_apply<R><<<dim3((g.nb + S - 1) / S, nrhs), S * NP, smem, st>>>(
-      g, reinterpret_cast<const cpx<R>*>(Dc), n2, S, reinterpret_cast<const cpx<R>*>(x), reinterpret_cast<cpx<R>*>(y));
+  if (g5) {
+    // the backward terms read each thread's own columns: keep half of the
+    // unified L1 / shared memory as L1 so that their lines stay resident
+    // (a hint; measured 293 us against 311 with the default split)
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(k_coarse_apply_g5<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+      cudaGetLastError();
+    });
+  }
+  const dim3 grid((g.nb + S - 1) / S, nrhs);
+  const auto* Dcc = reinterpret_cast<const cpx<R>*>(Dc);
+  const auto* xc = reinterpret_cast<const cpx<R>*>(x);
+  auto* yc = reinterpret_cast<cpx<R>*>(y);
+  if (g5) k_coarse_apply_g5<R><<<grid, S * NP, smem, st>>>(g, Dcc, n2, S, xc, yc);
+  else k_coarse_apply<R><<<grid, S * NP, smem, st>>>(g, Dcc, n2, S, xc, yc);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -868,7 +972,7 @@ template cudaError_t coarse_export<double>(const double*, int, size_t, double*, 
                                           cudaStream_t);                                                \
   template cudaError_t invert_self_blocks<R>(const Geom&, const R*, int, R*, int*, cudaStream_t);       \
   template cudaError_t premultiply_odd<R>(const Geom&, const R*, const R*, int, R*, cudaStream_t);      \
-  template cudaError_t coarse_apply<R>(const Geom&, const R*, int, const R*, R*, int, cudaStream_t);    \
+  template cudaError_t coarse_apply<R>(const Geom&, const R*, int, const R*, R*, int, cudaStream_t, bool); \
   template cudaError_t coarse_from_f64<R>(const double*, R*, size_t, cudaStream_t);                     \
   template cudaError_t coarse_to_f64<R>(const R*, double*, size_t, cudaStream_t);                       \
 

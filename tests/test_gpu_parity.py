@@ -253,13 +253,48 @@ def test_coarse_operator(coarse_pair, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_coarse_stencil(coarse_pair, prec):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_coarse_stencil(coarse_pair, prec, variant):
+    """All nine blocks (0), or the self and forward blocks with the backward
+    ones from G5-hermiticity (1), on an assembled D_c whose coarse extents
+    include 2 (x + mu = x - mu)."""
+    P = _P()
     handles, lam, agg, cop = coarse_pair
     rng = np.random.default_rng(48)
     x = rng.standard_normal((2, agg.NX, 2 * lam.shape[0])) + 1j * rng.standard_normal((2, agg.NX, 2 * lam.shape[0]))
-    got = handles[prec].apply_coarse(x, prec)
+    P.pin_variant("coarse stencil", variant)
+    try:
+        got = handles[prec].apply_coarse(x, prec)
+    finally:
+        P.pin_variant("coarse stencil", -1)
     ref = cop.apply(t(x)).numpy()
     assert_close(got, ref, (TOL64 if prec == 0 else TOL32), etol=ETOL_STENCIL[prec])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coarse_stencil_given_operator_uses_all_blocks(prec):
+    """A stencil given through ddamg_set_coarse_op (here a random one, not
+    G5-hermitian) is applied with all nine blocks even where the G5 variant
+    is pinned."""
+    P = _P()
+    L, b, eps, m0, csw, n_v, seed = MID
+    s = make(MID, prec)
+    try:
+        n2 = 2 * n_v
+        Dc = syn.coarse_stencil(s.NX, n2, 9, 1.0, 0.21)
+        s.set_coarse_op(Dc)
+        geom = Aggregation(oracle_op(L, eps, seed, m0, csw).geom, b).coarse
+        cop = CoarseOperator(torch.from_numpy(Dc), geom)
+        rng = np.random.default_rng(52)
+        x = rng.standard_normal((1, s.NX, n2)) + 1j * rng.standard_normal((1, s.NX, n2))
+        P.pin_variant("coarse stencil", 1)
+        try:
+            got = s.apply_coarse(x, prec)
+        finally:
+            P.pin_variant("coarse stencil", -1)
+        assert_close(got, cop.apply(t(x)).numpy(), (TOL64 if prec == 0 else TOL32), etol=ETOL_STENCIL[prec])
+    finally:
+        s.close()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
