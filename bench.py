@@ -351,6 +351,13 @@ def run_ours(args):
         torch.cuda.empty_cache()
         large = large_batched()
 
+    three = None
+    if rank == 0 and world == 1 and not args.no_three_level:
+        solver.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        three = three_level()
+
     huge = None
     if rank == 0 and world == 1 and not args.no_huge:
         solver.close()                 # (idempotent) the child needs nearly all of the device memory
@@ -385,6 +392,7 @@ def run_ours(args):
             "stencils": sten,
             "batched_32x32x32x64": large,
             "light_mass_48x48x48x96": huge,
+            "three_level_32x32x32x64": three,
             "autotune": P.tuning(),
         }
         print(json.dumps(line))
@@ -663,6 +671,90 @@ def large_batched_child():
     out["oracle_check_s"] = round(time.perf_counter() - t_or, 1)
     # the line's headline for this workload: the BF16-storage batch
     out["value"] = out.get("bf16", out.get("f32", {})).get("value")
+    print(json.dumps(out))
+
+
+# three levels on the 32^3 x 64 lattice: level-2 blocks (= aggregates) of
+# 2^4 coarse sites (a 4^3 x 8 coarsest lattice), 16 level-2 test vectors
+THREE = dict(block2=(2, 2, 2, 2), n_v2=16, setup_iters2=2, sources=2)
+
+
+def three_level():
+    """The two- and three-level comparison on 32^3 x 64 in a child process;
+    returns its JSON object, or {"error": ...}."""
+    import subprocess
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--three-level-only"], cwd=ROOT,
+                           capture_output=True, text=True, timeout=1200)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"error": "exit %d: %s" % (r.returncode, (r.stderr or r.stdout)[-400:])}
+        return json.loads(lines[-1])
+    except Exception as e:                      # noqa: BLE001 - reported in the JSON line
+        return {"error": repr(e)[:400]}
+
+
+def three_level_child():
+    """32^3 x 64 (the batched workload's lattice and mass), FP32 inner
+    precision: after the two-level setup, the first point sources solved
+    one at a time with two levels, then with three after the level-2 setup.
+    Reports per level count the outer iterations, the coarse-solve
+    iterations per preconditioner call (the even-odd GMRES on D_c for two
+    levels, the FGMRES on D_c preconditioned by M2 for three), the time per
+    solve (CUDA events) and the level-2 setup time.  One JSON object."""
+    import torch
+    import paper_1811_00355_gb300 as P
+    import synthetic as syn
+    s, th = LARGE, THREE
+    if not torch.cuda.is_available():
+        raise SystemExit("no CUDA device")
+    U = syn.gauge_field_sliced(s["L"], s["eps"], s["seed"], workers=min(16, os.cpu_count() or 1))
+    torch.cuda.set_device(0)
+    P.load()
+    stream = torch.cuda.current_stream()
+    U_dev = torch.from_numpy(U).cuda()
+    b_dev = torch.from_numpy(syn.point_sources(s["L"])[:th["sources"]]).cuda()
+    params = P.default_params(L=s["L"], sap_block=s["block"], n_v=s["n_v"], m0=s["m0"], csw=s["csw"],
+                              outer_restart=s["outer_restart"], precision=P.FP32)
+    h = P.DDAMG(params, U_dev, stream=stream.cuda_stream)
+    out = {"lattice": "32x32x32x64", "m0": s["m0"], "csw": s["csw"], "n_v": s["n_v"],
+           "level2": {"block": list(th["block2"]), "n_v": th["n_v2"], "setup_iters": th["setup_iters2"]},
+           "rhs": "point sources %s, one at a time, to %g" % (list(range(th["sources"])), s["tol"]),
+           "timing": "CUDA events per solve"}
+    try:
+        h.run_setup()
+        for levels in (2, 3):
+            rec = {}
+            if levels == 3:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h.level2_init(P.level2_default_params(block=th["block2"], n_v=th["n_v2"],
+                                                      setup_iters=th["setup_iters2"]))
+                h.level2_setup()
+                torch.cuda.synchronize()
+                rec["level2_setup_s"] = round(time.perf_counter() - t0, 3)
+                h.set_levels(3)
+            times, infos = [], []
+            for k in range(th["sources"]):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x, info = h.solve(b_dev[k:k + 1], s["tol"])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                infos.append(info[0])
+            rec.update({"solve_s": [round(v, 3) for v in times],
+                        "outer_iters": [i["outer_iters"] for i in infos],
+                        "precond_calls": [i["precond_calls"] for i in infos],
+                        "coarse_iters_per_call": [round(i["coarse_iters"] / max(1, i["precond_calls"]), 1)
+                                                  for i in infos],
+                        "true_residual": [i["true_residual"] for i in infos],
+                        "all_converged": all(i["converged"] and i["true_residual"] <= s["tol"] for i in infos)})
+            out["levels_%d" % levels] = rec
+    finally:
+        h.close()
     print(json.dumps(out))
 
 
@@ -1063,6 +1155,8 @@ def main():
     ap.add_argument("--large-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-huge", action="store_true", help="skip the 48^3 x 96 light-mass workload")
     ap.add_argument("--huge-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-three-level", action="store_true", help="skip the two/three-level comparison")
+    ap.add_argument("--three-level-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--large-precisions", default=None,
                     help="comma list of f32,bf16,fp16 for the 32^3 x 64 workload (default all three)")
     ap.add_argument("--large-passes", type=int, default=None, help="passes of the 32^3 x 64 workload (default 2)")
@@ -1092,6 +1186,9 @@ def main():
         return
     if args.huge_only:
         huge_batched_child()
+        return
+    if args.three_level_only:
+        three_level_child()
         return
     if args.coarse_only:
         import torch

@@ -534,6 +534,68 @@ DDAMG_API const char *ddamg_server_last_error(ddamg_server_handle s);
 /* Finish the queued requests, stop the worker, release everything. */
 DDAMG_API void ddamg_server_destroy(ddamg_server_handle s);
 
+/* ---- third level ------------------------------------------------------------
+ * Paper Sec. 1 counts the recursion of the coarse-grid solve among the merits
+ * of the method; Sec. 2 fixes two levels.  These calls build a third level:
+ * the construction of Sec. 2 (Eq. 1-5) applied once more to D_c.  Level 2 is
+ * the coarse lattice of the handle's aggregates with D_c as its 9-point
+ * operator (2 n_v components per coarse site, coarse chirality G5 =
+ * diag(1_n, -1_n)); its Schwarz blocks equal its aggregates, blocks of
+ * coarse sites.  With three levels the coarse solve inside M (Eq. 5) is
+ * flexible GMRES on D_c, right-preconditioned by M2 (Eq. 5 on level 2, with
+ * the even-odd GMRES of the coarse solver on D_cc = P2^H D_c P2), stopped at
+ * the handle's coarse_tol.  Arithmetic in the handle's inner precision
+ * (FP32 for BF16/FP16), the level-2 test vectors kept and orthonormalised in
+ * FP64.  Coarse fields are host arrays of complex doubles [nrhs][NX][2 n_v]
+ * (NX = number of aggregates), level-2 test vectors [n_v2][NX][2 n_v],
+ * D_cc [NX2][9][2 n_v2][2 n_v2] row-major (NX2 = number of level-2 blocks).
+ * CUDA graphs are not used while three levels are on (the coarse FGMRES
+ * reads its coefficients on the host). */
+typedef struct {
+  int block[4];          /* level-2 blocks (= aggregates) in coarse sites: each
+                            even, dividing the coarse extents, with an even
+                            number of blocks per direction; block volume x
+                            2 n_v <= 1024                                   */
+  int n_v;               /* level-2 test vectors, 1..32                      */
+  int setup_iters;       /* adaptive setup iterations on D_c                 */
+  int n_sap;             /* level-2 Schwarz cycles per smoother application  */
+  int mr_iters;          /* MR iterations per level-2 block solve            */
+  double coarsest_tol;   /* even-odd GMRES on D_cc: relative residual        */
+  int coarsest_restart;  /* its restart length (<= 64)                       */
+  int coarsest_max_iter; /* its iteration cap                                */
+  int restart;           /* FGMRES on D_c: restart length (<= 63); its
+                            iteration cap is the handle's coarse_max_iter    */
+  uint64_t seed;         /* initial level-2 vectors when none are given      */
+} ddamg_level2_params;
+DDAMG_API ddamg_status ddamg_level2_default_params(ddamg_level2_params *p);
+/* Lay out level 2 (geometry, buffers) on a handle whose D_c exists; any
+ * earlier level 2 is released and the handle returns to two levels.
+ * DDAMG_EINVAL for a block shape or size the kernels do not take. */
+DDAMG_API ddamg_status ddamg_level2_init(ddamg_handle h, const ddamg_level2_params *p);
+/* The adaptive setup on D_c from the given initial vectors (host,
+ * [n_v2][NX][2 n_v], not orthonormalised) or, for NULL, Gaussian ones from
+ * the seed: smoothed by the level-2 SAP, then setup_iters times
+ * {orthonormalise per (block, coarse chirality); D_cc; lambda2 <- M2
+ * lambda2}, then orthonormalised and D_cc once more. */
+DDAMG_API ddamg_status ddamg_level2_setup(ddamg_handle h, const double *vecs);
+/* Replace the level-2 test vectors (host, as above; orthonormalised here)
+ * and build D_cc / read the current (orthonormal) ones. */
+DDAMG_API ddamg_status ddamg_level2_set_vectors(ddamg_handle h, const double *vecs);
+DDAMG_API ddamg_status ddamg_level2_get_vectors(ddamg_handle h, double *vecs);
+/* D_cc as built (host, [NX2][9][2 n_v2][2 n_v2] row-major). */
+DDAMG_API ddamg_status ddamg_level2_get_op(ddamg_handle h, double *out);
+/* Level-2 Schwarz smoother from a zero start / M2 / the level-1 coarse
+ * solve (FGMRES on D_c with M2, to tol) on nrhs host coarse fields; iters
+ * (nullable, nrhs ints) receives the FGMRES iteration counts. */
+DDAMG_API ddamg_status ddamg_level2_sap(ddamg_handle h, int nrhs, const double *in, double *out);
+DDAMG_API ddamg_status ddamg_level2_apply_M2(ddamg_handle h, int nrhs, const double *in, double *out);
+DDAMG_API ddamg_status ddamg_level2_coarse_solve(ddamg_handle h, int nrhs, const double *in, double *out,
+                                                 double tol, int *iters);
+/* Two levels (2) or three (3; needs ddamg_level2_setup or _set_vectors) for
+ * the solves of the handle.  A new setup, mass or D_c keeps the level-2
+ * test vectors and rebuilds D_cc from them. */
+DDAMG_API ddamg_status ddamg_set_levels(ddamg_handle h, int levels);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,8 +5,8 @@ The solver is the CUDA library ``libddamg.so`` behind the C ABI of
 package loads nothing; :func:`load` (or creating a :class:`DDAMG`) loads the
 library and fails loudly if it has not been built.
 """
-from ._ddamg import (BF16, FP16, FP32, FP64, DDAMG, DDAMGError, Params, RequestInfo, Server, SolveInfo,
-                     Stats, default_params, load, pin_variant, tuning)
+from ._ddamg import (BF16, FP16, FP32, FP64, DDAMG, DDAMGError, Level2Params, Params, RequestInfo, Server,
+                     SolveInfo, Stats, default_params, level2_default_params, load, pin_variant, tuning)
 
-__all__ = ["BF16", "FP16", "FP32", "FP64", "DDAMG", "DDAMGError", "Params", "RequestInfo", "Server", "SolveInfo",
-           "Stats", "default_params", "load", "pin_variant", "tuning"]
+__all__ = ["BF16", "FP16", "FP32", "FP64", "DDAMG", "DDAMGError", "Level2Params", "Params", "RequestInfo", "Server",
+           "SolveInfo", "Stats", "default_params", "level2_default_params", "load", "pin_variant", "tuning"]

@@ -44,6 +44,14 @@ class Params(C.Structure):
     ]
 
 
+class Level2Params(C.Structure):
+    _fields_ = [
+        ("block", C.c_int * 4), ("n_v", C.c_int), ("setup_iters", C.c_int), ("n_sap", C.c_int),
+        ("mr_iters", C.c_int), ("coarsest_tol", C.c_double), ("coarsest_restart", C.c_int),
+        ("coarsest_max_iter", C.c_int), ("restart", C.c_int), ("seed", C.c_uint64),
+    ]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [
         ("outer_iters", C.c_int), ("restarts", C.c_int), ("coarse_iters", C.c_int),
@@ -160,6 +168,16 @@ SIGNATURES = {
     "ddamg_server_device_bytes": (_I, [_H, C.POINTER(C.c_size_t)]),
     "ddamg_server_last_error": (C.c_char_p, [_H]),
     "ddamg_server_destroy": (None, [_H]),
+    "ddamg_level2_default_params": (_I, [C.POINTER(Level2Params)]),
+    "ddamg_level2_init": (_I, [_H, C.POINTER(Level2Params)]),
+    "ddamg_level2_setup": (_I, [_H, _P]),
+    "ddamg_level2_set_vectors": (_I, [_H, _P]),
+    "ddamg_level2_get_vectors": (_I, [_H, _P]),
+    "ddamg_level2_get_op": (_I, [_H, _P]),
+    "ddamg_level2_sap": (_I, [_H, _I, _P, _P]),
+    "ddamg_level2_apply_M2": (_I, [_H, _I, _P, _P]),
+    "ddamg_level2_coarse_solve": (_I, [_H, _I, _P, _P, _D, _P]),
+    "ddamg_set_levels": (_I, [_H, _I]),
     "ddamg_destroy": (None, [_H]),
 }
 
@@ -197,6 +215,18 @@ def tuning():
 def pin_variant(kernel: str, variant: int) -> None:
     """Fix the variant of a kernel with measured variants (variant < 0: measure)."""
     load().ddamg_pin_variant(kernel.encode(), int(variant))
+
+
+def level2_default_params(**kw) -> Level2Params:
+    """Third-level parameters (ddamg_level2_default_params, then the given fields)."""
+    p = Level2Params()
+    load().ddamg_level2_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "block":
+            p.block[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
 
 
 def default_params(**kw) -> Params:
@@ -505,6 +535,58 @@ class DDAMG:
                                                         C.c_void_p(out.data_ptr()), tol,
                                                         C.c_void_p(its.ctypes.data)))
         return out, its
+
+    # ---- third level (host numpy arrays of complex128) ------------------------
+    def level2_init(self, p2: "Level2Params"):
+        """Lay out level 2 on this handle's D_c (ddamg_level2_init)."""
+        self._check(self.lib.ddamg_level2_init(self.h, C.byref(p2)))
+        self.n_v2 = int(p2.n_v)
+        self.NX2 = self.NX // int(np.prod(list(p2.block)))
+
+    def level2_setup(self, vecs=None):
+        """Adaptive setup on D_c from host vectors [n_v2][NX][2 n_v] (None: seeded)."""
+        if vecs is None:
+            self._check(self.lib.ddamg_level2_setup(self.h, None))
+        else:
+            v = np.ascontiguousarray(vecs, np.complex128)
+            self._check(self.lib.ddamg_level2_setup(self.h, C.c_void_p(v.ctypes.data)))
+
+    def level2_set_vectors(self, vecs):
+        v = np.ascontiguousarray(vecs, np.complex128)
+        self._check(self.lib.ddamg_level2_set_vectors(self.h, C.c_void_p(v.ctypes.data)))
+
+    def level2_get_vectors(self):
+        out = np.empty((self.n_v2, self.NX, 2 * self.n_v), np.complex128)
+        self._check(self.lib.ddamg_level2_get_vectors(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def level2_get_op(self):
+        m2 = 2 * self.n_v2
+        out = np.empty((self.NX2, 9, m2, m2), np.complex128)
+        self._check(self.lib.ddamg_level2_get_op(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def _level2_fields(self, fn, x, *extra):
+        x = np.ascontiguousarray(x, np.complex128)
+        n = x.shape[0] if x.ndim == 3 else 1
+        out = np.empty(x.shape, np.complex128)
+        self._check(fn(self.h, n, C.c_void_p(x.ctypes.data), C.c_void_p(out.ctypes.data), *extra))
+        return out
+
+    def level2_sap(self, x):
+        return self._level2_fields(self.lib.ddamg_level2_sap, x)
+
+    def level2_apply_M2(self, x):
+        return self._level2_fields(self.lib.ddamg_level2_apply_M2, x)
+
+    def level2_coarse_solve(self, b, tol):
+        n = b.shape[0] if b.ndim == 3 else 1
+        its = np.zeros(n, np.int32)
+        out = self._level2_fields(self.lib.ddamg_level2_coarse_solve, b, tol, C.c_void_p(its.ctypes.data))
+        return out, its
+
+    def set_levels(self, levels: int):
+        self._check(self.lib.ddamg_set_levels(self.h, int(levels)))
 
     def apply_M(self, x, precision):
         n = self._nrhs(x)

@@ -17,6 +17,7 @@
 #include <complex>
 #include <chrono>
 #include <mutex>
+#include <random>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -192,6 +193,32 @@ struct ddamg_ctx {
   // the coarse GMRES grid barrier
   long long wait_sap = WAIT_SAP_DEFAULT;
   long long wait_grid = WAIT_GRID_DEFAULT;
+
+  // third level (ddamg_level2_*): the coarse-grid solve of M as FGMRES on
+  // D_c preconditioned by the two-level method built on D_c
+  int levels = 2;
+  struct Level2 {
+    bool ready = false;                 // geometry and buffers exist
+    bool have_ops = false;              // orthonormal test vectors and D_cc
+    ddamg_level2_params p{};
+    int NXp = 0, Vb = 0, n2v = 0;
+    L2Geom d{};
+    Geom g2{};                          // the coarsest lattice as the coarse kernels see it
+    std::vector<std::pair<void*, size_t>> mem;
+    double* lam64 = nullptr;            // [n2v][NX][2n] complex, FP64 master
+    void* lam = nullptr;                // the inner-precision copy (lam64 itself in FP64)
+    void* Dcc = nullptr;                // [NXp][9][2 n2v][2 n2v] column-major blocks
+    void* Ainv2 = nullptr;
+    void* AD2 = nullptr;
+    void* work2 = nullptr;              // coarsest GMRES scratch
+    void* V = nullptr;                  // level-1 FGMRES basis, restart + 1 coarse fields
+    void* Z = nullptr;                  // its preconditioned directions, restart fields
+    void* t[4] = {};                    // coarse temporaries
+    void* c2[2] = {};                   // coarsest fields
+    double* scr = nullptr;              // reduction scratch
+    double* dres = nullptr;             // reduction results
+    int* dit = nullptr;                 // [2] coarsest iterations of a call, and their sum
+  } l2;
 };
 
 namespace {
@@ -868,6 +895,391 @@ ddamg_status op_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double to
   return DDAMG_OK;
 }
 
+ddamg_status check_status(ddamg_ctx* h);
+
+// ---- third level ----------------------------------------------------------------
+// Paper Sec. 1 names the recursion of the coarse-grid solve as a merit of the
+// method; Sec. 2 then fixes two levels.  The third level applies the
+// construction of Sec. 2 (Eq. 1-5) once more, to D_c: a Schwarz smoother on
+// blocks of coarse sites, aggregates of coarse sites with their own test
+// vectors from the same adaptive setup run on D_c, D_cc = P2^H D_c P2, and
+// M2 (Eq. 5 on level 2) with the even-odd GMRES of the coarse solver on D_cc.
+// The level-1 coarse solve inside M becomes FGMRES on D_c right-preconditioned
+// by M2, stopped at the same relative residual.
+
+ddamg_status l2_alloc(ddamg_ctx* h, void** p, size_t bytes) {
+  TRY(dalloc(h, p, bytes));
+  h->l2.mem.emplace_back(*p, bytes);
+  return DDAMG_OK;
+}
+
+void l2_release(ddamg_ctx* h) {
+  for (auto& m : h->l2.mem) dfree(h, m.first, m.second);
+  h->l2 = ddamg_ctx::Level2{};
+  h->levels = 2;
+}
+
+// a coarse field of the inner precision: NX sites of 2n complex numbers
+size_t l2_field_reals(const ddamg_ctx* h) { return (size_t)h->g.nb * h->n2 * 2; }
+
+template <class R>
+ddamg_status l2_init(ddamg_ctx* h, const ddamg_level2_params& p) {
+  const int n1 = h->p.n_v, n2v = p.n_v, m2 = 2 * n2v;
+  int Lc[4], Lcc[4], Vb = 1, NXp = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    Lc[mu] = h->g.grid[mu];
+    if (p.block[mu] < 2 || p.block[mu] % 2 || Lc[mu] % p.block[mu] || (Lc[mu] / p.block[mu]) % 2)
+      return fail(h, DDAMG_EINVAL,
+                  "level-2 block extents must be even, divide the coarse lattice %dx%dx%dx%d and leave an even "
+                  "number of blocks in every direction", Lc[0], Lc[1], Lc[2], Lc[3]);
+    Lcc[mu] = Lc[mu] / p.block[mu];
+    Vb *= p.block[mu];
+    NXp *= Lcc[mu];
+  }
+  if (n2v < 1 || n2v > 32) return fail(h, DDAMG_EINVAL, "level-2 n_v must be in [1, 32]");
+  if (Vb * 2 * n1 > 1024) return fail(h, DDAMG_EINVAL, "a level-2 block holds at most 1024 / (2 n_v) coarse sites");
+  if (p.n_sap < 1 || p.mr_iters < 0 || p.setup_iters < 0)
+    return fail(h, DDAMG_EINVAL, "level-2 n_sap >= 1, mr_iters >= 0, setup_iters >= 0");
+  if (p.restart < 1 || p.restart > 63 || p.coarsest_restart < 1 || p.coarsest_restart > 64)
+    return fail(h, DDAMG_EINVAL, "level-2 restart in [1, 63], coarsest_restart in [1, 64]");
+  if (!(p.coarsest_tol > 0.0) || p.coarsest_max_iter < 1)
+    return fail(h, DDAMG_EINVAL, "level-2 coarsest_tol > 0 and coarsest_max_iter >= 1");
+  if (l2_assemble_smem(n1, n2v, sizeof(R)) > 200 * 1024)
+    return fail(h, DDAMG_EINVAL, "the level-2 assembly needs more shared memory than a CTA has (lower n_v)");
+  l2_release(h);
+  auto& L = h->l2;
+  const int NX = h->g.nb;
+  // level-1 coarse sites in blocks of coarse sites (lexicographic block index,
+  // colour = parity of the block coordinates, sites in increasing index)
+  std::vector<int> blk(NX), loc(NX), sites((size_t)NXp * Vb), cnt(NXp, 0), bcol, bodd;
+  for (int X = 0; X < NX; ++X) {
+    int c[4], r = X;
+    c[0] = r % Lc[0]; r /= Lc[0];
+    c[1] = r % Lc[1]; r /= Lc[1];
+    c[2] = r % Lc[2];
+    c[3] = r / Lc[2];
+    const int Xp = c[0] / p.block[0] + Lcc[0] * (c[1] / p.block[1] + Lcc[1] * (c[2] / p.block[2] + Lcc[2] * (c[3] / p.block[3])));
+    blk[X] = Xp;
+    loc[X] = cnt[Xp];
+    sites[(size_t)Xp * Vb + cnt[Xp]++] = X;
+  }
+  // the coarsest lattice (the coarse kernels' tables, as for level 1)
+  std::vector<int> cnbr((size_t)9 * NXp), cpar(NXp), ceven, codd, cpos(NXp);
+  for (int X = 0; X < NXp; ++X) {
+    int c[4], r = X;
+    c[0] = r % Lcc[0]; r /= Lcc[0];
+    c[1] = r % Lcc[1]; r /= Lcc[1];
+    c[2] = r % Lcc[2];
+    c[3] = r / Lcc[2];
+    cpar[X] = (c[0] + c[1] + c[2] + c[3]) & 1;
+    (cpar[X] ? bodd : bcol).push_back(X);
+    cnbr[X] = X;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int sg = 0; sg < 2; ++sg) {
+        int cc[4] = {c[0], c[1], c[2], c[3]};
+        cc[mu] = (cc[mu] + (sg == 0 ? 1 : -1) + Lcc[mu]) % Lcc[mu];
+        cnbr[(size_t)(1 + 2 * mu + sg) * NXp + X] = cc[0] + Lcc[0] * (cc[1] + Lcc[1] * (cc[2] + Lcc[2] * cc[3]));
+      }
+    if (cpar[X] == 0) { cpos[X] = (int)ceven.size(); ceven.push_back(X); }
+    else { cpos[X] = (int)codd.size(); codd.push_back(X); }
+  }
+  bcol.insert(bcol.end(), bodd.begin(), bodd.end());     // [colour 0 blocks][colour 1 blocks]
+  std::vector<int> tab;
+  auto put = [&](const std::vector<int>& v) { size_t o = tab.size(); tab.insert(tab.end(), v.begin(), v.end()); return o; };
+  const size_t o_blk = put(blk), o_loc = put(loc), o_sites = put(sites), o_bcol = put(bcol), o_cnbr = put(cnbr),
+               o_cpar = put(cpar), o_ceven = put(ceven), o_codd = put(codd), o_cpos = put(cpos);
+  void* dt = nullptr;
+  TRY(l2_alloc(h, &dt, tab.size() * sizeof(int)));
+  CK(cudaMemcpy(dt, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  const int* T = static_cast<const int*>(dt);
+  L.d.NX = NX;
+  L.d.NXp = NXp;
+  L.d.Vb = Vb;
+  L.d.cnbr = h->g.cnbr;
+  L.d.par = h->g.cparity;
+  L.d.blk = T + o_blk;
+  L.d.loc = T + o_loc;
+  L.d.sites = T + o_sites;
+  L.d.bcol = T + o_bcol;
+  L.g2 = h->g;
+  for (int mu = 0; mu < 4; ++mu) L.g2.grid[mu] = Lcc[mu];
+  L.g2.nb = NXp;
+  L.g2.cnbr = T + o_cnbr;
+  L.g2.cparity = T + o_cpar;
+  L.g2.ceven = T + o_ceven;
+  L.g2.codd = T + o_codd;
+  L.g2.cpos = T + o_cpos;
+  if (coarse_gmres_plan<R>(L.g2, n2v, p.coarsest_restart, 1).NR == 0) {
+    l2_release(h);
+    return fail(h, DDAMG_EINVAL, "no launch configuration of the coarsest GMRES for this level-2 lattice");
+  }
+  const size_t rs = sizeof(R), fr = l2_field_reals(h), NN2 = (size_t)m2 * m2;
+  void* q = nullptr;
+  TRY(l2_alloc(h, &q, (size_t)n2v * fr * sizeof(double)));
+  L.lam64 = static_cast<double*>(q);
+  TRY(l2_alloc(h, &L.lam, (size_t)n2v * fr * rs));
+  TRY(l2_alloc(h, &L.t[3], (size_t)n2v * fr * rs));       // n2v fields: the setup's new vectors
+  TRY(l2_alloc(h, &L.Dcc, (size_t)NXp * 9 * NN2 * 2 * rs));
+  TRY(l2_alloc(h, &L.Ainv2, (size_t)NXp * NN2 * 2 * rs));
+  TRY(l2_alloc(h, &L.AD2, (size_t)(NXp / 2) * 8 * NN2 * 2 * rs));
+  TRY(l2_alloc(h, &L.work2, coarse_gmres_work_bytes(L.g2, n2v, p.coarsest_restart, (int)rs)));
+  TRY(l2_alloc(h, &L.V, (size_t)(p.restart + 1) * fr * rs));
+  TRY(l2_alloc(h, &L.Z, (size_t)p.restart * fr * rs));
+  for (int k = 0; k < 3; ++k) TRY(l2_alloc(h, &L.t[k], fr * rs));
+  for (int k = 0; k < 2; ++k) TRY(l2_alloc(h, &L.c2[k], (size_t)NXp * m2 * 2 * rs));
+  TRY(l2_alloc(h, &q, (reduce_scratch_len(p.restart + 1) + 2 * (p.restart + 2)) * sizeof(double)));
+  L.scr = static_cast<double*>(q);
+  L.dres = L.scr + reduce_scratch_len(p.restart + 1);
+  TRY(l2_alloc(h, &q, 2 * sizeof(int)));
+  L.dit = static_cast<int*>(q);
+  CK(cudaMemsetAsync(L.dit, 0, 2 * sizeof(int), h->st));
+  L.p = p;
+  L.NXp = NXp;
+  L.Vb = Vb;
+  L.n2v = n2v;
+  L.ready = true;
+  return DDAMG_OK;
+}
+
+// orthonormalise the FP64 level-2 vectors (if ortho), copy them to the inner
+// precision, assemble D_cc and invert its self blocks
+template <class R>
+ddamg_status l2_build(ddamg_ctx* h, bool ortho) {
+  auto& L = h->l2;
+  const int n1 = h->p.n_v;
+  const size_t fr = l2_field_reals(h);
+  if (ortho) CK(l2_orthonormalise(L.d, L.lam64, n1, L.n2v, h->st));
+  if constexpr (sizeof(R) == 8)
+    CK(cudaMemcpyAsync(L.lam, L.lam64, (size_t)L.n2v * fr * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  else
+    CK(convert_field<float, double>(L.lam64, (float*)L.lam, (size_t)L.n2v * fr, h->st));
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+  CK(l2_assemble<R>(L.d, (const R*)h->Dc, (const R*)L.lam, n1, L.n2v, (R*)L.Dcc, h->st));
+  CK(invert_self_blocks<R>(L.g2, (const R*)L.Dcc, L.n2v, (R*)L.Ainv2, h->d_status, h->st));
+  CK(premultiply_odd<R>(L.g2, (const R*)L.Dcc, (const R*)L.Ainv2, L.n2v, (R*)L.AD2, h->st));
+  int sing = 0;
+  CK(cudaMemcpyAsync(&sing, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (sing) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
+    L.have_ops = false;
+    return fail(h, DDAMG_ENUMERIC, "a self block of D_cc is singular");
+  }
+  L.have_ops = true;
+  return DDAMG_OK;
+}
+
+// x = S2 b: n_sap level-2 Schwarz cycles from x = 0 on nf coarse fields
+// (the first colour-0 sweep writes x on its blocks only: the other sites
+// start from the zeros set here)
+template <class R>
+ddamg_status l2_smooth(ddamg_ctx* h, const R* b, R* x, int nf) {
+  auto& L = h->l2;
+  CK(cudaMemsetAsync(x, 0, (size_t)nf * l2_field_reals(h) * sizeof(R), h->st));
+  for (int cyc = 0; cyc < L.p.n_sap; ++cyc)
+    for (int c = 0; c < 2; ++c)
+      CK(l2_sap_sweep<R>(L.d, (const R*)h->Dc, (const R*)h->Ainv, h->p.n_v, c, L.p.mr_iters, cyc == 0 && c == 0, b, x,
+                         nf, h->st));
+  return DDAMG_OK;
+}
+
+// out = M2 in (Eq. 5 on level 2), one coarse field:
+// x1 = P2 D_cc^-1 R2 in; out = x1 + S2 (in - D_c x1); uses t[0], t[1], c2
+template <class R>
+ddamg_status l2_M2(ddamg_ctx* h, const R* in, R* out) {
+  auto& L = h->l2;
+  const int n1 = h->p.n_v;
+  const size_t fr = l2_field_reals(h);
+  R* t0 = (R*)L.t[0];
+  R* t1 = (R*)L.t[1];
+  CK(l2_restrict<R>(L.d, (const R*)L.lam, n1, L.n2v, in, (R*)L.c2[0], 1, h->st));
+  CoarseSolveArgs a;
+  a.Dc = L.Dcc;
+  a.Ainv = L.Ainv2;
+  a.AinvD = L.AD2;
+  a.n = L.n2v;
+  a.tol = L.p.coarsest_tol;
+  a.restart = L.p.coarsest_restart;
+  a.max_iter = L.p.coarsest_max_iter;
+  a.wait_limit = h->wait_grid;
+  CK(coarse_gmres<R>(L.g2, a, (const R*)L.c2[0], (R*)L.c2[1], 1, L.work2, L.dit, L.dit + 1, h->d_status, h->st));
+  CK(l2_prolong<R>(L.d, (const R*)L.lam, n1, L.n2v, (const R*)L.c2[1], out, 1, false, h->st));
+  CK(coarse_apply<R>(h->g, (const R*)h->Dc, n1, out, t0, 1, h->st));
+  CK(axpby<R>(1.0, in, -1.0, t0, fr, h->st));
+  TRY(l2_smooth<R>(h, t0, t1, 1));
+  CK(axpby<R>(1.0, t1, 1.0, out, fr, h->st));
+  return DDAMG_OK;
+}
+
+// the adaptive setup on D_c (level by level, after level 1's): the initial
+// vectors (in lam64) through S2, then setup_iters times {orthonormalise,
+// D_cc, lambda2 <- M2 lambda2}, then a last orthonormalisation and D_cc
+template <class R>
+ddamg_status l2_setup(ddamg_ctx* h) {
+  auto& L = h->l2;
+  const size_t fr = l2_field_reals(h), all = (size_t)L.n2v * fr;
+  R* lam = (R*)L.lam;
+  R* nw = (R*)L.t[3];
+  auto to_master = [&]() -> cudaError_t {
+    if constexpr (sizeof(R) == 8)
+      return cudaMemcpyAsync(L.lam64, nw, all * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+    else
+      return convert_field<double, float>((const float*)nw, L.lam64, all, h->st);
+  };
+  if constexpr (sizeof(R) == 8)
+    CK(cudaMemcpyAsync(lam, L.lam64, all * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  else
+    CK(convert_field<float, double>(L.lam64, (float*)lam, all, h->st));
+  TRY(l2_smooth<R>(h, lam, nw, L.n2v));
+  CK(to_master());
+  for (int it = 0; it < L.p.setup_iters; ++it) {
+    TRY(l2_build<R>(h, true));
+    for (int k = 0; k < L.n2v; ++k) TRY(l2_M2<R>(h, lam + (size_t)k * fr, nw + (size_t)k * fr));
+    CK(to_master());
+  }
+  TRY(l2_build<R>(h, true));
+  return check_status(h);
+}
+
+// FGMRES on D_c right-preconditioned by M2 (the level-1 coarse solve of the
+// three-level method) for one coarse field, from x = 0, to ||b - D_c x|| <=
+// tol ||b||: classical Gram-Schmidt twice, complex Givens rotations, the
+// recurrence residual tested after every step and the true residual at
+// every restart
+template <class R>
+ddamg_status l2_fgmres(ddamg_ctx* h, const R* b, R* x, double tol, int max_iter, int* iters) {
+  using cd = std::complex<double>;
+  auto& L = h->l2;
+  const int m = L.p.restart;
+  const size_t fr = l2_field_reals(h), nc = fr / 2;
+  R* V = (R*)L.V;
+  R* Z = (R*)L.Z;
+  R* w = (R*)L.t[2];
+  R* r = (R*)L.t[3];      // (the setup's vectors live there only between M2 calls of the setup)
+  double* dres = L.dres;
+  std::vector<double> hh(2 * (m + 2));
+  auto dot_host = [&](int k) -> ddamg_status {           // hh[0 .. 2k) = V_j^H w, j < k
+    std::vector<const R*> vl(k);
+    for (int j = 0; j < k; ++j) vl[j] = V + (size_t)j * fr;
+    CK(multi_dot<R>(vl.data(), k, w, nc, L.scr, dres, h->st));
+    return DDAMG_OK;
+  };
+  auto norm_host = [&](const R* v, double* out) -> ddamg_status {
+    CK(norm2<R>(v, nc, L.scr, dres, h->st));
+    CK(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return DDAMG_OK;
+  };
+  CK(cudaMemsetAsync(x, 0, fr * sizeof(R), h->st));
+  double bn2 = 0.0;
+  TRY(norm_host(b, &bn2));
+  const double bnorm = std::sqrt(bn2);
+  *iters = 0;
+  if (bnorm == 0.0) return DDAMG_OK;
+  CK(cudaMemcpyAsync(r, b, fr * sizeof(R), cudaMemcpyDeviceToDevice, h->st));
+  int total = 0;
+  for (;;) {
+    double beta2 = 0.0;
+    TRY(norm_host(r, &beta2));
+    const double beta = std::sqrt(beta2);
+    if (beta <= tol * bnorm || total >= max_iter) break;
+    CK(scale_by_inv_norm<R>(r, V, dres, fr, h->st));      // dres[0] holds ||r||^2
+    std::vector<std::vector<cd>> H(m + 1, std::vector<cd>(m, cd(0.0)));
+    std::vector<double> cs(m, 0.0);
+    std::vector<cd> sn(m, cd(0.0)), g(m + 1, cd(0.0));
+    g[0] = cd(beta);
+    int kd = 0;
+    for (int k = 0; k < m; ++k) {
+      TRY(l2_M2<R>(h, V + (size_t)k * fr, Z + (size_t)k * fr));
+      CK(coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, Z + (size_t)k * fr, w, 1, h->st));
+      std::vector<const R*> vl(k + 1);
+      for (int j = 0; j <= k; ++j) vl[j] = V + (size_t)j * fr;
+      std::vector<cd> hk(k + 1, cd(0.0));
+      for (int pass = 0; pass < 2; ++pass) {
+        TRY(dot_host(k + 1));
+        CK(multi_axpy<R>(vl.data(), k + 1, dres, -1.0, w, nc, h->st));
+        CK(cudaMemcpyAsync(hh.data(), dres, 2 * (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (int j = 0; j <= k; ++j) hk[j] += cd(hh[2 * j], hh[2 * j + 1]);
+      }
+      double hn2 = 0.0;
+      TRY(norm_host(w, &hn2));
+      const double hn = std::sqrt(hn2);
+      if (hn > 0.0) CK(scale_by_inv_norm<R>(w, V + (size_t)(k + 1) * fr, dres, fr, h->st));
+      for (int j = 0; j <= k; ++j) H[j][k] = hk[j];
+      H[k + 1][k] = cd(hn);
+      for (int j = 0; j < k; ++j) {
+        const cd t = cs[j] * H[j][k] + sn[j] * H[j + 1][k];
+        H[j + 1][k] = -std::conj(sn[j]) * H[j][k] + cs[j] * H[j + 1][k];
+        H[j][k] = t;
+      }
+      {  // rotation with [c, s; -conj(s), c] [h1; h2] = [rho; 0], c real
+        const cd h1 = H[k][k], h2 = H[k + 1][k];
+        const double a1 = std::abs(h1), a2 = std::abs(h2);
+        if (a2 == 0.0) { cs[k] = 1.0; sn[k] = 0.0; }
+        else if (a1 == 0.0) { cs[k] = 0.0; sn[k] = std::conj(h2) / a2; H[k][k] = cd(a2); }
+        else {
+          const double rho = std::hypot(a1, a2);
+          const cd ph = h1 / a1;
+          cs[k] = a1 / rho;
+          sn[k] = ph * std::conj(h2) / rho;
+          H[k][k] = ph * rho;
+        }
+      }
+      H[k + 1][k] = cd(0.0);
+      g[k + 1] = -std::conj(sn[k]) * g[k];
+      g[k] = cs[k] * g[k];
+      ++total;
+      kd = k + 1;
+      if (std::abs(g[k + 1]) <= tol * bnorm || total >= max_iter || hn == 0.0) break;
+    }
+    std::vector<cd> y(kd);
+    for (int i = kd - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int j = i + 1; j < kd; ++j) acc -= H[i][j] * y[j];
+      y[i] = acc / H[i][i];
+    }
+    for (int i = 0; i < kd; ++i) { hh[2 * i] = y[i].real(); hh[2 * i + 1] = y[i].imag(); }
+    CK(cudaMemcpyAsync(dres, hh.data(), 2 * kd * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    std::vector<const R*> zl(kd);
+    for (int i = 0; i < kd; ++i) zl[i] = Z + (size_t)i * fr;
+    CK(multi_axpy<R>(zl.data(), kd, dres, 1.0, x, nc, h->st));
+    CK(coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, x, r, 1, h->st));
+    CK(axpby<R>(1.0, b, -1.0, r, fr, h->st));
+  }
+  *iters = total;
+  return check_status(h);
+}
+
+// the level-1 coarse solve of M with three levels: nf coarse fields one after
+// the other; the total FGMRES iteration count goes to *cit_dev (if given)
+// and joins the coarse-iteration total of the solve (d_iters_acc)
+template <class R>
+ddamg_status l2_coarse_solve(ddamg_ctx* h, const R* bc, R* xc, int nf, double tol, int* cit_dev) {
+  const size_t fr = l2_field_reals(h);
+  int total = 0;
+  for (int k = 0; k < nf; ++k) {
+    int it = 0;
+    TRY(l2_fgmres<R>(h, bc + (size_t)k * fr, xc + (size_t)k * fr, tol, h->p.coarse_max_iter, &it));
+    total += it;
+  }
+  int acc = 0;
+  CK(cudaMemcpyAsync(&acc, h->d_iters_acc, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  acc += total;
+  CK(cudaMemcpyAsync(h->d_iters_acc, &acc, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  if (cit_dev) CK(cudaMemcpyAsync(cit_dev, &total, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+// D_cc again after D_c changed (new setup, new mass, a given D_c)
+ddamg_status l2_refresh(ddamg_ctx* h) {
+  if (!h->l2.have_ops) return DDAMG_OK;
+  if (inner32(h)) return l2_build<float>(h, false);
+  return l2_build<double>(h, false);
+}
+
 // out = M in  (Eq. 5): x1 = P D_c^-1 R in; out = x1 + SAP(in - D x1)
 // uses tmp[0..3]
 template <class R>
@@ -877,10 +1289,10 @@ ddamg_status op_M(ddamg_ctx* h, const R* in, R* out, int nf, int* cit_dev = null
   R* e = (R*)h->tmp[1];
   R* bc = (R*)h->tmp[2];
   R* xc = (R*)h->tmp[3];
-  const int n = h->p.n_v;
   addf(h, 2.0 * nf * flops_rp(h) + nf * 2.0 * h->V24);
   CK(restrict_inner<R>(h, in, bc, nf));
-  TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, cit_dev));
+  if (h->levels == 3) TRY(l2_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, cit_dev));
+  else TRY(op_coarse_solve<R>(h, bc, xc, nf, h->p.coarse_tol, cit_dev));
   CK(prolong_inner<R>(h, xc, out, nf));
   TRY(op_dslash<R>(h, DSLASH_RES, out, in, r1, nf));
   TRY(op_sap<R>(h, r1, e, nf));
@@ -1019,7 +1431,7 @@ ddamg_status build_coarse_op(ddamg_ctx* h) {
   }
   h->have_coarse = true;
   h->dc_g5 = true;
-  return DDAMG_OK;
+  return l2_refresh(h);
 }
 
 // ---- precision changes of spinor fields -----------------------------------------------
@@ -1279,7 +1691,8 @@ constexpr double REORTH_RATIO = 1e-2;
 template <class R>
 ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlist, double* vk, double* zk,
                            double* vk1) {
-  if (!h->graphs_on) return enqueue_iteration<R>(h, k, vlist, vk, zk, vk1);
+  // (three levels: the coarse FGMRES reads its coefficients on the host)
+  if (!h->graphs_on || h->levels == 3) return enqueue_iteration<R>(h, k, vlist, vk, zk, vk1);
   auto& G = h->graphs[k];
   if (!G.exec || G.gen != h->gen || G.timing != h->timing) {
     if (G.exec) {
@@ -1342,7 +1755,7 @@ ddamg_status run_iteration(ddamg_ctx* h, int k, std::vector<const double*>& vlis
 // the batch width changed.  With kernel timing on every run is eager.
 template <class F>
 ddamg_status graph_run(ddamg_ctx* h, ddamg_ctx::IterGraph& G, int nb, F&& enqueue) {
-  if (h->timing || !h->graphs_on) return enqueue();
+  if (h->timing || !h->graphs_on || h->levels == 3) return enqueue();
   if (G.exec && (G.gen != h->gen || G.nb != nb)) {
     cudaGraphExecDestroy(G.exec);
     G.exec = nullptr;
@@ -2008,6 +2421,46 @@ ddamg_status coarse_solve_noalloc_impl(ddamg_ctx* h, int nrhs, const double* in,
 // =====================================================================================
 // C ABI
 // =====================================================================================
+namespace {
+
+// the level-2 calls on host coarse fields (op: 0 smoother, 1 M2, 2 coarse solve)
+template <class R>
+ddamg_status l2_call(ddamg_ctx* h, int op, int nrhs, const double* in, double* out, double tol, int* iters) {
+  auto& L = h->l2;
+  const size_t fr = l2_field_reals(h), nc = (size_t)nrhs * fr / 2;
+  TRY(need_tmp(h, nrhs, 6));
+  R* a = (R*)h->tmp[0];
+  R* b = (R*)h->tmp[1];
+  TRY(coarse_in<R>(h, in, 0, nc, a));
+  if (op == 0) {
+    TRY(l2_smooth<R>(h, a, b, nrhs));
+    TRY(check_status(h));
+  } else {
+    for (int k = 0; k < nrhs; ++k) {
+      if (op == 1) {
+        TRY(l2_M2<R>(h, a + (size_t)k * fr, b + (size_t)k * fr));
+        TRY(check_status(h));
+      } else {
+        int it = 0;
+        TRY(l2_fgmres<R>(h, a + (size_t)k * fr, b + (size_t)k * fr, tol, h->p.coarse_max_iter, &it));
+        if (iters) iters[k] = it;
+      }
+    }
+  }
+  (void)L;
+  return coarse_out<R>(h, b, nc, out, 0);
+}
+
+ddamg_status l2_call_checked(ddamg_ctx* h, int op, int nrhs, const double* in, double* out, double tol, int* iters) {
+  if (!h || nrhs < 1 || nrhs > 4096 || !in || !out) return DDAMG_EINVAL;
+  if (!h->l2.have_ops) return fail(h, DDAMG_ESTATE, "no level 2: ddamg_level2_init, then set or set up its vectors");
+  if (op == 2 && !(tol > 0.0)) return fail(h, DDAMG_EINVAL, "tolerance must be positive");
+  if (inner32(h)) return l2_call<float>(h, op, nrhs, in, out, tol, iters);
+  return l2_call<double>(h, op, nrhs, in, out, tol, iters);
+}
+
+}  // namespace
+
 extern "C" {
 
 void ddamg_default_params(ddamg_params* p) {
@@ -2447,6 +2900,105 @@ ddamg_status ddamg_orthonormalize(ddamg_handle h) {
   return DDAMG_OK;
 }
 
+ddamg_status ddamg_level2_default_params(ddamg_level2_params* p) {
+  if (!p) return DDAMG_EINVAL;
+  *p = ddamg_level2_params{};
+  for (int mu = 0; mu < 4; ++mu) p->block[mu] = 2;
+  p->n_v = 8;
+  p->setup_iters = 2;
+  p->n_sap = 4;
+  p->mr_iters = 4;
+  p->coarsest_tol = 5e-2;
+  p->coarsest_restart = 30;
+  p->coarsest_max_iter = 300;
+  p->restart = 30;
+  p->seed = 4321;
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_level2_init(ddamg_handle h, const ddamg_level2_params* p) {
+  if (!h || !p) return DDAMG_EINVAL;
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "level 2 is built on D_c: run the setup first");
+  CK(cudaStreamSynchronize(h->st));
+  if (inner32(h)) return l2_init<float>(h, *p);
+  return l2_init<double>(h, *p);
+}
+
+ddamg_status ddamg_level2_setup(ddamg_handle h, const double* vecs) {
+  if (!h) return DDAMG_EINVAL;
+  auto& L = h->l2;
+  if (!L.ready) return fail(h, DDAMG_ESTATE, "ddamg_level2_init first");
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no D_c");
+  const size_t nreal = (size_t)L.n2v * l2_field_reals(h);
+  if (vecs) {
+    CK(cudaMemcpyAsync(L.lam64, vecs, nreal * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  } else {
+    std::mt19937_64 gen(L.p.seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<double> v(nreal);
+    for (auto& e : v) e = nd(gen);
+    CK(cudaMemcpyAsync(L.lam64, v.data(), nreal * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  if (inner32(h)) return l2_setup<float>(h);
+  return l2_setup<double>(h);
+}
+
+ddamg_status ddamg_level2_set_vectors(ddamg_handle h, const double* vecs) {
+  if (!h || !vecs) return DDAMG_EINVAL;
+  auto& L = h->l2;
+  if (!L.ready) return fail(h, DDAMG_ESTATE, "ddamg_level2_init first");
+  if (!h->have_coarse) return fail(h, DDAMG_ESTATE, "no D_c");
+  CK(cudaMemcpyAsync(L.lam64, vecs, (size_t)L.n2v * l2_field_reals(h) * sizeof(double), cudaMemcpyHostToDevice,
+                     h->st));
+  if (inner32(h)) return l2_build<float>(h, true);
+  return l2_build<double>(h, true);
+}
+
+ddamg_status ddamg_level2_get_vectors(ddamg_handle h, double* vecs) {
+  if (!h || !vecs) return DDAMG_EINVAL;
+  auto& L = h->l2;
+  if (!L.ready) return fail(h, DDAMG_ESTATE, "ddamg_level2_init first");
+  CK(cudaMemcpyAsync(vecs, L.lam64, (size_t)L.n2v * l2_field_reals(h) * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_level2_get_op(ddamg_handle h, double* out) {
+  if (!h || !out) return DDAMG_EINVAL;
+  auto& L = h->l2;
+  if (!L.have_ops) return fail(h, DDAMG_ESTATE, "no D_cc: set or set up the level-2 test vectors first");
+  const size_t m2 = 2 * (size_t)L.n2v, nd = (size_t)L.NXp * 9 * m2 * m2 * 2;
+  TRY(need_lexbuf(h, (nd + h->V24 - 1) / h->V24 + 1));
+  if (inner32(h)) CK(coarse_export<float>((const float*)L.Dcc, L.n2v, (size_t)L.NXp * 9, h->lexbuf, h->st));
+  else CK(coarse_export<double>((const double*)L.Dcc, L.n2v, (size_t)L.NXp * 9, h->lexbuf, h->st));
+  CK(cudaMemcpyAsync(out, h->lexbuf, nd * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return DDAMG_OK;
+}
+
+ddamg_status ddamg_level2_sap(ddamg_handle h, int nrhs, const double* in, double* out) {
+  return l2_call_checked(h, 0, nrhs, in, out, 0.0, nullptr);
+}
+
+ddamg_status ddamg_level2_apply_M2(ddamg_handle h, int nrhs, const double* in, double* out) {
+  return l2_call_checked(h, 1, nrhs, in, out, 0.0, nullptr);
+}
+
+ddamg_status ddamg_level2_coarse_solve(ddamg_handle h, int nrhs, const double* in, double* out, double tol,
+                                       int* iters) {
+  return l2_call_checked(h, 2, nrhs, in, out, tol, iters);
+}
+
+ddamg_status ddamg_set_levels(ddamg_handle h, int levels) {
+  if (!h) return DDAMG_EINVAL;
+  if (levels != 2 && levels != 3) return fail(h, DDAMG_EINVAL, "levels is 2 or 3");
+  if (levels == 3 && !h->l2.have_ops) return fail(h, DDAMG_ESTATE, "level 2 is not set up");
+  h->levels = levels;
+  return DDAMG_OK;
+}
+
 ddamg_status ddamg_set_graphs(ddamg_handle h, int on) {
   if (!h) return DDAMG_EINVAL;
   h->graphs_on = on != 0;
@@ -2532,7 +3084,7 @@ ddamg_status ddamg_set_coarse_op(ddamg_handle h, const double* dc, int on_device
   }
   h->have_coarse = true;
   h->dc_g5 = false;                  // a given stencil need not be G5-hermitian
-  return DDAMG_OK;
+  return l2_refresh(h);
 }
 
 ddamg_status ddamg_get_coarse_plan(ddamg_handle h, int nrhs, ddamg_coarse_plan* out) {

@@ -193,6 +193,40 @@ cudaError_t sap_sweep_h(const Geom& g, int colour, int mr_iters, bool x_is_zero,
                         int* status, long long wait_limit, cudaStream_t st, bool widen = true);
 bool sap_half_ok(const Geom& g);
 
+// ---- third level (kernels_level2.cu) ----------------------------------------------
+// The coarse lattice of level 1 cut into blocks of coarse sites (the level-2
+// Schwarz blocks and aggregates); device arrays
+struct L2Geom {
+  int NX;              // level-1 coarse sites
+  int NXp;             // level-2 blocks (= aggregates = coarsest sites)
+  int Vb;              // level-1 coarse sites per block
+  const int* cnbr;     // [9][NX] neighbours of the level-1 coarse stencil
+  const int* par;      // [NX] parity of the level-1 coarse sites
+  const int* blk;      // [NX] block of each level-1 coarse site
+  const int* loc;      // [NX] position of the site in its block's list
+  const int* sites;    // [NXp][Vb] sites of each block, in increasing index
+  const int* bcol;     // [2][NXp / 2] blocks of each colour
+};
+// one colour of the level-2 Schwarz sweep (blocks of that colour, nrhs
+// coarse fields [X][2 n1]): x += the even-odd MR block solve of b - D_c x
+// (x overwritten if x_is_zero); needs Vb * 2 n1 <= 1024
+template <class R>
+cudaError_t l2_sap_sweep(const L2Geom& d, const R* Dc, const R* Ainv, int n1, int colour, int mr_iters,
+                         bool x_is_zero, const R* b, R* x, int nrhs, cudaStream_t st);
+// b2 = R2 v ([r][X'][2 n2v]) and x (+)= P2 x2 with test vectors lam2 [n2v][X][2 n1]
+template <class R>
+cudaError_t l2_restrict(const L2Geom& d, const R* lam2, int n1, int n2v, const R* v, R* b2, int nrhs,
+                        cudaStream_t st);
+template <class R>
+cudaError_t l2_prolong(const L2Geom& d, const R* lam2, int n1, int n2v, const R* x2, R* x, int nrhs, bool accumulate,
+                       cudaStream_t st);
+// classical Gram-Schmidt twice per (block, coarse chirality), FP64
+cudaError_t l2_orthonormalise(const L2Geom& d, double* lam2, int n1, int n2v, cudaStream_t st);
+// D_cc = P2^H D_c P2: [X'][9][2 n2v][2 n2v], column-major blocks
+template <class R>
+cudaError_t l2_assemble(const L2Geom& d, const R* Dc, const R* lam2, int n1, int n2v, R* Dcc, cudaStream_t st);
+size_t l2_assemble_smem(int n1, int n2v, int real_size);
+
 // ---- coarse grid ----------------------------------------------------------------
 // classical Gram-Schmidt twice per (aggregate, chirality) on n FP64 or FP32
 // fields

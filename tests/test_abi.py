@@ -49,10 +49,10 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_sizes_match_header(lib):
     """Compile a tiny C program against the header and compare struct sizes
     with the ctypes mirrors."""
-    from paper_1811_00355_gb300._ddamg import CoarsePlan, Params, RequestInfo, SolveInfo, Stats
-    src = ('#include "ddamg.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu %zu %zu\\n",'
+    from paper_1811_00355_gb300._ddamg import CoarsePlan, Level2Params, Params, RequestInfo, SolveInfo, Stats
+    src = ('#include "ddamg.h"\n#include <stdio.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu\\n",'
            ' sizeof(ddamg_params), sizeof(ddamg_solve_info), sizeof(ddamg_stats),'
-           ' sizeof(ddamg_request_info), sizeof(ddamg_coarse_plan));return 0;}\n')
+           ' sizeof(ddamg_request_info), sizeof(ddamg_coarse_plan), sizeof(ddamg_level2_params));return 0;}\n')
     tmp = os.path.join(ROOT, "paper_1811_00355_gb300", "_build")
     os.makedirs(tmp, exist_ok=True)
     c = os.path.join(tmp, "sizes.c")
@@ -61,7 +61,7 @@ def test_struct_sizes_match_header(lib):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
     sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert sizes == [C.sizeof(Params), C.sizeof(SolveInfo), C.sizeof(Stats), C.sizeof(RequestInfo),
-                     C.sizeof(CoarsePlan)]
+                     C.sizeof(CoarsePlan), C.sizeof(Level2Params)]
 
 
 def _create(lib, **kw):
