@@ -676,7 +676,8 @@ def large_batched_child():
 
 # three levels on the 32^3 x 64 lattice: level-2 blocks (= aggregates) of
 # 2^4 coarse sites (a 4^3 x 8 coarsest lattice), 16 level-2 test vectors
-THREE = dict(block2=(2, 2, 2, 2), n_v2=16, setup_iters2=2, sources=2)
+THREE = dict(block2=(2, 2, 2, 2), n_v2=16, setup_iters2=2, sources=2,
+             smoothers2=((4, 4), (2, 2), (1, 2)))      # level-2 (SAP cycles, MR iterations); the first is the default
 
 
 def three_level():
@@ -723,16 +724,19 @@ def three_level_child():
            "timing": "CUDA events per solve"}
     try:
         h.run_setup()
-        for levels in (2, 3):
+        runs = [(2, None)] + [(3, sm) for sm in th["smoothers2"]]
+        for levels, sm in runs:
             rec = {}
             if levels == 3:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 h.level2_init(P.level2_default_params(block=th["block2"], n_v=th["n_v2"],
-                                                      setup_iters=th["setup_iters2"]))
+                                                      setup_iters=th["setup_iters2"], n_sap=sm[0],
+                                                      mr_iters=sm[1]))
                 h.level2_setup()
                 torch.cuda.synchronize()
                 rec["level2_setup_s"] = round(time.perf_counter() - t0, 3)
+                rec["level2_n_sap"], rec["level2_mr_iters"] = sm
                 h.set_levels(3)
             times, infos = [], []
             for k in range(th["sources"]):
@@ -752,7 +756,10 @@ def three_level_child():
                                                   for i in infos],
                         "true_residual": [i["true_residual"] for i in infos],
                         "all_converged": all(i["converged"] and i["true_residual"] <= s["tol"] for i in infos)})
-            out["levels_%d" % levels] = rec
+            if levels == 2 or sm == th["smoothers2"][0]:
+                out["levels_%d" % levels] = rec
+            else:
+                out.setdefault("levels_3_other_smoothers", []).append(rec)
     finally:
         h.close()
     print(json.dumps(out))
