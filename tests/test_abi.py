@@ -102,6 +102,29 @@ def test_null_handle_calls_are_rejected(lib):
     lib.ddamg_destroy(None)
 
 
+def test_level2_calls_reject_missing_handles_and_buffers(lib):
+    """The third level's entry points validate before any device work, and
+    its default parameters are the oracle's level-2 defaults."""
+    import paper_1811_00355_gb300 as P
+    from oracle.three_level import Level2Params as OracleLevel2
+    p = P.level2_default_params()
+    o = OracleLevel2()
+    assert tuple(p.block) == o.sap_block == o.agg_block
+    assert (p.n_v, p.setup_iters, p.n_sap, p.mr_iters) == (o.n_v, o.setup_iters, o.n_sap, o.mr_iters)
+    assert (p.coarsest_tol, p.coarsest_restart, p.coarsest_max_iter, p.restart) == \
+        (o.coarsest_tol, o.coarsest_restart, o.coarsest_maxiter, o.restart)
+    assert lib.ddamg_level2_default_params(None) == 1
+    assert lib.ddamg_level2_init(None, C.byref(p)) == 1
+    assert lib.ddamg_level2_setup(None, None) == 1
+    assert lib.ddamg_level2_set_vectors(None, None) == 1
+    assert lib.ddamg_level2_get_vectors(None, None) == 1
+    assert lib.ddamg_level2_get_op(None, None) == 1
+    assert lib.ddamg_level2_sap(None, 1, None, None) == 1
+    assert lib.ddamg_level2_apply_M2(None, 1, None, None) == 1
+    assert lib.ddamg_level2_coarse_solve(None, 1, None, None, 1e-2, None) == 1
+    assert lib.ddamg_set_levels(None, 3) == 1
+
+
 def test_server_rejects_invalid_arguments_before_device_work(lib):
     """The serving API validates its arguments before touching the GPU."""
     h = C.c_void_p()
