@@ -1027,7 +1027,7 @@ ddamg_status l2_init(ddamg_ctx* h, const ddamg_level2_params& p) {
   TRY(l2_alloc(h, &L.Z, (size_t)p.restart * fr * rs));
   for (int k = 0; k < 3; ++k) TRY(l2_alloc(h, &L.t[k], fr * rs));
   for (int k = 0; k < 2; ++k) TRY(l2_alloc(h, &L.c2[k], (size_t)NXp * m2 * 2 * rs));
-  TRY(l2_alloc(h, &q, (reduce_scratch_len(p.restart + 1) + 2 * (p.restart + 2)) * sizeof(double)));
+  TRY(l2_alloc(h, &q, (reduce_scratch_len(p.restart + 1) + 4 * (p.restart + 2) + 2) * sizeof(double)));
   L.scr = static_cast<double*>(q);
   L.dres = L.scr + reduce_scratch_len(p.restart + 1);
   TRY(l2_alloc(h, &q, 2 * sizeof(int)));
@@ -1157,13 +1157,12 @@ ddamg_status l2_fgmres(ddamg_ctx* h, const R* b, R* x, double tol, int max_iter,
   R* w = (R*)L.t[2];
   R* r = (R*)L.t[3];      // (the setup's vectors live there only between M2 calls of the setup)
   double* dres = L.dres;
-  std::vector<double> hh(2 * (m + 2));
-  auto dot_host = [&](int k) -> ddamg_status {           // hh[0 .. 2k) = V_j^H w, j < k
-    std::vector<const R*> vl(k);
-    for (int j = 0; j < k; ++j) vl[j] = V + (size_t)j * fr;
-    CK(multi_dot<R>(vl.data(), k, w, nc, L.scr, dres, h->st));
-    return DDAMG_OK;
-  };
+  // the two Gram-Schmidt passes' coefficients and ||w||^2 land side by side
+  // and come to the host in one copy per iteration
+  double* d1 = dres;
+  double* d2 = d1 + 2 * (m + 1);
+  double* dn = d2 + 2 * (m + 1);
+  std::vector<double> hh(4 * (m + 1) + 2);
   auto norm_host = [&](const R* v, double* out) -> ddamg_status {
     CK(norm2<R>(v, nc, L.scr, dres, h->st));
     CK(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -1194,18 +1193,18 @@ ddamg_status l2_fgmres(ddamg_ctx* h, const R* b, R* x, double tol, int max_iter,
       CK(coarse_apply<R>(h->g, (const R*)h->Dc, h->p.n_v, Z + (size_t)k * fr, w, 1, h->st));
       std::vector<const R*> vl(k + 1);
       for (int j = 0; j <= k; ++j) vl[j] = V + (size_t)j * fr;
-      std::vector<cd> hk(k + 1, cd(0.0));
-      for (int pass = 0; pass < 2; ++pass) {
-        TRY(dot_host(k + 1));
-        CK(multi_axpy<R>(vl.data(), k + 1, dres, -1.0, w, nc, h->st));
-        CK(cudaMemcpyAsync(hh.data(), dres, 2 * (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        for (int j = 0; j <= k; ++j) hk[j] += cd(hh[2 * j], hh[2 * j + 1]);
+      for (double* dp : {d1, d2}) {
+        CK(multi_dot<R>(vl.data(), k + 1, w, nc, L.scr, dp, h->st));
+        CK(multi_axpy<R>(vl.data(), k + 1, dp, -1.0, w, nc, h->st));
       }
-      double hn2 = 0.0;
-      TRY(norm_host(w, &hn2));
-      const double hn = std::sqrt(hn2);
-      if (hn > 0.0) CK(scale_by_inv_norm<R>(w, V + (size_t)(k + 1) * fr, dres, fr, h->st));
+      CK(norm2<R>(w, nc, L.scr, dn, h->st));
+      CK(cudaMemcpyAsync(hh.data(), dres, (4 * (m + 1) + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      std::vector<cd> hk(k + 1, cd(0.0));
+      for (int j = 0; j <= k; ++j)
+        hk[j] = cd(hh[2 * j], hh[2 * j + 1]) + cd(hh[2 * (m + 1) + 2 * j], hh[2 * (m + 1) + 2 * j + 1]);
+      const double hn = std::sqrt(hh[4 * (m + 1)]);
+      if (hn > 0.0) CK(scale_by_inv_norm<R>(w, V + (size_t)(k + 1) * fr, dn, fr, h->st));
       for (int j = 0; j <= k; ++j) H[j][k] = hk[j];
       H[k + 1][k] = cd(hn);
       for (int j = 0; j < k; ++j) {
